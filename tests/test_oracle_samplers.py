@@ -1,0 +1,205 @@
+"""Pins for the oracle's samplers (paper Sec. 2): closed-form posterior moments
+of the linear theory map, leapfrog reversibility / volume preservation and the
+O(eps^2) energy error of HMC, reversibility of MH on a two-state coarse
+graining, the stretch-factor law of AIES (Eq. (2.15) against g(z) of
+Eq. (2.14)) and its affine invariance."""
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle as O
+import synthetic as S
+
+
+def _linear_problem(d=6, n_data=64, seed=0):
+    t = S.target(d, linear=True, seed=seed, n_data=n_data)
+    J = t["A"] @ t["B"]
+    y = t["data"] - t["A"] @ t["c"]
+    P = J.T @ J / t["sigma"] ** 2
+    cov = np.linalg.inv(P)
+    mean = cov @ (J.T @ y) / t["sigma"] ** 2
+    return t, mean, cov
+
+
+def _model(t, mu, L, **kw):
+    return O.Model(t["d"], lik="analytic", analytic=t, lower=t["lower"], upper=t["upper"],
+                   gauss=t["gauss"], mu=mu, L=L, **kw)
+
+
+def _check_moments(samples, mean, cov, nsig=5.0):
+    """samples[n_draws][n_chains][d]; MCSE from the spread of independent chains."""
+    n, M, d = samples.shape
+    cm = samples.mean(axis=0)                          # per-chain means [M][d]
+    m_hat = cm.mean(axis=0)
+    se_m = cm.std(axis=0, ddof=1) / np.sqrt(M)
+    assert np.all(np.abs(m_hat - mean) < nsig * se_m + 1e-12), (m_hat - mean) / se_m
+    dev = samples - mean
+    cc = np.einsum("tca,tcb->cab", dev, dev) / n      # per-chain second moments about truth
+    c_hat = cc.mean(axis=0)
+    se_c = cc.std(axis=0, ddof=1) / np.sqrt(M)
+    z = (c_hat - cov) / se_c
+    assert np.all(np.abs(z) < nsig), z
+
+
+@pytest.mark.parametrize("kernel,eps,steps,extra", [
+    ("mh", 0.3, 3000, {}),
+    ("mala", 0.3, 3000, {}),
+    ("hmc", 0.25, 1000, {"n_leapfrog": 10}),
+    ("nuts", 0.35, 1000, {"max_depth": 8}),
+    # large step: many leaves fall outside the slice, so the in-subtree and
+    # top-level selection probabilities matter
+    ("nuts", 1.3, 3000, {"max_depth": 8}),
+    ("hmc", 0.9, 1500, {"n_leapfrog": 3}),
+])
+def test_closed_form_posterior(kernel, eps, steps, extra):
+    t, mean, cov = _linear_problem()
+    Lp = np.linalg.cholesky(cov)
+    # deliberately imperfect whitening: the sampler must still be exact
+    mu = mean + 0.3 * np.sqrt(np.diag(cov))
+    L = 1.2 * Lp
+    m = _model(t, mu, L)
+    z0 = np.linalg.solve(L, (mean + S.chains_init(64, 6, seed=7) @ Lp.T - mu).T).T
+    r = O.run(m, kernel, z0, eps=eps, n_steps=steps, seed=42, **extra)
+    keep = r["samples"][steps // 5:]
+    _check_moments(keep, mean, cov)
+    acc = r["accepts"].sum() / (64 * steps)
+    assert 0.05 < acc <= 1.0
+
+
+def test_aies_closed_form_posterior():
+    t, mean, cov = _linear_problem()
+    Lp = np.linalg.cholesky(cov)
+    m = _model(t, np.zeros(6), np.eye(6))
+    n_ens = 32
+    x0 = mean + S.chains_init(n_ens * 64, 6, seed=8) @ Lp.T
+    steps = 800
+    r = O.run(m, "aies", x0, eps=0.0, n_steps=steps, seed=3, aies_walkers=64)
+    keep = r["samples"][steps // 4:]
+    # walkers of one ensemble are correlated: use ensembles as the independent units
+    ens = keep.reshape(keep.shape[0], n_ens, 64, 6).transpose(0, 2, 1, 3).reshape(-1, n_ens, 6)
+    _check_moments(ens, mean, cov)
+
+
+def test_hmc_energy_error_is_second_order():
+    t, mean, cov = _linear_problem()
+    m = _model(t, mean, np.linalg.cholesky(cov))
+    z0 = S.chains_init(256, 6, seed=1)
+    rms = []
+    epss = [0.2, 0.1, 0.05]
+    for eps in epss:
+        Lf = int(round(1.0 / eps))
+        r = O.run(m, "hmc", z0, eps=eps, n_leapfrog=Lf, n_steps=1, seed=5, trace=True)
+        rms.append(np.sqrt(np.mean(r["log_alpha"] ** 2)))
+    slope = np.polyfit(np.log(epss), np.log(rms), 1)[0]
+    assert abs(slope - 2.0) < 0.1, slope
+
+
+def test_leapfrog_reversible_and_volume_preserving():
+    t = S.target(2, seed=4, n_data=32)
+    m = _model(t, np.zeros(2), np.eye(2) * 0.05)
+    z = np.array([0.3, -0.2]) + np.linalg.solve(np.eye(2) * 0.05, t["theta_star"])
+    _, g = m.logpost(z[None])
+    q = np.array([0.7, -1.1])
+    z1, q1, g1, _ = O.leapfrog(m, z, q, g[0], 0.05, 15)
+    z2, q2, _, _ = O.leapfrog(m, z1, -q1, g1, 0.05, 15)
+    assert np.allclose(z2, z, atol=1e-10) and np.allclose(-q2, q, atol=1e-10)
+
+    def phi(v):
+        zz, qq = v[:2], v[2:]
+        _, gg = m.logpost(zz[None])
+        a, b, _, _ = O.leapfrog(m, zz, qq, gg[0], 0.05, 15)
+        return np.concatenate([a, b])
+
+    v0 = np.concatenate([z, q])
+    Jm = np.zeros((4, 4))
+    h = 1e-6
+    for i in range(4):
+        e = np.zeros(4); e[i] = h
+        Jm[:, i] = (phi(v0 + e) - phi(v0 - e)) / (2 * h)
+    assert abs(np.linalg.det(Jm) - 1.0) < 1e-5
+
+
+def test_mh_detailed_balance_coarse_grained():
+    """Coarse-grain a 1-D MH chain into three intervals.  Detailed balance makes
+    the i->j and j->i transition counts equal in expectation for every pair
+    (a non-reversible kernel could circulate A->B->C->A); the occupancy of an
+    interval of the linear (Gaussian) target is its normal probability."""
+    t, mean, cov = _linear_problem(d=1, n_data=16, seed=2)
+    sd = np.sqrt(cov[0, 0])
+    m = _model(t, mean, np.array([[sd]]))
+    z0 = S.chains_init(256, 1, seed=4)
+    r = O.run(m, "mh", z0, eps=2.0, n_steps=4000, seed=9)
+    x = (r["samples"][:, :, 0] - mean[0]) / sd
+    cut = np.array([-0.3, 0.8])
+    st = np.digitize(x, cut)
+    for i in range(3):
+        for j in range(i + 1, 3):
+            nij = np.sum((st[:-1] == i) & (st[1:] == j))
+            nji = np.sum((st[:-1] == j) & (st[1:] == i))
+            assert nij > 1000 and abs(nij - nji) < 5 * np.sqrt(nij + nji), (i, j, nij, nji)
+    occ = (st == 1).mean(axis=0)
+    p_b = stats.norm.cdf(0.8) - stats.norm.cdf(-0.3)
+    assert abs(occ.mean() - p_b) < 5 * occ.std(ddof=1) / np.sqrt(occ.size)
+
+
+def test_aies_stretch_factor_law():
+    """d = 1, flat target: every stretch is accepted and, with all partners at 0
+    and the moving walkers at 1, the new position is the stretch factor Z."""
+    d, a = 1, 2.0
+    e = S.emulator(d, width=8, depth=1, seed=0)
+    W, b, wo, bo = S.unpack_emulator(e)
+    flat = dict(e, params=S.pack_emulator([np.zeros_like(W[0])], b, np.zeros_like(wo), 0.0))
+    m = O.Model(d, emulator=flat, lower=[-100.0], upper=[100.0])
+    n_ens, W_ = 200, 64
+    z0 = np.zeros((n_ens * W_, 1))
+    for e_ in range(n_ens):
+        z0[e_ * W_: e_ * W_ + 32] = 1.0
+    r = O.run(m, "aies", z0, eps=0.0, n_steps=1, seed=21, aies_walkers=W_, aies_a=a)
+    Z = np.concatenate([r["samples"][0, e_ * W_: e_ * W_ + 32, 0] for e_ in range(n_ens)])
+    assert Z.min() >= 1 / a and Z.max() <= a
+    F = lambda z: (np.sqrt(z) - 1 / np.sqrt(a)) / (np.sqrt(a) - 1 / np.sqrt(a))
+    assert stats.kstest(Z, F).pvalue > 1e-4
+    assert r["accepts"][: 32].sum() == 32
+
+
+def test_aies_affine_invariance():
+    t, mean, cov = _linear_problem()
+    rng = np.random.default_rng(3)
+    Mx = np.tril(rng.normal(size=(6, 6))) * 0.3 + np.eye(6)
+    bvec = rng.normal(size=6) * 0.1
+    m1 = _model(t, np.zeros(6), np.eye(6))
+    m2 = _model(t, bvec, Mx)
+    x0 = mean + S.chains_init(128, 6, seed=2) @ np.linalg.cholesky(cov).T
+    z0 = np.linalg.solve(Mx, (x0 - bvec).T).T
+    r1 = O.run(m1, "aies", x0, eps=0.0, n_steps=50, seed=13)
+    r2 = O.run(m2, "aies", z0, eps=0.0, n_steps=50, seed=13)
+    assert np.array_equal(r1["accepts"], r2["accepts"])
+    assert np.allclose(r1["samples"], r2["samples"], rtol=1e-9, atol=1e-9)
+
+
+def test_nuts_tree_bookkeeping():
+    t, mean, cov = _linear_problem()
+    m = _model(t, mean, np.linalg.cholesky(cov))
+    z0 = S.chains_init(64, 6, seed=1)
+    r = O.run(m, "nuts", z0, eps=0.3, n_steps=20, seed=3, max_depth=8, trace=True)
+    depth, nleaf = r["depth"], r["nleaf"]
+    assert np.all((depth >= 1) & (depth <= 8))
+    # leapfrogs per iteration lie between 2^(j-1) (first doubling of the last depth)
+    # and 2^j - 1 (all doublings complete)
+    assert np.all(nleaf <= 2 ** depth - 1) and np.all(nleaf >= 2 ** (depth - 1))
+    assert r["evals"].sum() == nleaf.sum()
+    # max_depth caps the tree
+    r1 = O.run(m, "nuts", z0, eps=0.01, n_steps=3, seed=3, max_depth=3, trace=True)
+    assert np.all(r1["depth"] == 3) and np.all(r1["nleaf"] == 7)
+
+
+def test_mala_proposal_reduces_to_gaussian_kernel():
+    """On the whitened exact Gaussian N(0, I) (grad = -z) the MALA proposal mean is
+    (1 - eps) z and its log-acceptance depends only on the two points; with eps -> 0
+    every proposal is accepted."""
+    t, mean, cov = _linear_problem()
+    m = _model(t, mean, np.linalg.cholesky(cov))
+    z0 = S.chains_init(256, 6, seed=6)
+    r = O.run(m, "mala", z0, eps=1e-6, n_steps=3, seed=1, trace=True)
+    assert np.all(r["accept"] == 1)
+    assert np.all(np.abs(r["log_alpha"]) < 1e-3)
