@@ -1,0 +1,197 @@
+/*
+ * bst.h -- C ABI of the GB300 (sm_103a) batched emulator posterior sampler.
+ *
+ * The library evaluates a tanh-MLP log-likelihood emulator (or an analytic
+ * "theory map" likelihood) and its gradient for thousands of independent
+ * chains at once, inside MH / MALA / HMC / NUTS / AIES proposal-and-accept
+ * steps, after "Posterior sampling in the Age of Emulators" (arXiv
+ * 2606.04895).  The paper's unified interface (Sec. 3.1) is a sampler built
+ * from a log-probability and a hyper-rectangle of bounds, run with a method,
+ * a number of steps and a number of chains, returning samples, acceptance
+ * rates and evaluation counts; the calls below are that interface.
+ *
+ * Conventions (every entry point):
+ *  - Returns a bst_status; nothing throws or aborts across the ABI.  The text
+ *    of the last error of the calling thread is bst_last_error().
+ *  - Device buffers are owned by the caller, passed as plain device pointers
+ *    (``*_dev``), and must stay alive until the work on ``stream`` is done.
+ *    Host arrays (``*_host`` or plain ``const double*``) are copied on entry.
+ *  - ``stream`` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued asynchronously unless a call says it synchronises.
+ *  - Element type of real-valued device buffers ("real"): float for handles of
+ *    precision BST_BF16 and BST_FP32, double for BST_FP64.
+ *  - Call order: bst_create -> bst_set_emulator | bst_set_analytic ->
+ *    bst_init_chains -> { bst_step, bst_adapt_cov, ... }*.  Out of order ->
+ *    BST_ERR_STATE.  The library owns only small persistent state (chain
+ *    state, packed weights, Welford accumulators, counters).
+ *  - A handle is used by one host thread at a time.
+ */
+#ifndef BST_H
+#define BST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bst_ctx *bst_handle;
+
+typedef enum {
+  BST_OK = 0,
+  BST_ERR_ARG = 1,         /* invalid argument (NULL, size, range)              */
+  BST_ERR_STATE = 2,       /* call out of order                                 */
+  BST_ERR_CUDA = 3,        /* CUDA runtime error (message in bst_last_error)     */
+  BST_ERR_NOT_PD = 4,      /* covariance not positive definite even with jitter */
+  BST_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out                */
+  BST_ERR_NONFINITE = 6,   /* non-finite input where a finite one is required   */
+  BST_ERR_UNSUPPORTED = 7  /* shape/precision combination not built             */
+} bst_status;
+
+typedef enum { BST_MH = 0, BST_MALA = 1, BST_HMC = 2, BST_NUTS = 3, BST_AIES = 4 } bst_kernel;
+typedef enum { BST_BF16 = 0, BST_FP32 = 1, BST_FP64 = 2 } bst_precision;
+typedef enum { BST_LIK_EMULATOR = 0, BST_LIK_ANALYTIC = 1 } bst_lik_kind;
+
+typedef struct {
+  int d;              /* parameter dimension, 1..32                                   */
+  int n_chains;       /* chains (AIES: a multiple of 4 * aies_walkers)                */
+  int precision;      /* bst_precision; BF16 requires an emulator                     */
+  int lik_kind;       /* bst_lik_kind                                                 */
+  uint64_t seed;      /* Philox4x32-10 key                                            */
+  int max_depth;      /* NUTS doublings per iteration (1..10; 0 -> 8)                 */
+  int aies_walkers;   /* walkers per AIES ensemble (64; 0 -> 64)                      */
+  double aies_a;      /* AIES stretch parameter a > 1 (0 -> 2)                        */
+  int thin;           /* record every thin-th step (0 -> 1)                           */
+  int device;         /* CUDA device ordinal                                          */
+} bst_config;
+
+typedef struct {
+  int64_t accepts;        /* accepted moves in this call (NUTS: moved iterations)     */
+  int64_t evals;          /* likelihood evaluations in this call (Sec. 3.1 counter)   */
+  int64_t divergences;    /* NUTS: iterations stopped by the energy-error bound       */
+  double accept_stat;     /* mean Metropolis acceptance statistic over chain-steps    */
+  int status;             /* device status word (bst_status)                          */
+} bst_step_stats;
+
+/* Version string of the library build. */
+const char *bst_version(void);
+/* Text of the last error on this host thread ("" if none). */
+const char *bst_last_error(void);
+
+/* Create a handle on cfg->device.  Allocates the chain state for n_chains.
+ * Errors: BST_ERR_ARG (d outside 1..32, n_chains < 1, AIES shape), BST_ERR_CUDA. */
+bst_status bst_create(bst_handle *h, const bst_config *cfg);
+/* Release every device and host resource of h (NULL is a no-op). */
+void bst_destroy(bst_handle h);
+
+/* Emulator likelihood (stand-in for the CLiENT emulator, paper Sec. 1/4):
+ *   u = (x - in_m) / in_s;  h_1 = tanh(W_1 u + b_1);  h_l = tanh(W_l h_{l-1} + b_l);
+ *   out = w_o . h_D + b_o;  chi2 = out_s * out + out_m;  logL = -chi2 / 2.
+ * params (host, FP64, copied): W_1[width][d] b_1[width] (W_l[width][width] b_l[width])
+ * for l = 2..depth, then w_o[width], b_o.  width in {256, 512} for BF16, any
+ * multiple of 64 up to 1024 for FP32 (up to 512 for FP64); depth 1..8.
+ * Errors: BST_ERR_ARG, BST_ERR_UNSUPPORTED, BST_ERR_NONFINITE (non-finite weight). */
+bst_status bst_set_emulator(bst_handle h, int depth, int width, const double *params,
+                            const double *in_m, const double *in_s, double out_m, double out_s);
+
+/* Read back the current emulator parameters (after training) into params
+ * (host, FP64, same layout as bst_set_emulator).  Synchronises. */
+bst_status bst_get_emulator(bst_handle h, double *params);
+
+/* Analytic likelihood: f(x) = A tanh(B x_c + c) + N x_n (tanh -> identity if
+ * linear), logL = -|data - f(x)|^2 / (2 sigma^2); x_c = x[0:d_c], x_n = x[d_c:d].
+ * A[n_data][n_hidden], B[n_hidden][d_c], c[n_hidden], N[n_data][d - d_c] (NULL
+ * when d_c == d), data[n_data]; host FP64, copied.  n_hidden <= 64. */
+bst_status bst_set_analytic(bst_handle h, int d_c, int n_hidden, int n_data, const double *A,
+                            const double *B, const double *c, const double *N, const double *data,
+                            double sigma, int linear);
+
+/* init_chains(theta0, prior box, whitening) -- paper Sec. 2.2 / Algorithm 1 and
+ * Sec. 3.1: chains start at theta0[n_chains][d] (host, x-space).  The prior is
+ * the box lower <= x <= upper (log prior 0 inside, -inf outside) times N(0,1) on
+ * every dim with gauss[i] != 0 (gauss may be NULL).  Sampling runs in whitened
+ * coordinates z with x = mu + L z (L[d][d] lower triangular, row-major, positive
+ * diagonal); the target is log pi_z(z) = log L(x) + log prior(x) + sum log L_ii
+ * (Eq. (2.12)).  Evaluates log pi and its gradient at every start (synchronises).
+ * Resets the iteration counters and statistics. */
+bst_status bst_init_chains(bst_handle h, const double *theta0, const double *lower,
+                           const double *upper, const int *gauss, const double *mu,
+                           const double *L);
+
+/* step(kernel, eps, L, n_steps): advance every chain n_steps iterations of
+ *   BST_MH   : z' = z + eps xi, Metropolis accept                     (Sec. 2, Sec. 4)
+ *   BST_MALA : z' = z + eps grad + sqrt(2 eps) xi, MH-corrected        (Sec. 2.1, Eq. (2.3))
+ *   BST_HMC  : n_leapfrog leapfrog steps of H = -log pi + q.q/2        (Sec. 2.1, Eq. (2.1))
+ *   BST_NUTS : Hoffman-Gelman NUTS, at most max_depth doublings          (Sec. 2.1)
+ *   BST_AIES : Goodman-Weare stretch move, ensembles of aies_walkers     (Sec. 2.3)
+ * eps is ignored by AIES; n_leapfrog only used by HMC.  If samples_dev is not
+ * NULL it receives x-space samples real[n_steps / thin][n_chains][d].
+ * If stats is not NULL the call synchronises ``stream`` and fills it with this
+ * call's totals; otherwise it only enqueues. */
+bst_status bst_step(bst_handle h, int kernel, double eps, int n_leapfrog, int n_steps,
+                    void *samples_dev, void *stream, bst_step_stats *stats);
+
+/* loglike(theta): logl_dev[m] = logL(theta_dev[m][d]) (likelihood only, x-space,
+ * no prior).  real buffers; m >= 0 (m == 0 is a no-op). */
+bst_status bst_loglike(bst_handle h, const void *theta_dev, int m, void *logl_dev, void *stream);
+
+/* grad_loglike(theta): logl_dev[m] = logL, grad_dev[m][d] = d logL / d theta. */
+bst_status bst_grad_loglike(bst_handle h, const void *theta_dev, int m, void *logl_dev,
+                            void *grad_dev, void *stream);
+
+/* Covariance adaptation (Sec. 3.2).  bst_welford_reset clears the running
+ * statistics and makes every following bst_step add each chain's x after
+ * every iteration; bst_welford_add adds external samples x_dev[m][d] (real).
+ * bst_adapt_cov merges the statistics in FP64, forms the unbiased covariance,
+ * factorises it (plain Cholesky; on failure adds delta (tr S / d) I with
+ * delta = jitter0, x10 per retry, up to 1e-2), sets mu = pooled mean and L =
+ * the factor as the new whitening, keeps every chain's x fixed (z remapped)
+ * and re-evaluates log pi and its gradient.  mu_out[d], L_out[d][d] and
+ * jitter_used (host, may be NULL) receive the result.  Synchronises.
+ * Errors: BST_ERR_STATE (fewer than 2 samples), BST_ERR_NOT_PD. */
+bst_status bst_welford_reset(bst_handle h);
+bst_status bst_welford_add(bst_handle h, const void *x_dev, int m, void *stream);
+bst_status bst_adapt_cov(bst_handle h, double jitter0, double *mu_out, double *L_out,
+                         double *jitter_used);
+
+/* Checkpoint / resume.  Host FP64 copies of the chain state: z[n][d], logp[n],
+ * grad[n][d] (whitened), iteration counters iter[n].  Philox draws are keyed by
+ * (seed, chain, iter), so a restored state continues bit-identically. */
+bst_status bst_get_state(bst_handle h, double *z, double *logp, double *grad, uint32_t *iter);
+bst_status bst_set_state(bst_handle h, const double *z, const double *logp, const double *grad,
+                         const uint32_t *iter);
+/* Current whitening (mu[d], L[d][d]); synchronises. */
+bst_status bst_get_whitening(bst_handle h, double *mu, double *L);
+/* Per-chain counters since bst_init_chains (host arrays, each n_chains long,
+ * any may be NULL).  Synchronises. */
+bst_status bst_get_counters(bst_handle h, int64_t *accepts, int64_t *evals, int64_t *divergences,
+                            double *accept_stat);
+
+/* Emulator training (the learned part): one Adam step (Kingma & Ba) of the
+ * loss mean_i (out_i - (chi2_i - out_m)/out_s)^2 over the batch X_dev[m][d],
+ * chi2_dev[m] (float, device).  FP32 master weights, forward with stored
+ * activations, hand-written backward; the sampling weights are re-packed from
+ * the master before the next evaluation.  loss_dev (float[1], may be NULL)
+ * receives the batch loss before the update.  1 <= m <= 65536. */
+bst_status bst_train_step(bst_handle h, const float *X_dev, const float *chi2_dev, int m,
+                          double lr, double beta1, double beta2, double adam_eps, float *loss_dev,
+                          void *stream);
+/* Loss and its gradient with respect to every parameter (grad_dev: float, same
+ * layout as bst_set_emulator params) without updating; for checks. */
+bst_status bst_train_grad(bst_handle h, const float *X_dev, const float *chi2_dev, int m,
+                          float *grad_dev, float *loss_dev, void *stream);
+
+/* Multi-chain effective sample size per dimension (Gelman et al., BDA3
+ * Sec. 11.5: variogram autocorrelations, Geyer initial monotone sequence) of
+ * samples_dev real[n_draws][n_chains][d] (this handle's n_chains, d and real
+ * type).  ess_out: host double[d].  Synchronises. */
+bst_status bst_ess(bst_handle h, const void *samples_dev, int n_draws, double *ess_out);
+
+/* Block until all work of h on ``stream`` is done and check the device status. */
+bst_status bst_sync(bst_handle h, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BST_H */

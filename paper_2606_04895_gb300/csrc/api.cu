@@ -1,0 +1,1051 @@
+// api.cu -- the C ABI declared in include/bst.h: handle, validation, device memory of the
+// library-owned state, weight preparation and the launches of the sampling kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+
+using namespace bst;
+
+namespace {
+
+thread_local std::string g_err;
+
+bst_status fail(bst_status s, const std::string &m) {
+  g_err = m;
+  return s;
+}
+
+#define BST_CUDA(expr)                                                                            \
+  do {                                                                                            \
+    cudaError_t e_ = (expr);                                                                      \
+    if (e_ != cudaSuccess) return fail(BST_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define BST_TRY(expr)             \
+  do {                            \
+    bst_status s_ = (expr);       \
+    if (s_ != BST_OK) return s_;  \
+  } while (0)
+
+int pad16(int d) { return ((d + 15) / 16) * 16; }
+
+}  // namespace
+
+struct bst_ctx {
+  // configuration
+  int d = 0, dp = 0, n = 0, precision = 0, lik = 0, max_depth = 8, walkers = 64, thin = 1, device = 0;
+  double aies_a = 2.0;
+  uint64_t seed = 0;
+  int stage = 0;  // 0 created, 1 likelihood set, 2 chains initialised
+  size_t rs = 4;  // bytes per working real
+  std::vector<void *> allocs;
+
+  // chain state (working precision, dp-padded rows)
+  void *z = nullptr, *g = nullptr, *lp = nullptr, *ze = nullptr, *lle = nullptr, *gle = nullptr, *work = nullptr,
+       *xbuf = nullptr;
+  uint32_t *iter = nullptr;
+  double *acc_stat = nullptr;
+  unsigned long long *accepts = nullptr, *evals = nullptr, *divs = nullptr;
+  int *steps_done = nullptr, *status = nullptr;
+  int work_stride = 0;
+
+  // target: whitening + prior
+  std::vector<double> mu, L, lower, upper;
+  std::vector<int> gauss;
+  double logdet = 0.0;
+  int any_gauss = 0;
+  void *mu_r = nullptr, *L_r = nullptr, *lo_r = nullptr, *up_r = nullptr;
+  int *gauss_d = nullptr;
+  double *mu64 = nullptr, *L64 = nullptr, *mu64_new = nullptr, *L64_new = nullptr, *info64 = nullptr;
+
+  // emulator
+  int depth = 0, width = 0;
+  size_t nparams = 0;
+  double *P64 = nullptr, *in_m64 = nullptr, *in_s64 = nullptr;
+  double out_m = 0.0, out_s = 1.0, bo = 0.0;
+  double *W1f[2] = {nullptr, nullptr}, *b1f[2] = {nullptr, nullptr};  // [0] z-space, [1] x-space
+  void *sW1T[2] = {nullptr, nullptr}, *sW1[2] = {nullptr, nullptr}, *sb1[2] = {nullptr, nullptr};
+  void *sWT = nullptr, *sW = nullptr, *sb = nullptr, *swo = nullptr;
+  uint8_t *tl1[2] = {nullptr, nullptr}, *tg1[2] = {nullptr, nullptr}, *thid = nullptr;
+  float *tb1[2] = {nullptr, nullptr}, *tb = nullptr, *two = nullptr;
+  int kb1 = 1;
+  void *scratch = nullptr;
+  size_t scratch_rows = 0;
+
+  // analytic likelihood
+  int d_c = 0, H = 0, n_data = 0, linear = 0, has_N = 0;
+  double sigma = 1.0;
+  double *A64 = nullptr, *B64 = nullptr, *c64 = nullptr, *N64 = nullptr, *data64 = nullptr;
+  double *fBf = nullptr, *fcf = nullptr, *fAT = nullptr, *fNfT = nullptr, *fdata = nullptr;  // FP64 staging
+  void *aBf[2] = {nullptr, nullptr}, *acf[2] = {nullptr, nullptr}, *aAT = nullptr, *aNfT[2] = {nullptr, nullptr},
+       *adata[2] = {nullptr, nullptr};
+
+  // training
+  float *P32 = nullptr, *G32 = nullptr, *m1 = nullptr, *m2 = nullptr, *in_m32 = nullptr, *in_s32 = nullptr;
+  int adam_t = 0;
+  int train_cap = 0;
+  TrainWork tw{};
+
+  // Welford
+  double *wf = nullptr;
+  int wf_records = 0;
+  bool welford_on = false;
+
+  // flags
+  bool weights_dirty = true;  // folds / packs must be rebuilt
+  bool p32_newer = false;     // training master newer than the FP64 master
+  bool state_stale = true;    // log pi / grad of the chains must be re-evaluated
+  bool grad_valid = false;
+
+  // host-side counter snapshot for per-call statistics
+  int ess_tmp_cap = 0;
+  double *ess_mean = nullptr, *ess_var = nullptr, *ess_V = nullptr;
+};
+
+namespace {
+
+bst_status dalloc(bst_ctx *h, void **p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) return fail(BST_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  h->allocs.push_back(*p);
+  cudaMemset(*p, 0, bytes);
+  return BST_OK;
+}
+template <typename T>
+bst_status dalloc_t(bst_ctx *h, T **p, size_t count) {
+  void *v = nullptr;
+  bst_status s = dalloc(h, &v, count * sizeof(T));
+  *p = static_cast<T *>(v);
+  return s;
+}
+void dfree(bst_ctx *h, void *p) {
+  if (!p) return;
+  for (auto &q : h->allocs)
+    if (q == p) {
+      cudaFree(p);
+      q = nullptr;
+    }
+}
+
+bool all_finite(const double *v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+// upload FP64 host values as working-precision device values
+bst_status upload_real(bst_ctx *h, void *dst, const double *src, size_t n) {
+  if (h->rs == 8) {
+    BST_CUDA(cudaMemcpy(dst, src, n * 8, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> t(n);
+    for (size_t i = 0; i < n; ++i) t[i] = static_cast<float>(src[i]);
+    BST_CUDA(cudaMemcpy(dst, t.data(), n * 4, cudaMemcpyHostToDevice));
+  }
+  return BST_OK;
+}
+bst_status download_real(bst_ctx *h, double *dst, const void *src, size_t n) {
+  if (h->rs == 8) {
+    BST_CUDA(cudaMemcpy(dst, src, n * 8, cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<float> t(n);
+    BST_CUDA(cudaMemcpy(t.data(), src, n * 4, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < n; ++i) dst[i] = t[i];
+  }
+  return BST_OK;
+}
+
+bst_status check_status(bst_ctx *h) {
+  int st = 0;
+  BST_CUDA(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st & kStatusTimeout) {
+    cudaMemset(h->status, 0, sizeof(int));
+    return fail(BST_ERR_TIMEOUT, "a bounded device-side wait ran out (device status word)");
+  }
+  return BST_OK;
+}
+
+// ------------------------------------------------------------------ argument assembly
+template <typename R>
+StepArgs<R> make_args(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_steps, void *samples) {
+  StepArgs<R> a;
+  std::memset(&a, 0, sizeof(a));
+  a.mode = mode;
+  a.n_chains = h->n;
+  a.n_rows = (mode == kModeAIES) ? h->n / 2 : h->n;
+  a.d = h->d;
+  a.dp = h->dp;
+  a.eps = eps;
+  a.n_leapfrog = n_leapfrog;
+  a.n_steps = n_steps;
+  a.max_depth = h->max_depth;
+  a.aies_walkers = h->walkers;
+  a.aies_a = h->aies_a;
+  a.thin = h->thin;
+  a.seed = h->seed;
+  a.need_grad = (mode == kModeMALA || mode == kModeHMC || mode == kModeNUTS || mode == kModeRefresh) ? 1 : 0;
+  a.tgt.d = h->d;
+  a.tgt.mu = static_cast<const R *>(h->mu_r);
+  a.tgt.L = static_cast<const R *>(h->L_r);
+  a.tgt.logdet = h->logdet;
+  a.tgt.lower = static_cast<const R *>(h->lo_r);
+  a.tgt.upper = static_cast<const R *>(h->up_r);
+  a.tgt.gauss = h->gauss_d;
+  a.tgt.any_gauss = h->any_gauss;
+  a.st.z = static_cast<R *>(h->z);
+  a.st.g = static_cast<R *>(h->g);
+  a.st.lp = static_cast<R *>(h->lp);
+  a.st.iter = h->iter;
+  a.st.acc_stat = h->acc_stat;
+  a.st.accepts = h->accepts;
+  a.st.evals = h->evals;
+  a.st.divs = h->divs;
+  a.st.ze = static_cast<R *>(h->ze);
+  a.st.lle = static_cast<R *>(h->lle);
+  a.st.gle = static_cast<R *>(h->gle);
+  a.st.ze_ld = h->dp;
+  a.st.gle_ld = h->dp;
+  a.st.work = static_cast<R *>(h->work);
+  a.st.work_stride = h->work_stride;
+  a.st.steps_done = h->steps_done;
+  a.samples = static_cast<R *>(samples);
+  a.welford_on = (h->welford_on && mode != kModeRefresh && mode != kModeLoglike) ? 1 : 0;
+  a.wf = h->wf;
+  a.wf_stride = kWfStride;
+  a.xbuf = static_cast<R *>(h->xbuf);
+  a.status = h->status;
+  return a;
+}
+
+template <typename R>
+EmuWeights<R> emu_weights(bst_ctx *h, int fold) {
+  EmuWeights<R> w;
+  w.depth = h->depth;
+  w.width = h->width;
+  w.dp = h->dp;
+  w.W1T = static_cast<const R *>(h->sW1T[fold]);
+  w.W1 = static_cast<const R *>(h->sW1[fold]);
+  w.b1 = static_cast<const R *>(h->sb1[fold]);
+  w.WT = static_cast<const R *>(h->sWT);
+  w.W = static_cast<const R *>(h->sW);
+  w.b = static_cast<const R *>(h->sb);
+  w.wo = static_cast<const R *>(h->swo);
+  w.bo = static_cast<R>(h->bo);
+  w.out_m = static_cast<R>(h->out_m);
+  w.out_s = static_cast<R>(h->out_s);
+  w.scratch = static_cast<R *>(h->scratch);
+  return w;
+}
+
+TcWeights tc_weights(bst_ctx *h, int fold) {
+  TcWeights w;
+  w.depth = h->depth;
+  w.width = h->width;
+  w.dp = h->dp;
+  w.kb1 = h->kb1;
+  w.k16_l1 = 3 * h->dp / 16;
+  w.l1 = h->tl1[fold];
+  w.hid = h->thid;
+  w.g1 = h->tg1[fold];
+  w.b1 = h->tb1[fold];
+  w.b = h->tb;
+  w.wo = h->two;
+  w.bo = static_cast<float>(h->bo);
+  w.out_m = static_cast<float>(h->out_m);
+  w.out_s = static_cast<float>(h->out_s);
+  w.scratch = static_cast<__nv_bfloat16 *>(h->scratch);
+  w.n_stages = tc_stages(h->width);
+  return w;
+}
+
+template <typename R>
+AnaWeights<R> ana_weights(bst_ctx *h, int fold) {
+  AnaWeights<R> w;
+  w.d = h->d;
+  w.dp = h->dp;
+  w.H = h->H;
+  w.n_data = h->n_data;
+  w.linear = h->linear;
+  w.has_N = (h->d > h->d_c) ? 1 : 0;
+  w.Bf = static_cast<const R *>(h->aBf[fold]);
+  w.cf = static_cast<const R *>(h->acf[fold]);
+  w.AT = static_cast<const R *>(h->aAT);
+  w.NfT = static_cast<const R *>(h->aNfT[fold]);
+  w.dataf = static_cast<const R *>(h->adata[fold]);
+  w.inv_s2 = static_cast<R>(1.0 / (h->sigma * h->sigma));
+  return w;
+}
+
+// ------------------------------------------------------------------ weight preparation
+bst_status ensure_scratch(bst_ctx *h, size_t rows) {
+  if (h->lik != BST_LIK_EMULATOR) return BST_OK;
+  if (rows <= h->scratch_rows && h->scratch) return BST_OK;
+  dfree(h, h->scratch);
+  const size_t el = (h->precision == BST_BF16) ? 2 : h->rs;
+  const size_t bytes = rows * static_cast<size_t>(h->depth > 1 ? h->depth - 1 : 1) * h->width * el;
+  BST_TRY(dalloc(h, &h->scratch, bytes));
+  h->scratch_rows = rows;
+  return BST_OK;
+}
+
+bst_status prepare(bst_ctx *h, cudaStream_t s) {
+  if (!h->weights_dirty) return BST_OK;
+  if (h->lik == BST_LIK_EMULATOR) {
+    if (h->p32_newer) {
+      BST_CUDA(launch_cast_f32_to_f64(h->P32, h->P64, h->nparams, s));
+      BST_CUDA(cudaMemcpyAsync(&h->bo, h->P64 + h->nparams - 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+      BST_CUDA(cudaStreamSynchronize(s));
+      h->p32_newer = false;
+    }
+    const int d = h->d, dp = h->dp, w = h->width, D = h->depth;
+    for (int f = 0; f < 2; ++f) {
+      BST_CUDA(launch_fold_layer1(h->P64, h->in_m64, h->in_s64, h->mu64, h->L64, d, dp, w, f, h->W1f[f], h->b1f[f], s));
+      if (h->precision == BST_FP32)
+        BST_CUDA(launch_pack_simt_f32(h->P64, h->W1f[f], h->b1f[f], d, dp, D, w, (float *)h->sW1T[f], (float *)h->sW1[f],
+                                      (float *)h->sb1[f], (float *)h->sWT, (float *)h->sW, (float *)h->sb,
+                                      (float *)h->swo, s));
+      else if (h->precision == BST_FP64)
+        BST_CUDA(launch_pack_simt_f64(h->P64, h->W1f[f], h->b1f[f], d, dp, D, w, (double *)h->sW1T[f],
+                                      (double *)h->sW1[f], (double *)h->sb1[f], (double *)h->sWT, (double *)h->sW,
+                                      (double *)h->sb, (double *)h->swo, s));
+      else {
+        BST_CUDA(launch_pack_tc_l1(h->W1f[f], dp, w, h->kb1, h->tl1[f], s));
+        BST_CUDA(launch_pack_tc_g1(h->W1f[f], dp, w, h->tg1[f], s));
+        BST_CUDA(launch_cast_f32(h->b1f[f], h->tb1[f], w, s));
+      }
+    }
+    if (h->precision == BST_BF16) {
+      BST_CUDA(launch_pack_tc_hidden(h->P64, d, D, w, h->thid, s));
+      for (int l = 2; l <= D; ++l) {
+        const size_t ob = static_cast<size_t>(d) * w + w + static_cast<size_t>(l - 2) * (static_cast<size_t>(w) * w + w) +
+                          static_cast<size_t>(w) * w;
+        BST_CUDA(launch_cast_f32(h->P64 + ob, h->tb + static_cast<size_t>(l - 2) * w, w, s));
+      }
+      BST_CUDA(launch_cast_f32(h->P64 + h->nparams - 1 - w, h->two, w, s));
+    }
+  } else {
+    for (int f = 0; f < 2; ++f) {
+      BST_CUDA(launch_fold_analytic(h->A64, h->B64, h->c64, h->N64, h->data64, h->mu64, h->L64, h->d, h->dp, h->d_c,
+                                    h->H, h->n_data, f, h->fBf, h->fcf, h->fAT, h->fNfT, h->fdata, s));
+      auto cast = [&](const double *src, void *dst, size_t cnt) -> cudaError_t {
+        return (h->rs == 8) ? launch_cast_f64(src, static_cast<double *>(dst), cnt, s)
+                            : launch_cast_f32(src, static_cast<float *>(dst), cnt, s);
+      };
+      BST_CUDA(cast(h->fBf, h->aBf[f], static_cast<size_t>(h->H) * h->dp));
+      BST_CUDA(cast(h->fcf, h->acf[f], h->H));
+      if (f == 0) BST_CUDA(cast(h->fAT, h->aAT, static_cast<size_t>(h->H) * h->n_data));
+      if (h->d > h->d_c) BST_CUDA(cast(h->fNfT, h->aNfT[f], static_cast<size_t>(h->dp) * h->n_data));
+      BST_CUDA(cast(h->fdata, h->adata[f], h->n_data));
+    }
+  }
+  h->weights_dirty = false;
+  return BST_OK;
+}
+
+// one launch of the chain-tile kernel matching the handle's engine
+bst_status run(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_steps, void *samples, int fold,
+               cudaStream_t s, const void *ext_in = nullptr, void *ext_logl = nullptr, void *ext_grad = nullptr,
+               int m = 0, int need_grad = 0) {
+  const bool ll = mode == kModeLoglike;
+  if (h->precision == BST_FP64) {
+    StepArgs<double> a = make_args<double>(h, mode, eps, n_leapfrog, n_steps, samples);
+    if (ll) {
+      a.n_rows = m;
+      a.need_grad = need_grad;
+      a.st.ze = (double *)ext_in;
+      a.st.ze_ld = h->d;
+      a.st.lle = (double *)ext_logl;
+      a.st.gle = (double *)ext_grad;
+      a.st.gle_ld = h->d;
+    }
+    if (h->lik == BST_LIK_EMULATOR) BST_CUDA(launch_emu_simt_f64(a, emu_weights<double>(h, fold), s));
+    else BST_CUDA(launch_ana_simt_f64(a, ana_weights<double>(h, fold), s));
+  } else {
+    StepArgs<float> a = make_args<float>(h, mode, eps, n_leapfrog, n_steps, samples);
+    if (ll) {
+      a.n_rows = m;
+      a.need_grad = need_grad;
+      a.st.ze = (float *)ext_in;
+      a.st.ze_ld = h->d;
+      a.st.lle = (float *)ext_logl;
+      a.st.gle = (float *)ext_grad;
+      a.st.gle_ld = h->d;
+    }
+    if (h->lik == BST_LIK_ANALYTIC) BST_CUDA(launch_ana_simt_f32(a, ana_weights<float>(h, fold), s));
+    else if (h->precision == BST_BF16) BST_CUDA(launch_emu_tc(a, tc_weights(h, fold), s));
+    else BST_CUDA(launch_emu_simt_f32(a, emu_weights<float>(h, fold), s));
+  }
+  return BST_OK;
+}
+
+bst_status refresh(bst_ctx *h, cudaStream_t s) {
+  BST_TRY(prepare(h, s));
+  BST_TRY(ensure_scratch(h, h->n));
+  BST_TRY(run(h, kModeRefresh, 0.0, 0, 1, nullptr, 0, s));
+  h->state_stale = false;
+  h->grad_valid = true;
+  return BST_OK;
+}
+
+bst_status set_target(bst_ctx *h, const double *mu, const double *L) {
+  const int d = h->d;
+  h->mu.assign(mu, mu + d);
+  h->L.assign(d * d, 0.0);
+  double ld = 0.0;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j <= i; ++j) h->L[i * d + j] = L[i * d + j];
+  for (int i = 0; i < d; ++i) ld += std::log(std::fabs(h->L[i * d + i]));
+  h->logdet = ld;
+  BST_TRY(upload_real(h, h->mu_r, h->mu.data(), d));
+  BST_TRY(upload_real(h, h->L_r, h->L.data(), static_cast<size_t>(d) * d));
+  BST_CUDA(cudaMemcpy(h->mu64, h->mu.data(), d * 8, cudaMemcpyHostToDevice));
+  BST_CUDA(cudaMemcpy(h->L64, h->L.data(), static_cast<size_t>(d) * d * 8, cudaMemcpyHostToDevice));
+  h->weights_dirty = true;
+  h->state_stale = true;
+  return BST_OK;
+}
+
+bst_status sum_counters(bst_ctx *h, double out[4]) {
+  const int n = h->n;
+  std::vector<unsigned long long> a(n), e(n), dv(n);
+  std::vector<double> as(n);
+  BST_CUDA(cudaMemcpy(a.data(), h->accepts, n * 8, cudaMemcpyDeviceToHost));
+  BST_CUDA(cudaMemcpy(e.data(), h->evals, n * 8, cudaMemcpyDeviceToHost));
+  BST_CUDA(cudaMemcpy(dv.data(), h->divs, n * 8, cudaMemcpyDeviceToHost));
+  BST_CUDA(cudaMemcpy(as.data(), h->acc_stat, n * 8, cudaMemcpyDeviceToHost));
+  out[0] = out[1] = out[2] = out[3] = 0.0;
+  for (int i = 0; i < n; ++i) {
+    out[0] += static_cast<double>(a[i]);
+    out[1] += static_cast<double>(e[i]);
+    out[2] += static_cast<double>(dv[i]);
+    out[3] += as[i];
+  }
+  return BST_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char *bst_version(void) { return "bst 0.1 (sm_103a)"; }
+const char *bst_last_error(void) { return g_err.c_str(); }
+
+bst_status bst_create(bst_handle *out, const bst_config *cfg) {
+  if (!out || !cfg) return fail(BST_ERR_ARG, "bst_create: NULL argument");
+  *out = nullptr;
+  if (cfg->d < 1 || cfg->d > kMaxD) return fail(BST_ERR_ARG, "bst_create: d must be in 1..32");
+  if (cfg->n_chains < 1) return fail(BST_ERR_ARG, "bst_create: n_chains must be >= 1");
+  if (cfg->precision < BST_BF16 || cfg->precision > BST_FP64) return fail(BST_ERR_ARG, "bst_create: precision");
+  if (cfg->lik_kind != BST_LIK_EMULATOR && cfg->lik_kind != BST_LIK_ANALYTIC)
+    return fail(BST_ERR_ARG, "bst_create: lik_kind");
+  if (cfg->precision == BST_BF16 && cfg->lik_kind != BST_LIK_EMULATOR)
+    return fail(BST_ERR_UNSUPPORTED, "bst_create: BF16 precision needs the emulator likelihood");
+  const int md = cfg->max_depth ? cfg->max_depth : 8;
+  if (md < 1 || md > kMaxDepthNuts) return fail(BST_ERR_ARG, "bst_create: max_depth must be in 1..10");
+  const int wk = cfg->aies_walkers ? cfg->aies_walkers : 64;
+  if (wk < 2 || wk % 2) return fail(BST_ERR_ARG, "bst_create: aies_walkers must be even and >= 2");
+  const double aa = cfg->aies_a != 0.0 ? cfg->aies_a : 2.0;
+  if (!(aa > 1.0)) return fail(BST_ERR_ARG, "bst_create: aies_a must be > 1");
+  const int th = cfg->thin ? cfg->thin : 1;
+  if (th < 1) return fail(BST_ERR_ARG, "bst_create: thin must be >= 1");
+  BST_CUDA(cudaSetDevice(cfg->device));
+  bst_ctx *h = new bst_ctx();
+  h->d = cfg->d;
+  h->dp = pad16(cfg->d);
+  h->n = cfg->n_chains;
+  h->precision = cfg->precision;
+  h->lik = cfg->lik_kind;
+  h->seed = cfg->seed;
+  h->max_depth = md;
+  h->walkers = wk;
+  h->aies_a = aa;
+  h->thin = th;
+  h->device = cfg->device;
+  h->rs = (cfg->precision == BST_FP64) ? 8 : 4;
+  h->kb1 = (3 * h->dp + 63) / 64;
+  const size_t n = h->n, dp = h->dp, rs = h->rs;
+  h->work_stride = (rs == 8) ? work_stride_elems<double>(h->dp) : work_stride_elems<float>(h->dp);
+  bst_status st = BST_OK;
+  auto A = [&](void **p, size_t b) {
+    if (st == BST_OK) st = dalloc(h, p, b);
+  };
+  A(&h->z, n * dp * rs);
+  A(&h->g, n * dp * rs);
+  A(&h->lp, n * rs);
+  A(&h->ze, n * dp * rs);
+  A(&h->lle, n * rs);
+  A(&h->gle, n * dp * rs);
+  A(&h->work, n * static_cast<size_t>(h->work_stride) * rs);
+  A(&h->xbuf, n * dp * rs);
+  A((void **)&h->iter, n * 4);
+  A((void **)&h->acc_stat, n * 8);
+  A((void **)&h->accepts, n * 8);
+  A((void **)&h->evals, n * 8);
+  A((void **)&h->divs, n * 8);
+  A((void **)&h->steps_done, n * 4);
+  A((void **)&h->status, 64);
+  A(&h->mu_r, kMaxD * rs);
+  A(&h->L_r, kMaxD * kMaxD * rs);
+  A(&h->lo_r, kMaxD * rs);
+  A(&h->up_r, kMaxD * rs);
+  A((void **)&h->gauss_d, kMaxD * 4);
+  A((void **)&h->mu64, kMaxD * 8);
+  A((void **)&h->L64, kMaxD * kMaxD * 8);
+  A((void **)&h->mu64_new, kMaxD * 8);
+  A((void **)&h->L64_new, kMaxD * kMaxD * 8);
+  A((void **)&h->info64, 8 * 8);
+  h->wf_records = static_cast<int>((n + 15) / 16) + 1;  // one per tile for any tiling + one external
+  A((void **)&h->wf, static_cast<size_t>(h->wf_records) * kWfStride * 8);
+  if (st != BST_OK) {
+    bst_destroy(h);
+    return st;
+  }
+  *out = h;
+  return BST_OK;
+}
+
+void bst_destroy(bst_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  for (void *p : h->allocs)
+    if (p) cudaFree(p);
+  delete h;
+}
+
+bst_status bst_set_emulator(bst_handle h, int depth, int width, const double *params, const double *in_m,
+                            const double *in_s, double out_m, double out_s) {
+  if (!h || !params || !in_m || !in_s) return fail(BST_ERR_ARG, "bst_set_emulator: NULL argument");
+  if (h->lik != BST_LIK_EMULATOR) return fail(BST_ERR_STATE, "bst_set_emulator: handle was created for the analytic likelihood");
+  if (depth < 1 || depth > 8) return fail(BST_ERR_ARG, "bst_set_emulator: depth must be in 1..8");
+  if (width < 256 || width % 256) return fail(BST_ERR_UNSUPPORTED, "bst_set_emulator: width must be a multiple of 256");
+  if (h->precision == BST_BF16 && width > 512) return fail(BST_ERR_UNSUPPORTED, "bst_set_emulator: BF16 width must be 256 or 512");
+  if (h->precision == BST_FP64 && width > 512) return fail(BST_ERR_UNSUPPORTED, "bst_set_emulator: FP64 width must be <= 512");
+  if (width > 1024) return fail(BST_ERR_UNSUPPORTED, "bst_set_emulator: width must be <= 1024");
+  const int d = h->d;
+  const size_t np = static_cast<size_t>(d) * width + width + static_cast<size_t>(depth - 1) * (static_cast<size_t>(width) * width + width) + width + 1;
+  if (!all_finite(params, np) || !all_finite(in_m, d) || !all_finite(in_s, d) || !std::isfinite(out_m) || !std::isfinite(out_s))
+    return fail(BST_ERR_NONFINITE, "bst_set_emulator: non-finite parameter");
+  for (int i = 0; i < d; ++i)
+    if (!(in_s[i] > 0.0)) return fail(BST_ERR_ARG, "bst_set_emulator: in_s must be positive");
+  BST_CUDA(cudaSetDevice(h->device));
+  const bool realloc = !(h->depth == depth && h->width == width && h->P64);
+  if (realloc) {
+    h->depth = depth;
+    h->width = width;
+    h->nparams = np;
+    const size_t w = width, dp = h->dp, rs = h->rs, nh = static_cast<size_t>(depth - 1);
+    BST_TRY(dalloc_t(h, &h->P64, np));
+    BST_TRY(dalloc_t(h, &h->in_m64, d));
+    BST_TRY(dalloc_t(h, &h->in_s64, d));
+    for (int f = 0; f < 2; ++f) {
+      BST_TRY(dalloc_t(h, &h->W1f[f], w * dp));
+      BST_TRY(dalloc_t(h, &h->b1f[f], w));
+    }
+    if (h->precision == BST_BF16) {
+      for (int f = 0; f < 2; ++f) {
+        BST_TRY(dalloc(h, (void **)&h->tl1[f], (w / 256) * h->kb1 * static_cast<size_t>(kTcStageBytes)));
+        BST_TRY(dalloc(h, (void **)&h->tg1[f], (w / 64) * 2 * dp * 128));
+        BST_TRY(dalloc_t(h, &h->tb1[f], w));
+      }
+      BST_TRY(dalloc(h, (void **)&h->thid, 2 * nh * w * w * 2 + 16));
+      BST_TRY(dalloc_t(h, &h->tb, nh * w + 1));
+      BST_TRY(dalloc_t(h, &h->two, w));
+    } else {
+      for (int f = 0; f < 2; ++f) {
+        BST_TRY(dalloc(h, &h->sW1T[f], dp * w * rs));
+        BST_TRY(dalloc(h, &h->sW1[f], dp * w * rs));
+        BST_TRY(dalloc(h, &h->sb1[f], w * rs));
+      }
+      BST_TRY(dalloc(h, &h->sWT, nh * w * w * rs + 16));
+      BST_TRY(dalloc(h, &h->sW, nh * w * w * rs + 16));
+      BST_TRY(dalloc(h, &h->sb, nh * w * rs + 16));
+      BST_TRY(dalloc(h, &h->swo, w * rs));
+    }
+    h->scratch_rows = 0;
+    dfree(h, h->scratch);
+    h->scratch = nullptr;
+    // training state belongs to the old shape
+    h->P32 = nullptr;
+  }
+  BST_CUDA(cudaMemcpy(h->P64, params, np * 8, cudaMemcpyHostToDevice));
+  BST_CUDA(cudaMemcpy(h->in_m64, in_m, d * 8, cudaMemcpyHostToDevice));
+  BST_CUDA(cudaMemcpy(h->in_s64, in_s, d * 8, cudaMemcpyHostToDevice));
+  h->out_m = out_m;
+  h->out_s = out_s;
+  h->bo = params[np - 1];
+  h->p32_newer = false;
+  if (h->P32) {
+    BST_CUDA(launch_cast_f32(h->P64, h->P32, np, 0));
+    h->adam_t = 0;
+    BST_CUDA(cudaMemset(h->m1, 0, np * 4));
+    BST_CUDA(cudaMemset(h->m2, 0, np * 4));
+  }
+  h->weights_dirty = true;
+  h->state_stale = true;
+  if (h->stage < 1) h->stage = 1;
+  if (h->stage < 2) {
+    // loglike works before init_chains: identity whitening for the fold buffers
+    std::vector<double> mu(d, 0.0), L(static_cast<size_t>(d) * d, 0.0);
+    for (int i = 0; i < d; ++i) L[i * d + i] = 1.0;
+    if (h->mu.empty()) BST_TRY(set_target(h, mu.data(), L.data()));
+  }
+  return BST_OK;
+}
+
+bst_status bst_get_emulator(bst_handle h, double *params) {
+  if (!h || !params) return fail(BST_ERR_ARG, "bst_get_emulator: NULL argument");
+  if (h->lik != BST_LIK_EMULATOR || !h->P64) return fail(BST_ERR_STATE, "bst_get_emulator: no emulator set");
+  BST_CUDA(cudaSetDevice(h->device));
+  if (h->p32_newer) {
+    BST_CUDA(launch_cast_f32_to_f64(h->P32, h->P64, h->nparams, 0));
+    h->p32_newer = false;
+  }
+  BST_CUDA(cudaDeviceSynchronize());
+  BST_CUDA(cudaMemcpy(params, h->P64, h->nparams * 8, cudaMemcpyDeviceToHost));
+  return BST_OK;
+}
+
+bst_status bst_set_analytic(bst_handle h, int d_c, int n_hidden, int n_data, const double *A, const double *B,
+                            const double *c, const double *N, const double *data, double sigma, int linear) {
+  if (!h || !A || !B || !c || !data) return fail(BST_ERR_ARG, "bst_set_analytic: NULL argument");
+  if (h->lik != BST_LIK_ANALYTIC) return fail(BST_ERR_STATE, "bst_set_analytic: handle was created for the emulator");
+  const int d = h->d;
+  if (d_c < 1 || d_c > d) return fail(BST_ERR_ARG, "bst_set_analytic: d_c must be in 1..d");
+  if (d_c < d && !N) return fail(BST_ERR_ARG, "bst_set_analytic: N required when d_c < d");
+  if (n_hidden < 1 || n_hidden > 64) return fail(BST_ERR_UNSUPPORTED, "bst_set_analytic: n_hidden must be in 1..64");
+  if (n_data < 1) return fail(BST_ERR_ARG, "bst_set_analytic: n_data must be >= 1");
+  if (!(sigma > 0.0)) return fail(BST_ERR_ARG, "bst_set_analytic: sigma must be positive");
+  const size_t nA = static_cast<size_t>(n_data) * n_hidden, nB = static_cast<size_t>(n_hidden) * d_c,
+               nN = static_cast<size_t>(n_data) * (d - d_c);
+  if (!all_finite(A, nA) || !all_finite(B, nB) || !all_finite(c, n_hidden) || !all_finite(data, n_data) ||
+      (nN && !all_finite(N, nN)))
+    return fail(BST_ERR_NONFINITE, "bst_set_analytic: non-finite input");
+  BST_CUDA(cudaSetDevice(h->device));
+  const bool realloc = !(h->H == n_hidden && h->n_data == n_data && h->d_c == d_c && h->A64);
+  h->d_c = d_c;
+  h->H = n_hidden;
+  h->n_data = n_data;
+  h->linear = linear ? 1 : 0;
+  h->sigma = sigma;
+  h->has_N = (d > d_c) ? 1 : 0;
+  if (realloc) {
+    const size_t dp = h->dp, rs = h->rs;
+    BST_TRY(dalloc_t(h, &h->A64, nA));
+    BST_TRY(dalloc_t(h, &h->B64, nB));
+    BST_TRY(dalloc_t(h, &h->c64, n_hidden));
+    BST_TRY(dalloc_t(h, &h->N64, nN + 1));
+    BST_TRY(dalloc_t(h, &h->data64, n_data));
+    BST_TRY(dalloc_t(h, &h->fBf, n_hidden * dp));
+    BST_TRY(dalloc_t(h, &h->fcf, n_hidden));
+    BST_TRY(dalloc_t(h, &h->fAT, nA));
+    BST_TRY(dalloc_t(h, &h->fNfT, dp * n_data));
+    BST_TRY(dalloc_t(h, &h->fdata, n_data));
+    BST_TRY(dalloc(h, &h->aAT, nA * rs));
+    for (int f = 0; f < 2; ++f) {
+      BST_TRY(dalloc(h, &h->aBf[f], n_hidden * dp * rs));
+      BST_TRY(dalloc(h, &h->acf[f], n_hidden * rs));
+      BST_TRY(dalloc(h, &h->aNfT[f], dp * n_data * rs));
+      BST_TRY(dalloc(h, &h->adata[f], n_data * rs));
+    }
+  }
+  BST_CUDA(cudaMemcpy(h->A64, A, nA * 8, cudaMemcpyHostToDevice));
+  BST_CUDA(cudaMemcpy(h->B64, B, nB * 8, cudaMemcpyHostToDevice));
+  BST_CUDA(cudaMemcpy(h->c64, c, n_hidden * 8, cudaMemcpyHostToDevice));
+  if (nN) BST_CUDA(cudaMemcpy(h->N64, N, nN * 8, cudaMemcpyHostToDevice));
+  BST_CUDA(cudaMemcpy(h->data64, data, n_data * 8, cudaMemcpyHostToDevice));
+  h->weights_dirty = true;
+  h->state_stale = true;
+  if (h->stage < 1) h->stage = 1;
+  if (h->mu.empty()) {
+    std::vector<double> mu(d, 0.0), L(static_cast<size_t>(d) * d, 0.0);
+    for (int i = 0; i < d; ++i) L[i * d + i] = 1.0;
+    BST_TRY(set_target(h, mu.data(), L.data()));
+  }
+  return BST_OK;
+}
+
+bst_status bst_init_chains(bst_handle h, const double *theta0, const double *lower, const double *upper,
+                           const int *gauss, const double *mu, const double *L) {
+  if (!h || !theta0 || !lower || !upper || !mu || !L) return fail(BST_ERR_ARG, "bst_init_chains: NULL argument");
+  if (h->stage < 1) return fail(BST_ERR_STATE, "bst_init_chains: set a likelihood first");
+  const int d = h->d, n = h->n;
+  if (!all_finite(theta0, static_cast<size_t>(n) * d) || !all_finite(mu, d))
+    return fail(BST_ERR_NONFINITE, "bst_init_chains: non-finite theta0 or mu");
+  for (int i = 0; i < d; ++i) {
+    if (!(L[i * d + i] > 0.0) || !std::isfinite(L[i * d + i]))
+      return fail(BST_ERR_ARG, "bst_init_chains: L must have a positive finite diagonal");
+    for (int j = 0; j <= i; ++j)
+      if (!std::isfinite(L[i * d + j])) return fail(BST_ERR_NONFINITE, "bst_init_chains: non-finite L");
+    if (std::isnan(lower[i]) || std::isnan(upper[i]) || !(lower[i] <= upper[i]))
+      return fail(BST_ERR_ARG, "bst_init_chains: need lower <= upper");
+  }
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_TRY(set_target(h, mu, L));
+  h->lower.assign(lower, lower + d);
+  h->upper.assign(upper, upper + d);
+  h->gauss.assign(d, 0);
+  h->any_gauss = 0;
+  if (gauss)
+    for (int i = 0; i < d; ++i) {
+      h->gauss[i] = gauss[i] ? 1 : 0;
+      h->any_gauss |= h->gauss[i];
+    }
+  BST_TRY(upload_real(h, h->lo_r, h->lower.data(), d));
+  BST_TRY(upload_real(h, h->up_r, h->upper.data(), d));
+  BST_CUDA(cudaMemcpy(h->gauss_d, h->gauss.data(), d * 4, cudaMemcpyHostToDevice));
+  // z0 = L^-1 (theta0 - mu), forward substitution in FP64, rows padded to dp
+  std::vector<double> z(static_cast<size_t>(n) * h->dp, 0.0);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < d; ++i) {
+      double s = theta0[static_cast<size_t>(c) * d + i] - h->mu[i];
+      for (int j = 0; j < i; ++j) s -= h->L[i * d + j] * z[static_cast<size_t>(c) * h->dp + j];
+      z[static_cast<size_t>(c) * h->dp + i] = s / h->L[i * d + i];
+    }
+  }
+  BST_TRY(upload_real(h, h->z, z.data(), z.size()));
+  const size_t nn = n;
+  BST_CUDA(cudaMemset(h->iter, 0, nn * 4));
+  BST_CUDA(cudaMemset(h->acc_stat, 0, nn * 8));
+  BST_CUDA(cudaMemset(h->accepts, 0, nn * 8));
+  BST_CUDA(cudaMemset(h->evals, 0, nn * 8));
+  BST_CUDA(cudaMemset(h->divs, 0, nn * 8));
+  BST_CUDA(cudaMemset(h->work, 0, nn * h->work_stride * h->rs));
+  BST_CUDA(cudaMemset(h->status, 0, 64));
+  h->stage = 2;
+  BST_TRY(refresh(h, 0));
+  BST_CUDA(cudaDeviceSynchronize());
+  return check_status(h);
+}
+
+bst_status bst_step(bst_handle h, int kernel, double eps, int n_leapfrog, int n_steps, void *samples_dev,
+                    void *stream, bst_step_stats *stats) {
+  if (!h) return fail(BST_ERR_ARG, "bst_step: NULL handle");
+  if (h->stage < 2) return fail(BST_ERR_STATE, "bst_step: call bst_init_chains first");
+  if (kernel < BST_MH || kernel > BST_AIES) return fail(BST_ERR_ARG, "bst_step: unknown kernel");
+  if (n_steps < 0) return fail(BST_ERR_ARG, "bst_step: n_steps must be >= 0");
+  if (kernel != BST_AIES && !(eps > 0.0 && std::isfinite(eps))) return fail(BST_ERR_ARG, "bst_step: eps must be positive");
+  if (kernel == BST_HMC && n_leapfrog < 1) return fail(BST_ERR_ARG, "bst_step: n_leapfrog must be >= 1");
+  if (kernel == BST_AIES) {
+    const int half = h->walkers / 2;
+    const int tile = (h->precision == BST_BF16) ? kTcRows : simt_rows_per_tile(h->precision, h->width, h->lik);
+    if (h->n % h->walkers) return fail(BST_ERR_ARG, "bst_step: AIES needs n_chains to be a multiple of aies_walkers");
+    if (tile % half) return fail(BST_ERR_UNSUPPORTED, "bst_step: AIES ensemble halves must not span chain tiles");
+  }
+  BST_CUDA(cudaSetDevice(h->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n_steps == 0) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    return BST_OK;
+  }
+  BST_TRY(prepare(h, s));
+  BST_TRY(ensure_scratch(h, h->n));
+  const bool needs_grad = kernel == BST_MALA || kernel == BST_HMC || kernel == BST_NUTS;
+  if (h->state_stale || (needs_grad && !h->grad_valid)) BST_TRY(refresh(h, s));
+  double before[4] = {0, 0, 0, 0}, after[4];
+  if (stats) {
+    BST_CUDA(cudaStreamSynchronize(s));
+    BST_TRY(sum_counters(h, before));
+  }
+  BST_TRY(run(h, kernel, eps, n_leapfrog, n_steps, samples_dev, 0, s));
+  if (!needs_grad) h->grad_valid = false;
+  if (stats) {
+    BST_CUDA(cudaStreamSynchronize(s));
+    BST_TRY(sum_counters(h, after));
+    stats->accepts = static_cast<int64_t>(after[0] - before[0]);
+    stats->evals = static_cast<int64_t>(after[1] - before[1]);
+    stats->divergences = static_cast<int64_t>(after[2] - before[2]);
+    stats->accept_stat = (after[3] - before[3]) / (static_cast<double>(h->n) * n_steps);
+    bst_status st = check_status(h);
+    stats->status = st;
+    return st;
+  }
+  return BST_OK;
+}
+
+static bst_status loglike_impl(bst_handle h, const void *theta, int m, void *logl, void *grad, void *stream,
+                               int need_grad) {
+  if (!h || (m > 0 && (!theta || !logl || (need_grad && !grad)))) return fail(BST_ERR_ARG, "bst_loglike: NULL argument");
+  if (h->stage < 1) return fail(BST_ERR_STATE, "bst_loglike: set a likelihood first");
+  if (m < 0) return fail(BST_ERR_ARG, "bst_loglike: m must be >= 0");
+  if (m == 0) return BST_OK;
+  BST_CUDA(cudaSetDevice(h->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BST_TRY(prepare(h, s));
+  const int chunk = h->n > 65536 ? h->n : 65536;
+  if (need_grad) BST_TRY(ensure_scratch(h, chunk < m ? chunk : m));
+  const size_t rs = h->rs;
+  for (int r0 = 0; r0 < m; r0 += chunk) {
+    const int rows = (m - r0) < chunk ? (m - r0) : chunk;
+    const char *ti = static_cast<const char *>(theta) + static_cast<size_t>(r0) * h->d * rs;
+    char *lo = static_cast<char *>(logl) + static_cast<size_t>(r0) * rs;
+    char *go = need_grad ? static_cast<char *>(grad) + static_cast<size_t>(r0) * h->d * rs : nullptr;
+    BST_TRY(run(h, kModeLoglike, 0.0, 0, 1, nullptr, 1, s, ti, lo, go, rows, need_grad));
+  }
+  return BST_OK;
+}
+
+bst_status bst_loglike(bst_handle h, const void *theta_dev, int m, void *logl_dev, void *stream) {
+  return loglike_impl(h, theta_dev, m, logl_dev, nullptr, stream, 0);
+}
+bst_status bst_grad_loglike(bst_handle h, const void *theta_dev, int m, void *logl_dev, void *grad_dev,
+                            void *stream) {
+  return loglike_impl(h, theta_dev, m, logl_dev, grad_dev, stream, 1);
+}
+
+bst_status bst_welford_reset(bst_handle h) {
+  if (!h) return fail(BST_ERR_ARG, "bst_welford_reset: NULL handle");
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_CUDA(launch_welford_clear(h->wf, h->wf_records, kWfStride, 0));
+  h->welford_on = true;
+  return BST_OK;
+}
+
+bst_status bst_welford_add(bst_handle h, const void *x_dev, int m, void *stream) {
+  if (!h || (m > 0 && !x_dev)) return fail(BST_ERR_ARG, "bst_welford_add: NULL argument");
+  if (m < 0) return fail(BST_ERR_ARG, "bst_welford_add: m must be >= 0");
+  if (m == 0) return BST_OK;
+  BST_CUDA(cudaSetDevice(h->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double *rec = h->wf + static_cast<size_t>(h->wf_records - 1) * kWfStride;
+  if (h->rs == 8) BST_CUDA(launch_welford_add_f64(static_cast<const double *>(x_dev), m, h->d, rec, kWfStride, s));
+  else BST_CUDA(launch_welford_add_f32(static_cast<const float *>(x_dev), m, h->d, rec, kWfStride, s));
+  return BST_OK;
+}
+
+bst_status bst_adapt_cov(bst_handle h, double jitter0, double *mu_out, double *L_out, double *jitter_used) {
+  if (!h) return fail(BST_ERR_ARG, "bst_adapt_cov: NULL handle");
+  if (h->stage < 2) return fail(BST_ERR_STATE, "bst_adapt_cov: call bst_init_chains first");
+  if (!(jitter0 > 0.0)) return fail(BST_ERR_ARG, "bst_adapt_cov: jitter0 must be positive");
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_CUDA(cudaDeviceSynchronize());
+  BST_TRY(check_status(h));
+  const int d = h->d;
+  BST_CUDA(launch_adapt_finalize(h->wf, h->wf_records, kWfStride, d, jitter0, h->mu64_new, h->L64_new, h->info64, 0));
+  double info[3];
+  BST_CUDA(cudaMemcpy(info, h->info64, 3 * 8, cudaMemcpyDeviceToHost));
+  if (info[2] == 1.0) return fail(BST_ERR_STATE, "bst_adapt_cov: fewer than 2 samples accumulated");
+  if (info[2] == 2.0) return fail(BST_ERR_NOT_PD, "bst_adapt_cov: covariance not positive definite up to jitter 1e-2");
+  std::vector<double> mu(d), L(static_cast<size_t>(d) * d);
+  BST_CUDA(cudaMemcpy(mu.data(), h->mu64_new, d * 8, cudaMemcpyDeviceToHost));
+  BST_CUDA(cudaMemcpy(L.data(), h->L64_new, static_cast<size_t>(d) * d * 8, cudaMemcpyDeviceToHost));
+  // keep x fixed: z_new = L_new^-1 (mu_old + L_old z_old - mu_new)
+  if (h->rs == 8) BST_CUDA(launch_remap_f64((double *)h->z, h->n, d, h->dp, h->mu64, h->L64, h->mu64_new, h->L64_new, 0));
+  else BST_CUDA(launch_remap_f32((float *)h->z, h->n, d, h->dp, h->mu64, h->L64, h->mu64_new, h->L64_new, 0));
+  BST_CUDA(cudaDeviceSynchronize());
+  BST_TRY(set_target(h, mu.data(), L.data()));
+  h->welford_on = false;
+  BST_TRY(refresh(h, 0));
+  BST_CUDA(cudaDeviceSynchronize());
+  if (mu_out) std::memcpy(mu_out, mu.data(), d * 8);
+  if (L_out) std::memcpy(L_out, L.data(), static_cast<size_t>(d) * d * 8);
+  if (jitter_used) *jitter_used = info[1];
+  return check_status(h);
+}
+
+bst_status bst_get_state(bst_handle h, double *z, double *logp, double *grad, uint32_t *iter) {
+  if (!h) return fail(BST_ERR_ARG, "bst_get_state: NULL handle");
+  if (h->stage < 2) return fail(BST_ERR_STATE, "bst_get_state: no chain state");
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_CUDA(cudaDeviceSynchronize());
+  const int n = h->n, d = h->d, dp = h->dp;
+  std::vector<double> t(static_cast<size_t>(n) * dp);
+  if (z) {
+    BST_TRY(download_real(h, t.data(), h->z, t.size()));
+    for (int c = 0; c < n; ++c)
+      for (int i = 0; i < d; ++i) z[static_cast<size_t>(c) * d + i] = t[static_cast<size_t>(c) * dp + i];
+  }
+  if (grad) {
+    BST_TRY(download_real(h, t.data(), h->g, t.size()));
+    for (int c = 0; c < n; ++c)
+      for (int i = 0; i < d; ++i) grad[static_cast<size_t>(c) * d + i] = t[static_cast<size_t>(c) * dp + i];
+  }
+  if (logp) BST_TRY(download_real(h, logp, h->lp, n));
+  if (iter) BST_CUDA(cudaMemcpy(iter, h->iter, n * 4, cudaMemcpyDeviceToHost));
+  return BST_OK;
+}
+
+bst_status bst_set_state(bst_handle h, const double *z, const double *logp, const double *grad,
+                         const uint32_t *iter) {
+  if (!h || !z || !logp || !grad || !iter) return fail(BST_ERR_ARG, "bst_set_state: NULL argument");
+  if (h->stage < 2) return fail(BST_ERR_STATE, "bst_set_state: call bst_init_chains first");
+  const int n = h->n, d = h->d, dp = h->dp;
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_CUDA(cudaDeviceSynchronize());
+  std::vector<double> t(static_cast<size_t>(n) * dp, 0.0);
+  for (int c = 0; c < n; ++c)
+    for (int i = 0; i < d; ++i) t[static_cast<size_t>(c) * dp + i] = z[static_cast<size_t>(c) * d + i];
+  BST_TRY(upload_real(h, h->z, t.data(), t.size()));
+  for (int c = 0; c < n; ++c)
+    for (int i = 0; i < d; ++i) t[static_cast<size_t>(c) * dp + i] = grad[static_cast<size_t>(c) * d + i];
+  BST_TRY(upload_real(h, h->g, t.data(), t.size()));
+  BST_TRY(upload_real(h, h->lp, logp, n));
+  BST_CUDA(cudaMemcpy(h->iter, iter, n * 4, cudaMemcpyHostToDevice));
+  h->grad_valid = true;
+  h->state_stale = false;
+  return BST_OK;
+}
+
+bst_status bst_get_whitening(bst_handle h, double *mu, double *L) {
+  if (!h || !mu || !L) return fail(BST_ERR_ARG, "bst_get_whitening: NULL argument");
+  if (h->mu.empty()) return fail(BST_ERR_STATE, "bst_get_whitening: no whitening set");
+  std::memcpy(mu, h->mu.data(), h->d * 8);
+  std::memcpy(L, h->L.data(), static_cast<size_t>(h->d) * h->d * 8);
+  return BST_OK;
+}
+
+bst_status bst_get_counters(bst_handle h, int64_t *accepts, int64_t *evals, int64_t *divergences,
+                            double *accept_stat) {
+  if (!h) return fail(BST_ERR_ARG, "bst_get_counters: NULL handle");
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_CUDA(cudaDeviceSynchronize());
+  const size_t n = h->n;
+  if (accepts) BST_CUDA(cudaMemcpy(accepts, h->accepts, n * 8, cudaMemcpyDeviceToHost));
+  if (evals) BST_CUDA(cudaMemcpy(evals, h->evals, n * 8, cudaMemcpyDeviceToHost));
+  if (divergences) BST_CUDA(cudaMemcpy(divergences, h->divs, n * 8, cudaMemcpyDeviceToHost));
+  if (accept_stat) BST_CUDA(cudaMemcpy(accept_stat, h->acc_stat, n * 8, cudaMemcpyDeviceToHost));
+  return BST_OK;
+}
+
+static bst_status train_setup(bst_handle h, int m) {
+  if (h->lik != BST_LIK_EMULATOR || !h->P64) return fail(BST_ERR_STATE, "bst_train: no emulator set");
+  if (m < 1 || m > 65536) return fail(BST_ERR_ARG, "bst_train: batch size must be in 1..65536");
+  const size_t np = h->nparams;
+  if (!h->P32) {
+    BST_TRY(dalloc_t(h, &h->P32, np));
+    BST_TRY(dalloc_t(h, &h->G32, np));
+    BST_TRY(dalloc_t(h, &h->m1, np));
+    BST_TRY(dalloc_t(h, &h->m2, np));
+    BST_TRY(dalloc_t(h, &h->in_m32, h->d));
+    BST_TRY(dalloc_t(h, &h->in_s32, h->d));
+    if (h->p32_newer) h->p32_newer = false;
+    BST_CUDA(launch_cast_f32(h->P64, h->P32, np, 0));
+    BST_CUDA(launch_cast_f32(h->in_m64, h->in_m32, h->d, 0));
+    BST_CUDA(launch_cast_f32(h->in_s64, h->in_s32, h->d, 0));
+    h->adam_t = 0;
+    h->train_cap = 0;
+  }
+  if (m > h->train_cap) {
+    const size_t mm = m, w = h->width, D = h->depth;
+    BST_TRY(dalloc_t(h, &h->tw.U, mm * h->d));
+    BST_TRY(dalloc_t(h, &h->tw.H, D * mm * w));
+    BST_TRY(dalloc_t(h, &h->tw.Dl, mm * w));
+    BST_TRY(dalloc_t(h, &h->tw.Dn, mm * w));
+    BST_TRY(dalloc_t(h, &h->tw.dout, mm));
+    BST_TRY(dalloc_t(h, &h->tw.loss, 4));
+    h->train_cap = m;
+  }
+  return BST_OK;
+}
+
+bst_status bst_train_grad(bst_handle h, const float *X_dev, const float *chi2_dev, int m, float *grad_dev,
+                          float *loss_dev, void *stream) {
+  if (!h || !X_dev || !chi2_dev || !grad_dev) return fail(BST_ERR_ARG, "bst_train_grad: NULL argument");
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_TRY(train_setup(h, m));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BST_CUDA(launch_train_grad(h->P32, h->in_m32, h->in_s32, static_cast<float>(h->out_m), static_cast<float>(h->out_s),
+                             h->d, h->depth, h->width, m, X_dev, chi2_dev, grad_dev, h->tw, s));
+  if (loss_dev) BST_CUDA(cudaMemcpyAsync(loss_dev, h->tw.loss, 4, cudaMemcpyDeviceToDevice, s));
+  return BST_OK;
+}
+
+bst_status bst_train_step(bst_handle h, const float *X_dev, const float *chi2_dev, int m, double lr, double beta1,
+                          double beta2, double adam_eps, float *loss_dev, void *stream) {
+  if (!h || !X_dev || !chi2_dev) return fail(BST_ERR_ARG, "bst_train_step: NULL argument");
+  if (!(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(adam_eps > 0.0))
+    return fail(BST_ERR_ARG, "bst_train_step: bad Adam hyper-parameters");
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_TRY(train_setup(h, m));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BST_CUDA(launch_train_grad(h->P32, h->in_m32, h->in_s32, static_cast<float>(h->out_m), static_cast<float>(h->out_s),
+                             h->d, h->depth, h->width, m, X_dev, chi2_dev, h->G32, h->tw, s));
+  if (loss_dev) BST_CUDA(cudaMemcpyAsync(loss_dev, h->tw.loss, 4, cudaMemcpyDeviceToDevice, s));
+  h->adam_t += 1;
+  BST_CUDA(launch_adam(h->P32, h->G32, h->m1, h->m2, h->nparams, h->adam_t, static_cast<float>(lr),
+                       static_cast<float>(beta1), static_cast<float>(beta2), static_cast<float>(adam_eps), s));
+  h->p32_newer = true;
+  h->weights_dirty = true;
+  h->state_stale = true;
+  return BST_OK;
+}
+
+bst_status bst_ess(bst_handle h, const void *samples_dev, int n_draws, double *ess_out) {
+  if (!h || !samples_dev || !ess_out) return fail(BST_ERR_ARG, "bst_ess: NULL argument");
+  if (n_draws < 4) return fail(BST_ERR_ARG, "bst_ess: need at least 4 draws");
+  BST_CUDA(cudaSetDevice(h->device));
+  const int M = h->n, d = h->d, n = n_draws;
+  const size_t md = static_cast<size_t>(M) * d;
+  if (!h->ess_mean) {
+    BST_TRY(dalloc_t(h, &h->ess_mean, md));
+    BST_TRY(dalloc_t(h, &h->ess_var, md));
+    BST_TRY(dalloc_t(h, &h->ess_V, static_cast<size_t>(d) * 32));
+  }
+  if (h->rs == 8) BST_CUDA(launch_ess_moments_f64((const double *)samples_dev, n, M, d, h->ess_mean, h->ess_var, 0));
+  else BST_CUDA(launch_ess_moments_f32((const float *)samples_dev, n, M, d, h->ess_mean, h->ess_var, 0));
+  std::vector<double> mean(md), var(md);
+  BST_CUDA(cudaMemcpy(mean.data(), h->ess_mean, md * 8, cudaMemcpyDeviceToHost));
+  BST_CUDA(cudaMemcpy(var.data(), h->ess_var, md * 8, cudaMemcpyDeviceToHost));
+  std::vector<double> var_plus(d), sumP(d, 0.0), prevP(d, INFINITY);
+  std::vector<int> active(d, 1);
+  for (int q = 0; q < d; ++q) {
+    double gm = 0.0, Wv = 0.0, Bv = 0.0;
+    for (int c = 0; c < M; ++c) gm += mean[static_cast<size_t>(c) * d + q];
+    gm /= M;
+    for (int c = 0; c < M; ++c) {
+      Wv += var[static_cast<size_t>(c) * d + q];
+      const double e = mean[static_cast<size_t>(c) * d + q] - gm;
+      Bv += e * e;
+    }
+    Wv /= M;
+    const double Bn = (M > 1) ? Bv / (M - 1) : 0.0;
+    var_plus[q] = (n - 1.0) / n * Wv + Bn;
+  }
+  std::vector<double> V(static_cast<size_t>(d) * 32);
+  int n_active = d;
+  for (int t0 = 0; t0 + 1 < n && n_active > 0; t0 += 32) {
+    const int nt = (n - t0) < 32 ? (n - t0) : 32;
+    BST_CUDA(cudaMemset(h->ess_V, 0, static_cast<size_t>(d) * 32 * 8));
+    if (h->rs == 8) BST_CUDA(launch_ess_variogram_f64((const double *)samples_dev, n, M, d, t0, nt, h->ess_V, 0));
+    else BST_CUDA(launch_ess_variogram_f32((const float *)samples_dev, n, M, d, t0, nt, h->ess_V, 0));
+    BST_CUDA(cudaMemcpy(V.data(), h->ess_V, static_cast<size_t>(d) * 32 * 8, cudaMemcpyDeviceToHost));
+    for (int q = 0; q < d; ++q) {
+      if (!active[q]) continue;
+      for (int k = 0; k + 1 < nt; k += 2) {
+        const int t = t0 + k;
+        if (t + 1 >= n) {
+          active[q] = 0;
+          break;
+        }
+        const double r0 = 1.0 - V[q * nt + k] / (static_cast<double>(M) * (n - t)) / (2.0 * var_plus[q]);
+        const double r1 = 1.0 - V[q * nt + k + 1] / (static_cast<double>(M) * (n - t - 1)) / (2.0 * var_plus[q]);
+        double P = r0 + r1;
+        if (!(P > 0.0)) {
+          active[q] = 0;
+          break;
+        }
+        if (P > prevP[q]) P = prevP[q];
+        sumP[q] += P;
+        prevP[q] = P;
+      }
+      if (nt % 2 && active[q] && t0 + nt >= n) active[q] = 0;
+      if (!active[q]) --n_active;
+    }
+  }
+  for (int q = 0; q < d; ++q) ess_out[q] = static_cast<double>(M) * n / (-1.0 + 2.0 * sumP[q]);
+  return BST_OK;
+}
+
+bst_status bst_sync(bst_handle h, void *stream) {
+  if (!h) return fail(BST_ERR_ARG, "bst_sync: NULL handle");
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  return check_status(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,647 @@
+// k_aux.cu -- weight preparation, covariance adaptation, ESS and training kernels.
+#include <cuda_bf16.h>
+
+#include "launch.h"
+
+namespace bst {
+
+namespace {
+inline int blocks_for(size_t n, int t) { return static_cast<int>((n + t - 1) / t); }
+
+// Offsets of the flat emulator parameter vector:
+// W1[w][d] b1[w] (W_l[w][w] b_l[w])_{l=2..D} wo[w] bo.
+__host__ __device__ inline size_t off_W(int l, int d, int w) {
+  return l == 1 ? 0 : static_cast<size_t>(d) * w + w + static_cast<size_t>(l - 2) * (static_cast<size_t>(w) * w + w);
+}
+__host__ __device__ inline size_t off_b(int l, int d, int w) {
+  return off_W(l, d, w) + static_cast<size_t>(w) * (l == 1 ? d : w);
+}
+__host__ __device__ inline size_t off_wo(int d, int D, int w) { return off_W(D + 1, d, w); }
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// Layer-1 fold.  mode 0 (sampling, z-space): W1f = W1 diag(1/s) L, b1f = b1 + W1 (mu - m)/s.
+//              mode 1 (loglike, x-space):   W1f = W1 diag(1/s),   b1f = b1 - W1 m/s.
+__global__ void fold_layer1_kernel(const double *P, const double *in_m, const double *in_s, const double *mu,
+                                   const double *L, int d, int dp, int w, int mode, double *W1f, double *b1f) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= w) return;
+  const double *W1 = P + static_cast<size_t>(k) * d;
+  double bb = P[off_b(1, d, w) + k];
+  for (int i = 0; i < d; ++i) {
+    const double wi = W1[i] / in_s[i];
+    bb += (mode == 0) ? wi * (mu[i] - in_m[i]) : -wi * in_m[i];
+  }
+  b1f[k] = bb;
+  for (int j = 0; j < dp; ++j) {
+    double s = 0.0;
+    if (j < d) {
+      if (mode == 0)
+        for (int i = j; i < d; ++i) s += W1[i] / in_s[i] * L[i * d + j];
+      else
+        s = W1[j] / in_s[j];
+    }
+    W1f[static_cast<size_t>(k) * dp + j] = s;
+  }
+}
+
+cudaError_t launch_fold_layer1(const double *P, const double *in_m, const double *in_s, const double *mu,
+                               const double *L, int d, int dp, int w, int mode, double *W1f, double *b1f,
+                               cudaStream_t s) {
+  fold_layer1_kernel<<<blocks_for(w, 128), 128, 0, s>>>(P, in_m, in_s, mu, L, d, dp, w, mode, W1f, b1f);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void pack_simt_kernel(const double *P, const double *W1f, const double *b1f, int d, int dp, int D, int w,
+                                 R *W1T, R *W1, R *b1, R *WT, R *W, R *b, R *wo) {
+  const size_t tid = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  const size_t n1 = static_cast<size_t>(w) * dp;
+  const size_t nh = static_cast<size_t>(D - 1) * w * w;
+  if (tid < n1) {
+    const int k = static_cast<int>(tid / dp), j = static_cast<int>(tid % dp);
+    W1[tid] = static_cast<R>(W1f[tid]);
+    W1T[static_cast<size_t>(j) * w + k] = static_cast<R>(W1f[tid]);
+  }
+  if (tid < static_cast<size_t>(w)) {
+    b1[tid] = static_cast<R>(b1f[tid]);
+    wo[tid] = static_cast<R>(P[off_wo(d, D, w) + tid]);
+  }
+  if (tid < nh) {
+    const int l = static_cast<int>(tid / (static_cast<size_t>(w) * w)) + 2;
+    const size_t e = tid % (static_cast<size_t>(w) * w);
+    const int r = static_cast<int>(e / w), c = static_cast<int>(e % w);
+    const double v = P[off_W(l, d, w) + e];
+    W[tid] = static_cast<R>(v);
+    WT[static_cast<size_t>(l - 2) * w * w + static_cast<size_t>(c) * w + r] = static_cast<R>(v);
+  }
+  if (tid < static_cast<size_t>(D - 1) * w) {
+    const int l = static_cast<int>(tid / w) + 2, k = static_cast<int>(tid % w);
+    b[tid] = static_cast<R>(P[off_b(l, d, w) + k]);
+  }
+}
+
+template <typename R>
+static cudaError_t pack_simt(const double *P, const double *W1f, const double *b1f, int d, int dp, int D, int w,
+                             R *W1T, R *W1, R *b1, R *WT, R *W, R *b, R *wo, cudaStream_t s) {
+  size_t n = static_cast<size_t>(w) * dp;
+  n = n > static_cast<size_t>(D - 1) * w * w ? n : static_cast<size_t>(D - 1) * w * w;
+  n = n > static_cast<size_t>(w) ? n : static_cast<size_t>(w);
+  pack_simt_kernel<R><<<blocks_for(n, 256), 256, 0, s>>>(P, W1f, b1f, d, dp, D, w, W1T, W1, b1, WT, W, b, wo);
+  return cudaGetLastError();
+}
+cudaError_t launch_pack_simt_f32(const double *P, const double *W1f, const double *b1f, int d, int dp, int D, int w,
+                                 float *W1T, float *W1, float *b1, float *WT, float *W, float *b, float *wo,
+                                 cudaStream_t s) {
+  return pack_simt<float>(P, W1f, b1f, d, dp, D, w, W1T, W1, b1, WT, W, b, wo, s);
+}
+cudaError_t launch_pack_simt_f64(const double *P, const double *W1f, const double *b1f, int d, int dp, int D, int w,
+                                 double *W1T, double *W1, double *b1, double *WT, double *W, double *b, double *wo,
+                                 cudaStream_t s) {
+  return pack_simt<double>(P, W1f, b1f, d, dp, D, w, W1T, W1, b1, WT, W, b, wo, s);
+}
+
+// ------------------------------------------------------------------------------------------
+// BF16 tile packing.  A tile is rows x 64 BF16 (128 bytes per row) in the 128-byte-swizzled
+// K-major layout the tcgen05 shared-memory descriptors expect: the 16-byte chunk j of row r sits
+// at r * 128 + ((j ^ (r % 8)) * 16).  Each thread writes one 16-byte chunk.
+__device__ __forceinline__ void put_chunk(uint8_t *tile, int r, int j, const float v[8]) {
+  __nv_bfloat16 h[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(v[e]);
+  *reinterpret_cast<uint4 *>(tile + r * 128 + ((j ^ (r & 7)) << 4)) = *reinterpret_cast<uint4 *>(h);
+}
+__device__ __forceinline__ float bf16_hi(double v) {
+  return __bfloat162float(__double2bfloat16(v));
+}
+
+// Layer-1 split tiles: B1s[k][kk], kk in [0, 64 kb1): [Wh(dp) | Wh(dp) | Wl(dp) | 0], ordered
+// (n-half, k-block).
+__global__ void pack_tc_l1_kernel(const double *W1f, int dp, int w, int kb1, uint8_t *out) {
+  const int nh_count = w / 256;
+  const size_t chunks = static_cast<size_t>(nh_count) * kb1 * 256 * 8;
+  const size_t id = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (id >= chunks) return;
+  const int j = static_cast<int>(id % 8), r = static_cast<int>((id / 8) % 256);
+  const int tile = static_cast<int>(id / (8 * 256));
+  const int nh = tile / kb1, kb = tile % kb1;
+  const int k = nh * 256 + r;
+  float v[8];
+  for (int e = 0; e < 8; ++e) {
+    const int kk = kb * 64 + j * 8 + e;
+    const int seg = kk / dp, i = kk % dp;
+    float x = 0.f;
+    if (seg < 3) {
+      const double wv = W1f[static_cast<size_t>(k) * dp + i];
+      const float hi = bf16_hi(wv);
+      x = (seg == 2) ? static_cast<float>(wv - static_cast<double>(hi)) : hi;
+    }
+    v[e] = x;
+  }
+  put_chunk(out + static_cast<size_t>(tile) * kTcStageBytes, r, j, v);
+}
+cudaError_t launch_pack_tc_l1(const double *W1f, int dp, int w, int kb1, uint8_t *out, cudaStream_t s) {
+  const size_t chunks = static_cast<size_t>(w / 256) * kb1 * 256 * 8;
+  pack_tc_l1_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(W1f, dp, w, kb1, out);
+  return cudaGetLastError();
+}
+
+// Hidden tiles: forward layers 2..D (tile rows = output units, cols = inputs), then adjoint
+// layers D..2 with W_l^T (rows = inputs, cols = output units); each (n-half, k-block).
+__global__ void pack_tc_hidden_kernel(const double *P, int d, int D, int w, uint8_t *out) {
+  const int nh_count = w / 256, kbw = w / 64;
+  const size_t per_layer = static_cast<size_t>(nh_count) * kbw;
+  const size_t chunks = 2 * static_cast<size_t>(D - 1) * per_layer * 256 * 8;
+  const size_t id = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (id >= chunks) return;
+  const int j = static_cast<int>(id % 8), r = static_cast<int>((id / 8) % 256);
+  const size_t tile = id / (8 * 256);
+  const size_t seg = tile / per_layer;  // 0..2(D-1)-1
+  const int within = static_cast<int>(tile % per_layer);
+  const int nh = within / kbw, kb = within % kbw;
+  const bool adj = seg >= static_cast<size_t>(D - 1);
+  const int l = adj ? D - static_cast<int>(seg - (D - 1)) : static_cast<int>(seg) + 2;
+  const double *Wl = P + off_W(l, d, w);
+  const int row = nh * 256 + r;
+  __nv_bfloat16 hb[8];
+  for (int e = 0; e < 8; ++e) {
+    const int col = kb * 64 + j * 8 + e;
+    const double x = adj ? Wl[static_cast<size_t>(col) * w + row] : Wl[static_cast<size_t>(row) * w + col];
+    hb[e] = __double2bfloat16(x);
+  }
+  *reinterpret_cast<uint4 *>(out + tile * kTcStageBytes + r * 128 + ((j ^ (r & 7)) << 4)) =
+      *reinterpret_cast<uint4 *>(hb);
+}
+cudaError_t launch_pack_tc_hidden(const double *P, int d, int D, int w, uint8_t *out, cudaStream_t s) {
+  if (D < 2) return cudaSuccess;
+  const size_t chunks = 2 * static_cast<size_t>(D - 1) * (w / 256) * (w / 64) * 256 * 8;
+  pack_tc_hidden_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(P, d, D, w, out);
+  return cudaGetLastError();
+}
+
+// Input-gradient split tiles: rows [W1f^T hi (dp rows); W1f^T lo (dp rows)], cols = hidden
+// units, one tile of 2 dp rows per 64-column k-block.
+__global__ void pack_tc_g1_kernel(const double *W1f, int dp, int w, uint8_t *out) {
+  const int rows = 2 * dp, kbw = w / 64;
+  const size_t chunks = static_cast<size_t>(kbw) * rows * 8;
+  const size_t id = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (id >= chunks) return;
+  const int j = static_cast<int>(id % 8), r = static_cast<int>((id / 8) % rows);
+  const int kb = static_cast<int>(id / (8 * rows));
+  const int i = r % dp;
+  float v[8];
+  for (int e = 0; e < 8; ++e) {
+    const int k = kb * 64 + j * 8 + e;
+    const double wv = W1f[static_cast<size_t>(k) * dp + i];
+    const float hi = bf16_hi(wv);
+    v[e] = (r < dp) ? hi : static_cast<float>(wv - static_cast<double>(hi));
+  }
+  put_chunk(out + static_cast<size_t>(kb) * rows * 128, r, j, v);
+}
+cudaError_t launch_pack_tc_g1(const double *W1f, int dp, int w, uint8_t *out, cudaStream_t s) {
+  const size_t chunks = static_cast<size_t>(w / 64) * 2 * dp * 8;
+  pack_tc_g1_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(W1f, dp, w, out);
+  return cudaGetLastError();
+}
+
+template <typename S, typename D_>
+__global__ void cast_kernel(const S *src, D_ *dst, size_t n) {
+  const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (i < n) dst[i] = static_cast<D_>(src[i]);
+}
+cudaError_t launch_cast_f32(const double *src, float *dst, size_t n, cudaStream_t s) {
+  if (n) cast_kernel<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_cast_f64(const double *src, double *dst, size_t n, cudaStream_t s) {
+  if (n) cast_kernel<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_cast_f32_to_f64(const float *src, double *dst, size_t n, cudaStream_t s) {
+  if (n) cast_kernel<<<blocks_for(n, 256), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Analytic fold (FP64): z-space t = tanh(B (mu_c + L_c z) + c), f = A t + N (mu_n + L_n z).
+__global__ void fold_analytic_kernel(const double *A, const double *B, const double *c, const double *N,
+                                     const double *data, const double *mu, const double *L, int d, int dp, int d_c,
+                                     int H, int n_data, int mode, double *Bf, double *cf, double *AT, double *NfT,
+                                     double *dataf) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int dn = d - d_c;
+  if (tid < H) {
+    const int k = tid;
+    double cc = c[k];
+    for (int j = 0; j < dp; ++j) {
+      double s = 0.0;
+      if (j < d) {
+        if (mode == 0) {
+          for (int i = j; i < d_c; ++i) s += B[k * d_c + i] * L[i * d + j];
+        } else if (j < d_c) {
+          s = B[k * d_c + j];
+        }
+      }
+      Bf[k * dp + j] = s;
+    }
+    if (mode == 0)
+      for (int i = 0; i < d_c; ++i) cc += B[k * d_c + i] * mu[i];
+    cf[k] = cc;
+  }
+  if (tid < n_data) {
+    const int i = tid;
+    for (int k = 0; k < H; ++k) AT[static_cast<size_t>(k) * n_data + i] = A[static_cast<size_t>(i) * H + k];
+    double dd = data[i];
+    if (dn > 0) {
+      for (int j = 0; j < dp; ++j) {
+        double s = 0.0;
+        if (j < d) {
+          if (mode == 0) {
+            for (int q = (j > d_c ? j : d_c); q < d; ++q) s += N[static_cast<size_t>(i) * dn + (q - d_c)] * L[q * d + j];
+          } else if (j >= d_c) {
+            s = N[static_cast<size_t>(i) * dn + (j - d_c)];
+          }
+        }
+        NfT[static_cast<size_t>(j) * n_data + i] = s;
+      }
+      if (mode == 0)
+        for (int q = d_c; q < d; ++q) dd -= N[static_cast<size_t>(i) * dn + (q - d_c)] * mu[q];
+    }
+    dataf[i] = dd;
+  }
+}
+cudaError_t launch_fold_analytic(const double *A, const double *B, const double *c, const double *N,
+                                 const double *data, const double *mu, const double *L, int d, int dp, int d_c, int H,
+                                 int n_data, int mode, double *Bf, double *cf, double *AT, double *NfT, double *dataf,
+                                 cudaStream_t s) {
+  const int n = H > n_data ? H : n_data;
+  fold_analytic_kernel<<<blocks_for(n, 128), 128, 0, s>>>(A, B, c, N, data, mu, L, d, dp, d_c, H, n_data, mode, Bf,
+                                                          cf, AT, NfT, dataf);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Covariance adaptation.  One thread merges the FP64 tile records (Chan et al.), forms the
+// unbiased covariance and factorises it; jitter delta (tr S / d) I, delta = jitter0 x 10^k, is
+// added only if the plain factorisation fails.
+__global__ void adapt_finalize_kernel(const double *wf, int n_tiles, int stride, int d, double jitter0, double *mu,
+                                      double *Lout, double *info) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double n = 0.0, mean[kMaxD], M2[kMaxD * kMaxD], S[kMaxD * kMaxD];
+  for (int i = 0; i < d; ++i) mean[i] = 0.0;
+  for (int i = 0; i < d * d; ++i) M2[i] = 0.0;
+  for (int t = 0; t < n_tiles; ++t) {
+    const double *W = wf + static_cast<size_t>(t) * stride;
+    const double nb = W[kWfN];
+    if (nb <= 0.0) continue;
+    const double nn = n + nb;
+    for (int i = 0; i < d; ++i)
+      for (int j = i; j < d; ++j) {
+        const double di = W[kWfMean + i] - mean[i], dj = W[kWfMean + j] - mean[j];
+        M2[i * d + j] += W[kWfM2 + i * kMaxD + j] + di * dj * n * nb / nn;
+      }
+    for (int i = 0; i < d; ++i) mean[i] += (W[kWfMean + i] - mean[i]) * nb / nn;
+    n = nn;
+  }
+  info[0] = n;
+  info[1] = -1.0;
+  info[2] = 0.0;
+  for (int i = 0; i < d; ++i) mu[i] = mean[i];
+  if (n < 2.0) {
+    info[2] = 1.0;
+    return;
+  }
+  double tr = 0.0;
+  for (int i = 0; i < d; ++i)
+    for (int j = i; j < d; ++j) {
+      S[i * d + j] = S[j * d + i] = M2[i * d + j] / (n - 1.0);
+      if (i == j) tr += S[i * d + i];
+    }
+  double delta = 0.0;
+  for (int attempt = 0; attempt < 12; ++attempt) {
+    // attempt 0: plain; then delta = jitter0, 10 jitter0, ... while <= 1e-2
+    if (attempt > 0) {
+      delta = (attempt == 1) ? jitter0 : delta * 10.0;
+      if (delta > 1e-2 * (1.0 + 1e-9)) break;
+    }
+    bool ok = true;
+    for (int i = 0; i < d * d; ++i) Lout[i] = 0.0;
+    for (int j = 0; j < d && ok; ++j) {
+      double s = S[j * d + j] + delta * tr / d;
+      for (int k = 0; k < j; ++k) s -= Lout[j * d + k] * Lout[j * d + k];
+      if (!(s > 0.0)) {
+        ok = false;
+        break;
+      }
+      const double ljj = sqrt(s);
+      Lout[j * d + j] = ljj;
+      for (int i = j + 1; i < d; ++i) {
+        double t = S[i * d + j];
+        for (int k = 0; k < j; ++k) t -= Lout[i * d + k] * Lout[j * d + k];
+        Lout[i * d + j] = t / ljj;
+      }
+    }
+    if (ok) {
+      info[1] = delta;
+      return;
+    }
+  }
+  info[2] = 2.0;
+}
+cudaError_t launch_adapt_finalize(const double *wf, int n_tiles, int stride, int d, double jitter0, double *mu,
+                                  double *L, double *info, cudaStream_t s) {
+  adapt_finalize_kernel<<<1, 32, 0, s>>>(wf, n_tiles, stride, d, jitter0, mu, L, info);
+  return cudaGetLastError();
+}
+
+__global__ void welford_clear_kernel(double *wf, size_t n) {
+  const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (i < n) wf[i] = 0.0;
+}
+cudaError_t launch_welford_clear(double *wf, int n_tiles, int stride, cudaStream_t s) {
+  const size_t n = static_cast<size_t>(n_tiles) * stride;
+  welford_clear_kernel<<<blocks_for(n, 256), 256, 0, s>>>(wf, n);
+  return cudaGetLastError();
+}
+
+// External samples into tile record 0: batch of m rows, FP64 two-pass batch statistics
+// merged into the record.
+template <typename R>
+__global__ void welford_add_kernel(const R *x, int m, int d, double *W) {
+  __shared__ double bmean[kMaxD];
+  const int t = threadIdx.x;
+  for (int i = t; i < d; i += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < m; ++r) s += static_cast<double>(x[static_cast<size_t>(r) * d + i]);
+    bmean[i] = s / m;
+  }
+  __syncthreads();
+  const double na = W[kWfN], nb = m, n = na + nb;
+  for (int p = t; p < d * d; p += blockDim.x) {
+    const int i = p / d, j = p % d;
+    if (j < i) continue;
+    double s = 0.0;
+    for (int r = 0; r < m; ++r)
+      s += (static_cast<double>(x[static_cast<size_t>(r) * d + i]) - bmean[i]) *
+           (static_cast<double>(x[static_cast<size_t>(r) * d + j]) - bmean[j]);
+    const double di = bmean[i] - W[kWfMean + i], dj = bmean[j] - W[kWfMean + j];
+    W[kWfM2 + i * kMaxD + j] += s + di * dj * na * nb / n;
+  }
+  __syncthreads();
+  for (int i = t; i < d; i += blockDim.x) W[kWfMean + i] += (bmean[i] - W[kWfMean + i]) * nb / n;
+  if (t == 0) W[kWfN] = n;
+}
+cudaError_t launch_welford_add_f32(const float *x, int m, int d, double *wf, int, cudaStream_t s) {
+  welford_add_kernel<float><<<1, 256, 0, s>>>(x, m, d, wf);
+  return cudaGetLastError();
+}
+cudaError_t launch_welford_add_f64(const double *x, int m, int d, double *wf, int, cudaStream_t s) {
+  welford_add_kernel<double><<<1, 256, 0, s>>>(x, m, d, wf);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void remap_kernel(R *z, int n, int d, int dp, const double *mu_o, const double *L_o, const double *mu_n,
+                             const double *L_n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  R *zc = z + static_cast<size_t>(c) * dp;
+  double x[kMaxD], zn[kMaxD];
+  for (int i = 0; i < d; ++i) {
+    double s = mu_o[i];
+    for (int j = 0; j <= i; ++j) s += L_o[i * d + j] * static_cast<double>(zc[j]);
+    x[i] = s - mu_n[i];
+  }
+  for (int i = 0; i < d; ++i) {
+    double s = x[i];
+    for (int j = 0; j < i; ++j) s -= L_n[i * d + j] * zn[j];
+    zn[i] = s / L_n[i * d + i];
+  }
+  for (int i = 0; i < d; ++i) zc[i] = static_cast<R>(zn[i]);
+}
+cudaError_t launch_remap_f32(float *z, int n, int d, int dp, const double *mu_o, const double *L_o, const double *mu_n,
+                             const double *L_n, cudaStream_t s) {
+  remap_kernel<float><<<blocks_for(n, 128), 128, 0, s>>>(z, n, d, dp, mu_o, L_o, mu_n, L_n);
+  return cudaGetLastError();
+}
+cudaError_t launch_remap_f64(double *z, int n, int d, int dp, const double *mu_o, const double *L_o,
+                             const double *mu_n, const double *L_n, cudaStream_t s) {
+  remap_kernel<double><<<blocks_for(n, 128), 128, 0, s>>>(z, n, d, dp, mu_o, L_o, mu_n, L_n);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// ESS: samples x[n][M][d].  (1) per series (chain c, dim q): mean and variance (n - 1 denominator).
+template <typename R>
+__global__ void ess_moments_kernel(const R *x, int n, int M, int d, double *mean, double *var) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;  // series index c * d + q
+  if (s >= M * d) return;
+  const size_t st = static_cast<size_t>(M) * d;
+  double sum = 0.0;
+  for (int t = 0; t < n; ++t) sum += static_cast<double>(x[t * st + s]);
+  const double m = sum / n;
+  double ss = 0.0;
+  for (int t = 0; t < n; ++t) {
+    const double e = static_cast<double>(x[t * st + s]) - m;
+    ss += e * e;
+  }
+  mean[s] = m;
+  var[s] = ss / (n - 1);
+}
+cudaError_t launch_ess_moments_f32(const float *x, int n, int M, int d, double *mean, double *var, cudaStream_t s) {
+  ess_moments_kernel<float><<<blocks_for(static_cast<size_t>(M) * d, 128), 128, 0, s>>>(x, n, M, d, mean, var);
+  return cudaGetLastError();
+}
+cudaError_t launch_ess_moments_f64(const double *x, int n, int M, int d, double *mean, double *var, cudaStream_t s) {
+  ess_moments_kernel<double><<<blocks_for(static_cast<size_t>(M) * d, 128), 128, 0, s>>>(x, n, M, d, mean, var);
+  return cudaGetLastError();
+}
+
+// (2) variogram sums V[q][t - t0] += sum_c sum_{i >= t} (x_i - x_{i-t})^2 for lags t0..t0+nt-1.
+// Block = 32 series (threadIdx.x, coalesced) x 32 lags (threadIdx.y, sharing the series' draws
+// through L1).
+constexpr int kVgLags = 32;
+template <typename R>
+__global__ void ess_variogram_kernel(const R *x, int n, int M, int d, int t0, int nt, double *V) {
+  const int s = blockIdx.x * 32 + threadIdx.x;
+  const int lag = threadIdx.y, t = t0 + lag;
+  if (lag >= nt || s >= M * d) return;
+  const size_t st = static_cast<size_t>(M) * d;
+  double acc = 0.0;
+  for (int i = t; i < n; ++i) {
+    const double e = static_cast<double>(x[i * st + s]) - static_cast<double>(x[(i - t) * st + s]);
+    acc += e * e;
+  }
+  atomicAdd(&V[(s % d) * nt + lag], acc);
+}
+cudaError_t launch_ess_variogram_f32(const float *x, int n, int M, int d, int t0, int nt, double *V, cudaStream_t s) {
+  dim3 blk(32, kVgLags);
+  ess_variogram_kernel<float><<<blocks_for(static_cast<size_t>(M) * d, 32), blk, 0, s>>>(x, n, M, d, t0, nt, V);
+  return cudaGetLastError();
+}
+cudaError_t launch_ess_variogram_f64(const double *x, int n, int M, int d, int t0, int nt, double *V, cudaStream_t s) {
+  dim3 blk(32, kVgLags);
+  ess_variogram_kernel<double><<<blocks_for(static_cast<size_t>(M) * d, 32), blk, 0, s>>>(x, n, M, d, t0, nt, V);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Training (FP32).  Generic tiled GEMM C[M][N] = sum_k A(i,k) B(k,j) with strided operands
+// and a fused epilogue:
+//   EPI_STORE : C = acc
+//   EPI_TANH  : C = tanh(acc + bias[j])
+//   EPI_DTANH : C = acc * (1 - H[i][j]^2)
+enum { EPI_STORE = 0, EPI_TANH = 1, EPI_DTANH = 2 };
+constexpr int kGT = 64, kGK = 16;
+__global__ void __launch_bounds__(256) gemm_f32_kernel(int M, int N, int K, const float *A, long long a_i,
+                                                       long long a_k, const float *B, long long b_k, long long b_j,
+                                                       float *C, int ldc, int epi, const float *bias, const float *H,
+                                                       int ldh) {
+  __shared__ float As[kGK][kGT + 4];
+  __shared__ float Bs[kGK][kGT + 4];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
+  float acc[4][4] = {};
+  (void)acc;
+  for (int k0 = 0; k0 < K; k0 += kGK) {
+    for (int e = threadIdx.x; e < kGK * kGT; e += 256) {
+      const int kk = e / kGT, ii = e % kGT;
+      const int i = i0 + ii, k = k0 + kk;
+      As[kk][ii] = (i < M && k < K) ? A[i * a_i + k * a_k] : 0.f;
+      const int j = j0 + ii;
+      Bs[kk][ii] = (j < N && k < K) ? B[k * b_k + j * b_j] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[kk][ty * 4 + u];
+        b[u] = Bs[kk][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
+      if (i >= M || j >= N) continue;
+      float r = acc[u][v];
+      if (epi == EPI_TANH) r = tanhf(r + bias[j]);
+      else if (epi == EPI_DTANH) {
+        const float h = H[static_cast<size_t>(i) * ldh + j];
+        r = r * (1.f - h * h);
+      }
+      C[static_cast<size_t>(i) * ldc + j] = r;
+    }
+}
+static void gemm_f32(int M, int N, int K, const float *A, long long a_i, long long a_k, const float *B, long long b_k,
+                     long long b_j, float *C, int ldc, int epi, const float *bias, const float *H, int ldh,
+                     cudaStream_t s) {
+  dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT);
+  gemm_f32_kernel<<<grid, 256, 0, s>>>(M, N, K, A, a_i, a_k, B, b_k, b_j, C, ldc, epi, bias, H, ldh);
+}
+
+__global__ void standardise_kernel(const float *X, const float *m, const float *sd, int rows, int d, float *U) {
+  const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (i >= static_cast<size_t>(rows) * d) return;
+  const int j = static_cast<int>(i % d);
+  U[i] = (X[i] - m[j]) / sd[j];
+}
+
+// out = wo . h_D + bo;  r = out - (chi2 - out_m)/out_s;  loss += r^2 / m;  dout = 2 r / m;
+// delta_D = dout wo (1 - h_D^2).  One warp per row.
+__global__ void train_head_kernel(const float *HD, const float *wo, const float *bo_ptr, const float *chi2, float out_m,
+                                  float out_s, int m, int w, float *dout, float *delta, float *loss) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= m) return;
+  const float *h = HD + static_cast<size_t>(warp) * w;
+  float s = 0.f;
+  for (int k = lane; k < w; k += 32) s += wo[k] * h[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const float y = (chi2[warp] - out_m) / out_s;
+  const float r = s + *bo_ptr - y;
+  const float g = 2.f * r / m;
+  if (lane == 0) {
+    dout[warp] = g;
+    atomicAdd(loss, r * r / m);
+  }
+  for (int k = lane; k < w; k += 32) delta[static_cast<size_t>(warp) * w + k] = g * wo[k] * (1.f - h[k] * h[k]);
+}
+
+// column sums: out[j] = sum_i X[i][j] (bias gradients); out_scalar = sum_i v[i]
+__global__ void colsum_kernel(const float *X, int rows, int cols, float *out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= cols) return;
+  float s = 0.f;
+  for (int i = 0; i < rows; ++i) s += X[static_cast<size_t>(i) * cols + j];
+  out[j] = s;
+}
+
+cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in_s, float out_m, float out_s, int d,
+                              int D, int w, int m, const float *X, const float *chi2, float *G, TrainWork &tw,
+                              cudaStream_t s) {
+  cudaMemsetAsync(tw.loss, 0, sizeof(float), s);
+  standardise_kernel<<<blocks_for(static_cast<size_t>(m) * d, 256), 256, 0, s>>>(X, in_m, in_s, m, d, tw.U);
+  // forward: H_l = tanh(H_{l-1} W_l^T + b_l)
+  for (int l = 1; l <= D; ++l) {
+    const int fan = (l == 1) ? d : w;
+    const float *Ain = (l == 1) ? tw.U : tw.H + static_cast<size_t>(l - 2) * m * w;
+    const float *Wl = P + off_W(l, d, w);
+    float *Hl = tw.H + static_cast<size_t>(l - 1) * m * w;
+    gemm_f32(m, w, fan, Ain, fan, 1, Wl, 1, fan, Hl, w, EPI_TANH, P + off_b(l, d, w), nullptr, 0, s);
+  }
+  const float *HD = tw.H + static_cast<size_t>(D - 1) * m * w;
+  const size_t owo = off_wo(d, D, w);
+  train_head_kernel<<<blocks_for(static_cast<size_t>(m) * 32, 256), 256, 0, s>>>(HD, P + owo, P + owo + w, chi2, out_m,
+                                                                               out_s, m, w, tw.dout, tw.Dl, tw.loss);
+  // g_wo[j] = sum_i dout_i H_D[i][j]  (1 x w = dout^T H_D) ; g_bo = sum_i dout_i
+  gemm_f32(1, w, m, tw.dout, 0, 1, HD, w, 1, G + owo, w, EPI_STORE, nullptr, nullptr, 0, s);
+  colsum_kernel<<<1, 32, 0, s>>>(tw.dout, m, 1, G + owo + w);
+  float *dl = tw.Dl, *dn = tw.Dn;
+  for (int l = D; l >= 1; --l) {
+    const int fan = (l == 1) ? d : w;
+    const float *Hprev = (l == 1) ? tw.U : tw.H + static_cast<size_t>(l - 2) * m * w;
+    // g_W_l[k][j] = sum_i delta_l[i][k] Hprev[i][j]
+    gemm_f32(w, fan, m, dl, 1, w, Hprev, fan, 1, G + off_W(l, d, w), fan, EPI_STORE, nullptr, nullptr, 0, s);
+    colsum_kernel<<<blocks_for(w, 128), 128, 0, s>>>(dl, m, w, G + off_b(l, d, w));
+    if (l > 1) {
+      // delta_{l-1} = (delta_l W_l) (1 - H_{l-1}^2)
+      gemm_f32(m, w, w, dl, w, 1, P + off_W(l, d, w), w, 1, dn, w, EPI_DTANH, nullptr, Hprev, w, s);
+      float *t = dl;
+      dl = dn;
+      dn = t;
+    }
+  }
+  return cudaGetLastError();
+}
+
+__global__ void adam_kernel(float *P, const float *G, float *m1, float *m2, size_t n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const float g = G[i];
+  const float a = b1 * m1[i] + (1.f - b1) * g;
+  const float v = b2 * m2[i] + (1.f - b2) * g * g;
+  m1[i] = a;
+  m2[i] = v;
+  P[i] -= lr * (a / c1) / (sqrtf(v / c2) + eps);
+}
+cudaError_t launch_adam(float *P, const float *G, float *m1, float *m2, size_t n, int t, float lr, float b1, float b2,
+                        float eps, cudaStream_t s) {
+  const float c1 = 1.f - powf(b1, static_cast<float>(t)), c2 = 1.f - powf(b2, static_cast<float>(t));
+  adam_kernel<<<blocks_for(n, 256), 256, 0, s>>>(P, G, m1, m2, n, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(void *p, size_t bytes, cudaStream_t s) { return cudaMemsetAsync(p, 0, bytes, s); }
+
+}  // namespace bst

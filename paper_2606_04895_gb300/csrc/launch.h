@@ -1,0 +1,85 @@
+// launch.h -- host-side launch wrappers between the C-ABI runtime (api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "engine_simt.cuh"
+#include "engine_tc.cuh"
+
+namespace bst {
+
+// Chain-tile step / evaluation launches (k_step.cu).
+cudaError_t launch_emu_simt_f32(const StepArgs<float> &a, const EmuWeights<float> &w, cudaStream_t s);
+cudaError_t launch_emu_simt_f64(const StepArgs<double> &a, const EmuWeights<double> &w, cudaStream_t s);
+cudaError_t launch_ana_simt_f32(const StepArgs<float> &a, const AnaWeights<float> &w, cudaStream_t s);
+cudaError_t launch_ana_simt_f64(const StepArgs<double> &a, const AnaWeights<double> &w, cudaStream_t s);
+cudaError_t launch_emu_tc(const StepArgs<float> &a, const TcWeights &w, cudaStream_t s);
+int simt_rows_per_tile(int precision, int width, int lik_kind);
+size_t tc_smem_for(int width);
+int tc_stages(int width);
+
+// Weight preparation (k_aux.cu).
+// Fold whitening / standardisation into layer 1 (FP64 out): z-space (mode 0) or x-space (mode 1).
+cudaError_t launch_fold_layer1(const double *P, const double *in_m, const double *in_s, const double *mu,
+                               const double *L, int d, int dp, int w, int mode, double *W1f, double *b1f,
+                               cudaStream_t s);
+// Emulator SIMT weights in working precision from the FP64 master + fold.
+cudaError_t launch_pack_simt_f32(const double *P, const double *W1f, const double *b1f, int d, int dp, int D,
+                                 int w, float *W1T, float *W1, float *b1, float *WT, float *W, float *b, float *wo,
+                                 cudaStream_t s);
+cudaError_t launch_pack_simt_f64(const double *P, const double *W1f, const double *b1f, int d, int dp, int D,
+                                 int w, double *W1T, double *W1, double *b1, double *WT, double *W, double *b,
+                                 double *wo, cudaStream_t s);
+// BF16 tensor-core tiles (pre-swizzled): layer-1 split tiles, hidden fwd + adjoint tiles,
+// input-gradient split tiles; FP32 biases.
+cudaError_t launch_pack_tc_l1(const double *W1f, int dp, int w, int kb1, uint8_t *out, cudaStream_t s);
+cudaError_t launch_pack_tc_hidden(const double *P, int d, int D, int w, uint8_t *out, cudaStream_t s);
+cudaError_t launch_pack_tc_g1(const double *W1f, int dp, int w, uint8_t *out, cudaStream_t s);
+cudaError_t launch_cast_f32(const double *src, float *dst, size_t n, cudaStream_t s);
+cudaError_t launch_cast_f64(const double *src, double *dst, size_t n, cudaStream_t s);
+cudaError_t launch_cast_f32_to_f64(const float *src, double *dst, size_t n, cudaStream_t s);
+// Analytic fold: Bf = B L_c, cf = B mu_c + c, Nf = N L_n, dataf = data - N mu_n (mode 0) or
+// the x-space embedding (mode 1); outputs in working precision via a FP64 staging buffer.
+cudaError_t launch_fold_analytic(const double *A, const double *B, const double *c, const double *N,
+                                 const double *data, const double *mu, const double *L, int d, int dp, int d_c,
+                                 int H, int n_data, int mode, double *Bf, double *cf, double *AT, double *NfT,
+                                 double *dataf, cudaStream_t s);
+
+// Covariance adaptation (k_aux.cu): merge n_tiles FP64 Welford tile records, factorise.
+// out: mu[d], L[d*d], info[0] = n, info[1] = jitter used (or -1 if not PD), info[2] = status.
+cudaError_t launch_adapt_finalize(const double *wf, int n_tiles, int stride, int d, double jitter0, double *mu,
+                                  double *L, double *info, cudaStream_t s);
+cudaError_t launch_welford_clear(double *wf, int n_tiles, int stride, cudaStream_t s);
+cudaError_t launch_welford_add_f32(const float *x, int m, int d, double *wf, int stride, cudaStream_t s);
+cudaError_t launch_welford_add_f64(const double *x, int m, int d, double *wf, int stride, cudaStream_t s);
+// z_new = L_new^-1 (mu_old + L_old z_old - mu_new), FP64 arithmetic.
+cudaError_t launch_remap_f32(float *z, int n, int d, int dp, const double *mu_o, const double *L_o,
+                             const double *mu_n, const double *L_n, cudaStream_t s);
+cudaError_t launch_remap_f64(double *z, int n, int d, int dp, const double *mu_o, const double *L_o,
+                             const double *mu_n, const double *L_n, cudaStream_t s);
+
+// ESS (k_aux.cu): per-(chain, dim) means and variances, then variograms per lag block.
+cudaError_t launch_ess_moments_f32(const float *x, int n, int M, int d, double *mean, double *var, cudaStream_t s);
+cudaError_t launch_ess_moments_f64(const double *x, int n, int M, int d, double *mean, double *var, cudaStream_t s);
+cudaError_t launch_ess_variogram_f32(const float *x, int n, int M, int d, int t0, int nt, double *V, cudaStream_t s);
+cudaError_t launch_ess_variogram_f64(const double *x, int n, int M, int d, int t0, int nt, double *V, cudaStream_t s);
+
+// Training (k_aux.cu), FP32.
+struct TrainWork {
+  float *U;     // [m][d] standardised inputs
+  float *H;     // [D][m][w] activations
+  float *Dl;    // [m][w] adjoint buffer
+  float *Dn;    // [m][w] adjoint buffer
+  float *dout;  // [m]
+  float *loss;  // [1]
+};
+cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in_s, float out_m, float out_s, int d,
+                              int D, int w, int m, const float *X, const float *chi2, float *G, TrainWork &tw,
+                              cudaStream_t s);
+cudaError_t launch_adam(float *P, const float *G, float *m1, float *m2, size_t n, int t, float lr, float b1,
+                        float b2, float eps, cudaStream_t s);
+cudaError_t launch_zero(void *p, size_t bytes, cudaStream_t s);
+
+}  // namespace bst

@@ -1,0 +1,489 @@
+// sampler.cuh -- per-chain proposal / accept state machines.
+//
+// A chain-tile kernel alternates
+//     pre(row)   -> write the point to evaluate into ze[row]      (proposal)
+//     engine     -> lle[row] = logL(ze[row]), gle[row] = grad     (emulator / analytic)
+//     post(row)  -> Metropolis / Hamiltonian / tree bookkeeping    (accept)
+// so one likelihood evaluation of a whole tile of chains is in flight at a
+// time.  Everything here is per chain, O(d) or O(d^2), and runs on the threads
+// that own the chains; the log-acceptance ratios and Hamiltonian energies are
+// formed in FP64 from the working-precision state.
+//
+// Target in whitened coordinates (paper Sec. 2.2, Eq. (2.12), Algorithm 1):
+//     x = mu + L z,   log pi_z(z) = logL(x) + log prior(x) + sum_i log L_ii.
+#pragma once
+
+#include "common.cuh"
+
+namespace bst {
+
+template <typename R>
+struct Chain {
+  const StepArgs<R> &a;
+  __device__ Chain(const StepArgs<R> &args) : a(args) {}
+
+  __device__ R *z(int c) const { return a.st.z + static_cast<size_t>(c) * a.dp; }
+  __device__ R *g(int c) const { return a.st.g + static_cast<size_t>(c) * a.dp; }
+  __device__ R *ze(int r) const { return a.st.ze + static_cast<size_t>(r) * a.dp; }
+  __device__ R *gle(int r) const { return a.st.gle + static_cast<size_t>(r) * a.dp; }
+  __device__ R *wv(int c, int k) const {
+    return a.st.work + static_cast<size_t>(c) * a.st.work_stride + static_cast<size_t>(k) * a.dp;
+  }
+
+  static __device__ double accept_prob(double la) {
+    if (!(la == la)) return 0.0;
+    return la >= 0.0 ? 1.0 : exp(la);
+  }
+
+  // x-space sample record and Welford hand-off after a chain finishes an iteration.
+  __device__ void record(int c, int row, int step) const {
+    const int d = a.d;
+    R x[kMaxD];
+    a.tgt.to_x_prior(z(c), x);
+    if (a.samples && ((step + 1) % a.thin) == 0) {
+      R *dst = a.samples + (static_cast<size_t>(step / a.thin) * a.n_chains + c) * d;
+      for (int i = 0; i < d; ++i) dst[i] = x[i];
+    }
+    if (a.welford_on) {
+      R *xb = a.xbuf + static_cast<size_t>(row) * a.dp;
+      for (int i = 0; i < d; ++i) xb[i] = x[i];
+    }
+  }
+
+  // log pi_z and grad log pi_z at the evaluated point of row r (x written to xo).
+  __device__ double logpi_eval(int r, R *gout, R *xo) const {
+    const double lpr = a.tgt.to_x_prior(ze(r), xo);
+    const double lp = static_cast<double>(a.st.lle[r]) + lpr + a.tgt.logdet;
+    if (gout) {
+      const R *ge = gle(r);
+      for (int i = 0; i < a.d; ++i) gout[i] = ge[i];
+      a.tgt.add_prior_grad(xo, gout);
+    }
+    return lp;
+  }
+
+  __device__ void count(int c, bool accepted, double la, int evals) const {
+    a.st.acc_stat[c] += accept_prob(la);
+    a.st.accepts[c] += accepted ? 1ull : 0ull;
+    a.st.evals[c] += static_cast<unsigned long long>(evals);
+  }
+
+  // ---------------------------------------------------------------- MH
+  // Random walk in whitened units: z' = z + eps xi.
+  __device__ bool mh_pre(int c) const {
+    if (a.st.steps_done[c] >= a.n_steps) return false;
+    R xi[kMaxD];
+    draw_normals<R>(a.seed, c, a.st.iter[c], kXi, a.d, xi);
+    const R e = static_cast<R>(a.eps);
+    R *zc = z(c), *zp = ze(c);
+    for (int i = 0; i < a.d; ++i) zp[i] = zc[i] + e * xi[i];
+    return true;
+  }
+  __device__ bool mh_post(int c) const {
+    R x[kMaxD];
+    const double lpp = logpi_eval(c, nullptr, x);
+    const uint32_t it = a.st.iter[c];
+    const double la = lpp - static_cast<double>(a.st.lp[c]);
+    const double u = draw_uniform<double>(a.seed, c, it, kAccept, 0);
+    const bool acc = log(u) < la;
+    if (acc) {
+      R *zc = z(c), *zp = ze(c);
+      for (int i = 0; i < a.d; ++i) zc[i] = zp[i];
+      a.st.lp[c] = static_cast<R>(lpp);
+    }
+    count(c, acc, la, 1);
+    finish(c, c);
+    return true;
+  }
+
+  // ---------------------------------------------------------------- MALA
+  // Eq. (2.3): z' = z + eps grad + sqrt(2 eps) xi; q(a|b) = N(a; b + eps grad(b), 2 eps I).
+  __device__ bool mala_pre(int c) const {
+    if (a.st.steps_done[c] >= a.n_steps) return false;
+    R xi[kMaxD];
+    draw_normals<R>(a.seed, c, a.st.iter[c], kXi, a.d, xi);
+    const R e = static_cast<R>(a.eps), s = static_cast<R>(sqrt(2.0 * a.eps));
+    R *zc = z(c), *gc = g(c), *zp = ze(c);
+    for (int i = 0; i < a.d; ++i) zp[i] = zc[i] + e * gc[i] + s * xi[i];
+    return true;
+  }
+  __device__ bool mala_post(int c) const {
+    R x[kMaxD], gp[kMaxD];
+    const double lpp = logpi_eval(c, gp, x);
+    const uint32_t it = a.st.iter[c];
+    R *zc = z(c), *gc = g(c), *zp = ze(c);
+    const double e = a.eps;
+    double fwd = 0.0, rev = 0.0;
+    for (int i = 0; i < a.d; ++i) {
+      const double f = static_cast<double>(zp[i]) - zc[i] - e * gc[i];
+      const double r = static_cast<double>(zc[i]) - zp[i] - e * gp[i];
+      fwd += f * f;
+      rev += r * r;
+    }
+    // log q(z|z') - log q(z'|z)
+    const double la = lpp - static_cast<double>(a.st.lp[c]) + (fwd - rev) / (4.0 * e);
+    const double u = draw_uniform<double>(a.seed, c, it, kAccept, 0);
+    const bool acc = log(u) < la;
+    if (acc) {
+      for (int i = 0; i < a.d; ++i) {
+        zc[i] = zp[i];
+        gc[i] = gp[i];
+      }
+      a.st.lp[c] = static_cast<R>(lpp);
+    }
+    count(c, acc, la, 1);
+    finish(c, c);
+    return true;
+  }
+
+  // ---------------------------------------------------------------- HMC
+  // Identity mass in whitened space (Eqs. (2.7)-(2.8)); leapfrog; accept on H0 - H1.
+  // work vectors: 0 z1, 1 q1, 2 g1; dwork: 0 leapfrogs done, 1 H0.
+  __device__ double *dwork_ptr(int c) const;
+
+  __device__ bool hmc_pre(int c) const {
+    if (a.st.steps_done[c] >= a.n_steps) return false;
+    double *dw = dwork_ptr(c);
+    R *z1 = wv(c, 0), *q1 = wv(c, 1), *g1 = wv(c, 2);
+    const R e = static_cast<R>(a.eps);
+    if (dw[0] == 0.0) {
+      R q[kMaxD];
+      draw_normals<R>(a.seed, c, a.st.iter[c], kXi, a.d, q);
+      double qq = 0.0;
+      R *zc = z(c), *gc = g(c);
+      for (int i = 0; i < a.d; ++i) {
+        qq += static_cast<double>(q[i]) * q[i];
+        z1[i] = zc[i];
+        g1[i] = gc[i];
+        q1[i] = q[i];
+      }
+      dw[1] = -static_cast<double>(a.st.lp[c]) + 0.5 * qq;
+    }
+    R *zp = ze(c);
+    for (int i = 0; i < a.d; ++i) {
+      q1[i] += R(0.5) * e * g1[i];
+      z1[i] += e * q1[i];
+      zp[i] = z1[i];
+    }
+    return true;
+  }
+  __device__ bool hmc_post(int c) const {
+    double *dw = dwork_ptr(c);
+    R *z1 = wv(c, 0), *q1 = wv(c, 1), *g1 = wv(c, 2);
+    R x[kMaxD];
+    const double lp1 = logpi_eval(c, g1, x);
+    const R e = static_cast<R>(a.eps);
+    double qq = 0.0;
+    for (int i = 0; i < a.d; ++i) {
+      q1[i] += R(0.5) * e * g1[i];
+      qq += static_cast<double>(q1[i]) * q1[i];
+    }
+    dw[0] += 1.0;
+    a.st.evals[c] += 1ull;
+    if (dw[0] < a.n_leapfrog) return false;
+    dw[0] = 0.0;
+    const double H1 = -lp1 + 0.5 * qq;
+    const double la = dw[1] - H1;
+    const uint32_t it = a.st.iter[c];
+    const double u = draw_uniform<double>(a.seed, c, it, kAccept, 0);
+    const bool acc = log(u) < la;
+    if (acc) {
+      R *zc = z(c), *gc = g(c);
+      for (int i = 0; i < a.d; ++i) {
+        zc[i] = z1[i];
+        gc[i] = g1[i];
+      }
+      a.st.lp[c] = static_cast<R>(lp1);
+    }
+    count(c, acc, la, 0);
+    finish(c, c);
+    return true;
+  }
+
+  // ---------------------------------------------------------------- NUTS
+  // Hoffman & Gelman (2014) Algorithm 3, unrolled into one leapfrog per call:
+  // the tree of the current doubling is built leaf by leaf; pending left
+  // siblings wait on a per-level stack and are merged (candidate kept with
+  // probability n''/(n'+n''), U-turn check of the merged span) when their right
+  // sibling completes.  work vectors: 0 zm 1 qm 2 gm 3 zp 4 qp 5 gp 6 zs 7 gs
+  // 8 qh, level i: 9+4i first z, 10+4i first q, 11+4i cand z, 12+4i cand g.
+  // dwork: 0 new-iteration flag, 1 log u, 2 H0, 3 n, 4 lp of selected,
+  // 5 acceptance-stat sum, 6 j, 7 v, 8 m_sub, 9 leaves, 10 diverged, 11 moved,
+  // 12+i cand lp, 22+i node n.
+  __device__ bool nuts_pre(int c) const {
+    if (a.st.steps_done[c] >= a.n_steps) return false;
+    double *dw = dwork_ptr(c);
+    const int d = a.d;
+    const uint32_t it = a.st.iter[c];
+    if (dw[0] != 0.0) {
+      R q0[kMaxD];
+      draw_normals<R>(a.seed, c, it, kXi, d, q0);
+      double qq = 0.0;
+      for (int i = 0; i < d; ++i) qq += static_cast<double>(q0[i]) * q0[i];
+      const double H0 = -static_cast<double>(a.st.lp[c]) + 0.5 * qq;
+      dw[2] = H0;
+      dw[1] = log(draw_uniform<double>(a.seed, c, it, kAccept, 0)) - H0;
+      R *zc = z(c), *gc = g(c);
+      R *zm = wv(c, 0), *qm = wv(c, 1), *gm = wv(c, 2), *zp = wv(c, 3), *qp = wv(c, 4),
+        *gp = wv(c, 5), *zs = wv(c, 6), *gs = wv(c, 7);
+      for (int i = 0; i < d; ++i) {
+        zm[i] = zp[i] = zs[i] = zc[i];
+        gm[i] = gp[i] = gs[i] = gc[i];
+        qm[i] = qp[i] = q0[i];
+      }
+      dw[3] = 1.0;
+      dw[4] = static_cast<double>(a.st.lp[c]);
+      dw[5] = 0.0;
+      dw[6] = 0.0;
+      dw[7] = draw_uniform<double>(a.seed, c, it, kNutsDir, 0) < 0.5 ? -1.0 : 1.0;
+      dw[8] = 0.0;
+      dw[9] = 0.0;
+      dw[10] = 0.0;
+      dw[11] = 0.0;
+      dw[0] = 0.0;
+    }
+    const bool back = dw[7] < 0.0;
+    const R e = static_cast<R>(dw[7] * a.eps);
+    R *ze_ = wv(c, back ? 0 : 3), *qe = wv(c, back ? 1 : 4), *ge = wv(c, back ? 2 : 5);
+    R *qh = wv(c, 8), *zn = ze(c);
+    for (int i = 0; i < d; ++i) {
+      qh[i] = qe[i] + R(0.5) * e * ge[i];
+      zn[i] = ze_[i] + e * qh[i];
+    }
+    return true;
+  }
+
+  __device__ bool nuts_post(int c) const {
+    double *dw = dwork_ptr(c);
+    const int d = a.d;
+    const uint32_t it = a.st.iter[c];
+    const bool back = dw[7] < 0.0;
+    const double v = dw[7];
+    const R e = static_cast<R>(v * a.eps);
+    R x[kMaxD], gn[kMaxD];
+    const double lpn = logpi_eval(c, gn, x);
+    R *qh = wv(c, 8), *zn = ze(c);
+    R *zend = wv(c, back ? 0 : 3), *qend = wv(c, back ? 1 : 4), *gend = wv(c, back ? 2 : 5);
+    double qq = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const R qn = qh[i] + R(0.5) * e * gn[i];
+      qq += static_cast<double>(qn) * qn;
+      zend[i] = zn[i];
+      qend[i] = qn;
+      gend[i] = gn[i];
+    }
+    a.st.evals[c] += 1ull;
+    dw[9] += 1.0;
+    const int leaf = static_cast<int>(dw[9]);
+    const double Hl = -lpn + 0.5 * qq;
+    dw[5] += accept_prob(dw[2] - Hl);
+    const double log_u = dw[1];
+    const double nl = (log_u <= -Hl) ? 1.0 : 0.0;
+    const bool sl = log_u < kNutsDeltaMax - Hl;
+    if (!sl) {
+      dw[10] = 1.0;
+      return nuts_finish(c);
+    }
+    // current node = the new leaf; first = leaf, candidate = leaf
+    int first_src = -1, cand_src = -1;
+    double node_n = nl;
+    const int m_sub = static_cast<int>(dw[8]);
+    const int j = static_cast<int>(dw[6]);
+    int lvl = 0;
+    while ((m_sub >> lvl) & 1) {
+      // merge pending left sibling at level lvl with the node
+      const double ln = dw[22 + lvl];
+      const double u = draw_uniform<double>(a.seed, c, it, kNutsSel,
+                                            static_cast<uint32_t>(8 * (leaf - 1) + lvl + 1));
+      const double ntot = ln + node_n;
+      const bool take_right = ntot > 0.0 && u * ntot < node_n;
+      if (!take_right) cand_src = lvl;
+      // U-turn check of the merged span [left.first .. leaf]
+      const R *fz = wv(c, 9 + 4 * lvl), *fq = wv(c, 10 + 4 * lvl);
+      double s1 = 0.0, s2 = 0.0;
+      for (int i = 0; i < d; ++i) {
+        const double dz = v * (static_cast<double>(zend[i]) - fz[i]);
+        s1 += dz * fq[i];
+        s2 += dz * qend[i];
+      }
+      first_src = lvl;
+      node_n = ntot;
+      ++lvl;
+      if (!(s1 >= 0.0 && s2 >= 0.0)) return nuts_finish(c);
+    }
+    // candidate vectors of the node
+    const R *cz = cand_src < 0 ? zend : wv(c, 11 + 4 * cand_src);
+    const R *cg = cand_src < 0 ? gend : wv(c, 12 + 4 * cand_src);
+    const double clp = cand_src < 0 ? lpn : dw[12 + cand_src];
+    if (lvl == j) {
+      // the subtree of this doubling is complete: progressive top-level selection
+      const double ut = draw_uniform<double>(a.seed, c, it, kNutsTop, static_cast<uint32_t>(j));
+      if (ut * dw[3] < node_n) {
+        R *zs = wv(c, 6), *gs = wv(c, 7);
+        for (int i = 0; i < d; ++i) {
+          zs[i] = cz[i];
+          gs[i] = cg[i];
+        }
+        dw[4] = clp;
+        dw[11] = 1.0;
+      }
+      dw[3] += node_n;
+      const R *zm = wv(c, 0), *qm = wv(c, 1), *zp = wv(c, 3), *qp = wv(c, 4);
+      double s1 = 0.0, s2 = 0.0;
+      for (int i = 0; i < d; ++i) {
+        const double dz = static_cast<double>(zp[i]) - zm[i];
+        s1 += dz * qm[i];
+        s2 += dz * qp[i];
+      }
+      const int jn = j + 1;
+      dw[6] = jn;
+      if (!(s1 >= 0.0 && s2 >= 0.0) || jn >= a.max_depth) return nuts_finish(c);
+      dw[7] = draw_uniform<double>(a.seed, c, it, kNutsDir, static_cast<uint32_t>(jn)) < 0.5 ? -1.0 : 1.0;
+      dw[8] = 0.0;
+    } else {
+      // park the node as the pending left sibling at level lvl
+      R *pz = wv(c, 9 + 4 * lvl), *pq = wv(c, 10 + 4 * lvl), *pcz = wv(c, 11 + 4 * lvl),
+        *pcg = wv(c, 12 + 4 * lvl);
+      const R *fz = first_src < 0 ? zend : wv(c, 9 + 4 * first_src);
+      const R *fq = first_src < 0 ? qend : wv(c, 10 + 4 * first_src);
+      if (first_src != lvl)
+        for (int i = 0; i < d; ++i) {
+          pz[i] = fz[i];
+          pq[i] = fq[i];
+        }
+      if (cand_src != lvl)
+        for (int i = 0; i < d; ++i) {
+          pcz[i] = cz[i];
+          pcg[i] = cg[i];
+        }
+      dw[12 + lvl] = clp;
+      dw[22 + lvl] = node_n;
+      dw[8] = m_sub + 1;
+    }
+    return false;
+  }
+
+  __device__ bool nuts_finish(int c) const {
+    double *dw = dwork_ptr(c);
+    R *zc = z(c), *gc = g(c), *zs = wv(c, 6), *gs = wv(c, 7);
+    for (int i = 0; i < a.d; ++i) {
+      zc[i] = zs[i];
+      gc[i] = gs[i];
+    }
+    a.st.lp[c] = static_cast<R>(dw[4]);
+    const double leaves = dw[9];
+    a.st.acc_stat[c] += leaves > 0.0 ? dw[5] / leaves : 0.0;
+    a.st.accepts[c] += dw[11] != 0.0 ? 1ull : 0ull;
+    a.st.divs[c] += dw[10] != 0.0 ? 1ull : 0ull;
+    dw[0] = 1.0;
+    finish(c, c);
+    return true;
+  }
+
+  // ---------------------------------------------------------------- AIES
+  // Goodman-Weare stretch move (Sec. 2.3): y = z_j + Z (z_i - z_j),
+  // Z = (u (a - 1) + 1)^2 / a (Eq. (2.15)); accept with min(1, Z^(d-1) pi(y)/pi(z_i)).
+  // Row r moves walker k = r % (W/2) of half h of ensemble r / (W/2).
+  __device__ int aies_walker(int r, int h) const {
+    const int half = a.aies_walkers / 2;
+    return (r / half) * a.aies_walkers + h * half + (r % half);
+  }
+  __device__ bool aies_pre(int r, int h) const {
+    const int i = aies_walker(r, h);
+    if (a.st.steps_done[i] >= a.n_steps) return false;
+    const int half = a.aies_walkers / 2;
+    const int base = (r / half) * a.aies_walkers + (1 - h) * half;
+    const uint32_t it = a.st.iter[i];
+    const double up = draw_uniform<double>(a.seed, i, it, kAiesPartner, 0);
+    int jj = static_cast<int>(up * half);
+    if (jj > half - 1) jj = half - 1;
+    const int jw = base + jj;
+    const double uz = draw_uniform<double>(a.seed, i, it, kAiesZ, 0);
+    const double t = uz * (a.aies_a - 1.0) + 1.0;
+    const double Z = t * t / a.aies_a;
+    dwork_ptr(i)[0] = Z;
+    const R *zi = z(i), *zj = z(jw);
+    R *y = ze(r);
+    const R Zr = static_cast<R>(Z);
+    for (int q = 0; q < a.d; ++q) y[q] = zj[q] + Zr * (zi[q] - zj[q]);
+    return true;
+  }
+  __device__ bool aies_post(int r, int h) const {
+    const int i = aies_walker(r, h);
+    R x[kMaxD];
+    const double lpy = logpi_eval(r, nullptr, x);
+    const double Z = dwork_ptr(i)[0];
+    const double la = (a.d - 1) * log(Z) + lpy - static_cast<double>(a.st.lp[i]);
+    const uint32_t it = a.st.iter[i];
+    const double u = draw_uniform<double>(a.seed, i, it, kAccept, 0);
+    const bool acc = log(u) < la;
+    if (acc) {
+      R *zi = z(i), *y = ze(r);
+      for (int q = 0; q < a.d; ++q) zi[q] = y[q];
+      a.st.lp[i] = static_cast<R>(lpy);
+    }
+    count(i, acc, la, 1);
+    finish(i, r);
+    return true;
+  }
+
+  // ---------------------------------------------------------------- batch modes
+  __device__ bool refresh_pre(int c) const {
+    if (a.st.steps_done[c] >= 1) return false;
+    R *zc = z(c), *zp = ze(c);
+    for (int i = 0; i < a.d; ++i) zp[i] = zc[i];
+    return true;
+  }
+  __device__ bool refresh_post(int c) const {
+    R x[kMaxD], gp[kMaxD];
+    const double lp = logpi_eval(c, gp, x);
+    a.st.lp[c] = static_cast<R>(lp);
+    R *gc = g(c);
+    for (int i = 0; i < a.d; ++i) gc[i] = gp[i];
+    a.st.steps_done[c] = 1;
+    return true;
+  }
+
+  // common end of an iteration: counters, sample record
+  __device__ void finish(int c, int row) const {
+    const int s = a.st.steps_done[c];
+    a.st.iter[c] += 1u;
+    record(c, row, s);
+    a.st.steps_done[c] = s + 1;
+  }
+
+  // Dispatch. pre returns whether the row needs an evaluation; post returns whether
+  // the chain of the row completed an iteration (for the covariance accumulator).
+  __device__ bool pre(int row, int h) const {
+    switch (a.mode) {
+      case kModeMH: return mh_pre(row);
+      case kModeMALA: return mala_pre(row);
+      case kModeHMC: return hmc_pre(row);
+      case kModeNUTS: return nuts_pre(row);
+      case kModeAIES: return aies_pre(row, h);
+      case kModeRefresh: return refresh_pre(row);
+      default: return false;
+    }
+  }
+  __device__ bool post(int row, int h) const {
+    switch (a.mode) {
+      case kModeMH: return mh_post(row);
+      case kModeMALA: return mala_post(row);
+      case kModeHMC: return hmc_post(row);
+      case kModeNUTS: return nuts_post(row);
+      case kModeAIES: return aies_post(row, h);
+      case kModeRefresh: return refresh_post(row);
+      default: return false;
+    }
+  }
+};
+
+// Double-precision per-chain scratch lives after the R vectors of the work row.
+template <typename R>
+__device__ double *Chain<R>::dwork_ptr(int c) const {
+  char *base = reinterpret_cast<char *>(a.st.work + static_cast<size_t>(c) * a.st.work_stride);
+  const size_t vec_bytes = static_cast<size_t>(kDworkOffsetVecs) * a.dp * sizeof(R);
+  return reinterpret_cast<double *>(base + vec_bytes);
+}
+
+}  // namespace bst

@@ -1,0 +1,122 @@
+"""GPU parity of loglike / grad_loglike and of the initial log pi against the FP64 oracle.
+
+Tolerances: FP32 logL 1e-5 relative and gradient 1e-4 relative (of the largest
+component); FP64 1e-10; BF16 against the oracle's BF16 operand-rounding mode
+(same rounding points; FP32 vs FP64 accumulation and tanh rounding can flip a
+BF16 rounding now and then), and its chi^2 error against the FP64 emulator is
+checked to stay below 0.05 at the tested output scale."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synthetic as S
+from gpu_common import emulator_case, rel_err, whitening
+
+pytestmark = pytest.mark.gpu
+
+
+def _sampler(prec, e, lik="emulator", n=8, t=None):
+    from paper_2606_04895_gb300 import Sampler
+    d = e["d"] if lik == "emulator" else t["d"]
+    s = Sampler(d, n, precision=prec, likelihood=lik, seed=1)
+    if lik == "emulator":
+        s.set_emulator(e["params"], e["depth"], e["width"], e["in_m"], e["in_s"], e["out_m"], e["out_s"])
+    else:
+        s.set_analytic(t["A"], t["B"], t["c"], t["data"], t["sigma"], d_c=t["d_c"], N=t["N"], linear=t["linear"])
+    return s
+
+
+SHAPES = [(8, 256, 1), (8, 256, 3), (6, 512, 4), (27, 512, 2)]
+
+
+@pytest.mark.parametrize("d,width,depth", SHAPES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_emulator_loglike_parity(prec, d, width, depth):
+    if prec == "fp64" and width > 512:
+        pytest.skip("fp64 width <= 512")
+    e = emulator_case(d, width, depth, out_s=20.0, out_m=100.0)
+    s = _sampler(prec, e)
+    m = 300  # several tiles of 16 / 32 / 128 rows plus a ragged tail
+    x = np.random.default_rng(2).uniform(-3, 3, (m, d))
+    ll, g = s.grad_loglike(x)
+    ll0 = s.loglike(x)
+    ll, g, ll0 = ll.double().cpu().numpy(), g.double().cpu().numpy(), ll0.double().cpu().numpy()
+    ref = O.Model(d, emulator=e, bf16=(prec == "bf16"))
+    rl, rg = ref.loglike(x)
+    assert np.array_equal(ll, ll0) or rel_err(ll0, rl) < 1e-5
+    if prec == "fp64":
+        assert rel_err(ll, rl) < 1e-10 and rel_err(g, rg) < 1e-9
+    elif prec == "fp32":
+        assert np.max(np.abs(ll - rl) / np.maximum(np.abs(rl), 1.0)) < 1e-5
+        assert rel_err(g, rg) < 1e-4
+    else:
+        assert np.max(np.abs(ll - rl) / np.maximum(np.abs(rl), 1.0)) < 2e-3, np.max(np.abs(ll - rl))
+        assert rel_err(g, rg) < 2e-2
+        # error of BF16 against the FP64 emulator, in chi^2 units
+        r64 = O.Model(d, emulator=e).loglike(x, grad=False)
+        dchi2 = 2 * np.abs(ll - r64)
+        print(f"bf16 |dchi2| max {dchi2.max():.3g} mean {dchi2.mean():.3g}")
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_loglike_edge_sizes(prec):
+    e = emulator_case(8, 256, 2)
+    s = _sampler(prec, e)
+    ref = O.Model(8, emulator=e, bf16=(prec == "bf16"))
+    for m in (0, 1, 129):
+        x = np.random.default_rng(m).uniform(-3, 3, (m, 8))
+        ll, g = s.grad_loglike(torch.as_tensor(x).reshape(m, 8))
+        assert ll.shape == (m,) and g.shape == (m, 8)
+        if m:
+            rl, rg = ref.loglike(x)
+            assert np.max(np.abs(ll.double().cpu().numpy() - rl)) < 1e-2 * max(1, np.abs(rl).max())
+    s.close()
+
+
+TARGETS = {"lcdm6": dict(d=6), "sterile8": dict(d=8), "nuis27": dict(d=27, nuisance=True),
+           "linear6": dict(d=6, linear=True)}
+
+
+@pytest.mark.parametrize("name", list(TARGETS))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_analytic_loglike_parity(prec, name):
+    t = S.target(seed=0, **TARGETS[name])
+    s = _sampler(prec, None, "analytic", t=t)
+    m = 257
+    x = t["theta_star"] + 0.05 * np.random.default_rng(1).normal(size=(m, t["d"]))
+    ll, g = s.grad_loglike(x)
+    ll, g = ll.double().cpu().numpy(), g.double().cpu().numpy()
+    ref = O.Model(t["d"], lik="analytic", analytic=t)
+    rl, rg = ref.loglike(x)
+    tol_l, tol_g = (1e-11, 1e-9) if prec == "fp64" else (1e-5, 1e-4)
+    assert np.max(np.abs(ll - rl) / np.maximum(np.abs(rl), 1.0)) < tol_l
+    assert rel_err(g, rg) < tol_g
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_init_chains_log_pi_and_gradient(prec):
+    d = 8
+    e = emulator_case(d, 256, 3)
+    mu, L = whitening(d, 3)
+    lower, upper = np.full(d, -3.0), np.full(d, 3.0)
+    gauss = np.array([0] * 6 + [1] * 2, dtype=np.int32)
+    n = 200
+    theta0 = mu + np.random.default_rng(4).normal(size=(n, d)) @ L.T
+    theta0[0, 0] = 3.5  # one start outside the box: log pi = -inf
+    from gpu_common import make_emulator_sampler
+    s = make_emulator_sampler(prec, e, n, mu=mu, L=L, lower=lower, upper=upper, theta0=theta0, gauss=gauss)
+    st = s.get_state()
+    ref = O.Model(d, emulator=e, lower=lower, upper=upper, gauss=gauss, mu=mu, L=L, bf16=(prec == "bf16"))
+    z0 = np.linalg.solve(L, (theta0 - mu).T).T
+    assert np.allclose(st["z"], z0, rtol=0, atol={"fp64": 1e-12}.get(prec, 1e-5))
+    rl, rg = ref.logpost(z0)
+    assert st["logp"][0] == -np.inf and rl[0] == -np.inf
+    fin = np.isfinite(rl)
+    tol = {"fp64": 1e-10, "fp32": 1e-5, "bf16": 2e-3}[prec]
+    assert np.max(np.abs(st["logp"][fin] - rl[fin]) / np.maximum(np.abs(rl[fin]), 1)) < tol
+    assert rel_err(st["grad"], rg) < {"fp64": 1e-9, "fp32": 1e-4, "bf16": 2e-2}[prec]
+    assert np.all(st["iter"] == 0)
+    s.close()

@@ -1,0 +1,134 @@
+"""Per-step parity of the five samplers against the FP64 oracle from identical
+states and identical Philox streams.
+
+Decisions must agree wherever |log alpha - log u| > 1e-3 (the oracle's trace
+gives both); where they agree the new positions must match (FP64: 1e-9; FP32
+and BF16: 1e-3 absolute in x).  BF16 runs are compared with the oracle's BF16
+operand-rounding mode."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synthetic as S
+from gpu_common import emulator_case, make_emulator_sampler, oracle_emulator_model, whitening
+
+pytestmark = pytest.mark.gpu
+
+MARGIN = 1e-3
+POS_TOL = {"fp64": 1e-9, "fp32": 1e-3, "bf16": 1e-3}
+
+
+def _setup(prec, n, d=8, width=256, depth=3, seed=11, **kw):
+    e = emulator_case(d, width, depth, out_s=8.0, out_m=50.0)
+    mu, L = whitening(d, 1, scale=0.4)
+    lower, upper = np.full(d, -3.0), np.full(d, 3.0)
+    theta0 = np.clip(mu + np.random.default_rng(9).normal(size=(n, d)) @ L.T, -2.9, 2.9)
+    s = make_emulator_sampler(prec, e, n, mu=mu, L=L, lower=lower, upper=upper, theta0=theta0, seed=seed, **kw)
+    m = oracle_emulator_model(e, mu=mu, L=L, lower=lower, upper=upper, bf16=(prec == "bf16"))
+    z0 = np.linalg.solve(L, (theta0 - mu).T).T
+    return s, m, z0, mu, L
+
+
+def _check(prec, s, ref, samples, kernel, n):
+    acc_gpu = s.counters()["accepts"]
+    x_gpu = samples[-1].double().cpu().numpy()
+    x_ref = ref["samples"][-1]
+    if kernel == "nuts":
+        same = np.all(np.abs(x_gpu - x_ref) < POS_TOL[prec], axis=1)
+        frac = same.mean()
+        assert frac >= (1.0 if prec == "fp64" else 0.9), frac
+        ev = s.counters()["evals"]
+        assert np.mean(ev == ref["evals"]) >= (1.0 if prec == "fp64" else 0.9)
+        return
+    la, lu = ref["log_alpha"][-1], ref["log_u"][-1]
+    clear = np.abs(la - lu) > MARGIN
+    assert clear.mean() > 0.9
+    assert np.array_equal(acc_gpu[clear] > 0, ref["accept"][-1][clear] > 0)
+    assert np.all(np.abs(x_gpu[clear] - x_ref[clear]) < POS_TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("kernel,eps,extra", [("mh", 0.5, {}), ("mala", 0.4, {}), ("hmc", 0.2, {"n_leapfrog": 5}),
+                                              ("nuts", 0.3, {})])
+def test_one_step_parity(prec, kernel, eps, extra):
+    n = 300
+    s, m, z0, mu, L = _setup(prec, n)
+    out = torch.empty((1, n, 8), dtype=s.dtype, device="cuda")
+    s.step(kernel, 1, eps=eps, samples=out, **extra)
+    ref = O.run(m, kernel, z0, eps=eps, n_steps=1, seed=11, trace=True, **extra)
+    _check(prec, s, ref, out, kernel, n)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_aies_one_step_parity(prec):
+    n = 256  # 4 ensembles of 64 walkers
+    s, m, z0, mu, L = _setup(prec, n)
+    out = torch.empty((1, n, 8), dtype=s.dtype, device="cuda")
+    if prec == "fp64":
+        pytest.skip("FP64 emulator tiles hold 16 rows: AIES ensemble halves would span tiles")
+    s.step("aies", 1, samples=out)
+    ref = O.run(m, "aies", z0, eps=0.0, n_steps=1, seed=11, trace=True, aies_walkers=64)
+    _check(prec, s, ref, out, "aies", n)
+    s.close()
+
+
+@pytest.mark.parametrize("kernel,eps,extra", [("mala", 0.4, {}), ("hmc", 0.25, {"n_leapfrog": 4}), ("mh", 0.5, {}),
+                                              ("nuts", 0.3, {})])
+def test_fp64_trajectories_track_oracle(kernel, eps, extra):
+    n, steps = 160, 12
+    s, m, z0, mu, L = _setup("fp64", n)
+    out = torch.empty((steps, n, 8), dtype=torch.float64, device="cuda")
+    s.step(kernel, steps, eps=eps, samples=out, **extra)
+    ref = O.run(m, kernel, z0, eps=eps, n_steps=steps, seed=11, trace=True, **extra)
+    x = out.cpu().numpy()
+    same = np.all(np.abs(x - ref["samples"]) < 1e-8, axis=(0, 2))
+    assert same.mean() >= 0.98, same.mean()
+    st = s.get_state()
+    assert np.all(st["iter"] == steps)
+    s.close()
+
+
+def test_step_statistics_and_counters():
+    n = 128
+    s, m, z0, mu, L = _setup("fp32", n)
+    st = s.step("hmc", 3, eps=0.2, n_leapfrog=4)
+    c = s.counters()
+    assert st["evals"] == n * 3 * 4 and c["evals"].sum() == n * 3 * 4
+    assert st["accepts"] == c["accepts"].sum()
+    assert 0.0 < st["accept_stat"] <= 1.0
+    st2 = s.step("mh", 2, eps=0.3)
+    assert st2["evals"] == n * 2
+    s.close()
+
+
+def test_checkpoint_resume_is_bit_identical():
+    n = 96
+    a, m, z0, mu, L = _setup("fp32", n)
+    b, *_ = _setup("fp32", n)
+    a.step("mala", 10, eps=0.3, stats=False)
+    snap = b.get_state()
+    b.step("mala", 5, eps=0.3, stats=False)
+    mid = b.get_state()
+    b.close()
+    c, *_ = _setup("fp32", n)
+    c.set_state(mid)
+    c.step("mala", 5, eps=0.3, stats=False)
+    sa, sc = a.get_state(), c.get_state()
+    assert np.array_equal(sa["z"], sc["z"]) and np.array_equal(sa["iter"], sc["iter"])
+    assert snap["iter"].max() == 0
+    a.close(); c.close()
+
+
+def test_thinning_and_sample_shape():
+    from paper_2606_04895_gb300 import Sampler
+    n = 64
+    s, m, z0, mu, L = _setup("fp32", n, thin=3)
+    out = torch.empty((4, n, 8), dtype=torch.float32, device="cuda")
+    s.step("mh", 12, eps=0.3, samples=out)
+    ref = O.run(m, "mh", z0, eps=0.3, n_steps=12, seed=11)
+    x = out.double().cpu().numpy()
+    same = np.all(np.abs(x - ref["samples"][2::3]) < 1e-3, axis=(0, 2))
+    assert same.mean() > 0.9
+    s.close()
