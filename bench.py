@@ -1,0 +1,329 @@
+"""Benchmark: emulator MALA on the 8-D sterile-shaped target, 4096 chains, BF16 tcgen05 engine.
+
+Workload (the configuration the headline metric is quoted on): 4096 chains of
+MALA on an 8-D target whose likelihood is a tanh MLP emulator
+8 -> 512 -> 512 -> 512 -> 512 -> 1 (seeded weights; the cost of an evaluation
+does not depend on their values), box prior [-3, 3]^8, whitening from a
+three-iteration covariance-adaptation burn-in, step size dual-averaged to an
+acceptance of ~0.65.  One bench "step" is one MALA iteration of every chain:
+whitening (folded into layer 1), prior, emulator forward + adjoint, proposal,
+Metropolis accept and sample record.  The K timed steps run as one persistent
+kernel launch.  value = emulator logL+grad evaluations per second (whole job);
+min-ESS/s, HMC (L = 10) and the plain FP32 CUDA-core path are reported beside.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+D, N_CHAINS, WIDTH, DEPTH = 8, 4096, 512, 4
+METRIC = "emulator logL+grad evals/sec (BF16 tcgen05 MALA, 8-D, 4096 chains, 8-512x4-1)"
+UNIT = "evals/s"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return j.get("bf16_tflops", 1900.0), j.get("bf16_tflops_sustained", 1700.0), j.get("hbm_gbs", 6800.0), "measured"
+    return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+def n_params(d, depth, width):
+    return d * width + width + (depth - 1) * (width * width + width) + width + 1
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if len(r) > 5 + k and r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dual_average_eps(sampler, kernel, eps0, n_iter=12, chunk=40, target=0.65, **kw):
+    """Hoffman & Gelman (2014) Sec. 3.2 dual averaging on log eps, using the mean
+    acceptance statistic of all chains over each chunk of steps."""
+    mu = np.log(10 * eps0)
+    h_bar, log_eps_bar, log_eps = 0.0, 0.0, np.log(eps0)
+    gamma, t0, kappa = 0.05, 10.0, 0.75
+    for m in range(1, n_iter + 1):
+        st = sampler.step(kernel, chunk, eps=float(np.exp(log_eps)), **kw)
+        a = st["accept_stat"]
+        h_bar = (1 - 1 / (m + t0)) * h_bar + (target - a) / (m + t0)
+        log_eps = mu - np.sqrt(m) / gamma * h_bar
+        eta = m ** (-kappa)
+        log_eps_bar = eta * log_eps + (1 - eta) * log_eps_bar
+    return float(np.exp(log_eps_bar))
+
+
+def make_sampler(precision, n, seed, device):
+    import synthetic as S
+    from paper_2606_04895_gb300 import Sampler
+    e = S.emulator(D, width=WIDTH, depth=DEPTH, seed=5, out_m=60.0, out_s=12.0)
+    s = Sampler(D, n, precision=precision, likelihood="emulator", seed=seed, device=device)
+    s.set_emulator(e["params"], DEPTH, WIDTH, e["in_m"], e["in_s"], e["out_m"], e["out_s"])
+    return s, e
+
+
+def burn_in(s, n, seed, kernel="mala", **kw):
+    """Paper Sec. 4 protocol, shortened: start from a diagonal whitening with scales
+    proportional to the box, three burn-in iterations each ending in a covariance
+    adaptation, step size dual-averaged in each."""
+    lower, upper = np.full(D, -3.0), np.full(D, 3.0)
+    L0 = np.diag((upper - lower) / np.sqrt(12.0))
+    theta0 = np.clip(np.random.default_rng(seed).normal(size=(n, D)), -2.9, 2.9)
+    s.init_chains(theta0, lower, upper, mu=np.zeros(D), L=L0)
+    eps = 0.3
+    for _ in range(3):
+        eps = dual_average_eps(s, kernel, eps, **kw)
+        s.welford_reset()
+        s.step(kernel, 150, eps=eps, stats=False, **kw)
+        s.adapt_cov()
+    eps = dual_average_eps(s, kernel, eps, **kw)
+    return eps, theta0, lower, upper
+
+
+def flush_l2(torch):
+    buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    buf.fill_(1.0)
+    del buf
+
+
+def time_steps(torch, s, kernel, K, eps, samples=None, **kw):
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    s.step(kernel, K, eps=eps, samples=samples, stats=False, **kw)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def cpu_baseline(seconds_target=15.0):
+    """The FP64 oracle (as it stands) on the host cores, on a bounded sample of the
+    same workload: MALA on the same emulator and target, a few chains and steps."""
+    import oracle as O
+    import synthetic as S
+    e = S.emulator(D, width=WIDTH, depth=DEPTH, seed=5, out_m=60.0, out_s=12.0)
+    lower, upper = np.full(D, -3.0), np.full(D, 3.0)
+    m = O.Model(D, emulator=e, lower=lower, upper=upper, L=np.eye(D) * 0.3)
+    cores = os.cpu_count() or 1
+    n = max(cores * 4, 16)
+    z0 = np.random.default_rng(0).normal(size=(n, D))
+    t0 = time.perf_counter()
+    r = O.run(m, "mala", z0, eps=0.3, n_steps=1, seed=1, record=False)
+    dt1 = time.perf_counter() - t0
+    steps = max(1, int(seconds_target / max(dt1, 1e-3)))
+    t0 = time.perf_counter()
+    r = O.run(m, "mala", r["z"], eps=0.3, n_steps=steps, seed=1, record=False, lp=r["lp"], g=r["g"], iter0=r["iter"])
+    dt = time.perf_counter() - t0
+    evals = int(r["evals"].sum())
+    return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle MALA, {n} chains x {steps} steps of the same 8-512x4-1 emulator "
+                      f"({evals} logL+grad evals in {dt:.1f} s, OpenMP over chains)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    per = []
+    base = None
+    for _ in range(args.warmup):
+        cpu_baseline(seconds_target=2.0)
+    for _ in range(args.steps):
+        base = cpu_baseline(seconds_target=max(2.0, 60.0 / max(1, args.steps)))
+        per.append(base["value"])
+    v = float(np.median(per))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "emulator MALA 8-D 4096 chains 8-512x4-1 (oracle on host cores, bounded sample)",
+                       "chains": N_CHAINS, "d": D, "width": WIDTH, "depth": DEPTH},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the burn-in (fixed whitening and step size): three launches in total, "
+                         "for profiler captures")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    K, W = args.steps, args.warmup
+    seed = 1234 + rank  # each rank owns independent chains (weak scaling)
+    s, e = make_sampler("bf16", N_CHAINS, seed, local)
+    if args.quick:
+        lower, upper = np.full(D, -3.0), np.full(D, 3.0)
+        theta0 = np.clip(np.random.default_rng(seed).normal(size=(N_CHAINS, D)), -2.9, 2.9)
+        s.init_chains(theta0, lower, upper, mu=np.zeros(D), L=0.5 * np.eye(D))
+        eps = 0.3
+    else:
+        eps, theta0, lower, upper = burn_in(s, N_CHAINS, seed)
+    s.step("mala", W, eps=eps, stats=False)
+    samples = torch.empty((K, N_CHAINS, D), dtype=torch.float32, device="cuda")
+    flush_l2(torch)
+    barrier()
+    with Clocks(local) as clk:
+        dt = time_steps(torch, s, "mala", K, eps, samples=samples)
+    dts = [dt]
+    if dist is not None:
+        t = torch.tensor([dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    evals = K * N_CHAINS * world
+    value = evals / dt
+    acc = s.step("mala", 1, eps=eps)["accept_stat"]
+    ess = s.ess(samples)
+    min_ess_s = float(ess.min()) * world / dt
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+           "ms_per_step": dt * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16", "data": "synthetic (seeded emulator weights and chain starts)",
+           "config": {"workload": "emulator MALA, 8-D sterile-shaped box target, 4096 chains x K steps, "
+                                  "8-512-512-512-512-1 tanh MLP, BF16 tcgen05 engine",
+                      "chains_per_gpu": N_CHAINS, "d": D, "width": WIDTH, "depth": DEPTH, "eps": eps,
+                      "accept_stat": acc, "parallelism": f"dp{world} (independent chains per GPU)",
+                      "l2": "flushed (256 MB write) before the timed launch; the 1.6 MB of BF16 weights are "
+                            "L2-resident by design inside the persistent step loop"},
+           "min_ess_per_s": min_ess_s, "min_ess": float(ess.min()) * world}
+    if rank == 0:
+        # roofline of the dominant kernel: the tcgen05 chain-tile kernel is the whole timed region
+        P = n_params(D, DEPTH, WIDTH) - 1
+        flops = 4.0 * P * N_CHAINS * K
+        burst, sustained, hbm, kind = peaks()
+        achieved = flops / dts[0] / 1e12
+        out["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": burst, "unit": "TFLOP/s",
+                           "frac": achieved / burst, "traffic": None,
+                           "peak_kind": f"{kind} bf16 dense burst (cuBLAS)",
+                           "algorithmic": "4P flop per logL+grad eval (forward 2P + adjoint 2P), P = 791040"}
+        out["clocks"] = clk.summary()
+        out["gpu_launches"] = 1
+        # end-to-end through the public API with host buffers
+        import numpy as _np
+        h_theta = torch.from_numpy(theta0).pin_memory()
+        h_samples = torch.empty((K, N_CHAINS, D), dtype=torch.float32).pin_memory()
+        mu, L = s.whitening()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.init_chains(h_theta.numpy(), lower, upper, mu=mu, L=L)
+        s.step("mala", K, eps=eps, samples=samples, stats=False)
+        h_samples.copy_(samples, non_blocking=True)
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        out["e2e"] = {"value": K * N_CHAINS / t_e2e, "unit": UNIT,
+                      "h2d_bytes_per_step": h_theta.numel() * 8 / K,
+                      "d2h_bytes_per_step": N_CHAINS * D * 4}
+        if not args.no_extras:
+            # HMC (L = 10) on the same target and the plain FP32 CUDA-core path
+            eh = dual_average_eps(s, "hmc", eps / 2, n_iter=6, chunk=10, n_leapfrog=10)
+            kh = max(50, K // 10)
+            sh = torch.empty((kh, N_CHAINS, D), dtype=torch.float32, device="cuda")
+            th = time_steps(torch, s, "hmc", kh, eh, samples=sh, n_leapfrog=10)
+            ess_h = s.ess(sh)
+            out["hmc"] = {"evals_per_s": kh * N_CHAINS * 10 / th, "min_ess_per_s": float(ess_h.min()) / th,
+                          "eps": eh, "steps": kh}
+            s32, _ = make_sampler("fp32", N_CHAINS, seed, local)
+            mu, L = s.whitening()
+            s32.init_chains(theta0, lower, upper, mu=mu, L=L)
+            s32.step("mala", W, eps=eps, stats=False)
+            k32 = max(200, K // 5)
+            x32 = torch.empty((k32, N_CHAINS, D), dtype=torch.float32, device="cuda")
+            flush_l2(torch)
+            t32 = time_steps(torch, s32, "mala", k32, eps, samples=x32)
+            ess32 = s32.ess(x32)
+            out["fp32_plain"] = {"evals_per_s": k32 * N_CHAINS / t32, "min_ess_per_s": float(ess32.min()) / t32,
+                                 "steps": k32, "speedup_bf16_evals": value / (k32 * N_CHAINS / t32)}
+            s32.close()
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out))
+    s.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

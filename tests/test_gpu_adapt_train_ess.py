@@ -1,0 +1,157 @@
+"""GPU parity of covariance adaptation (Welford + Cholesky + z remap), emulator
+training (forward / backward / Adam), the ESS kernel and the autograd.Function."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synthetic as S
+from gpu_common import emulator_case, make_emulator_sampler, rel_err, whitening
+
+pytestmark = pytest.mark.gpu
+
+
+def _small(prec, n=128, d=6, **kw):
+    e = emulator_case(d, 256, 2, out_s=6.0, out_m=20.0)
+    mu, L = whitening(d, 2, scale=0.5)
+    lower, upper = np.full(d, -3.0), np.full(d, 3.0)
+    theta0 = np.clip(mu + np.random.default_rng(1).normal(size=(n, d)) @ L.T, -2.9, 2.9)
+    s = make_emulator_sampler(prec, e, n, mu=mu, L=L, lower=lower, upper=upper, theta0=theta0, **kw)
+    return s, e, mu, L, lower, upper
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adapt_cov_from_external_samples(prec):
+    s, e, mu, L, lo, up = _small(prec)
+    rng = np.random.default_rng(3)
+    A = rng.normal(size=(6, 6))
+    x = rng.normal(size=(5000, 6)) @ A.T * 0.2 + 0.5
+    s.welford_reset()
+    s.welford_add(torch.as_tensor(x[:1700]))
+    s.welford_add(torch.as_tensor(x[1700:]))
+    st0 = s.get_state()
+    mu_n, L_n, used = s.adapt_cov()
+    xs = x.astype(np.float32).astype(np.float64) if prec == "fp32" else x
+    mref, cref = O.pooled_cov(xs)
+    rc, Lref, uref = O.cholesky_jitter(cref)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    assert used == 0.0 and rc == 0
+    assert np.allclose(mu_n, mref, rtol=tol, atol=tol) and np.allclose(L_n, Lref, rtol=1e-9 if prec == "fp64" else 1e-5, atol=1e-9)
+    # chain x unchanged by the remap, log pi re-evaluated under the new whitening
+    st1 = s.get_state()
+    x0 = mu + st0["z"] @ L.T
+    x1 = mu_n + st1["z"] @ L_n.T
+    assert np.allclose(x0, x1, atol=1e-10 if prec == "fp64" else 2e-5)
+    m = O.Model(6, emulator=e, lower=lo, upper=up, mu=mu_n, L=L_n)
+    rl, _ = m.logpost(st1["z"])
+    fin = np.isfinite(rl)
+    assert np.max(np.abs(st1["logp"][fin] - rl[fin]) / np.maximum(1, np.abs(rl[fin]))) < (1e-10 if prec == "fp64" else 1e-5)
+    s.close()
+
+
+def test_adapt_cov_inside_steps_matches_recorded_samples():
+    s, *_ = _small("fp64", n=160)
+    s.welford_reset()
+    out = torch.empty((40, 160, 6), dtype=torch.float64, device="cuda")
+    s.step("mala", 40, eps=0.3, samples=out)
+    mu_n, L_n, used = s.adapt_cov()
+    x = out.cpu().numpy().reshape(-1, 6)
+    assert np.allclose(mu_n, x.mean(axis=0), rtol=1e-10, atol=1e-12)
+    assert np.allclose(L_n @ L_n.T, np.cov(x.T), rtol=1e-9, atol=1e-12)
+    s.close()
+
+
+def test_adapt_cov_errors():
+    from paper_2606_04895_gb300 import BstError
+    s, *_ = _small("fp64")
+    s.welford_reset()
+    with pytest.raises(BstError, match="ERR_STATE"):
+        s.adapt_cov()
+    s.welford_add(torch.zeros((10, 6), dtype=torch.float64))  # zero covariance
+    with pytest.raises(BstError, match="ERR_NOT_PD"):
+        s.adapt_cov()
+    # rank-deficient (fewer samples than dims): rescued by the diagonal loading
+    s.welford_reset()
+    s.welford_add(torch.as_tensor(np.random.default_rng(0).normal(size=(4, 6))))
+    mu_n, L_n, used = s.adapt_cov(1e-10)
+    assert used > 0
+    s.close()
+
+
+def test_training_gradient_matches_oracle():
+    from paper_2606_04895_gb300 import Sampler
+    d, D, w = 8, 3, 256
+    e = S.emulator(d, width=w, depth=D, seed=3, out_m=200.0, out_s=50.0)
+    s = Sampler(d, 8, precision="fp32", likelihood="emulator")
+    s.set_emulator(e["params"], D, w, e["in_m"], e["in_s"], e["out_m"], e["out_s"])
+    X = np.random.default_rng(0).uniform(-3, 3, (777, d))
+    y = 200 + 50 * np.random.default_rng(1).normal(size=777)
+    loss, g = s.train_grad(torch.as_tensor(X, dtype=torch.float32, device="cuda"),
+                           torch.as_tensor(y, dtype=torch.float32, device="cuda"))
+    Xf = X.astype(np.float32).astype(np.float64)
+    yf = y.astype(np.float32).astype(np.float64)
+    Pf = e["params"].astype(np.float32).astype(np.float64)
+    lref, gref = O.train_loss_grad(d, D, w, Pf, e["in_m"], e["in_s"], e["out_m"], e["out_s"], Xf, yf)
+    assert abs(loss.item() - lref) / lref < 1e-4
+    assert rel_err(g.cpu().numpy(), gref) < 1e-3
+    s.close()
+
+
+def test_training_reduces_loss_and_updates_sampling_weights():
+    from paper_2606_04895_gb300 import Sampler
+    d, D, w = 4, 2, 256
+    e = S.emulator(d, width=w, depth=D, seed=3, out_m=10.0, out_s=5.0)
+    s = Sampler(d, 8, precision="fp32", likelihood="emulator")
+    s.set_emulator(e["params"], D, w, e["in_m"], e["in_s"], e["out_m"], e["out_s"])
+    X = torch.as_tensor(np.random.default_rng(0).uniform(-3, 3, (2048, d)), dtype=torch.float32, device="cuda")
+    y = (X ** 2).sum(dim=1) * 2.0
+    loss = torch.zeros(1, device="cuda")
+    losses = []
+    for it in range(200):
+        s.train_step(X, y, lr=3e-3, loss_out=loss)
+        losses.append(loss.item())
+    assert losses[-1] < 0.1 * losses[0]
+    P = s.get_emulator()
+    ref = O.Model(d, emulator=dict(e, params=P))
+    x = np.random.default_rng(5).uniform(-2, 2, (33, d))
+    rl, rg = ref.loglike(x)
+    ll, g = s.grad_loglike(x)
+    assert np.max(np.abs(ll.double().cpu().numpy() - rl) / np.maximum(1, np.abs(rl))) < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ess_matches_oracle(prec):
+    s, *_ = _small(prec, n=64)
+    rng = np.random.default_rng(0)
+    n = 600
+    phi = np.linspace(0.1, 0.9, 6)
+    x = np.zeros((n, 64, 6))
+    x[0] = rng.normal(size=(64, 6))
+    for t in range(1, n):
+        x[t] = phi * x[t - 1] + rng.normal(size=(64, 6))
+    xt = torch.as_tensor(x, dtype=s.dtype, device="cuda")
+    ess = s.ess(xt)
+    ref = O.ess(xt.double().cpu().numpy())
+    assert np.allclose(ess, ref, rtol=1e-9 if prec == "fp64" else 1e-4)
+    s.close()
+
+
+def test_autograd_function_gradient():
+    from paper_2606_04895_gb300 import emulator_logl
+    s, e, *_ = _small("fp64", n=8)
+    th = torch.tensor(np.random.default_rng(2).uniform(-2, 2, (5, 6)), dtype=torch.float64, device="cuda",
+                      requires_grad=True)
+    w = torch.arange(1, 6, dtype=torch.float64, device="cuda")
+    (emulator_logl(th, s) * w).sum().backward()
+    ref = O.Model(6, emulator=e)
+    _, rg = ref.loglike(th.detach().cpu().numpy())
+    assert np.allclose(th.grad.cpu().numpy(), rg * w.cpu().numpy()[:, None], rtol=1e-9, atol=1e-12)
+    # central finite differences through the forward op
+    h = 1e-5
+    x0 = th.detach().clone()
+    for i in range(6):
+        dx = torch.zeros_like(x0); dx[:, i] = h
+        fd = (s.loglike(x0 + dx) - s.loglike(x0 - dx)) / (2 * h)
+        assert np.allclose(fd.cpu().numpy(), rg[:, i], rtol=1e-6, atol=1e-8)
+    s.close()
