@@ -608,6 +608,7 @@ bst_status bst_get_emulator(bst_handle h, double *params) {
   }
   BST_CUDA(cudaDeviceSynchronize());
   BST_CUDA(cudaMemcpy(params, h->P64, h->nparams * 8, cudaMemcpyDeviceToHost));
+  h->bo = params[h->nparams - 1];
   return BST_OK;
 }
 
