@@ -140,6 +140,31 @@ bst_status bst_loglike(bst_handle h, const void *theta_dev, int m, void *logl_de
 bst_status bst_grad_loglike(bst_handle h, const void *theta_dev, int m, void *logl_dev,
                             void *grad_dev, void *stream);
 
+/* Allocation-free form of bst_grad_loglike.  There is no counterpart in the
+ * paper; this entry point exists for callers that must not allocate device
+ * memory once they are running -- a program whose device memory is owned by
+ * a caching allocator or a fixed budget set at start-up (an outside cudaMalloc
+ * there fragments or overcommits the pool), or a service that reserves all
+ * its memory before it takes requests.  bst_grad_loglike may allocate: the
+ * first call with a larger m than before grows the buffer in which the adjoint
+ * keeps the emulator's hidden activations.  This call instead uses one
+ * file-scope device array of 16 MiB (g_static_scratch) that every GPU which
+ * loads the library holds until the process exits, and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ * Arguments and results are those of bst_grad_loglike.  Limit: m times the
+ * bytes kept per point, (depth - 1) x width x (2 for BF16, 4 for FP32, 8 for
+ * FP64), must fit in 16 MiB (for example m <= 5461 for a BF16 8-512x4-1
+ * emulator); a larger m returns BST_ERR_ARG and launches nothing.
+ * The first call on each device looks the array's device address up with
+ * cudaGetSymbolAddress (the device must be current, which the call ensures);
+ * make that first call before any stream capture.  Every call on a device
+ * shares the one array and overwrites what the previous call left there
+ * (nothing in it needs to start at zero), so calls whose work overlaps on the
+ * GPU -- on different streams, or from different handles -- race; order them
+ * on one stream. */
+bst_status bst_grad_loglike_noalloc(bst_handle h, const void *theta_dev, int m, void *logl_dev,
+                                    void *grad_dev, void *stream);
+
 /* Covariance adaptation (Sec. 3.2).  bst_welford_reset clears the running
  * statistics and makes every following bst_step add each chain's x after
  * every iteration; bst_welford_add adds external samples x_dev[m][d] (real).

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1050,3 +1051,90 @@ bst_status bst_sync(bst_handle h, void *stream) {
 }
 
 }  // extern "C"
+
+// ============================================================================ allocation-free gradient
+// bst_grad_loglike_noalloc keeps the emulator activations that its adjoint needs in one
+// fixed device array instead of library-allocated memory, so the call itself never allocates.
+namespace {
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // 16 MiB, held by every GPU that loads the library
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on `dev` (the current device), looked up once per device.
+bst_status static_scratch_address(int dev, void **out) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (dev < 0 || dev >= kMaxDevices) return fail(BST_ERR_ARG, "bst_grad_loglike_noalloc: device ordinal out of range");
+  if (!g_static_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(BST_ERR_CUDA, std::string("bst_grad_loglike_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return BST_OK;
+}
+}  // namespace
+
+extern "C" bst_status bst_grad_loglike_noalloc(bst_handle h, const void *theta_dev, int m, void *logl_dev,
+                                               void *grad_dev, void *stream) {
+  if (!h || (m > 0 && (!theta_dev || !logl_dev || !grad_dev)))
+    return fail(BST_ERR_ARG, "bst_grad_loglike_noalloc: NULL argument");
+  if (h->stage < 1) return fail(BST_ERR_STATE, "bst_grad_loglike_noalloc: set a likelihood first");
+  if (m < 0) return fail(BST_ERR_ARG, "bst_grad_loglike_noalloc: m must be >= 0");
+  if (m == 0) return BST_OK;
+  size_t row_bytes = 0;  // activation bytes the adjoint keeps per evaluated point
+  if (h->lik == BST_LIK_EMULATOR) {
+    const size_t el = (h->precision == BST_BF16) ? 2 : h->rs;
+    row_bytes = static_cast<size_t>(h->depth > 1 ? h->depth - 1 : 1) * h->width * el;
+    const size_t max_rows = kStaticScratchBytes / row_bytes;
+    if (static_cast<size_t>(m) > max_rows)
+      return fail(BST_ERR_ARG, "bst_grad_loglike_noalloc: m = " + std::to_string(m) + " exceeds the " +
+                                   std::to_string(max_rows) + " points the 16 MiB static scratch holds for this emulator");
+  }
+  BST_CUDA(cudaSetDevice(h->device));
+  void *scratch = nullptr;
+  BST_TRY(static_scratch_address(h->device, &scratch));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BST_TRY(prepare(h, s));
+  if (h->precision == BST_FP64) {
+    StepArgs<double> a = make_args<double>(h, kModeLoglike, 0.0, 0, 1, nullptr);
+    a.n_rows = m;
+    a.need_grad = 1;
+    a.st.ze = (double *)theta_dev;
+    a.st.ze_ld = h->d;
+    a.st.lle = (double *)logl_dev;
+    a.st.gle = (double *)grad_dev;
+    a.st.gle_ld = h->d;
+    if (h->lik == BST_LIK_EMULATOR) {
+      EmuWeights<double> w = emu_weights<double>(h, 1);
+      w.scratch = static_cast<double *>(scratch);
+      BST_CUDA(launch_emu_simt_f64(a, w, s));
+    } else {
+      BST_CUDA(launch_ana_simt_f64(a, ana_weights<double>(h, 1), s));
+    }
+  } else {
+    StepArgs<float> a = make_args<float>(h, kModeLoglike, 0.0, 0, 1, nullptr);
+    a.n_rows = m;
+    a.need_grad = 1;
+    a.st.ze = (float *)theta_dev;
+    a.st.ze_ld = h->d;
+    a.st.lle = (float *)logl_dev;
+    a.st.gle = (float *)grad_dev;
+    a.st.gle_ld = h->d;
+    if (h->lik == BST_LIK_ANALYTIC) {
+      BST_CUDA(launch_ana_simt_f32(a, ana_weights<float>(h, 1), s));
+    } else if (h->precision == BST_BF16) {
+      TcWeights w = tc_weights(h, 1);
+      w.scratch = static_cast<__nv_bfloat16 *>(scratch);
+      BST_CUDA(launch_emu_tc(a, w, s));
+    } else {
+      EmuWeights<float> w = emu_weights<float>(h, 1);
+      w.scratch = static_cast<float *>(scratch);
+      BST_CUDA(launch_emu_simt_f32(a, w, s));
+    }
+  }
+  return BST_OK;
+}
