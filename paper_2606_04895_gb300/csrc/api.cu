@@ -71,7 +71,7 @@ struct bst_ctx {
   double *W1f[2] = {nullptr, nullptr}, *b1f[2] = {nullptr, nullptr};  // [0] z-space, [1] x-space
   void *sW1T[2] = {nullptr, nullptr}, *sW1[2] = {nullptr, nullptr}, *sb1[2] = {nullptr, nullptr};
   void *sWT = nullptr, *sW = nullptr, *sb = nullptr, *swo = nullptr;
-  uint8_t *tl1[2] = {nullptr, nullptr}, *tg1[2] = {nullptr, nullptr}, *thid = nullptr;
+  uint8_t *tl1[2][3] = {}, *tg1[2] = {nullptr, nullptr}, *thid[3] = {};  // [fold][cluster size 1/2/4]
   float *tb1[2] = {nullptr, nullptr}, *tb = nullptr, *two = nullptr;
   int kb1 = 1;
   void *scratch = nullptr;
@@ -243,15 +243,22 @@ EmuWeights<R> emu_weights(bst_ctx *h, int fold) {
   return w;
 }
 
-TcWeights tc_weights(bst_ctx *h, int fold) {
-  TcWeights w;
+int cs_index(int cs) { return cs == 4 ? 2 : (cs == 2 ? 1 : 0); }
+
+Tc2Weights tc2_weights(bst_ctx *h, int fold, int n_rows) {
+  Tc2Weights w;
+  const int cs = tc2_cluster_size(n_rows), ci = cs_index(cs);
   w.depth = h->depth;
   w.width = h->width;
   w.dp = h->dp;
   w.kb1 = h->kb1;
   w.k16_l1 = 3 * h->dp / 16;
-  w.l1 = h->tl1[fold];
-  w.hid = h->thid;
+  w.cs = cs;
+  const size_t ns = h->width / cs;
+  w.l1 = h->tl1[fold][ci];
+  w.l1_stride = ns * h->kb1 * 128;
+  w.hid = h->thid[ci];
+  w.hid_stride = 2 * static_cast<size_t>(h->depth > 1 ? h->depth - 1 : 0) * ns * h->width * 2;
   w.g1 = h->tg1[fold];
   w.b1 = h->tb1[fold];
   w.b = h->tb;
@@ -260,7 +267,7 @@ TcWeights tc_weights(bst_ctx *h, int fold) {
   w.out_m = static_cast<float>(h->out_m);
   w.out_s = static_cast<float>(h->out_s);
   w.scratch = static_cast<__nv_bfloat16 *>(h->scratch);
-  w.n_stages = tc_stages(h->width);
+  w.n_stages = tc2_stages(h->width, cs);
   return w;
 }
 
@@ -315,13 +322,23 @@ bst_status prepare(bst_ctx *h, cudaStream_t s) {
                                       (double *)h->sW1[f], (double *)h->sb1[f], (double *)h->sWT, (double *)h->sW,
                                       (double *)h->sb, (double *)h->swo, s));
       else {
-        BST_CUDA(launch_pack_tc_l1(h->W1f[f], dp, w, h->kb1, h->tl1[f], s));
+        for (int ci = 0; ci < 3; ++ci) {
+          const int cs = 1 << ci, ns = w / cs, tr = ns < 256 ? ns : 256;
+          for (int rk = 0; rk < cs; ++rk)
+            BST_CUDA(launch_pack_tc2_l1(h->W1f[f], dp, h->kb1, rk, ns, tr,
+                                        h->tl1[f][ci] + static_cast<size_t>(rk) * ns * h->kb1 * 128, s));
+        }
         BST_CUDA(launch_pack_tc_g1(h->W1f[f], dp, w, h->tg1[f], s));
         BST_CUDA(launch_cast_f32(h->b1f[f], h->tb1[f], w, s));
       }
     }
     if (h->precision == BST_BF16) {
-      BST_CUDA(launch_pack_tc_hidden(h->P64, d, D, w, h->thid, s));
+      for (int ci = 0; ci < 3; ++ci) {
+        const int cs = 1 << ci, ns = w / cs, tr = ns < 256 ? ns : 256;
+        const size_t stride = 2 * static_cast<size_t>(D > 1 ? D - 1 : 0) * ns * w * 2;
+        for (int rk = 0; rk < cs; ++rk)
+          BST_CUDA(launch_pack_tc2_hidden(h->P64, d, D, w, rk, ns, tr, h->thid[ci] + rk * stride, s));
+      }
       for (int l = 2; l <= D; ++l) {
         const size_t ob = static_cast<size_t>(d) * w + w + static_cast<size_t>(l - 2) * (static_cast<size_t>(w) * w + w) +
                           static_cast<size_t>(w) * w;
@@ -378,7 +395,7 @@ bst_status run(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_steps, vo
       a.st.gle_ld = h->d;
     }
     if (h->lik == BST_LIK_ANALYTIC) BST_CUDA(launch_ana_simt_f32(a, ana_weights<float>(h, fold), s));
-    else if (h->precision == BST_BF16) BST_CUDA(launch_emu_tc(a, tc_weights(h, fold), s));
+    else if (h->precision == BST_BF16) BST_CUDA(launch_emu_tc2(a, tc2_weights(h, fold, a.n_rows), s));
     else BST_CUDA(launch_emu_simt_f32(a, emu_weights<float>(h, fold), s));
   }
   return BST_OK;
@@ -550,11 +567,11 @@ bst_status bst_set_emulator(bst_handle h, int depth, int width, const double *pa
     }
     if (h->precision == BST_BF16) {
       for (int f = 0; f < 2; ++f) {
-        BST_TRY(dalloc(h, (void **)&h->tl1[f], (w / 256) * h->kb1 * static_cast<size_t>(kTcStageBytes)));
+        for (int ci = 0; ci < 3; ++ci) BST_TRY(dalloc(h, (void **)&h->tl1[f][ci], w * h->kb1 * 128));
         BST_TRY(dalloc(h, (void **)&h->tg1[f], (w / 64) * 2 * dp * 128));
         BST_TRY(dalloc_t(h, &h->tb1[f], w));
       }
-      BST_TRY(dalloc(h, (void **)&h->thid, 2 * nh * w * w * 2 + 16));
+      for (int ci = 0; ci < 3; ++ci) BST_TRY(dalloc(h, (void **)&h->thid[ci], 2 * nh * w * w * 2 + 16));
       BST_TRY(dalloc_t(h, &h->tb, nh * w + 1));
       BST_TRY(dalloc_t(h, &h->two, w));
     } else {
@@ -735,7 +752,7 @@ bst_status bst_step(bst_handle h, int kernel, double eps, int n_leapfrog, int n_
   if (kernel == BST_HMC && n_leapfrog < 1) return fail(BST_ERR_ARG, "bst_step: n_leapfrog must be >= 1");
   if (kernel == BST_AIES) {
     const int half = h->walkers / 2;
-    const int tile = (h->precision == BST_BF16) ? kTcRows : simt_rows_per_tile(h->precision, h->width, h->lik);
+    const int tile = (h->precision == BST_BF16) ? kTcRows : simt_rows_per_tile(h->precision, h->width, h->lik);  // chains per tile
     if (h->n % h->walkers) return fail(BST_ERR_ARG, "bst_step: AIES needs n_chains to be a multiple of aies_walkers");
     if (tile % half) return fail(BST_ERR_UNSUPPORTED, "bst_step: AIES ensemble halves must not span chain tiles");
   }
@@ -1127,9 +1144,9 @@ extern "C" bst_status bst_grad_loglike_noalloc(bst_handle h, const void *theta_d
     if (h->lik == BST_LIK_ANALYTIC) {
       BST_CUDA(launch_ana_simt_f32(a, ana_weights<float>(h, 1), s));
     } else if (h->precision == BST_BF16) {
-      TcWeights w = tc_weights(h, 1);
+      Tc2Weights w = tc2_weights(h, 1, m);
       w.scratch = static_cast<__nv_bfloat16 *>(scratch);
-      BST_CUDA(launch_emu_tc(a, w, s));
+      BST_CUDA(launch_emu_tc2(a, w, s));
     } else {
       EmuWeights<float> w = emu_weights<float>(h, 1);
       w.scratch = static_cast<float *>(scratch);

@@ -322,8 +322,8 @@ struct AnaSimt {
 // `nthr` threads of the owner group with a group barrier `sync`.
 template <typename R, class Sync>
 __device__ void welford_tile(const StepArgs<R> &a, int row0, int nrows, const int *mask, int t,
-                             int nthr, Sync sync) {
-  double *W = a.wf + static_cast<size_t>(blockIdx.x) * a.wf_stride;
+                             int nthr, Sync sync, int tile) {
+  double *W = a.wf + static_cast<size_t>(tile) * a.wf_stride;
   const int d = a.d;
   const R *xb = a.xbuf;
   if (t == 0) {
@@ -407,7 +407,8 @@ simt_chain_kernel(const StepArgs<R> a, const Weights W) {
     if (tid < T) mask[tid] = done ? 1 : 0;
     __syncthreads();
     if (a.welford_on && __syncthreads_or(done)) {
-      welford_tile(a, row0, min(T, a.n_rows - row0), mask, tid, kSimtThreads, [] { __syncthreads(); });
+      welford_tile(a, row0, min(T, a.n_rows - row0), mask, tid, kSimtThreads, [] { __syncthreads(); },
+                   static_cast<int>(blockIdx.x));
     }
   }
 }

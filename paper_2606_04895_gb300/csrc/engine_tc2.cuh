@@ -1,0 +1,578 @@
+// engine_tc2.cuh -- BF16 tcgen05 engine with the layer width split across a thread-block cluster.
+//
+// A tile of 128 chains is owned by a cluster of CS CTAs (CS = 1, 2 or 4).  CTA rank r of the
+// cluster computes output columns [r NS, (r + 1) NS) of every layer (NS = W / CS):
+//
+//   warp 0      producer: streams this rank's pre-swizzled BF16 weight tiles (TR rows x 64)
+//               into a ring of shared-memory stages with cp.async.bulk;
+//   warp 1      MMA issuer: tcgen05.mma M=128, N=TR, K=16, BF16 -> FP32 accumulators in TMEM;
+//   warps 2-9   epilogue: two warps per TMEM lane quadrant, each on half of the slice's
+//               columns.  Warps 2-5 of rank 0 also run the per-chain samplers (one thread
+//               per chain).
+//
+// Per layer every CTA holds the whole input activation (128 x W BF16, 128-byte-swizzled
+// K-major) in shared memory, multiplies it by its slice of the weights, runs the epilogue
+// on its NS columns, writes the BF16 result into its own activation buffer and copies that
+// slice into every peer's buffer with cp.async.bulk shared::cluster (completion counted on
+// the peer's mbarrier).  A peer's buffer is written only after the peer's MMAs of the layer
+// have finished reading it ("free" arrivals).  The output dot w_o . h_D is reduced across
+// the cluster in a fixed order on rank 0.  All waits are bounded by a time limit; a timeout
+// sets a status bit and every role leaves its loop; a cluster barrier precedes exit so no
+// CTA leaves while a peer may still touch its shared memory.
+#pragma once
+
+#include "common.cuh"
+#include "engine_simt.cuh"
+#include "engine_tc.cuh"
+#include "sampler.cuh"
+
+namespace bst {
+
+constexpr int kTc2Threads = 320;  // 10 warps
+constexpr int kTc2EpiThreads = 256;
+
+struct Tc2Weights {
+  int depth, width, dp, kb1, k16_l1;
+  int cs;             // cluster size
+  const uint8_t *l1;  // [cs] streams of layer-1 tiles (this launch's fold set)
+  size_t l1_stride;   // bytes per rank
+  const uint8_t *hid; // [cs] streams: hidden forward tiles then adjoint tiles
+  size_t hid_stride;
+  const uint8_t *g1;  // input-gradient tiles (shared by all ranks)
+  const float *b1;    // [w]
+  const float *b;     // [D-1][w]
+  const float *wo;    // [w]
+  float bo, out_m, out_s;
+  __nv_bfloat16 *scratch;  // [rows][D-1][w]
+  int n_stages;
+};
+
+// ---------------------------------------------------------------- cluster helpers
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank) {
+  uint32_t d;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(d) : "r"(saddr), "r"(rank));
+  return d;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, int *status) {
+  for (int i = 0; i < 256; ++i)
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      set_status(status, kStatusTimeout);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void bulk_s2cluster(uint32_t dst_cluster, uint32_t src_cta, uint32_t bytes,
+                                               uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          dst_cluster),
+      "r"(src_cta), "r"(bytes), "r"(bar_cluster)
+      : "memory");
+}
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;\n" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;\n" ::: "memory"); }
+__device__ __forceinline__ bool epi_or(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 256, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(pred ? 1u : 0u)
+      : "memory");
+  return r != 0;
+}
+// sampler subgroup (warps 2-5): named barrier 2
+__device__ __forceinline__ void smp_sync() { asm volatile("bar.sync 2, 128;\n" ::: "memory"); }
+__device__ __forceinline__ bool smp_or(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 2, 128, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(pred ? 1u : 0u)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;\n" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------- the kernel
+template <int W, int CS>
+__global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArgs<float> a, const Tc2Weights E) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  constexpr int KBW = W / 64;           // K blocks of the hidden width
+  constexpr int NS = W / CS;            // output columns of this rank
+  constexpr int TR = NS < 256 ? NS : 256;  // rows of a weight tile == MMA N
+  constexpr int NSUB = NS / TR;
+  constexpr int STAGE = TR * 128;
+  constexpr int SLICE_BYTES = 128 * NS * 2;  // one rank's slice of an activation
+  constexpr int TCOLS = NS < 64 ? 64 : NS;   // TMEM columns (>= 2 dp for the input gradient)
+  constexpr int CPW = NS / 2 / 32;           // 32-column chunks per epilogue warp
+
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *act = base;
+  uint8_t *stages = act + KBW * 16384;
+  const int S = E.n_stages;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(stages + S * STAGE);
+  // bars: full[S] empty[S] go act_full acc fin peer_free part
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S);
+  const uint32_t go_bar = smem_u32(bars + 2 * S), actf_bar = smem_u32(bars + 2 * S + 1);
+  const uint32_t acc_bar = smem_u32(bars + 2 * S + 2), fin_bar = smem_u32(bars + 2 * S + 3);
+  const uint32_t free_bar = smem_u32(bars + 2 * S + 4), part_bar = smem_u32(bars + 2 * S + 5);
+  volatile int *cmd = reinterpret_cast<volatile int *>(bars + 2 * S + 6);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 7);
+  float *partial = reinterpret_cast<float *>(bars + 2 * S + 8);  // [CS][128] (rank 0 gathers)
+  float *red = partial + CS * 128;                                // [128] column-half combine
+  int *mask = reinterpret_cast<int *>(red + 128);                 // [128]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = (CS > 1) ? cluster_rank() : 0u;
+  const int tile = blockIdx.x / CS;
+  const int D = E.depth, dp = E.dp;
+  const bool grad = a.need_grad != 0;
+  const int nph = tc_num_phases(D, grad);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(go_bar, 1);
+    mbar_init(actf_bar, 1);
+    mbar_init(acc_bar, 1);
+    mbar_init(fin_bar, 1);
+    mbar_init(free_bar, CS > 1 ? CS - 1 : 1);
+    mbar_init(part_bar, CS);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(static_cast<uint32_t>(TCOLS))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (CS > 1) cluster_sync_all();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t fills[kTcMaxStages + 2] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int s = 0;
+      uint32_t go_par = 0;
+      bool ok = true;
+      const uint8_t *l1 = E.l1 + rank * E.l1_stride;
+      const uint8_t *hid = E.hid + rank * E.hid_stride;
+      while (ok) {
+        if (!mbar_wait_cluster(go_bar, go_par, a.status)) break;
+        go_par ^= 1;
+        const int c = *cmd;
+        if (c == 0) break;
+        const bool g = c == 2;
+        const int n_l1 = NSUB * E.kb1, n_h = (D - 1) * NSUB * KBW;
+        const int n_tiles = n_l1 + n_h + (g ? n_h + KBW : 0);
+        for (int t = 0; t < n_tiles && ok; ++t) {
+          const uint8_t *src;
+          uint32_t bytes = STAGE;
+          if (t < n_l1) {
+            src = l1 + static_cast<size_t>(t) * STAGE;
+          } else if (t < n_l1 + (g ? 2 : 1) * n_h) {
+            src = hid + static_cast<size_t>(t - n_l1) * STAGE;
+          } else {
+            bytes = 2 * dp * 128;
+            src = E.g1 + static_cast<size_t>(t - n_l1 - 2 * n_h) * bytes;
+          }
+          if (!mbar_wait(empty0 + 8 * s, (fills[s] & 1) ^ 1, a.status)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(full0 + 8 * s, bytes);
+          bulk_g2s(smem_u32(stages + s * STAGE), src, bytes, full0 + 8 * s);
+          fills[s]++;
+          s = (s + 1 == S) ? 0 : s + 1;
+        }
+      }
+      for (int q = 0; q < S; ++q)
+        if (fills[q]) mbar_wait(full0 + 8 * q, (fills[q] - 1) & 1, a.status);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t uses[kTcMaxStages + 2] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int s = 0;
+      uint32_t go_par = 0, act_par = 0;
+      bool ok = true;
+      const uint32_t idn = idesc_bf16(128, TR), idg = idesc_bf16(128, 2 * dp);
+      const uint32_t act_addr = smem_u32(act);
+      while (ok) {
+        if (!mbar_wait_cluster(go_bar, go_par, a.status)) break;
+        go_par ^= 1;
+        const int c = *cmd;
+        if (c == 0) break;
+        const int phases = tc_num_phases(D, c == 2);
+        for (int p = 0; p < phases && ok; ++p) {
+          if (!mbar_wait_cluster(actf_bar, act_par, a.status)) {
+            ok = false;
+            break;
+          }
+          act_par ^= 1;
+          tc_fence_after();
+          const bool last = (p == 2 * D - 1);
+          const int nsub = last ? 1 : NSUB;
+          const int nkb = (p == 0) ? E.kb1 : KBW;
+          for (int sb = 0; sb < nsub && ok; ++sb) {
+            for (int kb = 0; kb < nkb; ++kb) {
+              if (!mbar_wait(full0 + 8 * s, uses[s] & 1, a.status)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t b_addr = smem_u32(stages + s * STAGE);
+              const int k16 = (p == 0) ? min(4, E.k16_l1 - 4 * kb) : 4;
+              for (int k = 0; k < k16; ++k) {
+                const uint64_t ad = sw128_desc(act_addr + kb * 16384 + k * 32);
+                const uint64_t bd = sw128_desc(b_addr + k * 32);
+                mma_bf16(tmem + sb * TR, ad, bd, last ? idg : idn, (kb > 0 || k > 0) ? 1u : 0u);
+              }
+              mma_commit(empty0 + 8 * s);
+              uses[s]++;
+              s = (s + 1 == S) ? 0 : s + 1;
+            }
+          }
+          if (ok) mma_commit(acc_bar);
+        }
+      }
+      mma_commit(fin_bar);
+      mbar_wait(fin_bar, 0, a.status);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue (+ samplers on rank 0)
+    const int e = warp - 2;              // 0..7
+    const int q = warp & 3;              // TMEM lane quadrant
+    const int ch = e >> 2;               // column half of the slice
+    const int r = q * 32 + lane;         // tile row == TMEM lane
+    const int row = tile * kTcRows + r;
+    const bool valid = row < a.n_rows;
+    const int t = e * 32 + lane;         // 0..255 within the epilogue group
+    const bool sampler = (rank == 0) && (ch == 0);
+    const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
+    const uint32_t act_addr = smem_u32(act);
+    const int col0 = static_cast<int>(rank) * NS + ch * (NS / 2);  // first global column of this warp
+    Chain<float> chn(a);
+    const bool loglike = a.mode == kModeLoglike;
+    if (sampler && valid && !loglike) {
+      if (a.mode == kModeAIES) {
+        for (int h = 0; h < 2; ++h) a.st.steps_done[chn.aies_walker(row, h)] = 0;
+      } else {
+        a.st.steps_done[row] = 0;
+        if (a.mode == kModeHMC) chn.dwork_ptr(row)[0] = 0.0;
+        if (a.mode == kModeNUTS) chn.dwork_ptr(row)[0] = 1.0;
+      }
+    }
+    epi_sync();
+    uint32_t acc_par = 0, go_par = 0, free_par = 0, part_par = 0;
+    const size_t sstride = static_cast<size_t>(D > 1 ? D - 1 : 1) * W;
+    const float c0 = -0.5f * E.out_s;
+    for (int ev = 0;; ++ev) {
+      const int h = ev & 1;
+      bool need = false;
+      // ---- proposal (rank 0) and the go signal to every CTA of the cluster
+      if (rank == 0) {
+        if (ev > 0) epi_sync();  // a proposal may read positions other threads just accepted (AIES)
+        if (sampler) {
+          if (loglike) need = valid && ev == 0;
+          else need = valid && chn.pre(row, h);
+        }
+        const bool any = epi_or(need);
+        if (t == 0) {
+          const int c = any ? (grad ? 2 : 1) : 0;
+          for (int pr = 0; pr < CS; ++pr) {
+            st_cluster_u32(mapa(smem_u32(const_cast<int *>(cmd)), pr), static_cast<uint32_t>(c));
+            mbar_arrive_cluster(mapa(go_bar, pr));
+          }
+        }
+      }
+      if (!mbar_wait_cluster(go_bar, go_par, a.status)) break;
+      go_par ^= 1;
+      const int c = *cmd;
+      if (c == 0) break;
+      // ---- layer-1 operand [z_hi | z_lo | z_hi | 0] from ze (written by rank 0's samplers)
+      {
+        const float *zr = a.st.ze + static_cast<size_t>(row) * a.st.ze_ld;
+        float zv[kMaxD];
+        for (int i = 0; i < dp; ++i) zv[i] = (valid && i < a.d) ? zr[i] : 0.f;
+        const int nch = E.kb1 * 8;  // 16-byte chunks in the row
+        for (int j = ch * (nch / 2); j < (ch + 1) * (nch / 2); ++j) {
+          uint32_t w4[4];
+          for (int e2 = 0; e2 < 4; ++e2) {
+            float v2[2];
+            for (int u = 0; u < 2; ++u) {
+              const int kk = j * 8 + e2 * 2 + u;
+              const int seg = kk / dp, i = kk % dp;
+              float v = 0.f;
+              if (seg < 3) {
+                const float hi = __bfloat162float(__float2bfloat16_rn(zv[i]));
+                v = (seg == 1) ? (zv[i] - hi) : hi;
+              }
+              v2[u] = v;
+            }
+            w4[e2] = pack_bf16x2(v2[0], v2[1]);
+          }
+          st_shared_v4(act_addr + (j >> 3) * 16384 + sw128_off(r, j & 7), w4[0], w4[1], w4[2], w4[3]);
+        }
+      }
+      fence_proxy_async();
+      epi_sync();
+      if (t == 0) mbar_arrive(actf_bar);
+      bool ok = true;
+      for (int p = 0; p < nph; ++p) {
+        const bool waited = mbar_wait(acc_bar, acc_par, a.status);
+        acc_par ^= 1;
+        if (epi_or(!waited)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const bool fwd = p < D;
+        const bool last_fwd = p == D - 1;
+        const bool distribute = (p + 1 < nph);  // this phase's output feeds another phase
+        // our MMAs of this phase are done: peers may write into our activation buffer
+        if (CS > 1 && distribute && t == 0)
+          for (int pr = 0; pr < CS; ++pr)
+            if (pr != static_cast<int>(rank)) mbar_arrive_cluster(mapa(free_bar, pr));
+        if (p == 2 * D - 1) {
+          // input gradient: g_i = acc[i] + acc[dp + i] (every rank computes it, rank 0 writes)
+          if (ch == 0) {
+            uint32_t v0[32], v1[32];
+            tmem_ld32_nowait(trow, v0);
+            if (dp > 16) tmem_ld32_nowait(trow + 32, v1);
+            tmem_wait_ld();
+            if (rank == 0 && valid) {
+              float *gout = a.st.gle + static_cast<size_t>(row) * a.st.gle_ld;
+              for (int i = 0; i < a.d; ++i) {
+                const int j2 = dp + i;
+                const float hi = __uint_as_float(v0[i]);
+                const float lo = __uint_as_float(j2 < 32 ? v0[j2] : v1[j2 - 32]);
+                gout[i] = hi + lo;
+              }
+            }
+          }
+        } else {
+          const int l = fwd ? p + 1 : 2 * D - p;  // layer index (adjoint: layer whose W^T is applied)
+          const float *bias = fwd ? (l == 1 ? E.b1 : E.b + static_cast<size_t>(l - 2) * W) : nullptr;
+          const __nv_bfloat16 *hprev =
+              (!fwd && valid) ? E.scratch + static_cast<size_t>(row) * sstride + static_cast<size_t>(l - 2) * W : nullptr;
+          __nv_bfloat16 *hkeep = (fwd && grad && !last_fwd && valid)
+                                     ? E.scratch + static_cast<size_t>(row) * sstride + static_cast<size_t>(l - 1) * W
+                                     : nullptr;
+          float part = 0.f;
+#pragma unroll 1
+          for (int cc = 0; cc < CPW; ++cc) {
+            const int gcol = col0 + cc * 32;                        // global column of the chunk
+            const int tcol = ch * (NS / 2) + cc * 32;               // TMEM column
+            uint32_t raw[32];
+            tmem_ld32_nowait(trow + tcol, raw);
+            float aux[32];
+            if (fwd) {
+              const float4 *bp = reinterpret_cast<const float4 *>(bias + gcol);
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const float4 b4 = __ldg(bp + u);
+                aux[4 * u] = b4.x;
+                aux[4 * u + 1] = b4.y;
+                aux[4 * u + 2] = b4.z;
+                aux[4 * u + 3] = b4.w;
+              }
+            } else {
+              uint4 hb[4];
+              if (hprev) {
+                const uint4 *hp = reinterpret_cast<const uint4 *>(hprev + gcol);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) hb[u] = hp[u];
+              } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) hb[u] = make_uint4(0, 0, 0, 0);
+              }
+              const __nv_bfloat16 *hh = reinterpret_cast<const __nv_bfloat16 *>(hb);
+#pragma unroll
+              for (int i = 0; i < 32; ++i) aux[i] = __bfloat162float(hh[i]);
+            }
+            tmem_wait_ld();
+            float v[32];
+            if (fwd) {
+              if (last_fwd) {
+                const float4 *wp = reinterpret_cast<const float4 *>(E.wo + gcol);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                  const float4 w4 = __ldg(wp + u);
+                  const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+                  for (int k = 0; k < 4; ++k) {
+                    const int i = 4 * u + k;
+                    // the last hidden layer feeds the FP32 output dot: accurate tanh
+                    const float hv = tanhf(__uint_as_float(raw[i]) + aux[i]);
+                    part = fmaf(wv[k], hv, part);
+                    v[i] = c0 * wv[k] * (1.f - hv * hv);
+                  }
+                }
+              } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = tanh_fast(__uint_as_float(raw[i]) + aux[i]);
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(raw[i]) * (1.f - aux[i] * aux[i]);
+            }
+            if (distribute) {
+              uint32_t pk[16];
+#pragma unroll
+              for (int i = 0; i < 16; ++i) pk[i] = pack_bf16x2(v[2 * i], v[2 * i + 1]);
+              const int kb = gcol >> 6;
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int jj = ((gcol & 63) >> 3) + u;
+                st_shared_v4(act_addr + kb * 16384 + sw128_off(r, jj), pk[4 * u], pk[4 * u + 1], pk[4 * u + 2],
+                             pk[4 * u + 3]);
+              }
+              if (hkeep) {
+                uint4 *dst = reinterpret_cast<uint4 *>(hkeep + gcol);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) dst[u] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+              }
+            }
+          }
+          if (last_fwd) {
+            // per-row partial of w_o . h_D over this rank's columns, gathered on rank 0
+            if (ch == 1) red[r] = part;
+            epi_sync();
+            if (ch == 0) st_cluster_f32(mapa(smem_u32(partial + rank * 128 + r), 0), part + red[r]);
+            epi_sync();
+            if (t == 0) mbar_arrive_cluster(mapa(part_bar, 0));
+          }
+        }
+        if (distribute) {
+          fence_proxy_async();
+          epi_sync();
+          if (t == 0) {
+            if (CS > 1) {
+              // wait until every peer's MMAs of this phase have released its buffer, then copy
+              if (!mbar_wait_cluster(free_bar, free_par, a.status)) ok = false;
+              free_par ^= 1;
+              const uint32_t off = static_cast<uint32_t>(rank) * SLICE_BYTES;  // slice = NS/64 K blocks
+              mbar_expect_tx(actf_bar, (CS - 1) * SLICE_BYTES);
+              if (ok)
+                for (int pr = 0; pr < CS; ++pr)
+                  if (pr != static_cast<int>(rank))
+                    bulk_s2cluster(mapa(act_addr + off, pr), act_addr + off, SLICE_BYTES, mapa(actf_bar, pr));
+            } else {
+              mbar_arrive(actf_bar);
+            }
+          }
+        }
+        tc_fence_before();
+        if (epi_or(!ok)) {
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) {
+        if (rank == 0 && t == 0)
+          for (int pr = 0; pr < CS; ++pr) {
+            st_cluster_u32(mapa(smem_u32(const_cast<int *>(cmd)), pr), 0u);
+            mbar_arrive_cluster(mapa(go_bar, pr));
+          }
+        break;
+      }
+      // ---- accept (rank 0): logL from the cluster-reduced output dot, then the samplers
+      if (rank == 0) {
+        const bool got = mbar_wait_cluster(part_bar, part_par, a.status);
+        part_par ^= 1;
+        if (sampler && valid && got) {
+          float s_out = 0.f;
+          for (int pr = 0; pr < CS; ++pr) s_out += partial[pr * 128 + r];
+          a.st.lle[row] = -0.5f * (E.out_s * (s_out + E.bo) + E.out_m);
+        }
+        epi_sync();
+        bool done = false;
+        if (sampler && need && !loglike) done = chn.post(row, h);
+        if (sampler && !loglike && a.welford_on) {
+          mask[r] = done ? 1 : 0;
+          smp_sync();
+          if (smp_or(done))
+            welford_tile(a, tile * kTcRows, min(kTcRows, a.n_rows - tile * kTcRows), mask, t, 128,
+                         [] { smp_sync(); }, tile);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (CS > 1) cluster_sync_all();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(static_cast<uint32_t>(TCOLS))
+                 : "memory");
+  }
+}
+
+inline size_t tc2_smem_bytes(int width, int cs, int stages) {
+  const int ns = width / cs, tr = ns < 256 ? ns : 256;
+  return 1024 + static_cast<size_t>(width / 64) * 16384 + static_cast<size_t>(stages) * tr * 128 +
+         8 * (2 * stages + 8) + 4 * (cs * 128 + 256) + 64;
+}
+inline int tc2_stages_for(int width, int cs, int smem_cap) {
+  for (int s = kTcMaxStages + 2; s >= 2; --s)
+    if (tc2_smem_bytes(width, cs, s) <= static_cast<size_t>(smem_cap)) return s;
+  return 2;
+}
+
+}  // namespace bst

@@ -115,70 +115,6 @@ __device__ __forceinline__ float bf16_hi(double v) {
   return __bfloat162float(__double2bfloat16(v));
 }
 
-// Layer-1 split tiles: B1s[k][kk], kk in [0, 64 kb1): [Wh(dp) | Wh(dp) | Wl(dp) | 0], ordered
-// (n-half, k-block).
-__global__ void pack_tc_l1_kernel(const double *W1f, int dp, int w, int kb1, uint8_t *out) {
-  const int nh_count = w / 256;
-  const size_t chunks = static_cast<size_t>(nh_count) * kb1 * 256 * 8;
-  const size_t id = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
-  if (id >= chunks) return;
-  const int j = static_cast<int>(id % 8), r = static_cast<int>((id / 8) % 256);
-  const int tile = static_cast<int>(id / (8 * 256));
-  const int nh = tile / kb1, kb = tile % kb1;
-  const int k = nh * 256 + r;
-  float v[8];
-  for (int e = 0; e < 8; ++e) {
-    const int kk = kb * 64 + j * 8 + e;
-    const int seg = kk / dp, i = kk % dp;
-    float x = 0.f;
-    if (seg < 3) {
-      const double wv = W1f[static_cast<size_t>(k) * dp + i];
-      const float hi = bf16_hi(wv);
-      x = (seg == 2) ? static_cast<float>(wv - static_cast<double>(hi)) : hi;
-    }
-    v[e] = x;
-  }
-  put_chunk(out + static_cast<size_t>(tile) * kTcStageBytes, r, j, v);
-}
-cudaError_t launch_pack_tc_l1(const double *W1f, int dp, int w, int kb1, uint8_t *out, cudaStream_t s) {
-  const size_t chunks = static_cast<size_t>(w / 256) * kb1 * 256 * 8;
-  pack_tc_l1_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(W1f, dp, w, kb1, out);
-  return cudaGetLastError();
-}
-
-// Hidden tiles: forward layers 2..D (tile rows = output units, cols = inputs), then adjoint
-// layers D..2 with W_l^T (rows = inputs, cols = output units); each (n-half, k-block).
-__global__ void pack_tc_hidden_kernel(const double *P, int d, int D, int w, uint8_t *out) {
-  const int nh_count = w / 256, kbw = w / 64;
-  const size_t per_layer = static_cast<size_t>(nh_count) * kbw;
-  const size_t chunks = 2 * static_cast<size_t>(D - 1) * per_layer * 256 * 8;
-  const size_t id = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
-  if (id >= chunks) return;
-  const int j = static_cast<int>(id % 8), r = static_cast<int>((id / 8) % 256);
-  const size_t tile = id / (8 * 256);
-  const size_t seg = tile / per_layer;  // 0..2(D-1)-1
-  const int within = static_cast<int>(tile % per_layer);
-  const int nh = within / kbw, kb = within % kbw;
-  const bool adj = seg >= static_cast<size_t>(D - 1);
-  const int l = adj ? D - static_cast<int>(seg - (D - 1)) : static_cast<int>(seg) + 2;
-  const double *Wl = P + off_W(l, d, w);
-  const int row = nh * 256 + r;
-  __nv_bfloat16 hb[8];
-  for (int e = 0; e < 8; ++e) {
-    const int col = kb * 64 + j * 8 + e;
-    const double x = adj ? Wl[static_cast<size_t>(col) * w + row] : Wl[static_cast<size_t>(row) * w + col];
-    hb[e] = __double2bfloat16(x);
-  }
-  *reinterpret_cast<uint4 *>(out + tile * kTcStageBytes + r * 128 + ((j ^ (r & 7)) << 4)) =
-      *reinterpret_cast<uint4 *>(hb);
-}
-cudaError_t launch_pack_tc_hidden(const double *P, int d, int D, int w, uint8_t *out, cudaStream_t s) {
-  if (D < 2) return cudaSuccess;
-  const size_t chunks = 2 * static_cast<size_t>(D - 1) * (w / 256) * (w / 64) * 256 * 8;
-  pack_tc_hidden_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(P, d, D, w, out);
-  return cudaGetLastError();
-}
-
 // Input-gradient split tiles: rows [W1f^T hi (dp rows); W1f^T lo (dp rows)], cols = hidden
 // units, one tile of 2 dp rows per 64-column k-block.
 __global__ void pack_tc_g1_kernel(const double *W1f, int dp, int w, uint8_t *out) {
@@ -201,6 +137,69 @@ __global__ void pack_tc_g1_kernel(const double *W1f, int dp, int w, uint8_t *out
 cudaError_t launch_pack_tc_g1(const double *W1f, int dp, int w, uint8_t *out, cudaStream_t s) {
   const size_t chunks = static_cast<size_t>(w / 64) * 2 * dp * 8;
   pack_tc_g1_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(W1f, dp, w, out);
+  return cudaGetLastError();
+}
+
+// Per-rank streams for the cluster kernel: rank r owns output rows [r NS, (r + 1) NS) of
+// every layer, packed as tiles of TR rows x 64 columns (same swizzle as above).
+__global__ void pack_tc2_l1_kernel(const double *W1f, int dp, int kb1, int rank, int NS, int TR, uint8_t *out) {
+  const int nsub = NS / TR;
+  const size_t chunks = static_cast<size_t>(nsub) * kb1 * TR * 8;
+  const size_t id = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (id >= chunks) return;
+  const int j = static_cast<int>(id % 8), r = static_cast<int>((id / 8) % TR);
+  const int tile = static_cast<int>(id / (8 * static_cast<size_t>(TR)));
+  const int sub = tile / kb1, kb = tile % kb1;
+  const int k = rank * NS + sub * TR + r;
+  float v[8];
+  for (int e = 0; e < 8; ++e) {
+    const int kk = kb * 64 + j * 8 + e;
+    const int seg = kk / dp, i = kk % dp;
+    float x = 0.f;
+    if (seg < 3) {
+      const double wv = W1f[static_cast<size_t>(k) * dp + i];
+      const float hi = bf16_hi(wv);
+      x = (seg == 2) ? static_cast<float>(wv - static_cast<double>(hi)) : hi;
+    }
+    v[e] = x;
+  }
+  put_chunk(out + static_cast<size_t>(tile) * TR * 128, r, j, v);
+}
+cudaError_t launch_pack_tc2_l1(const double *W1f, int dp, int kb1, int rank, int NS, int TR, uint8_t *out,
+                               cudaStream_t s) {
+  const size_t chunks = static_cast<size_t>(NS / TR) * kb1 * TR * 8;
+  pack_tc2_l1_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(W1f, dp, kb1, rank, NS, TR, out);
+  return cudaGetLastError();
+}
+
+__global__ void pack_tc2_hidden_kernel(const double *P, int d, int D, int w, int rank, int NS, int TR, uint8_t *out) {
+  const int nsub = NS / TR, kbw = w / 64;
+  const size_t per_layer = static_cast<size_t>(nsub) * kbw;
+  const size_t chunks = 2 * static_cast<size_t>(D - 1) * per_layer * TR * 8;
+  const size_t id = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (id >= chunks) return;
+  const int j = static_cast<int>(id % 8), r = static_cast<int>((id / 8) % TR);
+  const size_t tile = id / (8 * static_cast<size_t>(TR));
+  const size_t seg = tile / per_layer;
+  const int within = static_cast<int>(tile % per_layer);
+  const int sub = within / kbw, kb = within % kbw;
+  const bool adj = seg >= static_cast<size_t>(D - 1);
+  const int l = adj ? D - static_cast<int>(seg - (D - 1)) : static_cast<int>(seg) + 2;
+  const double *Wl = P + off_W(l, d, w);
+  const int row = rank * NS + sub * TR + r;
+  __nv_bfloat16 hb[8];
+  for (int e = 0; e < 8; ++e) {
+    const int col = kb * 64 + j * 8 + e;
+    const double x = adj ? Wl[static_cast<size_t>(col) * w + row] : Wl[static_cast<size_t>(row) * w + col];
+    hb[e] = __double2bfloat16(x);
+  }
+  *reinterpret_cast<uint4 *>(out + tile * TR * 128 + r * 128 + ((j ^ (r & 7)) << 4)) = *reinterpret_cast<uint4 *>(hb);
+}
+cudaError_t launch_pack_tc2_hidden(const double *P, int d, int D, int w, int rank, int NS, int TR, uint8_t *out,
+                                   cudaStream_t s) {
+  if (D < 2) return cudaSuccess;
+  const size_t chunks = 2 * static_cast<size_t>(D - 1) * (NS / TR) * (w / 64) * TR * 8;
+  pack_tc2_hidden_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(P, d, D, w, rank, NS, TR, out);
   return cudaGetLastError();
 }
 

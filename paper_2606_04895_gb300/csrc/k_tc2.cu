@@ -1,0 +1,86 @@
+// k_tc2.cu -- instantiations and launch wrappers of the cluster tcgen05 chain-tile kernel.
+#include "launch.h"
+
+namespace bst {
+
+namespace {
+constexpr int kSmemCap = 232448;
+constexpr int kNumSMs = 152;
+
+template <int W, int CS>
+cudaError_t launch_one(const StepArgs<float> &a, const Tc2Weights &w, cudaStream_t s) {
+  const int tiles = (a.n_rows + kTcRows - 1) / kTcRows;
+  if (tiles == 0) return cudaSuccess;
+  const size_t smem = tc2_smem_bytes(W, CS, w.n_stages);
+  auto k = tc2_chain_kernel<W, CS>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  if (CS > 1) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tiles * CS, 1, 1);
+  cfg.blockDim = dim3(kTc2Threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, k, a, w);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+}  // namespace
+
+int tc2_stages(int width, int cs) { return tc2_stages_for(width, cs, kSmemCap); }
+
+// Clusters of this configuration that can be co-resident (diagnostic).
+int tc2_max_active_clusters(int width, int cs) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(kTc2Threads, 1, 1);
+  cfg.gridDim = dim3(cs * 64, 1, 1);
+  cfg.dynamicSmemBytes = tc2_smem_bytes(width, cs, tc2_stages(width, cs));
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = -1;
+  const void *k = nullptr;
+  if (width == 512) k = cs == 4 ? (const void *)tc2_chain_kernel<512, 4> : cs == 2 ? (const void *)tc2_chain_kernel<512, 2> : (const void *)tc2_chain_kernel<512, 1>;
+  else k = cs == 4 ? (const void *)tc2_chain_kernel<256, 4> : cs == 2 ? (const void *)tc2_chain_kernel<256, 2> : (const void *)tc2_chain_kernel<256, 1>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(cfg.dynamicSmemBytes));
+  if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) return -1;
+  return n;
+}
+
+// Split a layer across more CTAs while there are fewer 128-chain tiles than SMs.
+int tc2_cluster_size(int n_rows) {
+  const int tiles = (n_rows + kTcRows - 1) / kTcRows;
+  if (4 * tiles <= kNumSMs) return 4;
+  if (2 * tiles <= kNumSMs) return 2;
+  return 1;
+}
+
+cudaError_t launch_emu_tc2(const StepArgs<float> &a, const Tc2Weights &w, cudaStream_t s) {
+  if (w.width == 512) {
+    if (w.cs == 4) return launch_one<512, 4>(a, w, s);
+    if (w.cs == 2) return launch_one<512, 2>(a, w, s);
+    return launch_one<512, 1>(a, w, s);
+  }
+  if (w.width == 256) {
+    if (w.cs == 4) return launch_one<256, 4>(a, w, s);
+    if (w.cs == 2) return launch_one<256, 2>(a, w, s);
+    return launch_one<256, 1>(a, w, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace bst

@@ -7,18 +7,20 @@
 #include "common.cuh"
 #include "engine_simt.cuh"
 #include "engine_tc.cuh"
+#include "engine_tc2.cuh"
 
 namespace bst {
 
-// Chain-tile step / evaluation launches (k_step.cu).
+// Chain-tile step / evaluation launches (k_simt.cu, k_tc2.cu).
 cudaError_t launch_emu_simt_f32(const StepArgs<float> &a, const EmuWeights<float> &w, cudaStream_t s);
 cudaError_t launch_emu_simt_f64(const StepArgs<double> &a, const EmuWeights<double> &w, cudaStream_t s);
 cudaError_t launch_ana_simt_f32(const StepArgs<float> &a, const AnaWeights<float> &w, cudaStream_t s);
 cudaError_t launch_ana_simt_f64(const StepArgs<double> &a, const AnaWeights<double> &w, cudaStream_t s);
-cudaError_t launch_emu_tc(const StepArgs<float> &a, const TcWeights &w, cudaStream_t s);
 int simt_rows_per_tile(int precision, int width, int lik_kind);
-size_t tc_smem_for(int width);
-int tc_stages(int width);
+// cluster tcgen05 kernel: cs in {1, 2, 4}
+cudaError_t launch_emu_tc2(const StepArgs<float> &a, const Tc2Weights &w, cudaStream_t s);
+int tc2_stages(int width, int cs);
+int tc2_cluster_size(int n_rows);
 
 // Weight preparation (k_aux.cu).
 // Fold whitening / standardisation into layer 1 (FP64 out): z-space (mode 0) or x-space (mode 1).
@@ -34,8 +36,10 @@ cudaError_t launch_pack_simt_f64(const double *P, const double *W1f, const doubl
                                  double *wo, cudaStream_t s);
 // BF16 tensor-core tiles (pre-swizzled): layer-1 split tiles, hidden fwd + adjoint tiles,
 // input-gradient split tiles; FP32 biases.
-cudaError_t launch_pack_tc_l1(const double *W1f, int dp, int w, int kb1, uint8_t *out, cudaStream_t s);
-cudaError_t launch_pack_tc_hidden(const double *P, int d, int D, int w, uint8_t *out, cudaStream_t s);
+cudaError_t launch_pack_tc2_l1(const double *W1f, int dp, int kb1, int rank, int NS, int TR, uint8_t *out,
+                               cudaStream_t s);
+cudaError_t launch_pack_tc2_hidden(const double *P, int d, int D, int w, int rank, int NS, int TR, uint8_t *out,
+                                   cudaStream_t s);
 cudaError_t launch_pack_tc_g1(const double *W1f, int dp, int w, uint8_t *out, cudaStream_t s);
 cudaError_t launch_cast_f32(const double *src, float *dst, size_t n, cudaStream_t s);
 cudaError_t launch_cast_f64(const double *src, double *dst, size_t n, cudaStream_t s);
