@@ -12,7 +12,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/bst.h"
+#include "bst.h"  // include/ is on the include path
 
 namespace bst {
 

@@ -28,8 +28,9 @@
 
 namespace bst {
 
-constexpr int kTc2Threads = 320;  // 10 warps
-constexpr int kTc2EpiThreads = 256;
+constexpr int kTc2EQ = 2;                       // epilogue warps per TMEM lane quadrant
+constexpr int kTc2EpiThreads = 128 * kTc2EQ;    // 256
+constexpr int kTc2Threads = 64 + kTc2EpiThreads;  // producer warp, MMA warp, epilogue warps
 
 struct Tc2Weights {
   int depth, width, dp, kb1, k16_l1;
@@ -140,6 +141,18 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+// Wait for outstanding tcgen05.ld and make the destination registers depend on the wait, so
+// the compiler cannot read them before the data has arrived.
+__device__ __forceinline__ void tmem_wait_ld_regs(uint32_t *r) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+        "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+        "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+        "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+      :
+      : "memory");
+}
 
 // ---------------------------------------------------------------- the kernel
 template <int W, int CS>
@@ -152,7 +165,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
   constexpr int STAGE = TR * 128;
   constexpr int SLICE_BYTES = 128 * NS * 2;  // one rank's slice of an activation
   constexpr int TCOLS = NS < 64 ? 64 : NS;   // TMEM columns (>= 2 dp for the input gradient)
-  constexpr int CPW = NS / 2 / 32;           // 32-column chunks per epilogue warp
+  constexpr int CW = NS / kTc2EQ;            // slice columns per epilogue warp
+  constexpr int CPW = CW / 32;               // 32-column chunks per epilogue warp
 
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *act = base;
@@ -167,8 +181,9 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
   volatile int *cmd = reinterpret_cast<volatile int *>(bars + 2 * S + 6);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 7);
   float *partial = reinterpret_cast<float *>(bars + 2 * S + 8);  // [CS][128] (rank 0 gathers)
-  float *red = partial + CS * 128;                                // [128] column-half combine
-  int *mask = reinterpret_cast<int *>(red + 128);                 // [128]
+  float *red = partial + CS * 128;                                // [EQ-1][128] column-group combine
+  int *mask = reinterpret_cast<int *>(red + (kTc2EQ - 1) * 128);  // [128]
+  float *sbias = reinterpret_cast<float *>(mask + 128);           // [D + 1][NS]: b_1..b_D, w_o slices
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = (CS > 1) ? cluster_rank() : 0u;
@@ -196,6 +211,13 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
+  {
+    const int c0g = static_cast<int>(rank) * NS;
+    for (int i = threadIdx.x; i < (D + 1) * NS; i += kTc2Threads) {
+      const int l = i / NS, j = c0g + i % NS;  // l = 0..D-1: bias of layer l+1; l = D: w_o
+      sbias[i] = (l == 0) ? E.b1[j] : (l < D ? E.b[static_cast<size_t>(l - 1) * W + j] : E.wo[j]);
+    }
+  }
   tc_fence_before();
   __syncthreads();
   if (CS > 1) cluster_sync_all();
@@ -206,42 +228,45 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       uint32_t fills[kTcMaxStages + 2] = {0, 0, 0, 0, 0, 0, 0, 0};
-      int s = 0;
       uint32_t go_par = 0;
       bool ok = true;
       const uint8_t *l1 = E.l1 + rank * E.l1_stride;
       const uint8_t *hid = E.hid + rank * E.hid_stride;
+      const int rot = tile % KBW;  // clusters start each layer at different K blocks (spreads L2 reads)
+      uint32_t tcount = 0;           // tiles of every evaluation so far (stage ring position)
       while (ok) {
         if (!mbar_wait_cluster(go_bar, go_par, a.status)) break;
         go_par ^= 1;
         const int c = *cmd;
         if (c == 0) break;
-        const bool g = c == 2;
-        const int n_l1 = NSUB * E.kb1, n_h = (D - 1) * NSUB * KBW;
-        const int n_tiles = n_l1 + n_h + (g ? n_h + KBW : 0);
-        for (int t = 0; t < n_tiles && ok; ++t) {
-          const uint8_t *src;
-          uint32_t bytes = STAGE;
-          if (t < n_l1) {
-            src = l1 + static_cast<size_t>(t) * STAGE;
-          } else if (t < n_l1 + (g ? 2 : 1) * n_h) {
-            src = hid + static_cast<size_t>(t - n_l1) * STAGE;
-          } else {
-            bytes = 2 * dp * 128;
-            src = E.g1 + static_cast<size_t>(t - n_l1 - 2 * n_h) * bytes;
-          }
-          if (!mbar_wait(empty0 + 8 * s, (fills[s] & 1) ^ 1, a.status)) {
-            ok = false;
-            break;
-          }
-          mbar_expect_tx(full0 + 8 * s, bytes);
-          bulk_g2s(smem_u32(stages + s * STAGE), src, bytes, full0 + 8 * s);
-          fills[s]++;
-          s = (s + 1 == S) ? 0 : s + 1;
+        const int phases = tc_num_phases(D, c == 2);
+        for (int p = 0; p < phases && ok; ++p) {
+          const bool last = (p == 2 * D - 1);
+          const int nsub = last ? 1 : NSUB;
+          const int nkb = (p == 0) ? E.kb1 : KBW;
+          const uint32_t bytes = last ? 2 * dp * 128 : STAGE;
+          if (!ok) break;
+          for (int sb = 0; sb < nsub && ok; ++sb)
+            for (int j = 0; j < nkb; ++j) {
+              const int kb = (p == 0) ? j : (j + rot) % KBW;
+              const int s = tcount % S;
+              ++tcount;
+              const uint8_t *src;
+              if (p == 0) src = l1 + static_cast<size_t>(sb * nkb + kb) * STAGE;
+              else if (!last) src = hid + (static_cast<size_t>(p - 1) * NSUB * KBW + sb * KBW + kb) * STAGE;
+              else src = E.g1 + static_cast<size_t>(kb) * bytes;
+              if (!mbar_wait(empty0 + 8 * s, (fills[s] & 1) ^ 1, a.status)) {
+                ok = false;
+                break;
+              }
+              mbar_expect_tx(full0 + 8 * s, bytes);
+              bulk_g2s(smem_u32(stages + s * STAGE), src, bytes, full0 + 8 * s);
+              fills[s]++;
+            }
         }
       }
-      for (int q = 0; q < S; ++q)
-        if (fills[q]) mbar_wait(full0 + 8 * q, (fills[q] - 1) & 1, a.status);
+      for (int q2 = 0; q2 < S; ++q2)
+        if (fills[q2]) mbar_wait(full0 + 8 * q2, (fills[q2] - 1) & 1, a.status);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -252,6 +277,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
       bool ok = true;
       const uint32_t idn = idesc_bf16(128, TR), idg = idesc_bf16(128, 2 * dp);
       const uint32_t act_addr = smem_u32(act);
+      const int rot = tile % KBW;
       while (ok) {
         if (!mbar_wait_cluster(go_bar, go_par, a.status)) break;
         go_par ^= 1;
@@ -269,7 +295,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
           const int nsub = last ? 1 : NSUB;
           const int nkb = (p == 0) ? E.kb1 : KBW;
           for (int sb = 0; sb < nsub && ok; ++sb) {
-            for (int kb = 0; kb < nkb; ++kb) {
+            for (int j = 0; j < nkb; ++j) {
+              const int kb = (p == 0) ? j : (j + rot) % KBW;
               if (!mbar_wait(full0 + 8 * s, uses[s] & 1, a.status)) {
                 ok = false;
                 break;
@@ -280,7 +307,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
               for (int k = 0; k < k16; ++k) {
                 const uint64_t ad = sw128_desc(act_addr + kb * 16384 + k * 32);
                 const uint64_t bd = sw128_desc(b_addr + k * 32);
-                mma_bf16(tmem + sb * TR, ad, bd, last ? idg : idn, (kb > 0 || k > 0) ? 1u : 0u);
+                mma_bf16(tmem + sb * TR, ad, bd, last ? idg : idn, (j > 0 || k > 0) ? 1u : 0u);
               }
               mma_commit(empty0 + 8 * s);
               uses[s]++;
@@ -296,17 +323,17 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue (+ samplers on rank 0)
-    const int e = warp - 2;              // 0..7
+    const int e = warp - 2;              // 0..4 EQ - 1
     const int q = warp & 3;              // TMEM lane quadrant
-    const int ch = e >> 2;               // column half of the slice
+    const int ch = e >> 2;               // column group of the slice
     const int r = q * 32 + lane;         // tile row == TMEM lane
     const int row = tile * kTcRows + r;
     const bool valid = row < a.n_rows;
-    const int t = e * 32 + lane;         // 0..255 within the epilogue group
+    const int t = e * 32 + lane;         // index within the epilogue group
     const bool sampler = (rank == 0) && (ch == 0);
     const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
     const uint32_t act_addr = smem_u32(act);
-    const int col0 = static_cast<int>(rank) * NS + ch * (NS / 2);  // first global column of this warp
+    const int col0 = static_cast<int>(rank) * NS + ch * CW;  // first global column of this warp
     Chain<float> chn(a);
     const bool loglike = a.mode == kModeLoglike;
     if (sampler && valid && !loglike) {
@@ -351,7 +378,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         float zv[kMaxD];
         for (int i = 0; i < dp; ++i) zv[i] = (valid && i < a.d) ? zr[i] : 0.f;
         const int nch = E.kb1 * 8;  // 16-byte chunks in the row
-        for (int j = ch * (nch / 2); j < (ch + 1) * (nch / 2); ++j) {
+        for (int j = ch * (nch / kTc2EQ); j < (ch + 1) * (nch / kTc2EQ); ++j) {
           uint32_t w4[4];
           for (int e2 = 0; e2 < 4; ++e2) {
             float v2[2];
@@ -375,6 +402,18 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
       if (t == 0) mbar_arrive(actf_bar);
       bool ok = true;
       for (int p = 0; p < nph; ++p) {
+        // adjoint phases read the stored activation h_{l-1}: start loading its first chunk now
+        const bool adj_phase = (p >= D) && (p != 2 * D - 1);
+        const __nv_bfloat16 *hprev =
+            (adj_phase && valid)
+                ? E.scratch + static_cast<size_t>(row) * sstride + static_cast<size_t>(2 * D - p - 2) * W
+                : nullptr;
+        uint4 hcur[4];
+        {
+          const uint4 *hp = hprev ? reinterpret_cast<const uint4 *>(hprev + col0) : nullptr;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) hcur[u] = hp ? hp[u] : make_uint4(0, 0, 0, 0);
+        }
         const bool waited = mbar_wait(acc_bar, acc_par, a.status);
         acc_par ^= 1;
         if (epi_or(!waited)) {
@@ -408,9 +447,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
           }
         } else {
           const int l = fwd ? p + 1 : 2 * D - p;  // layer index (adjoint: layer whose W^T is applied)
-          const float *bias = fwd ? (l == 1 ? E.b1 : E.b + static_cast<size_t>(l - 2) * W) : nullptr;
-          const __nv_bfloat16 *hprev =
-              (!fwd && valid) ? E.scratch + static_cast<size_t>(row) * sstride + static_cast<size_t>(l - 2) * W : nullptr;
+          const float *bias = fwd ? sbias + (l - 1) * NS + ch * CW : nullptr;  // this warp's columns
+          const float *wos = sbias + D * NS + ch * CW;
           __nv_bfloat16 *hkeep = (fwd && grad && !last_fwd && valid)
                                      ? E.scratch + static_cast<size_t>(row) * sstride + static_cast<size_t>(l - 1) * W
                                      : nullptr;
@@ -418,42 +456,43 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
 #pragma unroll 1
           for (int cc = 0; cc < CPW; ++cc) {
             const int gcol = col0 + cc * 32;                        // global column of the chunk
-            const int tcol = ch * (NS / 2) + cc * 32;               // TMEM column
+            const int tcol = ch * CW + cc * 32;                     // TMEM column
             uint32_t raw[32];
             tmem_ld32_nowait(trow + tcol, raw);
+            tmem_wait_ld_regs(raw);
             float aux[32];
+            uint4 hnext[4];
             if (fwd) {
-              const float4 *bp = reinterpret_cast<const float4 *>(bias + gcol);
+              const float4 *bp = reinterpret_cast<const float4 *>(bias + cc * 32);
 #pragma unroll
               for (int u = 0; u < 8; ++u) {
-                const float4 b4 = __ldg(bp + u);
+                const float4 b4 = bp[u];
                 aux[4 * u] = b4.x;
                 aux[4 * u + 1] = b4.y;
                 aux[4 * u + 2] = b4.z;
                 aux[4 * u + 3] = b4.w;
               }
             } else {
-              uint4 hb[4];
-              if (hprev) {
-                const uint4 *hp = reinterpret_cast<const uint4 *>(hprev + gcol);
+              // stored activations of this chunk were loaded one chunk ahead; start the next one
+              const bool more = hprev && cc + 1 < CPW;
+              const uint4 *hp = more ? reinterpret_cast<const uint4 *>(hprev + gcol + 32) : nullptr;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) hb[u] = hp[u];
-              } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) hb[u] = make_uint4(0, 0, 0, 0);
-              }
-              const __nv_bfloat16 *hh = reinterpret_cast<const __nv_bfloat16 *>(hb);
+              for (int u = 0; u < 4; ++u) hnext[u] = more ? hp[u] : make_uint4(0, 0, 0, 0);
+              const __nv_bfloat16 *hh = reinterpret_cast<const __nv_bfloat16 *>(hcur);
 #pragma unroll
               for (int i = 0; i < 32; ++i) aux[i] = __bfloat162float(hh[i]);
             }
-            tmem_wait_ld();
+            if (!fwd) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) hcur[u] = hnext[u];
+            }
             float v[32];
             if (fwd) {
               if (last_fwd) {
-                const float4 *wp = reinterpret_cast<const float4 *>(E.wo + gcol);
+                const float4 *wp = reinterpret_cast<const float4 *>(wos + cc * 32);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                  const float4 w4 = __ldg(wp + u);
+                  const float4 w4 = wp[u];
                   const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
                   for (int k = 0; k < 4; ++k) {
@@ -492,9 +531,13 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
           }
           if (last_fwd) {
             // per-row partial of w_o . h_D over this rank's columns, gathered on rank 0
-            if (ch == 1) red[r] = part;
+            if (ch > 0) red[(ch - 1) * 128 + r] = part;
             epi_sync();
-            if (ch == 0) st_cluster_f32(mapa(smem_u32(partial + rank * 128 + r), 0), part + red[r]);
+            if (ch == 0) {
+              float tot = part;
+              for (int g2 = 1; g2 < kTc2EQ; ++g2) tot += red[(g2 - 1) * 128 + r];
+              st_cluster_f32(mapa(smem_u32(partial + rank * 128 + r), 0), tot);
+            }
             epi_sync();
             if (t == 0) mbar_arrive_cluster(mapa(part_bar, 0));
           }
@@ -567,7 +610,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
 inline size_t tc2_smem_bytes(int width, int cs, int stages) {
   const int ns = width / cs, tr = ns < 256 ? ns : 256;
   return 1024 + static_cast<size_t>(width / 64) * 16384 + static_cast<size_t>(stages) * tr * 128 +
-         8 * (2 * stages + 8) + 4 * (cs * 128 + 256) + 64;
+         8 * (2 * stages + 8) + 4 * (cs * 128 + kTc2EQ * 128) + 4 * 9 * ns + 64;
 }
 inline int tc2_stages_for(int width, int cs, int smem_cap) {
   for (int s = kTcMaxStages + 2; s >= 2; --s)

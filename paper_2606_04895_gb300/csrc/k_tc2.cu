@@ -1,4 +1,6 @@
 // k_tc2.cu -- instantiations and launch wrappers of the cluster tcgen05 chain-tile kernel.
+#include <cstdlib>
+
 #include "launch.h"
 
 namespace bst {
@@ -55,17 +57,26 @@ int tc2_max_active_clusters(int width, int cs) {
   int n = -1;
   const void *k = nullptr;
   if (width == 512) k = cs == 4 ? (const void *)tc2_chain_kernel<512, 4> : cs == 2 ? (const void *)tc2_chain_kernel<512, 2> : (const void *)tc2_chain_kernel<512, 1>;
-  else k = cs == 4 ? (const void *)tc2_chain_kernel<256, 4> : cs == 2 ? (const void *)tc2_chain_kernel<256, 2> : (const void *)tc2_chain_kernel<256, 1>;
+  else k = cs == 2 ? (const void *)tc2_chain_kernel<256, 2> : (const void *)tc2_chain_kernel<256, 1>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(cfg.dynamicSmemBytes));
   if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) return -1;
   return n;
 }
 
-// Split a layer across more CTAs while there are fewer 128-chain tiles than SMs.
-int tc2_cluster_size(int n_rows) {
+// Split a layer across more CTAs while there are fewer 128-chain tiles than SMs.  The
+// environment variable BST_TC_CLUSTER (1, 2 or 4) overrides the choice (tuning).
+int tc2_cluster_size(int n_rows, int width) {
+  // every epilogue warp needs at least one 32-column chunk of its rank's slice
+  const int cs_max = width / (32 * kTc2EQ);
+  static const int forced = [] {
+    const char *v = getenv("BST_TC_CLUSTER");
+    const int c = v ? atoi(v) : 0;
+    return (c == 1 || c == 2 || c == 4) ? c : 0;
+  }();
+  if (forced) return forced <= cs_max ? forced : cs_max;
   const int tiles = (n_rows + kTcRows - 1) / kTcRows;
-  if (4 * tiles <= kNumSMs) return 4;
-  if (2 * tiles <= kNumSMs) return 2;
+  if (4 * tiles <= kNumSMs && cs_max >= 4) return 4;
+  if (2 * tiles <= kNumSMs && cs_max >= 2) return 2;
   return 1;
 }
 
@@ -76,7 +87,6 @@ cudaError_t launch_emu_tc2(const StepArgs<float> &a, const Tc2Weights &w, cudaSt
     return launch_one<512, 1>(a, w, s);
   }
   if (w.width == 256) {
-    if (w.cs == 4) return launch_one<256, 4>(a, w, s);
     if (w.cs == 2) return launch_one<256, 2>(a, w, s);
     return launch_one<256, 1>(a, w, s);
   }
