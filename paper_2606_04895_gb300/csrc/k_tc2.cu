@@ -57,7 +57,7 @@ int tc2_max_active_clusters(int width, int cs) {
   int n = -1;
   const void *k = nullptr;
   if (width == 512) k = cs == 4 ? (const void *)tc2_chain_kernel<512, 4> : cs == 2 ? (const void *)tc2_chain_kernel<512, 2> : (const void *)tc2_chain_kernel<512, 1>;
-  else k = cs == 2 ? (const void *)tc2_chain_kernel<256, 2> : (const void *)tc2_chain_kernel<256, 1>;
+  else k = cs == 4 ? (const void *)tc2_chain_kernel<256, 4> : cs == 2 ? (const void *)tc2_chain_kernel<256, 2> : (const void *)tc2_chain_kernel<256, 1>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(cfg.dynamicSmemBytes));
   if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) return -1;
   return n;
@@ -87,6 +87,7 @@ cudaError_t launch_emu_tc2(const StepArgs<float> &a, const Tc2Weights &w, cudaSt
     return launch_one<512, 1>(a, w, s);
   }
   if (w.width == 256) {
+    if (w.cs == 4) return launch_one<256, 4>(a, w, s);
     if (w.cs == 2) return launch_one<256, 2>(a, w, s);
     return launch_one<256, 1>(a, w, s);
   }

@@ -1,0 +1,100 @@
+"""Long-run statistics of the GPU samplers against the closed-form posterior of
+the linear theory map (paper Sec. 2 samplers; the linear variant of the
+synthetic likelihood makes the posterior exactly Gaussian):
+mean and covariance within 5 Monte Carlo standard errors, with the standard
+errors taken from the spread of independent chains (ensembles for AIES)."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _closed_form(seed=0, n_data=64):
+    t = S.target(6, linear=True, seed=seed, n_data=n_data)
+    J = t["A"] @ t["B"]
+    y = t["data"] - t["A"] @ t["c"]
+    cov = np.linalg.inv(J.T @ J / t["sigma"] ** 2)
+    mean = cov @ (J.T @ y) / t["sigma"] ** 2
+    return t, mean, cov
+
+
+def _check(samples, mean, cov, nsig=5.0):
+    n, M, d = samples.shape
+    cm = samples.mean(axis=0)
+    se_m = cm.std(axis=0, ddof=1) / np.sqrt(M)
+    zm = (cm.mean(axis=0) - mean) / se_m
+    dev = samples - mean
+    cc = np.einsum("tca,tcb->cab", dev, dev) / n
+    zc = (cc.mean(axis=0) - cov) / (cc.std(axis=0, ddof=1) / np.sqrt(M))
+    assert np.all(np.abs(zm) < nsig), zm
+    assert np.all(np.abs(zc) < nsig), zc
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("kernel,eps,steps,kw", [("mh", 0.6, 3000, {}), ("mala", 0.5, 2000, {}),
+                                                 ("hmc", 0.3, 500, {"n_leapfrog": 8}), ("nuts", 0.5, 400, {}),
+                                                 ("nuts", 1.2, 800, {})])
+def test_closed_form_moments(prec, kernel, eps, steps, kw):
+    from paper_2606_04895_gb300 import Sampler
+    t, mean, cov = _closed_form()
+    Lp = np.linalg.cholesky(cov)
+    n = 256
+    s = Sampler(6, n, precision=prec, likelihood="analytic", seed=17)
+    s.set_analytic(t["A"], t["B"], t["c"], t["data"], t["sigma"], linear=True)
+    theta0 = mean + S.chains_init(n, 6, seed=2) @ Lp.T
+    # imperfect whitening on purpose
+    s.init_chains(theta0, t["lower"], t["upper"], mu=mean + 0.2 * np.sqrt(np.diag(cov)), L=1.15 * Lp)
+    out = torch.empty((steps, n, 6), dtype=s.dtype, device="cuda")
+    s.step(kernel, steps, eps=eps, samples=out, **kw)
+    x = out.double().cpu().numpy()[steps // 5:]
+    _check(x, mean, cov)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32"])
+def test_aies_closed_form_moments(prec):
+    from paper_2606_04895_gb300 import Sampler
+    t, mean, cov = _closed_form()
+    Lp = np.linalg.cholesky(cov)
+    n_ens = 32
+    n = 64 * n_ens
+    s = Sampler(6, n, precision=prec, likelihood="analytic", seed=5)
+    s.set_analytic(t["A"], t["B"], t["c"], t["data"], t["sigma"], linear=True)
+    theta0 = mean + S.chains_init(n, 6, seed=3) @ Lp.T
+    s.init_chains(theta0, t["lower"], t["upper"])
+    steps = 1200
+    out = torch.empty((steps, n, 6), dtype=s.dtype, device="cuda")
+    s.step("aies", steps, samples=out)
+    x = out.double().cpu().numpy()[steps // 4:]
+    ens = x.reshape(x.shape[0], n_ens, 64, 6).transpose(0, 2, 1, 3).reshape(-1, n_ens, 6)
+    _check(ens, mean, cov)
+    s.close()
+
+
+def test_bf16_emulator_chains_cover_their_target():
+    """BF16 tensor-core MALA on an emulator target: the chains' moments agree with the
+    same emulator sampled by the FP64 CUDA-core path (independent chains, same target
+    up to BF16 rounding)."""
+    from paper_2606_04895_gb300 import Sampler
+    d = 8
+    e = S.emulator(d, width=256, depth=3, seed=5, out_m=30.0, out_s=6.0)
+    res = {}
+    for prec in ("bf16", "fp64"):
+        n = 1024
+        s = Sampler(d, n, precision=prec, likelihood="emulator", seed=23 if prec == "bf16" else 29)
+        s.set_emulator(e["params"], 3, 256, e["in_m"], e["in_s"], e["out_m"], e["out_s"])
+        th = np.clip(np.random.default_rng(1).normal(size=(n, d)), -2.5, 2.5)
+        s.init_chains(th, np.full(d, -3.0), np.full(d, 3.0), L=0.6 * np.eye(d))
+        s.step("mala", 500, eps=0.25, stats=False)
+        out = torch.empty((1500, n, d), dtype=s.dtype, device="cuda")
+        s.step("mala", 1500, eps=0.25, samples=out)
+        x = out.double().cpu().numpy()
+        cm = x.mean(axis=0)
+        res[prec] = (cm.mean(axis=0), cm.std(axis=0, ddof=1) / np.sqrt(n))
+        s.close()
+    (m1, s1), (m2, s2) = res["bf16"], res["fp64"]
+    z = (m1 - m2) / np.sqrt(s1 ** 2 + s2 ** 2)
+    assert np.all(np.abs(z) < 5), z
