@@ -91,15 +91,21 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+DIST = None  # torch.distributed when launched with several ranks
+
+
 def dual_average_eps(sampler, kernel, eps0, n_iter=12, chunk=40, target=0.65, **kw):
     """Hoffman & Gelman (2014) Sec. 3.2 dual averaging on log eps, using the mean
-    acceptance statistic of all chains over each chunk of steps."""
+    acceptance statistic of all chains (of every rank) over each chunk of steps."""
     mu = np.log(10 * eps0)
     h_bar, log_eps_bar, log_eps = 0.0, 0.0, np.log(eps0)
     gamma, t0, kappa = 0.05, 10.0, 0.75
     for m in range(1, n_iter + 1):
         st = sampler.step(kernel, chunk, eps=float(np.exp(log_eps)), **kw)
         a = st["accept_stat"]
+        if DIST is not None:
+            from paper_2606_04895_gb300 import distributed as PD
+            a = PD.mean_accept(st, sampler.n, chunk)
         h_bar = (1 - 1 / (m + t0)) * h_bar + (target - a) / (m + t0)
         log_eps = mu - np.sqrt(m) / gamma * h_bar
         eta = m ** (-kappa)
@@ -129,7 +135,11 @@ def burn_in(s, n, seed, kernel="mala", **kw):
         eps = dual_average_eps(s, kernel, eps, **kw)
         s.welford_reset()
         s.step(kernel, 150, eps=eps, stats=False, **kw)
-        s.adapt_cov()
+        if DIST is not None:
+            from paper_2606_04895_gb300 import distributed as PD
+            PD.adapt_cov(s)  # pooled over every rank's chains
+        else:
+            s.adapt_cov()
     eps = dual_average_eps(s, kernel, eps, **kw)
     return eps, theta0, lower, upper
 
@@ -222,9 +232,11 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = None
+    global DIST
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        DIST = dist
 
     def barrier():
         if dist is not None:

@@ -180,6 +180,17 @@ bst_status bst_welford_add(bst_handle h, const void *x_dev, int m, void *stream)
 bst_status bst_adapt_cov(bst_handle h, double jitter0, double *mu_out, double *L_out,
                          double *jitter_used);
 
+/* Covariance statistics across processes (one process per GPU, Sec. 3.2 pooled
+ * over every rank's chains).  bst_welford_stats returns the statistics this
+ * handle has accumulated, merged in FP64: count n, mean[d] and the centred sum
+ * of squares M2[d][d] (covariance = M2 / (n - 1)).  bst_welford_merge adds a
+ * triple obtained elsewhere (Chan, Golub & LeVeque pairwise merge); reset, then
+ * merging every rank's triple in rank order gives bit-identical statistics on
+ * every rank, so bst_adapt_cov then returns the same whitening everywhere.
+ * Both synchronise. */
+bst_status bst_welford_stats(bst_handle h, double *n, double *mean, double *M2);
+bst_status bst_welford_merge(bst_handle h, double n, const double *mean, const double *M2);
+
 /* Checkpoint / resume.  Host FP64 copies of the chain state: z[n][d], logp[n],
  * grad[n][d] (whitened), iteration counters iter[n].  Philox draws are keyed by
  * (seed, chain, iter), so a restored state continues bit-identically. */
@@ -206,6 +217,13 @@ bst_status bst_train_step(bst_handle h, const float *X_dev, const float *chi2_de
  * layout as bst_set_emulator params) without updating; for checks. */
 bst_status bst_train_grad(bst_handle h, const float *X_dev, const float *chi2_dev, int m,
                           float *grad_dev, float *loss_dev, void *stream);
+
+/* One Adam step with a gradient supplied by the caller (grad_dev: float, layout
+ * of bst_set_emulator params) -- for data-parallel training, where each rank
+ * computes bst_train_grad on its batch and the gradients are averaged across
+ * ranks before this call. */
+bst_status bst_train_apply(bst_handle h, const float *grad_dev, double lr, double beta1, double beta2,
+                           double adam_eps, void *stream);
 
 /* Multi-chain effective sample size per dimension (Gelman et al., BDA3
  * Sec. 11.5: variogram autocorrelations, Geyer initial monotone sequence) of

@@ -171,6 +171,15 @@ class Sampler:
         x = self._as_dev(x)
         _lib.check(self.lib.bst_welford_add(self.h, C.c_void_p(x.data_ptr()), x.shape[0], _stream_ptr(stream)))
 
+    def welford_stats(self):
+        n = np.zeros(1); mean = np.zeros(self.d); M2 = np.zeros((self.d, self.d))
+        _lib.check(self.lib.bst_welford_stats(self.h, _p(n), _p(mean), _p(M2)))
+        return float(n[0]), mean, M2
+
+    def welford_merge(self, n, mean, M2):
+        mean, M2 = _f64(mean), _f64(M2)
+        _lib.check(self.lib.bst_welford_merge(self.h, float(n), _p(mean), _p(M2)))
+
     def adapt_cov(self, jitter0=1e-10):
         mu = np.zeros(self.d)
         L = np.zeros((self.d, self.d))
@@ -208,6 +217,11 @@ class Sampler:
                                            lr, beta1, beta2, eps,
                                            None if loss_out is None else C.c_void_p(loss_out.data_ptr()),
                                            _stream_ptr(stream)))
+
+    def train_apply(self, grad, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        g = grad.contiguous().float()
+        _lib.check(self.lib.bst_train_apply(self.h, C.c_void_p(g.data_ptr()), lr, beta1, beta2, eps,
+                                            _stream_ptr(stream)))
 
     def train_grad(self, X, chi2, stream=None):
         X = X.contiguous().float(); y = chi2.contiguous().float()

@@ -62,6 +62,7 @@ struct bst_ctx {
   void *mu_r = nullptr, *L_r = nullptr, *lo_r = nullptr, *up_r = nullptr;
   int *gauss_d = nullptr;
   double *mu64 = nullptr, *L64 = nullptr, *mu64_new = nullptr, *L64_new = nullptr, *info64 = nullptr;
+  double *stats64 = nullptr;  // [1 + kMaxD + kMaxD^2] Welford triple staging
 
   // emulator
   int depth = 0, width = 0;
@@ -518,6 +519,7 @@ bst_status bst_create(bst_handle *out, const bst_config *cfg) {
   A((void **)&h->mu64_new, kMaxD * 8);
   A((void **)&h->L64_new, kMaxD * kMaxD * 8);
   A((void **)&h->info64, 8 * 8);
+  A((void **)&h->stats64, (1 + kMaxD + kMaxD * kMaxD) * 8);
   h->wf_records = static_cast<int>((n + 15) / 16) + 1;  // one per tile for any tiling + one external
   A((void **)&h->wf, static_cast<size_t>(h->wf_records) * kWfStride * 8);
   if (st != BST_OK) {
@@ -837,6 +839,38 @@ bst_status bst_welford_add(bst_handle h, const void *x_dev, int m, void *stream)
   return BST_OK;
 }
 
+bst_status bst_welford_stats(bst_handle h, double *n, double *mean, double *M2) {
+  if (!h || !n || !mean || !M2) return fail(BST_ERR_ARG, "bst_welford_stats: NULL argument");
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_CUDA(cudaDeviceSynchronize());
+  const int d = h->d;
+  std::vector<double> host(1 + d + static_cast<size_t>(d) * d);
+  BST_CUDA(launch_welford_stats(h->wf, h->wf_records, kWfStride, d, h->stats64, 0));
+  BST_CUDA(cudaMemcpy(host.data(), h->stats64, host.size() * 8, cudaMemcpyDeviceToHost));
+  *n = host[0];
+  std::memcpy(mean, host.data() + 1, d * 8);
+  std::memcpy(M2, host.data() + 1 + d, static_cast<size_t>(d) * d * 8);
+  return BST_OK;
+}
+
+bst_status bst_welford_merge(bst_handle h, double n, const double *mean, const double *M2) {
+  if (!h || !mean || !M2) return fail(BST_ERR_ARG, "bst_welford_merge: NULL argument");
+  if (!(n >= 0.0)) return fail(BST_ERR_ARG, "bst_welford_merge: n must be >= 0");
+  const int d = h->d;
+  std::vector<double> host(1 + d + static_cast<size_t>(d) * d);
+  host[0] = n;
+  std::memcpy(host.data() + 1, mean, d * 8);
+  std::memcpy(host.data() + 1 + d, M2, static_cast<size_t>(d) * d * 8);
+  if (!all_finite(host.data(), host.size())) return fail(BST_ERR_NONFINITE, "bst_welford_merge: non-finite input");
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_CUDA(cudaDeviceSynchronize());
+  BST_CUDA(cudaMemcpy(h->stats64, host.data(), host.size() * 8, cudaMemcpyHostToDevice));
+  double *rec = h->wf + static_cast<size_t>(h->wf_records - 1) * kWfStride;
+  BST_CUDA(launch_welford_merge(rec, d, h->stats64, 0));
+  BST_CUDA(cudaDeviceSynchronize());
+  return BST_OK;
+}
+
 bst_status bst_adapt_cov(bst_handle h, double jitter0, double *mu_out, double *L_out, double *jitter_used) {
   if (!h) return fail(BST_ERR_ARG, "bst_adapt_cov: NULL handle");
   if (h->stage < 2) return fail(BST_ERR_STATE, "bst_adapt_cov: call bst_init_chains first");
@@ -987,6 +1021,23 @@ bst_status bst_train_step(bst_handle h, const float *X_dev, const float *chi2_de
   if (loss_dev) BST_CUDA(cudaMemcpyAsync(loss_dev, h->tw.loss, 4, cudaMemcpyDeviceToDevice, s));
   h->adam_t += 1;
   BST_CUDA(launch_adam(h->P32, h->G32, h->m1, h->m2, h->nparams, h->adam_t, static_cast<float>(lr),
+                       static_cast<float>(beta1), static_cast<float>(beta2), static_cast<float>(adam_eps), s));
+  h->p32_newer = true;
+  h->weights_dirty = true;
+  h->state_stale = true;
+  return BST_OK;
+}
+
+bst_status bst_train_apply(bst_handle h, const float *grad_dev, double lr, double beta1, double beta2,
+                           double adam_eps, void *stream) {
+  if (!h || !grad_dev) return fail(BST_ERR_ARG, "bst_train_apply: NULL argument");
+  if (!(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(adam_eps > 0.0))
+    return fail(BST_ERR_ARG, "bst_train_apply: bad Adam hyper-parameters");
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_TRY(train_setup(h, 1));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->adam_t += 1;
+  BST_CUDA(launch_adam(h->P32, grad_dev, h->m1, h->m2, h->nparams, h->adam_t, static_cast<float>(lr),
                        static_cast<float>(beta1), static_cast<float>(beta2), static_cast<float>(adam_eps), s));
   h->p32_newer = true;
   h->weights_dirty = true;

@@ -353,6 +353,54 @@ cudaError_t launch_adapt_finalize(const double *wf, int n_tiles, int stride, int
   return cudaGetLastError();
 }
 
+// Merged statistics of every record (n, mean, M2 upper triangle mirrored), no factorisation.
+__global__ void welford_stats_kernel(const double *wf, int n_tiles, int stride, int d, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double n = 0.0, mean[kMaxD], M2[kMaxD * kMaxD];
+  for (int i = 0; i < d; ++i) mean[i] = 0.0;
+  for (int i = 0; i < d * d; ++i) M2[i] = 0.0;
+  for (int t = 0; t < n_tiles; ++t) {
+    const double *W = wf + static_cast<size_t>(t) * stride;
+    const double nb = W[kWfN];
+    if (nb <= 0.0) continue;
+    const double nn = n + nb;
+    for (int i = 0; i < d; ++i)
+      for (int j = i; j < d; ++j) {
+        const double di = W[kWfMean + i] - mean[i], dj = W[kWfMean + j] - mean[j];
+        M2[i * d + j] += W[kWfM2 + i * kMaxD + j] + di * dj * n * nb / nn;
+      }
+    for (int i = 0; i < d; ++i) mean[i] += (W[kWfMean + i] - mean[i]) * nb / nn;
+    n = nn;
+  }
+  out[0] = n;
+  for (int i = 0; i < d; ++i) out[1 + i] = mean[i];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) out[1 + d + i * d + j] = (j >= i) ? M2[i * d + j] : M2[j * d + i];
+}
+cudaError_t launch_welford_stats(const double *wf, int n_tiles, int stride, int d, double *out, cudaStream_t s) {
+  welford_stats_kernel<<<1, 32, 0, s>>>(wf, n_tiles, stride, d, out);
+  return cudaGetLastError();
+}
+
+// Chan merge of one (n, mean, M2) triple (device copy of host values) into record W.
+__global__ void welford_merge_kernel(double *W, int d, const double *in) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double na = W[kWfN], nb = in[0];
+  if (nb <= 0.0) return;
+  const double n = na + nb;
+  for (int i = 0; i < d; ++i)
+    for (int j = i; j < d; ++j) {
+      const double di = in[1 + i] - W[kWfMean + i], dj = in[1 + j] - W[kWfMean + j];
+      W[kWfM2 + i * kMaxD + j] += in[1 + d + i * d + j] + di * dj * na * nb / n;
+    }
+  for (int i = 0; i < d; ++i) W[kWfMean + i] += (in[1 + i] - W[kWfMean + i]) * nb / n;
+  W[kWfN] = n;
+}
+cudaError_t launch_welford_merge(double *W, int d, const double *in, cudaStream_t s) {
+  welford_merge_kernel<<<1, 32, 0, s>>>(W, d, in);
+  return cudaGetLastError();
+}
+
 __global__ void welford_clear_kernel(double *wf, size_t n) {
   const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
   if (i < n) wf[i] = 0.0;

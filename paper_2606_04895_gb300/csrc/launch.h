@@ -56,6 +56,9 @@ cudaError_t launch_fold_analytic(const double *A, const double *B, const double 
 cudaError_t launch_adapt_finalize(const double *wf, int n_tiles, int stride, int d, double jitter0, double *mu,
                                   double *L, double *info, cudaStream_t s);
 cudaError_t launch_welford_clear(double *wf, int n_tiles, int stride, cudaStream_t s);
+// out = [n, mean[d], M2[d][d]] of all records merged; merge of such a triple into one record.
+cudaError_t launch_welford_stats(const double *wf, int n_tiles, int stride, int d, double *out, cudaStream_t s);
+cudaError_t launch_welford_merge(double *W, int d, const double *in, cudaStream_t s);
 cudaError_t launch_welford_add_f32(const float *x, int m, int d, double *wf, int stride, cudaStream_t s);
 cudaError_t launch_welford_add_f64(const double *x, int m, int d, double *wf, int stride, cudaStream_t s);
 // z_new = L_new^-1 (mu_old + L_old z_old - mu_new), FP64 arithmetic.

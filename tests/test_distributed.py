@@ -1,0 +1,101 @@
+"""Multi-process host logic of the multi-GPU path, on CPU with gloo and two ranks:
+chain sharding, the rank-order Welford merge behind covariance adaptation (checked
+against a single pass over all ranks' samples with numpy.cov), the pooled mean
+acceptance and the gradient average.  The library's device-side merge is replaced
+by the oracle's Chan merge in a stand-in sampler (test infrastructure)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_shard_covers_every_chain_once():
+    from paper_2606_04895_gb300.distributed import shard
+    for n, w, m in [(4096, 1, 1), (4096, 2, 1), (4097, 3, 1), (16384, 8, 64), (256, 3, 64)]:
+        spans = [shard(n, r, w, m) for r in range(w)]
+        assert sum(c for _, c in spans) == n
+        pos = 0
+        for first, count in spans:
+            assert first == pos and count % m == 0
+            pos += count
+        assert max(c for _, c in spans) - min(c for _, c in spans) <= m
+    with pytest.raises(ValueError):
+        shard(100, 0, 2, 64)
+
+
+class _Stand:
+    """Holds (n, mean, M2) like a handle's Welford record; merges with the oracle."""
+
+    def __init__(self, x):
+        import oracle as O
+        self.O = O
+        self.d = x.shape[1]
+        m, c = O.pooled_cov(x)
+        self.state = (float(len(x)), m, c * (len(x) - 1))
+        self.merged = None
+
+    def welford_stats(self):
+        return self.state
+
+    def welford_reset(self):
+        self.merged = (0.0, np.zeros(self.d), np.zeros((self.d, self.d)))
+
+    def welford_merge(self, n, mean, M2):
+        na, ma, Ma = self.merged
+        if na == 0:
+            self.merged = (n, np.array(mean), np.array(M2))
+        else:
+            self.merged = self.O.chan_merge(na, ma, Ma, n, mean, M2)
+
+    def adapt_cov(self, jitter0):
+        n, mean, M2 = self.merged
+        return mean, M2 / (n - 1), 0.0
+
+
+def _worker(rank, world, port, q):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2606_04895_gb300 import distributed as D
+    rng = np.random.default_rng(100 + rank)
+    x = rng.normal(size=(300 + 50 * rank, 5)) @ np.diag([1, 2, 3, 4, 5]) + rank
+    s = _Stand(x)
+    mean, cov, _ = D.adapt_cov(s)
+    acc = D.mean_accept({"accept_stat": 0.5 + 0.2 * rank}, 100 * (rank + 1), 10)
+    g = torch.full((7,), float(rank + 1))
+    D.average_gradients(g)
+    q.put((rank, mean, cov, acc, g.numpy()))
+    dist.destroy_process_group()
+
+
+def test_two_rank_adaptation_and_reductions():
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted([q.get(timeout=120) for _ in ps], key=lambda t: t[0])
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    xs = [np.random.default_rng(100 + r).normal(size=(300 + 50 * r, 5)) @ np.diag([1, 2, 3, 4, 5]) + r
+          for r in range(2)]
+    allx = np.concatenate(xs)
+    for r in range(2):
+        _, mean, cov, acc, g = res[r]
+        assert np.allclose(mean, allx.mean(axis=0), rtol=1e-12, atol=1e-12)
+        assert np.allclose(cov, np.cov(allx.T), rtol=1e-10)
+        assert acc == pytest.approx((0.5 * 100 + 0.7 * 200) / 300)
+        assert np.allclose(g, 1.5)
+    # bit-identical on both ranks
+    assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][2], res[1][2])

@@ -155,3 +155,49 @@ def test_autograd_function_gradient():
         fd = (s.loglike(x0 + dx) - s.loglike(x0 - dx)) / (2 * h)
         assert np.allclose(fd.cpu().numpy(), rg[:, i], rtol=1e-6, atol=1e-8)
     s.close()
+
+
+def test_welford_stats_and_rank_order_merge():
+    """Two handles standing in for two ranks: merging their statistics in rank order
+    reproduces the pooled covariance of all samples (numpy.cov)."""
+    sa, *_ = _small("fp64")
+    sb, *_ = _small("fp64")
+    rng = np.random.default_rng(8)
+    xa = rng.normal(size=(700, 6)) * 0.3 + 1.0
+    xb = rng.normal(size=(500, 6)) * 0.5 - 0.5
+    for s, x in ((sa, xa), (sb, xb)):
+        s.welford_reset()
+        s.welford_add(torch.as_tensor(x))
+    na, ma, Ma = sa.welford_stats()
+    nb, mb, Mb = sb.welford_stats()
+    assert na == 700 and np.allclose(ma, xa.mean(axis=0), rtol=1e-12)
+    assert np.allclose(Ma / (na - 1), np.cov(xa.T), rtol=1e-10)
+    for s in (sa, sb):
+        s.welford_reset()
+        s.welford_merge(na, ma, Ma)
+        s.welford_merge(nb, mb, Mb)
+    mu_a, L_a, _ = sa.adapt_cov()
+    mu_b, L_b, _ = sb.adapt_cov()
+    allx = np.concatenate([xa, xb])
+    assert np.array_equal(mu_a, mu_b) and np.array_equal(L_a, L_b)
+    assert np.allclose(mu_a, allx.mean(axis=0), rtol=1e-12)
+    assert np.allclose(L_a @ L_a.T, np.cov(allx.T), rtol=1e-9)
+    sa.close(); sb.close()
+
+
+def test_train_apply_equals_train_step():
+    from paper_2606_04895_gb300 import Sampler
+    d, D, w = 4, 2, 256
+    e = S.emulator(d, width=w, depth=D, seed=3, out_m=10.0, out_s=5.0)
+    X = torch.as_tensor(np.random.default_rng(0).uniform(-3, 3, (1024, d)), dtype=torch.float32, device="cuda")
+    y = (X ** 2).sum(dim=1)
+    a = Sampler(d, 8, precision="fp32", likelihood="emulator")
+    b = Sampler(d, 8, precision="fp32", likelihood="emulator")
+    for s in (a, b):
+        s.set_emulator(e["params"], D, w, e["in_m"], e["in_s"], e["out_m"], e["out_s"])
+    for _ in range(3):
+        a.train_step(X, y, lr=1e-3)
+        _, g = b.train_grad(X, y)
+        b.train_apply(g, lr=1e-3)
+    assert np.array_equal(a.get_emulator(), b.get_emulator())
+    a.close(); b.close()
