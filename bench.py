@@ -209,6 +209,126 @@ def run_reference(args):
     return 0
 
 
+def _emulator_target(d, n, precision, seed, device, width=WIDTH, depth=DEPTH, nuis=0):
+    """Seeded emulator target: box [-3, 3] on the leading d - nuis dims, N(0, 1) on the rest."""
+    import synthetic as S
+    from paper_2606_04895_gb300 import Sampler
+    e = S.emulator(d, width=width, depth=depth, seed=7, out_m=60.0, out_s=12.0)
+    s = Sampler(d, n, precision=precision, likelihood="emulator", seed=seed, device=device)
+    s.set_emulator(e["params"], depth, width, e["in_m"], e["in_s"], e["out_m"], e["out_s"])
+    lower, upper = np.full(d, -3.0), np.full(d, 3.0)
+    gauss = np.zeros(d, dtype=np.int32)
+    if nuis:
+        lower[d - nuis:], upper[d - nuis:] = -1e30, 1e30
+        gauss[d - nuis:] = 1
+    th = np.clip(0.5 * np.random.default_rng(seed).normal(size=(n, d)), -2.5, 2.5)
+    s.init_chains(th, lower, upper, mu=np.zeros(d), L=0.5 * np.eye(d), gauss=gauss)
+    return s
+
+
+def extras(torch, device, seed, eps_mala, K):
+    """Other samplers / targets / paths at their configurations (reported beside the headline)."""
+    out = {}
+    P27 = n_params(27, DEPTH, WIDTH) - 1
+    # NUTS and AIES on the 27-D nuisance-extended target, 16384 chains
+    s = _emulator_target(27, 16384, "bf16", seed + 11, device, nuis=21)
+    eps_n = dual_average_eps(s, "nuts", 0.3, n_iter=6, chunk=4, target=0.8)
+    it = 40
+    x = torch.empty((it, 16384, 27), dtype=torch.float32, device="cuda")
+    c0 = s.counters()["evals"].sum()
+    t = time_steps(torch, s, "nuts", it, eps_n, samples=x)
+    ev = s.counters()["evals"].sum() - c0
+    ess = s.ess(x)
+    out["nuts_27d"] = {"chains": 16384, "iterations": it, "eps": eps_n, "evals_per_s": ev / t,
+                       "leapfrogs_per_iter": ev / (16384 * it), "min_ess_per_s": float(ess.min()) / t,
+                       "tflops": 4.0 * P27 * ev / t / 1e12}
+    s.close()
+    s = _emulator_target(27, 16384, "bf16", seed + 12, device, nuis=21)
+    s.step("aies", 200, stats=False)
+    ka = 400
+    x = torch.empty((ka, 16384, 27), dtype=torch.float32, device="cuda")
+    t = time_steps(torch, s, "aies", ka, 0.0, samples=x)
+    ess = s.ess(x)
+    out["aies_27d"] = {"walkers": 16384, "ensembles": 256, "steps": ka, "evals_per_s": ka * 16384 / t,
+                       "min_ess_per_s": float(ess.min()) / t, "tflops": 2.0 * P27 * ka * 16384 / t / 1e12}
+    s.close()
+    # MH (forward only) on the headline target
+    s, _ = make_sampler("bf16", N_CHAINS, seed, device)
+    s.init_chains(np.clip(np.random.default_rng(1).normal(size=(N_CHAINS, D)), -2.9, 2.9), np.full(D, -3.0),
+                  np.full(D, 3.0), L=0.3 * np.eye(D))
+    km = max(500, K // 5)
+    t = time_steps(torch, s, "mh", km, 0.1)
+    out["mh"] = {"evals_per_s": km * N_CHAINS / t, "tflops": 2.0 * (n_params(D, DEPTH, WIDTH) - 1) * km * N_CHAINS / t / 1e12}
+    s.close()
+    # the plain method: analytic 8-D theory-map likelihood, FP32 CUDA cores, MALA, 4096 chains
+    import synthetic as S
+    from paper_2606_04895_gb300 import learn
+    tgt = S.target(8, seed=0)
+    a = learn.analytic_sampler(tgt, n_chains=N_CHAINS, precision="fp32", seed=seed)
+    Lp = np.linalg.cholesky(tgt["laplace_cov"])
+    a.init_chains(tgt["theta_star"] + S.chains_init(N_CHAINS, 8, seed=2) @ Lp.T, tgt["lower"], tgt["upper"],
+                  mu=tgt["theta_star"], L=Lp)
+    ka = max(500, K // 5)
+    x = torch.empty((ka, N_CHAINS, 8), dtype=torch.float32, device="cuda")
+    t = time_steps(torch, a, "mala", ka, 0.5, samples=x)
+    out["analytic_fp32"] = {"evals_per_s": ka * N_CHAINS / t, "min_ess_per_s": float(a.ess(x).min()) / t,
+                            "flop_per_eval": 4 * 256 * (32 + 8)}
+    a.close()
+    # training throughput of the hand-written FP32 training kernels (batch 4096, 8-512x4-1)
+    s, _ = make_sampler("bf16", 8, seed, device)
+    X = torch.rand((4096, D), device="cuda") * 6 - 3
+    y = (X ** 2).sum(dim=1) * 10
+    s.train_step(X, y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nsteps = 30
+    for _ in range(nsteps):
+        s.train_step(X, y)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    P = n_params(D, DEPTH, WIDTH) - 1
+    out["training"] = {"samples_per_s": nsteps * 4096 / dt, "tflops": 6.0 * P * nsteps * 4096 / dt / 1e12,
+                       "batch": 4096, "precision": "fp32 CUDA cores"}
+    s.close()
+    return out
+
+
+def sweep(torch, device):
+    """Throughput over chains x width x depth x dims x kernel x precision (reduced grid)."""
+    pts = []
+    for prec in ("bf16", "fp32", "fp64"):
+        for n in (1024, 4096, 16384, 65536, 262144):
+            if prec == "fp64" and n > 16384:
+                continue
+            if prec == "fp32" and n > 65536:
+                continue
+            pts.append(dict(prec=prec, n=n, d=8, width=512, depth=4, kernel="mala"))
+    for width in (256, 1024):
+        for prec in ("bf16", "fp32"):
+            if prec == "bf16" and width > 512:
+                continue
+            pts.append(dict(prec=prec, n=16384, d=8, width=width, depth=4, kernel="mala"))
+    for depth in (5, 6):
+        pts.append(dict(prec="bf16", n=16384, d=8, width=512, depth=depth, kernel="mala"))
+    for d in (6, 27):
+        pts.append(dict(prec="bf16", n=16384, d=d, width=512, depth=4, kernel="mala"))
+    for k in ("mh", "hmc"):
+        pts.append(dict(prec="bf16", n=16384, d=8, width=512, depth=4, kernel=k))
+    burst, _, _, kind = peaks()
+    for p in pts:
+        s = _emulator_target(p["d"], p["n"], p["prec"], 5, device, width=p["width"], depth=p["depth"])
+        steps = max(3, min(200, int(2e11 / (p["n"] * 4 * n_params(p["d"], p["depth"], p["width"])))))
+        kw = {"n_leapfrog": 10} if p["kernel"] == "hmc" else {}
+        s.step(p["kernel"], 2, eps=0.1, stats=False, **kw)
+        t = time_steps(torch, s, p["kernel"], steps, 0.1, **kw)
+        evals = steps * p["n"] * (10 if p["kernel"] == "hmc" else 1)
+        fl = (2 if p["kernel"] == "mh" else 4) * (n_params(p["d"], p["depth"], p["width"]) - 1) * evals / t
+        row = dict(p, evals_per_s=evals / t, tflops=fl / 1e12,
+                   frac_bf16_peak=fl / 1e12 / burst if p["prec"] == "bf16" else None, steps=steps)
+        print(json.dumps(row), flush=True)
+        s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,6 +337,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="print one JSON line per point of the throughput grid")
     ap.add_argument("--quick", action="store_true",
                     help="skip the burn-in (fixed whitening and step size): three launches in total, "
                          "for profiler captures")
@@ -231,6 +352,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.sweep:
+        sweep(torch, local)
+        return 0
     dist = None
     global DIST
     if world > 1:
@@ -325,8 +449,10 @@ def main():
             t32 = time_steps(torch, s32, "mala", k32, eps, samples=x32)
             ess32 = s32.ess(x32)
             out["fp32_plain"] = {"evals_per_s": k32 * N_CHAINS / t32, "min_ess_per_s": float(ess32.min()) / t32,
-                                 "steps": k32, "speedup_bf16_evals": value / (k32 * N_CHAINS / t32)}
+                                 "steps": k32, "speedup_bf16_evals": value / (k32 * N_CHAINS / t32),
+                                 "speedup_bf16_min_ess": min_ess_s / (float(ess32.min()) / t32)}
             s32.close()
+            out.update(extras(torch, local, seed, eps, K))
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out))
