@@ -92,6 +92,14 @@ __device__ __forceinline__ void bulk_s2cluster(uint32_t dst_cluster, uint32_t sr
       "r"(src_cta), "r"(bytes), "r"(bar_cluster)
       : "memory");
 }
+// Arrive on the barrier at `bar`'s offset in every CTA of `mask` once this thread's
+// tcgen05 operations issued so far have completed.
+__device__ __forceinline__ void mma_commit_multicast(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n" ::"r"(bar),
+      "h"(mask)
+      : "memory");
+}
 __device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;\n" ::"r"(addr), "f"(v) : "memory");
 }
@@ -278,6 +286,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
       const uint32_t idn = idesc_bf16(128, TR), idg = idesc_bf16(128, 2 * dp);
       const uint32_t act_addr = smem_u32(act);
       const int rot = tile % KBW;
+      const uint16_t peer_mask = static_cast<uint16_t>(((1u << CS) - 1u) & ~(1u << rank));
       while (ok) {
         if (!mbar_wait_cluster(go_bar, go_par, a.status)) break;
         go_par ^= 1;
@@ -314,7 +323,11 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
               s = (s + 1 == S) ? 0 : s + 1;
             }
           }
-          if (ok) mma_commit(acc_bar);
+          if (ok) {
+            mma_commit(acc_bar);
+            // once these MMAs are done our activation buffer may be overwritten by the peers
+            if (CS > 1 && p + 1 < phases) mma_commit_multicast(free_bar, peer_mask);
+          }
         }
       }
       mma_commit(fin_bar);
@@ -424,10 +437,6 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         const bool fwd = p < D;
         const bool last_fwd = p == D - 1;
         const bool distribute = (p + 1 < nph);  // this phase's output feeds another phase
-        // our MMAs of this phase are done: peers may write into our activation buffer
-        if (CS > 1 && distribute && t == 0)
-          for (int pr = 0; pr < CS; ++pr)
-            if (pr != static_cast<int>(rank)) mbar_arrive_cluster(mapa(free_bar, pr));
         if (p == 2 * D - 1) {
           // input gradient: g_i = acc[i] + acc[dp + i] (every rank computes it, rank 0 writes)
           if (ch == 0) {
