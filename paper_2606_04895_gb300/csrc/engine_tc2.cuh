@@ -235,13 +235,13 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      uint32_t fills[kTcMaxStages + 2] = {0, 0, 0, 0, 0, 0, 0, 0};
-      uint32_t go_par = 0;
+      // bit s of fpar: parity of the fills of stage s so far; bit s of used: stage s filled
+      uint32_t fpar = 0, used = 0, go_par = 0;
+      int s = 0;
       bool ok = true;
       const uint8_t *l1 = E.l1 + rank * E.l1_stride;
       const uint8_t *hid = E.hid + rank * E.hid_stride;
       const int rot = tile % KBW;  // clusters start each layer at different K blocks (spreads L2 reads)
-      uint32_t tcount = 0;           // tiles of every evaluation so far (stage ring position)
       while (ok) {
         if (!mbar_wait_cluster(go_bar, go_par, a.status)) break;
         go_par ^= 1;
@@ -253,38 +253,41 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
           const int nsub = last ? 1 : NSUB;
           const int nkb = (p == 0) ? E.kb1 : KBW;
           const uint32_t bytes = last ? 2 * dp * 128 : STAGE;
-          if (!ok) break;
-          for (int sb = 0; sb < nsub && ok; ++sb)
+          for (int sb = 0; sb < nsub && ok; ++sb) {
+            int kb = (p == 0) ? 0 : rot;
             for (int j = 0; j < nkb; ++j) {
-              const int kb = (p == 0) ? j : (j + rot) % KBW;
-              const int s = tcount % S;
-              ++tcount;
               const uint8_t *src;
               if (p == 0) src = l1 + static_cast<size_t>(sb * nkb + kb) * STAGE;
               else if (!last) src = hid + (static_cast<size_t>(p - 1) * NSUB * KBW + sb * KBW + kb) * STAGE;
               else src = E.g1 + static_cast<size_t>(kb) * bytes;
-              if (!mbar_wait(empty0 + 8 * s, (fills[s] & 1) ^ 1, a.status)) {
+              if (!mbar_wait(empty0 + 8 * s, ((fpar >> s) & 1u) ^ 1u, a.status)) {
                 ok = false;
                 break;
               }
               mbar_expect_tx(full0 + 8 * s, bytes);
               bulk_g2s(smem_u32(stages + s * STAGE), src, bytes, full0 + 8 * s);
-              fills[s]++;
+              fpar ^= 1u << s;
+              used |= 1u << s;
+              s = (s + 1 == S) ? 0 : s + 1;
+              kb = (kb + 1 == nkb) ? 0 : kb + 1;
             }
+          }
         }
       }
       for (int q2 = 0; q2 < S; ++q2)
-        if (fills[q2]) mbar_wait(full0 + 8 * q2, (fills[q2] - 1) & 1, a.status);
+        if ((used >> q2) & 1u) mbar_wait(full0 + 8 * q2, ((fpar >> q2) & 1u) ^ 1u, a.status);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      uint32_t uses[kTcMaxStages + 2] = {0, 0, 0, 0, 0, 0, 0, 0};
+      uint32_t upar = 0;  // bit s: parity of the next wait on stage s
       int s = 0;
       uint32_t go_par = 0, act_par = 0;
       bool ok = true;
       const uint32_t idn = idesc_bf16(128, TR), idg = idesc_bf16(128, 2 * dp);
-      const uint32_t act_addr = smem_u32(act);
+      // descriptors of K block 0 of the activation and of stage 0; K block kb / stage s / the
+      // k-th 16-wide step are offsets of kb * 16384, s * STAGE and k * 32 bytes (address >> 4)
+      const uint64_t adesc0 = sw128_desc(smem_u32(act)), bdesc0 = sw128_desc(smem_u32(stages));
       const int rot = tile % KBW;
       const uint16_t peer_mask = static_cast<uint16_t>(((1u << CS) - 1u) & ~(1u << rank));
       while (ok) {
@@ -303,24 +306,25 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
           const bool last = (p == 2 * D - 1);
           const int nsub = last ? 1 : NSUB;
           const int nkb = (p == 0) ? E.kb1 : KBW;
+          const uint32_t id = last ? idg : idn;
           for (int sb = 0; sb < nsub && ok; ++sb) {
+            int kb = (p == 0) ? 0 : rot;
+            const uint32_t dcol = tmem + sb * TR;
             for (int j = 0; j < nkb; ++j) {
-              const int kb = (p == 0) ? j : (j + rot) % KBW;
-              if (!mbar_wait(full0 + 8 * s, uses[s] & 1, a.status)) {
+              if (!mbar_wait(full0 + 8 * s, (upar >> s) & 1u, a.status)) {
                 ok = false;
                 break;
               }
+              upar ^= 1u << s;
               tc_fence_after();
-              const uint32_t b_addr = smem_u32(stages + s * STAGE);
+              const uint64_t ad = adesc0 + static_cast<uint64_t>(kb * (16384 >> 4));
+              const uint64_t bd = bdesc0 + static_cast<uint64_t>(s * (STAGE >> 4));
               const int k16 = (p == 0) ? min(4, E.k16_l1 - 4 * kb) : 4;
-              for (int k = 0; k < k16; ++k) {
-                const uint64_t ad = sw128_desc(act_addr + kb * 16384 + k * 32);
-                const uint64_t bd = sw128_desc(b_addr + k * 32);
-                mma_bf16(tmem + sb * TR, ad, bd, last ? idg : idn, (j > 0 || k > 0) ? 1u : 0u);
-              }
+              for (int k = 0; k < k16; ++k)
+                mma_bf16(dcol, ad + 2 * k, bd + 2 * k, id, (j > 0 || k > 0) ? 1u : 0u);
               mma_commit(empty0 + 8 * s);
-              uses[s]++;
               s = (s + 1 == S) ? 0 : s + 1;
+              kb = (kb + 1 == nkb) ? 0 : kb + 1;
             }
           }
           if (ok) {
@@ -349,6 +353,11 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
     const int col0 = static_cast<int>(rank) * NS + ch * CW;  // first global column of this warp
     Chain<float> chn(a);
     const bool loglike = a.mode == kModeLoglike;
+    const bool mala = a.mode == kModeMALA;
+    // MALA / MH with d <= 8 (padded to 16) keep the chain in the sampler thread's registers
+    const bool fast = (mala || a.mode == kModeMH) && a.d <= RegChain8<float>::DB && dp == 16;
+    RegChain8<float> rc;
+    if (fast && sampler && valid) rc.load(a, row);
     if (sampler && valid && !loglike) {
       if (a.mode == kModeAIES) {
         for (int h = 0; h < 2; ++h) a.st.steps_done[chn.aies_walker(row, h)] = 0;
@@ -370,15 +379,13 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         if (ev > 0) epi_sync();  // a proposal may read positions other threads just accepted (AIES)
         if (sampler) {
           if (loglike) need = valid && ev == 0;
-          else need = valid && chn.pre(row, h);
+          else need = valid && (fast ? rc.pre(a, row, mala) : chn.pre(row, h));
         }
         const bool any = epi_or(need);
-        if (t == 0) {
+        if (t < CS) {  // thread t signals rank t (the release arrives run in parallel)
           const int c = any ? (grad ? 2 : 1) : 0;
-          for (int pr = 0; pr < CS; ++pr) {
-            st_cluster_u32(mapa(smem_u32(const_cast<int *>(cmd)), pr), static_cast<uint32_t>(c));
-            mbar_arrive_cluster(mapa(go_bar, pr));
-          }
+          st_cluster_u32(mapa(smem_u32(const_cast<int *>(cmd)), t), static_cast<uint32_t>(c));
+          mbar_arrive_cluster(mapa(go_bar, t));
         }
       }
       if (!mbar_wait_cluster(go_bar, go_par, a.status)) break;
@@ -444,7 +451,16 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
             tmem_ld32_nowait(trow, v0);
             if (dp > 16) tmem_ld32_nowait(trow + 32, v1);
             tmem_wait_ld();
-            if (rank == 0 && valid) {
+            if (rank == 0 && valid && fast) {
+              float *gout = a.st.gle + static_cast<size_t>(row) * a.st.gle_ld;
+#pragma unroll
+              for (int i = 0; i < RegChain8<float>::DB; ++i)
+                if (i < a.d) {
+                  const float gi = __uint_as_float(v0[i]) + __uint_as_float(v0[16 + i]);  // dp == 16
+                  rc.gp[i] = gi;
+                  gout[i] = gi;
+                }
+            } else if (rank == 0 && valid) {
               float *gout = a.st.gle + static_cast<size_t>(row) * a.st.gle_ld;
               for (int i = 0; i < a.d; ++i) {
                 const int j2 = dp + i;
@@ -588,14 +604,16 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
       if (rank == 0) {
         const bool got = mbar_wait_cluster(part_bar, part_par, a.status);
         part_par ^= 1;
+        float lle_v = 0.f;
         if (sampler && valid && got) {
           float s_out = 0.f;
           for (int pr = 0; pr < CS; ++pr) s_out += partial[pr * 128 + r];
-          a.st.lle[row] = -0.5f * (E.out_s * (s_out + E.bo) + E.out_m);
+          lle_v = -0.5f * (E.out_s * (s_out + E.bo) + E.out_m);
+          a.st.lle[row] = lle_v;
         }
         epi_sync();
         bool done = false;
-        if (sampler && need && !loglike) done = chn.post(row, h);
+        if (sampler && need && !loglike) done = fast ? rc.post(a, row, row, lle_v, mala) : chn.post(row, h);
         if (sampler && !loglike && a.welford_on) {
           mask[r] = done ? 1 : 0;
           smp_sync();

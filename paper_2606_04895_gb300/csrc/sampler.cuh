@@ -478,6 +478,207 @@ struct Chain {
   }
 };
 
+// ---------------------------------------------------------------- register-resident MALA / MH
+// For d <= 8 the BF16 engine keeps a chain's position, gradient, proposal and log density in
+// the registers of the thread that owns the chain for the whole launch, instead of reading
+// them back from the state arrays around every evaluation.  Proposals (Eq. (2.3) and the
+// random walk), Philox streams and accept decisions are those of mala_* / mh_* above; the
+// state arrays are written through on every change, so they are current after each step.
+//
+// The decision log u < log alpha is first taken in FP32: log alpha is formed in FP32 together
+// with a bound on its rounding error relative to the FP64 expression of mala_post / mh_post,
+// and only when |log alpha - log u| is inside that bound is the FP64 expression evaluated,
+// so the outcome is always the FP64 one.  The acceptance statistic min(1, alpha) that feeds
+// step-size adaptation is summed from the FP32 log alpha.
+template <typename R>
+struct RegChain8 {
+  static constexpr int DB = 8;
+  R z[DB], g[DB], zp[DB], gp[DB];
+  R lp, e, s;
+  uint32_t iter;
+  int steps;
+
+  __device__ void load(const StepArgs<R> &a, int c) {
+    const R *zc = a.st.z + static_cast<size_t>(c) * a.dp, *gc = a.st.g + static_cast<size_t>(c) * a.dp;
+#pragma unroll
+    for (int i = 0; i < DB; ++i) {
+      z[i] = i < a.d ? zc[i] : R(0);
+      g[i] = i < a.d ? gc[i] : R(0);
+      zp[i] = R(0);
+      gp[i] = R(0);
+    }
+    lp = a.st.lp[c];
+    iter = a.st.iter[c];
+    steps = 0;
+    e = static_cast<R>(a.eps);
+    s = static_cast<R>(sqrt(2.0 * a.eps));
+  }
+
+  // x = mu + L v on the first d entries (same summation order as TargetView::to_x_prior)
+  static __device__ __forceinline__ void to_x(const TargetView<R> &t, const R *v, R *x) {
+#pragma unroll
+    for (int i = 0; i < DB; ++i) {
+      R acc = R(0);
+      if (i < t.d) {
+        acc = t.mu[i];
+#pragma unroll
+        for (int j = 0; j <= i; ++j) acc += t.L[i * t.d + j] * v[j];
+      }
+      x[i] = acc;
+    }
+  }
+
+  __device__ bool pre(const StepArgs<R> &a, int c, bool mala) {
+    if (steps >= a.n_steps) return false;
+    R xi[DB];
+#pragma unroll
+    for (int b = 0; b < DB / 4; ++b) {
+      R v[4] = {R(0), R(0), R(0), R(0)};
+      if (4 * b < a.d) {
+        uint32_t w[4];
+        Philox::block(a.seed, static_cast<uint32_t>(c), iter, kXi, static_cast<uint32_t>(b), w);
+        box_muller(u01<R>(w[0]), u01<R>(w[1]), v[0], v[1]);
+        box_muller(u01<R>(w[2]), u01<R>(w[3]), v[2], v[3]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) xi[4 * b + k] = v[k];
+    }
+    R *ze = a.st.ze + static_cast<size_t>(c) * a.dp;
+#pragma unroll
+    for (int i = 0; i < DB; ++i)
+      if (i < a.d) {
+        zp[i] = mala ? z[i] + e * g[i] + s * xi[i] : z[i] + e * xi[i];
+        ze[i] = zp[i];
+      }
+    return true;
+  }
+
+  // lle = logL at zp; gp (MALA) holds grad logL at zp.  Returns true (an iteration completed).
+  __device__ bool post(const StepArgs<R> &a, int c, int row, R lle, bool mala) {
+    const TargetView<R> &t = a.tgt;
+    const int d = a.d;
+    double acc_stat = a.st.acc_stat[c];
+    unsigned long long n_acc = a.st.accepts[c], n_ev = a.st.evals[c];
+    // log pi_z(zp) and its gradient (logpi_eval)
+    R x[DB];
+    to_x(t, zp, x);
+    bool inside = true;
+    double lpr = 0.0;
+#pragma unroll
+    for (int i = 0; i < DB; ++i)
+      if (i < d) {
+        if (!(x[i] >= t.lower[i] && x[i] <= t.upper[i])) inside = false;
+        if (t.any_gauss && t.gauss[i]) lpr -= 0.5 * static_cast<double>(x[i]) * static_cast<double>(x[i]);
+      }
+    const double lpp = static_cast<double>(lle) + (inside ? lpr : -INFINITY) + t.logdet;
+    if (mala && t.any_gauss) {
+#pragma unroll
+      for (int j = 0; j < DB; ++j)
+        if (j < d) {
+          R sg = 0;
+#pragma unroll
+          for (int i = j; i < DB; ++i)
+            if (i < d && t.gauss[i]) sg -= t.L[i * d + j] * x[i];
+          gp[j] += sg;
+        }
+    }
+    const double u = draw_uniform<double>(a.seed, static_cast<uint32_t>(c), iter, kAccept, 0);
+    bool acc;
+    float p;
+    if (!inside) {
+      acc = false;  // log alpha = -inf
+      p = 0.f;
+    } else {
+      float fwd = 0.f, rev = 0.f, fab = 0.f, rab = 0.f;
+      if (mala) {
+#pragma unroll
+        for (int i = 0; i < DB; ++i)
+          if (i < d) {
+            const float f = static_cast<float>(zp[i]) - static_cast<float>(z[i]) - static_cast<float>(e * g[i]);
+            const float r = static_cast<float>(z[i]) - static_cast<float>(zp[i]) - static_cast<float>(e * gp[i]);
+            const float fa = fabsf(static_cast<float>(zp[i])) + fabsf(static_cast<float>(z[i])) +
+                             fabsf(static_cast<float>(e * g[i]));
+            const float ra = fabsf(static_cast<float>(z[i])) + fabsf(static_cast<float>(zp[i])) +
+                             fabsf(static_cast<float>(e * gp[i]));
+            fwd += f * f;
+            rev += r * r;
+            fab += fa * fa;
+            rab += ra * ra;
+          }
+      }
+      const float inv4e = mala ? 0.25f / static_cast<float>(a.eps) : 0.f;
+      const float lpp32 = static_cast<float>(lpp), lp32 = static_cast<float>(lp);
+      const float la32 = (lpp32 - lp32) + (fwd - rev) * inv4e;
+      const float lu32 = logf(static_cast<float>(u));
+      // FP32 rounding of the sums of squares, of e*g, of the differences and of the final
+      // combination, with a factor 4 of margin; u has 25 significant bits (log u to 2^-24).
+      const float err = 0x1p-22f * (static_cast<float>(d + 10) * (fab + rab) * inv4e +
+                                    3.f * (fabsf(lpp32) + fabsf(lp32)) + 4.f * fabsf(lu32) + 4.f);
+      const float gap = la32 - lu32;
+      if (gap > err) acc = true;
+      else if (gap < -err) acc = false;
+      else {
+        // the FP64 expression of mala_post / mh_post
+        double la = lpp - static_cast<double>(lp);
+        if (mala) {
+          const double ed = a.eps;
+          double fw = 0.0, rv = 0.0;
+#pragma unroll
+          for (int i = 0; i < DB; ++i)
+            if (i < d) {
+              const double f = static_cast<double>(zp[i]) - z[i] - ed * g[i];
+              const double r = static_cast<double>(z[i]) - zp[i] - ed * gp[i];
+              fw += f * f;
+              rv += r * r;
+            }
+          la += (fw - rv) / (4.0 * ed);
+        }
+        acc = log(u) < la;
+      }
+      p = la32 >= 0.f ? 1.f : (la32 == la32 ? expf(la32) : 0.f);
+    }
+    R *zc = a.st.z + static_cast<size_t>(c) * a.dp, *gc = a.st.g + static_cast<size_t>(c) * a.dp;
+    if (acc) {
+#pragma unroll
+      for (int i = 0; i < DB; ++i)
+        if (i < d) {
+          z[i] = zp[i];
+          zc[i] = zp[i];
+          if (mala) {
+            g[i] = gp[i];
+            gc[i] = gp[i];
+          }
+        }
+      lp = static_cast<R>(lpp);
+      a.st.lp[c] = lp;
+    } else {
+      to_x(t, z, x);  // x-space record of the kept position
+    }
+    a.st.acc_stat[c] = acc_stat + static_cast<double>(p);
+    a.st.accepts[c] = n_acc + (acc ? 1ull : 0ull);
+    a.st.evals[c] = n_ev + 1ull;
+    // finish: iteration counter, sample record, Welford hand-off
+    const int st = steps;
+    iter += 1u;
+    a.st.iter[c] = iter;
+    if (a.samples && ((st + 1) % a.thin) == 0) {
+      R *dst = a.samples + (static_cast<size_t>(st / a.thin) * a.n_chains + c) * d;
+#pragma unroll
+      for (int i = 0; i < DB; ++i)
+        if (i < d) dst[i] = x[i];
+    }
+    if (a.welford_on) {
+      R *xb = a.xbuf + static_cast<size_t>(row) * a.dp;
+#pragma unroll
+      for (int i = 0; i < DB; ++i)
+        if (i < d) xb[i] = x[i];
+    }
+    steps = st + 1;
+    a.st.steps_done[c] = steps;
+    return true;
+  }
+};
+
 // Double-precision per-chain scratch lives after the R vectors of the work row.
 template <typename R>
 __device__ double *Chain<R>::dwork_ptr(int c) const {
