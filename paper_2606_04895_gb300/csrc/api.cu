@@ -268,7 +268,7 @@ Tc2Weights tc2_weights(bst_ctx *h, int fold, int n_rows) {
   w.out_m = static_cast<float>(h->out_m);
   w.out_s = static_cast<float>(h->out_s);
   w.scratch = static_cast<__nv_bfloat16 *>(h->scratch);
-  w.n_stages = tc2_stages(h->width, cs);
+  w.n_stages = tc2_stages(h->width, cs, h->depth);
   return w;
 }
 

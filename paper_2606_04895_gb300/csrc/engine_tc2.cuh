@@ -103,6 +103,10 @@ __device__ __forceinline__ void mma_commit_multicast(uint32_t bar, uint16_t mask
 __device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;\n" ::"r"(addr), "f"(v) : "memory");
 }
+__device__ __forceinline__ void st_cluster_v4f(uint32_t addr, float x, float y, float z, float w) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(x), "f"(y), "f"(z), "f"(w)
+               : "memory");
+}
 __device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared::cluster.u32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
 }
@@ -192,6 +196,11 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
   float *red = partial + CS * 128;                                // [EQ-1][128] column-group combine
   int *mask = reinterpret_cast<int *>(red + (kTc2EQ - 1) * 128);  // [128]
   float *sbias = reinterpret_cast<float *>(mask + 128);           // [D + 1][NS]: b_1..b_D, w_o slices
+  // register-resident chains (rank 0 writes them): [128][8] proposals (every rank), then on
+  // rank 0 [128][8] grad logL at the proposals and [128][8] the next proposal's noise
+  float *zbuf = sbias + (E.depth + 1) * NS;
+  float *gbuf = zbuf + 128 * 8;
+  float *xibuf = gbuf + 128 * 8;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = (CS > 1) ? cluster_rank() : 0u;
@@ -225,6 +234,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
       const int l = i / NS, j = c0g + i % NS;  // l = 0..D-1: bias of layer l+1; l = D: w_o
       sbias[i] = (l == 0) ? E.b1[j] : (l < D ? E.b[static_cast<size_t>(l - 1) * W + j] : E.wo[j]);
     }
+    for (int i = threadIdx.x; i < 3 * 128 * 8; i += kTc2Threads) zbuf[i] = 0.f;
   }
   tc_fence_before();
   __syncthreads();
@@ -357,7 +367,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
     // MALA / MH with d <= 8 (padded to 16) keep the chain in the sampler thread's registers
     const bool fast = (mala || a.mode == kModeMH) && a.d <= RegChain8<float>::DB && dp == 16;
     RegChain8<float> rc;
-    if (fast && sampler && valid) rc.load(a, row);
+    if (fast && sampler && valid) rc.load(a, row, zbuf + r * 8, gbuf + r * 8, xibuf + r * 8);
     if (sampler && valid && !loglike) {
       if (a.mode == kModeAIES) {
         for (int h = 0; h < 2; ++h) a.st.steps_done[chn.aies_walker(row, h)] = 0;
@@ -380,6 +390,18 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         if (sampler) {
           if (loglike) need = valid && ev == 0;
           else need = valid && (fast ? rc.pre(a, row, mala) : chn.pre(row, h));
+          if (fast && need && CS > 1) {
+            // the proposal (already in this rank's staging buffer) goes straight into every
+            // peer's operand staging buffer
+            const uint32_t zb = smem_u32(zbuf + r * 8);
+            const float4 z0 = *reinterpret_cast<const float4 *>(zbuf + r * 8);
+            const float4 z1 = *reinterpret_cast<const float4 *>(zbuf + r * 8 + 4);
+            for (int pr = 1; pr < CS; ++pr) {
+              const uint32_t dst = mapa(zb, static_cast<uint32_t>(pr));
+              st_cluster_v4f(dst, z0.x, z0.y, z0.z, z0.w);
+              st_cluster_v4f(dst + 16, z1.x, z1.y, z1.z, z1.w);
+            }
+          }
         }
         const bool any = epi_or(need);
         if (t < CS) {  // thread t signals rank t (the release arrives run in parallel)
@@ -394,27 +416,21 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
       if (c == 0) break;
       // ---- layer-1 operand [z_hi | z_lo | z_hi | 0] from ze (written by rank 0's samplers)
       {
-        const float *zr = a.st.ze + static_cast<size_t>(row) * a.st.ze_ld;
-        float zv[kMaxD];
-        for (int i = 0; i < dp; ++i) zv[i] = (valid && i < a.d) ? zr[i] : 0.f;
-        const int nch = E.kb1 * 8;  // 16-byte chunks in the row
+        const float *zr = fast ? zbuf + r * 8 : a.st.ze + static_cast<size_t>(row) * a.st.ze_ld;
+        const int nch = E.kb1 * 8;  // 16-byte chunks in the row; dp is a multiple of 16, so a
+                                    // chunk (8 values) lies inside one segment
         for (int j = ch * (nch / kTc2EQ); j < (ch + 1) * (nch / kTc2EQ); ++j) {
-          uint32_t w4[4];
-          for (int e2 = 0; e2 < 4; ++e2) {
-            float v2[2];
-            for (int u = 0; u < 2; ++u) {
-              const int kk = j * 8 + e2 * 2 + u;
-              const int seg = kk / dp, i = kk % dp;
-              float v = 0.f;
-              if (seg < 3) {
-                const float hi = __bfloat162float(__float2bfloat16_rn(zv[i]));
-                v = (seg == 1) ? (zv[i] - hi) : hi;
-              }
-              v2[u] = v;
-            }
-            w4[e2] = pack_bf16x2(v2[0], v2[1]);
+          const int seg = (j * 8) / dp, i0 = j * 8 - seg * dp;
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u;
+            const float zval = (valid && seg < 3 && i < a.d) ? zr[i] : 0.f;
+            const float hi = __bfloat162float(__float2bfloat16_rn(zval));
+            v[u] = (seg == 1) ? (zval - hi) : hi;
           }
-          st_shared_v4(act_addr + (j >> 3) * 16384 + sw128_off(r, j & 7), w4[0], w4[1], w4[2], w4[3]);
+          st_shared_v4(act_addr + (j >> 3) * 16384 + sw128_off(r, j & 7), pack_bf16x2(v[0], v[1]),
+                       pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
         }
       }
       fence_proxy_async();
@@ -422,6 +438,12 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
       if (t == 0) mbar_arrive(actf_bar);
       bool ok = true;
       for (int p = 0; p < nph; ++p) {
+        // while the second layer is in flight the chain does the evaluation-independent part
+        // of its accept step and draws the next proposal's noise
+        if (p == 1 && fast && sampler && need) {
+          rc.prep(a, row);
+          rc.prep_next(a, row);
+        }
         // adjoint phases read the stored activation h_{l-1}: start loading its first chunk now
         const bool adj_phase = (p >= D) && (p != 2 * D - 1);
         const __nv_bfloat16 *hprev =
@@ -634,14 +656,15 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
   }
 }
 
-inline size_t tc2_smem_bytes(int width, int cs, int stages) {
+inline size_t tc2_smem_bytes(int width, int cs, int stages, int depth) {
   const int ns = width / cs, tr = ns < 256 ? ns : 256;
   return 1024 + static_cast<size_t>(width / 64) * 16384 + static_cast<size_t>(stages) * tr * 128 +
-         8 * (2 * stages + 8) + 4 * (cs * 128 + kTc2EQ * 128) + 4 * 9 * ns + 64;
+         8 * (2 * stages + 8) + 4 * (cs * 128 + kTc2EQ * 128) + 4 * static_cast<size_t>(depth + 1) * ns +
+         3 * 4 * 128 * 8 + 64;
 }
-inline int tc2_stages_for(int width, int cs, int smem_cap) {
+inline int tc2_stages_for(int width, int cs, int depth, int smem_cap) {
   for (int s = kTcMaxStages + 2; s >= 2; --s)
-    if (tc2_smem_bytes(width, cs, s) <= static_cast<size_t>(smem_cap)) return s;
+    if (tc2_smem_bytes(width, cs, s, depth) <= static_cast<size_t>(smem_cap)) return s;
   return 2;
 }
 

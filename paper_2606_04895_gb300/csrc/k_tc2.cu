@@ -13,7 +13,7 @@ template <int W, int CS>
 cudaError_t launch_one(const StepArgs<float> &a, const Tc2Weights &w, cudaStream_t s) {
   const int tiles = (a.n_rows + kTcRows - 1) / kTcRows;
   if (tiles == 0) return cudaSuccess;
-  const size_t smem = tc2_smem_bytes(W, CS, w.n_stages);
+  const size_t smem = tc2_smem_bytes(W, CS, w.n_stages, w.depth);
   auto k = tc2_chain_kernel<W, CS>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
@@ -39,14 +39,14 @@ cudaError_t launch_one(const StepArgs<float> &a, const Tc2Weights &w, cudaStream
 }
 }  // namespace
 
-int tc2_stages(int width, int cs) { return tc2_stages_for(width, cs, kSmemCap); }
+int tc2_stages(int width, int cs, int depth) { return tc2_stages_for(width, cs, depth, kSmemCap); }
 
 // Clusters of this configuration that can be co-resident (diagnostic).
-int tc2_max_active_clusters(int width, int cs) {
+int tc2_max_active_clusters(int width, int cs, int depth) {
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(kTc2Threads, 1, 1);
   cfg.gridDim = dim3(cs * 64, 1, 1);
-  cfg.dynamicSmemBytes = tc2_smem_bytes(width, cs, tc2_stages(width, cs));
+  cfg.dynamicSmemBytes = tc2_smem_bytes(width, cs, tc2_stages(width, cs, depth), depth);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cs;

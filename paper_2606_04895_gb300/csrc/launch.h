@@ -19,7 +19,7 @@ cudaError_t launch_ana_simt_f64(const StepArgs<double> &a, const AnaWeights<doub
 int simt_rows_per_tile(int precision, int width, int lik_kind);
 // cluster tcgen05 kernel: cs in {1, 2, 4}
 cudaError_t launch_emu_tc2(const StepArgs<float> &a, const Tc2Weights &w, cudaStream_t s);
-int tc2_stages(int width, int cs);
+int tc2_stages(int width, int cs, int depth);
 int tc2_cluster_size(int n_rows, int width);
 
 // Weight preparation (k_aux.cu).

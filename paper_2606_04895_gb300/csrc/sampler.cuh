@@ -479,9 +479,10 @@ struct Chain {
 };
 
 // ---------------------------------------------------------------- register-resident MALA / MH
-// For d <= 8 the BF16 engine keeps a chain's position, gradient, proposal and log density in
-// the registers of the thread that owns the chain for the whole launch, instead of reading
-// them back from the state arrays around every evaluation.  Proposals (Eq. (2.3) and the
+// For d <= 8 the BF16 engine keeps a chain's position, gradient and log density in the
+// registers of the thread that owns the chain for the whole launch (proposal and proposal
+// gradient in shared memory), instead of reading them back from the state arrays around
+// every evaluation.  Proposals (Eq. (2.3) and the
 // random walk), Philox streams and accept decisions are those of mala_* / mh_* above; the
 // state arrays are written through on every change, so they are current after each step.
 //
@@ -493,12 +494,22 @@ struct Chain {
 template <typename R>
 struct RegChain8 {
   static constexpr int DB = 8;
-  R z[DB], g[DB], zp[DB], gp[DB];
+  R z[DB], g[DB];
+  // proposal, grad logL there, and the next proposal's noise (have_xi): DB entries each in
+  // the caller's shared memory
+  R *zp, *gp, *xi;
   R lp, e, s;
   uint32_t iter;
   int steps;
+  double acc_stat, lpr, u;
+  unsigned long long n_acc, n_ev;
+  float lu32;
+  bool inside, prepped, have_xi;
 
-  __device__ void load(const StepArgs<R> &a, int c) {
+  __device__ void load(const StepArgs<R> &a, int c, R *zp_smem, R *gp_smem, R *xi_smem) {
+    zp = zp_smem;
+    gp = gp_smem;
+    xi = xi_smem;
     const R *zc = a.st.z + static_cast<size_t>(c) * a.dp, *gc = a.st.g + static_cast<size_t>(c) * a.dp;
 #pragma unroll
     for (int i = 0; i < DB; ++i) {
@@ -509,9 +520,13 @@ struct RegChain8 {
     }
     lp = a.st.lp[c];
     iter = a.st.iter[c];
+    acc_stat = a.st.acc_stat[c];
+    n_acc = a.st.accepts[c];
+    n_ev = a.st.evals[c];
     steps = 0;
     e = static_cast<R>(a.eps);
     s = static_cast<R>(sqrt(2.0 * a.eps));
+    prepped = have_xi = false;
   }
 
   // x = mu + L v on the first d entries (same summation order as TargetView::to_x_prior)
@@ -527,22 +542,27 @@ struct RegChain8 {
       x[i] = acc;
     }
   }
-
-  __device__ bool pre(const StepArgs<R> &a, int c, bool mala) {
-    if (steps >= a.n_steps) return false;
-    R xi[DB];
+  // normals 0..DB-1 of stream (c, it, kXi), as draw_normals
+  static __device__ __forceinline__ void normals(const StepArgs<R> &a, int c, uint32_t it, R *out) {
 #pragma unroll
     for (int b = 0; b < DB / 4; ++b) {
       R v[4] = {R(0), R(0), R(0), R(0)};
       if (4 * b < a.d) {
         uint32_t w[4];
-        Philox::block(a.seed, static_cast<uint32_t>(c), iter, kXi, static_cast<uint32_t>(b), w);
+        Philox::block(a.seed, static_cast<uint32_t>(c), it, kXi, static_cast<uint32_t>(b), w);
         box_muller(u01<R>(w[0]), u01<R>(w[1]), v[0], v[1]);
         box_muller(u01<R>(w[2]), u01<R>(w[3]), v[2], v[3]);
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) xi[4 * b + k] = v[k];
+      for (int k = 0; k < 4; ++k) out[4 * b + k] = v[k];
     }
+  }
+
+  // Proposal z' written to zp (and to the state's evaluation row).
+  __device__ bool pre(const StepArgs<R> &a, int c, bool mala) {
+    if (steps >= a.n_steps) return false;
+    if (!have_xi) normals(a, c, iter, xi);
+    have_xi = false;
     R *ze = a.st.ze + static_cast<size_t>(c) * a.dp;
 #pragma unroll
     for (int i = 0; i < DB; ++i)
@@ -553,23 +573,40 @@ struct RegChain8 {
     return true;
   }
 
+  // The part of post that does not depend on the evaluation in flight: x of the proposal and
+  // its prior term, the accept uniform, and the noise of the next iteration's proposal.
+  __device__ void prep(const StepArgs<R> &a, int c) {
+    const TargetView<R> &t = a.tgt;
+    R xp[DB];
+    to_x(t, zp, xp);
+    inside = true;
+    lpr = 0.0;
+#pragma unroll
+    for (int i = 0; i < DB; ++i)
+      if (i < a.d) {
+        if (!(xp[i] >= t.lower[i] && xp[i] <= t.upper[i])) inside = false;
+        if (t.any_gauss && t.gauss[i]) lpr -= 0.5 * static_cast<double>(xp[i]) * static_cast<double>(xp[i]);
+      }
+    u = draw_uniform<double>(a.seed, static_cast<uint32_t>(c), iter, kAccept, 0);
+    lu32 = logf(static_cast<float>(u));
+    prepped = true;
+  }
+  __device__ void prep_next(const StepArgs<R> &a, int c) {
+    if (steps + 1 < a.n_steps) {
+      normals(a, c, iter + 1u, xi);
+      have_xi = true;
+    }
+  }
+
   // lle = logL at zp; gp (MALA) holds grad logL at zp.  Returns true (an iteration completed).
   __device__ bool post(const StepArgs<R> &a, int c, int row, R lle, bool mala) {
     const TargetView<R> &t = a.tgt;
     const int d = a.d;
-    double acc_stat = a.st.acc_stat[c];
-    unsigned long long n_acc = a.st.accepts[c], n_ev = a.st.evals[c];
+    if (!prepped) prep(a, c);
+    prepped = false;
+    R xp[DB];
+    to_x(t, zp, xp);
     // log pi_z(zp) and its gradient (logpi_eval)
-    R x[DB];
-    to_x(t, zp, x);
-    bool inside = true;
-    double lpr = 0.0;
-#pragma unroll
-    for (int i = 0; i < DB; ++i)
-      if (i < d) {
-        if (!(x[i] >= t.lower[i] && x[i] <= t.upper[i])) inside = false;
-        if (t.any_gauss && t.gauss[i]) lpr -= 0.5 * static_cast<double>(x[i]) * static_cast<double>(x[i]);
-      }
     const double lpp = static_cast<double>(lle) + (inside ? lpr : -INFINITY) + t.logdet;
     if (mala && t.any_gauss) {
 #pragma unroll
@@ -578,11 +615,10 @@ struct RegChain8 {
           R sg = 0;
 #pragma unroll
           for (int i = j; i < DB; ++i)
-            if (i < d && t.gauss[i]) sg -= t.L[i * d + j] * x[i];
+            if (i < d && t.gauss[i]) sg -= t.L[i * d + j] * xp[i];
           gp[j] += sg;
         }
     }
-    const double u = draw_uniform<double>(a.seed, static_cast<uint32_t>(c), iter, kAccept, 0);
     bool acc;
     float p;
     if (!inside) {
@@ -609,7 +645,6 @@ struct RegChain8 {
       const float inv4e = mala ? 0.25f / static_cast<float>(a.eps) : 0.f;
       const float lpp32 = static_cast<float>(lpp), lp32 = static_cast<float>(lp);
       const float la32 = (lpp32 - lp32) + (fwd - rev) * inv4e;
-      const float lu32 = logf(static_cast<float>(u));
       // FP32 rounding of the sums of squares, of e*g, of the differences and of the final
       // combination, with a factor 4 of margin; u has 25 significant bits (log u to 2^-24).
       const float err = 0x1p-22f * (static_cast<float>(d + 10) * (fab + rab) * inv4e +
@@ -638,9 +673,11 @@ struct RegChain8 {
       p = la32 >= 0.f ? 1.f : (la32 == la32 ? expf(la32) : 0.f);
     }
     R *zc = a.st.z + static_cast<size_t>(c) * a.dp, *gc = a.st.g + static_cast<size_t>(c) * a.dp;
+    R x[DB];
     if (acc) {
 #pragma unroll
-      for (int i = 0; i < DB; ++i)
+      for (int i = 0; i < DB; ++i) {
+        x[i] = xp[i];
         if (i < d) {
           z[i] = zp[i];
           zc[i] = zp[i];
@@ -649,14 +686,18 @@ struct RegChain8 {
             gc[i] = gp[i];
           }
         }
+      }
       lp = static_cast<R>(lpp);
       a.st.lp[c] = lp;
     } else {
       to_x(t, z, x);  // x-space record of the kept position
     }
-    a.st.acc_stat[c] = acc_stat + static_cast<double>(p);
-    a.st.accepts[c] = n_acc + (acc ? 1ull : 0ull);
-    a.st.evals[c] = n_ev + 1ull;
+    acc_stat += static_cast<double>(p);
+    n_acc += acc ? 1ull : 0ull;
+    n_ev += 1ull;
+    a.st.acc_stat[c] = acc_stat;
+    a.st.accepts[c] = n_acc;
+    a.st.evals[c] = n_ev;
     // finish: iteration counter, sample record, Welford hand-off
     const int st = steps;
     iter += 1u;
