@@ -179,20 +179,25 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
   constexpr int TCOLS = NS < 64 ? 64 : NS;   // TMEM columns (>= 2 dp for the input gradient)
   constexpr int CW = NS / kTc2EQ;            // slice columns per epilogue warp
   constexpr int CPW = CW / 32;               // 32-column chunks per epilogue warp
+  // each epilogue warp sends its own rows x columns to the peers as soon as they are written
+  // (whole 64-column K blocks: 32 rows of a K block are 4 KB contiguous in the swizzled layout)
+  constexpr bool kWarpSend = CS > 1 && CW % 64 == 0;
 
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *act = base;
   uint8_t *stages = act + KBW * 16384;
   const int S = E.n_stages;
   uint64_t *bars = reinterpret_cast<uint64_t *>(stages + S * STAGE);
-  // bars: full[S] empty[S] go act_full acc fin peer_free part
+  // bars: full[S] empty[S] go act_full acc fin peer_free part peer_free_last
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S);
   const uint32_t go_bar = smem_u32(bars + 2 * S), actf_bar = smem_u32(bars + 2 * S + 1);
   const uint32_t acc_bar = smem_u32(bars + 2 * S + 2), fin_bar = smem_u32(bars + 2 * S + 3);
   const uint32_t free_bar = smem_u32(bars + 2 * S + 4), part_bar = smem_u32(bars + 2 * S + 5);
-  volatile int *cmd = reinterpret_cast<volatile int *>(bars + 2 * S + 6);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 7);
-  float *partial = reinterpret_cast<float *>(bars + 2 * S + 8);  // [CS][128] (rank 0 gathers)
+  const uint32_t free2_bar = smem_u32(bars + 2 * S + 6);
+  volatile int *cmd = reinterpret_cast<volatile int *>(bars + 2 * S + 7);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 8);
+  // (slot 2 S + 9 is padding: everything from `partial` on is 16-byte aligned for vector access)
+  float *partial = reinterpret_cast<float *>(bars + 2 * S + 10);  // [CS][128] (rank 0 gathers)
   float *red = partial + CS * 128;                                // [EQ-1][128] column-group combine
   int *mask = reinterpret_cast<int *>(red + (kTc2EQ - 1) * 128);  // [128]
   float *sbias = reinterpret_cast<float *>(mask + 128);           // [D + 1][NS]: b_1..b_D, w_o slices
@@ -220,6 +225,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
     mbar_init(fin_bar, 1);
     mbar_init(free_bar, CS > 1 ? CS - 1 : 1);
     mbar_init(part_bar, CS);
+    mbar_init(free2_bar, CS > 1 ? CS - 1 : 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 1) {
@@ -339,8 +345,10 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
           }
           if (ok) {
             mma_commit(acc_bar);
-            // once these MMAs are done our activation buffer may be overwritten by the peers
-            if (CS > 1 && p + 1 < phases) mma_commit_multicast(free_bar, peer_mask);
+            // once these MMAs are done our activation buffer may be overwritten by the peers,
+            // and every slice they sent us for this phase has landed (the last phase of an
+            // evaluation signals a barrier of its own, so neither barrier runs two phases ahead)
+            if (CS > 1) mma_commit_multicast(p + 1 < phases ? free_bar : free2_bar, peer_mask);
           }
         }
       }
@@ -363,9 +371,9 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
     const int col0 = static_cast<int>(rank) * NS + ch * CW;  // first global column of this warp
     Chain<float> chn(a);
     const bool loglike = a.mode == kModeLoglike;
-    const bool mala = a.mode == kModeMALA;
-    // MALA / MH with d <= 8 (padded to 16) keep the chain in the sampler thread's registers
-    const bool fast = (mala || a.mode == kModeMH) && a.d <= RegChain8<float>::DB && dp == 16;
+    const bool mala = a.mode == kModeMALA, hmc = a.mode == kModeHMC;
+    // MALA / MH / HMC with d <= 8 (padded to 16) keep the chain in the sampler thread's registers
+    const bool fast = (mala || hmc || a.mode == kModeMH) && a.d <= RegChain8<float>::DB && dp == 16;
     RegChain8<float> rc;
     if (fast && sampler && valid) rc.load(a, row, zbuf + r * 8, gbuf + r * 8, xibuf + r * 8);
     if (sampler && valid && !loglike) {
@@ -378,7 +386,18 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
       }
     }
     epi_sync();
-    uint32_t acc_par = 0, go_par = 0, free_par = 0, part_par = 0;
+    uint32_t acc_par = 0, go_par = 0, free_par = 0, free2_par = 0, part_par = 0;
+    // The peers' MMAs of a phase release our activation buffer (free_bar).  The epilogue of a
+    // distributing phase waits for that before writing the buffer; the release of an
+    // evaluation's last phase (free2_bar) is taken before the next layer-1 operand is written
+    // (or at exit).
+    bool free_pending = false;
+    auto wait_free = [&](uint32_t bar, uint32_t &par) -> bool {
+      int got = 1;
+      if (lane == 0) got = mbar_wait_cluster(bar, par, a.status) ? 1 : 0;
+      par ^= 1;
+      return __shfl_sync(0xffffffffu, got, 0) != 0;
+    };
     const size_t sstride = static_cast<size_t>(D > 1 ? D - 1 : 1) * W;
     const float c0 = -0.5f * E.out_s;
     for (int ev = 0;; ++ev) {
@@ -389,7 +408,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         if (ev > 0) epi_sync();  // a proposal may read positions other threads just accepted (AIES)
         if (sampler) {
           if (loglike) need = valid && ev == 0;
-          else need = valid && (fast ? rc.pre(a, row, mala) : chn.pre(row, h));
+          else need = valid && (fast ? (hmc ? rc.hmc_pre(a, row) : rc.pre(a, row, mala)) : chn.pre(row, h));
           if (fast && need && CS > 1) {
             // the proposal (already in this rank's staging buffer) goes straight into every
             // peer's operand staging buffer
@@ -414,6 +433,10 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
       go_par ^= 1;
       const int c = *cmd;
       if (c == 0) break;
+      if (free_pending) {
+        wait_free(free2_bar, free2_par);  // a timeout is recorded in the status word
+        free_pending = false;
+      }
       // ---- layer-1 operand [z_hi | z_lo | z_hi | 0] from ze (written by rank 0's samplers)
       {
         const float *zr = fast ? zbuf + r * 8 : a.st.ze + static_cast<size_t>(row) * a.st.ze_ld;
@@ -466,6 +489,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         const bool fwd = p < D;
         const bool last_fwd = p == D - 1;
         const bool distribute = (p + 1 < nph);  // this phase's output feeds another phase
+        if (CS > 1 && distribute && !wait_free(free_bar, free_par)) ok = false;
         if (p == 2 * D - 1) {
           // input gradient: g_i = acc[i] + acc[dp + i] (every rank computes it, rank 0 writes)
           if (ch == 0) {
@@ -591,18 +615,28 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         }
         if (distribute) {
           fence_proxy_async();
+          if (kWarpSend) {
+            // this warp's rows (32 q ..) of its K blocks, to every peer's buffer at the same place
+            __syncwarp();
+            if (lane == 0 && ok)
+              for (int kb2 = 0; kb2 < CW / 64; ++kb2) {
+                const uint32_t src = act_addr + static_cast<uint32_t>(col0 / 64 + kb2) * 16384 + q * 4096;
+                for (int pr = 0; pr < CS; ++pr)
+                  if (pr != static_cast<int>(rank))
+                    bulk_s2cluster(mapa(src, pr), src, 4096, mapa(actf_bar, pr));
+              }
+          }
           epi_sync();
           if (t == 0) {
             if (CS > 1) {
-              // wait until every peer's MMAs of this phase have released its buffer, then copy
-              if (!mbar_wait_cluster(free_bar, free_par, a.status)) ok = false;
-              free_par ^= 1;
-              const uint32_t off = static_cast<uint32_t>(rank) * SLICE_BYTES;  // slice = NS/64 K blocks
+              // own slice written (the arrive) and (CS - 1) slices expected from the peers
               mbar_expect_tx(actf_bar, (CS - 1) * SLICE_BYTES);
-              if (ok)
+              if (!kWarpSend && ok) {
+                const uint32_t off = static_cast<uint32_t>(rank) * SLICE_BYTES;  // slice = NS/64 K blocks
                 for (int pr = 0; pr < CS; ++pr)
                   if (pr != static_cast<int>(rank))
                     bulk_s2cluster(mapa(act_addr + off, pr), act_addr + off, SLICE_BYTES, mapa(actf_bar, pr));
+              }
             } else {
               mbar_arrive(actf_bar);
             }
@@ -622,6 +656,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
           }
         break;
       }
+      free_pending = CS > 1;
       // ---- accept (rank 0): logL from the cluster-reduced output dot, then the samplers
       if (rank == 0) {
         const bool got = mbar_wait_cluster(part_bar, part_par, a.status);
@@ -635,7 +670,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         }
         epi_sync();
         bool done = false;
-        if (sampler && need && !loglike) done = fast ? rc.post(a, row, row, lle_v, mala) : chn.post(row, h);
+        if (sampler && need && !loglike)
+          done = fast ? (hmc ? rc.hmc_post(a, row, row, lle_v) : rc.post(a, row, row, lle_v, mala)) : chn.post(row, h);
         if (sampler && !loglike && a.welford_on) {
           mask[r] = done ? 1 : 0;
           smp_sync();
@@ -645,6 +681,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         }
       }
     }
+    // the peers' release of the last phase: no copy or MMA arrive may still target this CTA
+    if (free_pending) wait_free(free2_bar, free2_par);
   }
   tc_fence_before();
   __syncthreads();
@@ -659,7 +697,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
 inline size_t tc2_smem_bytes(int width, int cs, int stages, int depth) {
   const int ns = width / cs, tr = ns < 256 ? ns : 256;
   return 1024 + static_cast<size_t>(width / 64) * 16384 + static_cast<size_t>(stages) * tr * 128 +
-         8 * (2 * stages + 8) + 4 * (cs * 128 + kTc2EQ * 128) + 4 * static_cast<size_t>(depth + 1) * ns +
+         8 * (2 * stages + 10) + 4 * (cs * 128 + kTc2EQ * 128) + 4 * static_cast<size_t>(depth + 1) * ns +
          3 * 4 * 128 * 8 + 64;
 }
 inline int tc2_stages_for(int width, int cs, int depth, int smem_cap) {

@@ -478,29 +478,34 @@ struct Chain {
   }
 };
 
-// ---------------------------------------------------------------- register-resident MALA / MH
+// ---------------------------------------------------------------- register-resident MALA / MH / HMC
 // For d <= 8 the BF16 engine keeps a chain's position, gradient and log density in the
-// registers of the thread that owns the chain for the whole launch (proposal and proposal
-// gradient in shared memory), instead of reading them back from the state arrays around
-// every evaluation.  Proposals (Eq. (2.3) and the
-// random walk), Philox streams and accept decisions are those of mala_* / mh_* above; the
-// state arrays are written through on every change, so they are current after each step.
+// registers of the thread that owns the chain for the whole launch (the point under
+// evaluation, its gradient and the MALA noise / HMC momentum in shared memory), instead of
+// reading them back from the state arrays around every evaluation.  Proposals (Eq. (2.3),
+// the random walk, and the leapfrog of Eqs. (2.7)-(2.8)), Philox streams and accept decisions
+// are those of mala_* / mh_* / hmc_* above; the state arrays are written through on every
+// change, so they are current after each step.
 //
-// The decision log u < log alpha is first taken in FP32: log alpha is formed in FP32 together
-// with a bound on its rounding error relative to the FP64 expression of mala_post / mh_post,
-// and only when |log alpha - log u| is inside that bound is the FP64 expression evaluated,
-// so the outcome is always the FP64 one.  The acceptance statistic min(1, alpha) that feeds
+// The decision log u < log alpha is first taken in FP32: for MALA / MH log alpha is formed
+// in FP32 together with a bound on its rounding error relative to the FP64 expression of
+// mala_post / mh_post (HMC forms H0 - H1 in FP64 as hmc_post does), log u with logf, and only
+// when |log alpha - log u| is inside the bound is the FP64 comparison evaluated, so the
+// outcome is always the FP64 one.  The acceptance statistic min(1, alpha) that feeds
 // step-size adaptation is summed from the FP32 log alpha.
 template <typename R>
 struct RegChain8 {
   static constexpr int DB = 8;
   R z[DB], g[DB];
-  // proposal, grad logL there, and the next proposal's noise (have_xi): DB entries each in
-  // the caller's shared memory
+  // point under evaluation (MALA / MH proposal, HMC z1), grad logL there (HMC g1), and the
+  // next MALA proposal's noise (have_xi) or the HMC momentum q1: DB entries each in the
+  // caller's shared memory
   R *zp, *gp, *xi;
   R lp, e, s;
   uint32_t iter;
   int steps;
+  int nlf;    // HMC: leapfrogs of the current trajectory done
+  double h0;  // HMC: H at the start of the trajectory
   double acc_stat, lpr, u;
   unsigned long long n_acc, n_ev;
   float lu32;
@@ -524,6 +529,8 @@ struct RegChain8 {
     n_acc = a.st.accepts[c];
     n_ev = a.st.evals[c];
     steps = 0;
+    nlf = 0;
+    h0 = 0.0;
     e = static_cast<R>(a.eps);
     s = static_cast<R>(sqrt(2.0 * a.eps));
     prepped = have_xi = false;
@@ -592,10 +599,138 @@ struct RegChain8 {
     prepped = true;
   }
   __device__ void prep_next(const StepArgs<R> &a, int c) {
+    if (a.mode == kModeHMC) return;
     if (steps + 1 < a.n_steps) {
       normals(a, c, iter + 1u, xi);
       have_xi = true;
     }
+  }
+
+  // HMC: one leapfrog of the current trajectory (a new trajectory draws its momentum);
+  // z1 goes to zp for evaluation.  Same operations as hmc_pre.
+  __device__ bool hmc_pre(const StepArgs<R> &a, int c) {
+    if (steps >= a.n_steps) return false;
+    R *q1 = xi, *g1 = gp, *z1 = zp;
+    if (nlf == 0) {
+      normals(a, c, iter, q1);
+      double qq = 0.0;
+#pragma unroll
+      for (int i = 0; i < DB; ++i)
+        if (i < a.d) {
+          qq += static_cast<double>(q1[i]) * q1[i];
+          z1[i] = z[i];
+          g1[i] = g[i];
+        }
+      h0 = -static_cast<double>(lp) + 0.5 * qq;
+    }
+    R *ze = a.st.ze + static_cast<size_t>(c) * a.dp;
+#pragma unroll
+    for (int i = 0; i < DB; ++i)
+      if (i < a.d) {
+        q1[i] += R(0.5) * e * g1[i];
+        z1[i] += e * q1[i];
+        ze[i] = z1[i];
+      }
+    return true;
+  }
+  // HMC: close the leapfrog (gp holds grad logL at z1); after n_leapfrog of them, the
+  // accept of hmc_post.  Returns whether the trajectory (an iteration) completed.
+  __device__ bool hmc_post(const StepArgs<R> &a, int c, int row, R lle) {
+    const TargetView<R> &t = a.tgt;
+    const int d = a.d;
+    const bool last = nlf + 1 >= a.n_leapfrog;
+    if (!prepped) prep(a, c);
+    prepped = false;
+    R *q1 = xi, *g1 = gp, *z1 = zp;
+    R xp[DB];
+    to_x(t, z1, xp);
+    const double lp1 = static_cast<double>(lle) + (inside ? lpr : -INFINITY) + t.logdet;
+    if (t.any_gauss) {
+#pragma unroll
+      for (int j = 0; j < DB; ++j)
+        if (j < d) {
+          R sg = 0;
+#pragma unroll
+          for (int i = j; i < DB; ++i)
+            if (i < d && t.gauss[i]) sg -= t.L[i * d + j] * xp[i];
+          g1[j] += sg;
+        }
+    }
+    double qq = 0.0;
+#pragma unroll
+    for (int i = 0; i < DB; ++i)
+      if (i < d) {
+        q1[i] += R(0.5) * e * g1[i];
+        qq += static_cast<double>(q1[i]) * q1[i];
+      }
+    n_ev += 1ull;
+    a.st.evals[c] = n_ev;
+    nlf += 1;
+    if (!last) return false;
+    nlf = 0;
+    const double h1 = -lp1 + 0.5 * qq;
+    const double la = h0 - h1;
+    const float la32 = static_cast<float>(la);
+    const float err = 0x1p-21f * (1.f + fabsf(lu32));  // log u by logf; la is the FP64 value
+    const float gap = la32 - lu32;
+    bool acc;
+    if (!(la == la)) acc = false;
+    else if (gap > err) acc = true;
+    else if (gap < -err) acc = false;
+    else acc = log(u) < la;
+    const float p = la32 >= 0.f ? 1.f : (la32 == la32 ? expf(la32) : 0.f);
+    return finish_step(a, c, row, acc, p, z1, g1, lp1, xp, true);
+  }
+
+  // Accept bookkeeping shared by the three kernels: state update (write-through), counters,
+  // iteration counter, sample record and Welford hand-off.  xnew = x of znew.
+  __device__ bool finish_step(const StepArgs<R> &a, int c, int row, bool acc, float p, const R *znew,
+                              const R *gnew, double lpnew, const R *xnew, bool with_grad) {
+    const TargetView<R> &t = a.tgt;
+    const int d = a.d;
+    R *zc = a.st.z + static_cast<size_t>(c) * a.dp, *gc = a.st.g + static_cast<size_t>(c) * a.dp;
+    R x[DB];
+    if (acc) {
+#pragma unroll
+      for (int i = 0; i < DB; ++i) {
+        x[i] = xnew[i];
+        if (i < d) {
+          z[i] = znew[i];
+          zc[i] = z[i];
+          if (with_grad) {
+            g[i] = gnew[i];
+            gc[i] = g[i];
+          }
+        }
+      }
+      lp = static_cast<R>(lpnew);
+      a.st.lp[c] = lp;
+    } else {
+      to_x(t, z, x);  // x-space record of the kept position
+    }
+    acc_stat += static_cast<double>(p);
+    n_acc += acc ? 1ull : 0ull;
+    a.st.acc_stat[c] = acc_stat;
+    a.st.accepts[c] = n_acc;
+    // finish: iteration counter, sample record, Welford hand-off
+    const int st = steps;
+    iter += 1u;
+    a.st.iter[c] = iter;
+    if (a.samples && ((st + 1) % a.thin) == 0) {
+      R *dst = a.samples + (static_cast<size_t>(st / a.thin) * a.n_chains + c) * d;
+#pragma unroll
+      for (int i = 0; i < DB; ++i)
+        if (i < d) dst[i] = x[i];
+    }
+    if (a.welford_on) {
+      R *xb = a.xbuf + static_cast<size_t>(row) * a.dp;
+#pragma unroll
+      for (int i = 0; i < DB; ++i)
+        if (i < d) xb[i] = x[i];
+    }
+    steps = st + 1;
+    a.st.steps_done[c] = steps;
+    return true;
   }
 
   // lle = logL at zp; gp (MALA) holds grad logL at zp.  Returns true (an iteration completed).
@@ -672,51 +807,9 @@ struct RegChain8 {
       }
       p = la32 >= 0.f ? 1.f : (la32 == la32 ? expf(la32) : 0.f);
     }
-    R *zc = a.st.z + static_cast<size_t>(c) * a.dp, *gc = a.st.g + static_cast<size_t>(c) * a.dp;
-    R x[DB];
-    if (acc) {
-#pragma unroll
-      for (int i = 0; i < DB; ++i) {
-        x[i] = xp[i];
-        if (i < d) {
-          z[i] = zp[i];
-          zc[i] = zp[i];
-          if (mala) {
-            g[i] = gp[i];
-            gc[i] = gp[i];
-          }
-        }
-      }
-      lp = static_cast<R>(lpp);
-      a.st.lp[c] = lp;
-    } else {
-      to_x(t, z, x);  // x-space record of the kept position
-    }
-    acc_stat += static_cast<double>(p);
-    n_acc += acc ? 1ull : 0ull;
     n_ev += 1ull;
-    a.st.acc_stat[c] = acc_stat;
-    a.st.accepts[c] = n_acc;
     a.st.evals[c] = n_ev;
-    // finish: iteration counter, sample record, Welford hand-off
-    const int st = steps;
-    iter += 1u;
-    a.st.iter[c] = iter;
-    if (a.samples && ((st + 1) % a.thin) == 0) {
-      R *dst = a.samples + (static_cast<size_t>(st / a.thin) * a.n_chains + c) * d;
-#pragma unroll
-      for (int i = 0; i < DB; ++i)
-        if (i < d) dst[i] = x[i];
-    }
-    if (a.welford_on) {
-      R *xb = a.xbuf + static_cast<size_t>(row) * a.dp;
-#pragma unroll
-      for (int i = 0; i < DB; ++i)
-        if (i < d) xb[i] = x[i];
-    }
-    steps = st + 1;
-    a.st.steps_done[c] = steps;
-    return true;
+    return finish_step(a, c, row, acc, p, zp, gp, lpp, xp, mala);
   }
 };
 
