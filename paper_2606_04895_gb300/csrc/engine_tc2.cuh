@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
   constexpr int TCOLS = NS < 64 ? 64 : NS;   // TMEM columns (>= 2 dp for the input gradient)
   constexpr int CW = NS / kTc2EQ;            // slice columns per epilogue warp
   constexpr int CPW = CW / 32;               // 32-column chunks per epilogue warp
+  constexpr int NOWN = NS / 64;              // K blocks of a layer input this rank computed itself
   // each epilogue warp sends its own rows x columns to the peers as soon as they are written
   // (whole 64-column K blocks: 32 rows of a K block are 4 KB contiguous in the swizzled layout)
   constexpr bool kWarpSend = CS > 1 && CW % 64 == 0;
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
   uint8_t *stages = act + KBW * 16384;
   const int S = E.n_stages;
   uint64_t *bars = reinterpret_cast<uint64_t *>(stages + S * STAGE);
-  // bars: full[S] empty[S] go act_full acc fin peer_free part peer_free_last
+  // bars: full[S] empty[S] go act_full acc fin peer_free part peer_free_last (cmd tmem) own
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S);
   const uint32_t go_bar = smem_u32(bars + 2 * S), actf_bar = smem_u32(bars + 2 * S + 1);
   const uint32_t acc_bar = smem_u32(bars + 2 * S + 2), fin_bar = smem_u32(bars + 2 * S + 3);
@@ -196,7 +197,9 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
   const uint32_t free2_bar = smem_u32(bars + 2 * S + 6);
   volatile int *cmd = reinterpret_cast<volatile int *>(bars + 2 * S + 7);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 8);
-  // (slot 2 S + 9 is padding: everything from `partial` on is 16-byte aligned for vector access)
+  // own slice of the next layer input written (the peers' slices complete act_full)
+  const uint32_t own_bar = smem_u32(bars + 2 * S + 9);
+  // everything from `partial` on is 16-byte aligned for vector access
   float *partial = reinterpret_cast<float *>(bars + 2 * S + 10);  // [CS][128] (rank 0 gathers)
   float *red = partial + CS * 128;                                // [EQ-1][128] column-group combine
   int *mask = reinterpret_cast<int *>(red + (kTc2EQ - 1) * 128);  // [128]
@@ -226,6 +229,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
     mbar_init(free_bar, CS > 1 ? CS - 1 : 1);
     mbar_init(part_bar, CS);
     mbar_init(free2_bar, CS > 1 ? CS - 1 : 1);
+    mbar_init(own_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 1) {
@@ -257,7 +261,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
       bool ok = true;
       const uint8_t *l1 = E.l1 + rank * E.l1_stride;
       const uint8_t *hid = E.hid + rank * E.hid_stride;
-      const int rot = tile % KBW;  // clusters start each layer at different K blocks (spreads L2 reads)
+      // layers after the first start at this rank's own K blocks (ready before the peers')
+      const int rot = static_cast<int>(rank) * NOWN;
       while (ok) {
         if (!mbar_wait_cluster(go_bar, go_par, a.status)) break;
         go_par ^= 1;
@@ -298,13 +303,13 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
     if (lane == 0) {
       uint32_t upar = 0;  // bit s: parity of the next wait on stage s
       int s = 0;
-      uint32_t go_par = 0, act_par = 0;
+      uint32_t go_par = 0, act_par = 0, own_par = 0;
       bool ok = true;
       const uint32_t idn = idesc_bf16(128, TR), idg = idesc_bf16(128, 2 * dp);
       // descriptors of K block 0 of the activation and of stage 0; K block kb / stage s / the
       // k-th 16-wide step are offsets of kb * 16384, s * STAGE and k * 32 bytes (address >> 4)
       const uint64_t adesc0 = sw128_desc(smem_u32(act)), bdesc0 = sw128_desc(smem_u32(stages));
-      const int rot = tile % KBW;
+      const int rot = static_cast<int>(rank) * NOWN;  // own K blocks first (as the producer)
       const uint16_t peer_mask = static_cast<uint16_t>(((1u << CS) - 1u) & ~(1u << rank));
       while (ok) {
         if (!mbar_wait_cluster(go_bar, go_par, a.status)) break;
@@ -313,11 +318,11 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         if (c == 0) break;
         const int phases = tc_num_phases(D, c == 2);
         for (int p = 0; p < phases && ok; ++p) {
-          if (!mbar_wait_cluster(actf_bar, act_par, a.status)) {
+          if (!mbar_wait(own_bar, own_par, a.status)) {
             ok = false;
             break;
           }
-          act_par ^= 1;
+          own_par ^= 1;
           tc_fence_after();
           const bool last = (p == 2 * D - 1);
           const int nsub = last ? 1 : NSUB;
@@ -327,6 +332,15 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
             int kb = (p == 0) ? 0 : rot;
             const uint32_t dcol = tmem + sb * TR;
             for (int j = 0; j < nkb; ++j) {
+              if (CS > 1 && p > 0 && j == NOWN) {
+                // the peers' slices of this layer input have landed
+                if (!mbar_wait_cluster(actf_bar, act_par, a.status)) {
+                  ok = false;
+                  break;
+                }
+                act_par ^= 1;
+                tc_fence_after();
+              }
               if (!mbar_wait(full0 + 8 * s, (upar >> s) & 1u, a.status)) {
                 ok = false;
                 break;
@@ -458,7 +472,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
       }
       fence_proxy_async();
       epi_sync();
-      if (t == 0) mbar_arrive(actf_bar);
+      if (t == 0) mbar_arrive(own_bar);  // the whole layer-1 operand is local
       bool ok = true;
       for (int p = 0; p < nph; ++p) {
         // while the second layer is in flight the chain does the evaluation-independent part
@@ -628,8 +642,9 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
           }
           epi_sync();
           if (t == 0) {
+            mbar_arrive(own_bar);  // own slice written
             if (CS > 1) {
-              // own slice written (the arrive) and (CS - 1) slices expected from the peers
+              // (CS - 1) slices expected from the peers
               mbar_expect_tx(actf_bar, (CS - 1) * SLICE_BYTES);
               if (!kWarpSend && ok) {
                 const uint32_t off = static_cast<uint32_t>(rank) * SLICE_BYTES;  // slice = NS/64 K blocks
@@ -637,8 +652,6 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
                   if (pr != static_cast<int>(rank))
                     bulk_s2cluster(mapa(act_addr + off, pr), act_addr + off, SLICE_BYTES, mapa(actf_bar, pr));
               }
-            } else {
-              mbar_arrive(actf_bar);
             }
           }
         }
