@@ -248,7 +248,7 @@ int cs_index(int cs) { return cs == 4 ? 2 : (cs == 2 ? 1 : 0); }
 
 Tc2Weights tc2_weights(bst_ctx *h, int fold, int n_rows) {
   Tc2Weights w;
-  const int cs = tc2_cluster_size(n_rows, h->width), ci = cs_index(cs);
+  const int cs = tc2_cluster_size(n_rows, h->width, h->depth), ci = cs_index(cs);
   w.depth = h->depth;
   w.width = h->width;
   w.dp = h->dp;

@@ -32,6 +32,15 @@ constexpr int kTc2EQ = 2;                       // epilogue warps per TMEM lane 
 constexpr int kTc2EpiThreads = 128 * kTc2EQ;    // 256
 constexpr int kTc2Threads = 64 + kTc2EpiThreads;  // producer warp, MMA warp, epilogue warps
 
+// Configurations whose stored activations h_1..h_{D-1} live in tensor memory (after the
+// accumulator columns, this rank's NS columns as BF16 pairs) instead of global scratch, and the
+// deepest network that fits there.
+__host__ __device__ constexpr bool tc2_h_in_tmem(int W, int CS) { return (W == 512 && CS == 4) || (W == 256 && CS >= 2); }
+__host__ __device__ constexpr int tc2_tcols(int W, int CS) { return W / CS < 64 ? 64 : W / CS; }
+__host__ __device__ constexpr int tc2_tmem_max_depth(int W, int CS) {
+  return tc2_h_in_tmem(W, CS) ? (512 - tc2_tcols(W, CS)) / (W / CS / 2) + 1 : 1 << 20;
+}
+
 struct Tc2Weights {
   int depth, width, dp, kb1, k16_l1;
   int cs;             // cluster size
@@ -153,6 +162,30 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+// Makes r depend on a preceding tcgen05.wait::ld (both statements are volatile, so they stay
+// in order and later reads of r see the loaded values).
+__device__ __forceinline__ void tmem_after_wait16(uint32_t *r) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 // Wait for outstanding tcgen05.ld and make the destination registers depend on the wait, so
 // the compiler cannot read them before the data has arrived.
 __device__ __forceinline__ void tmem_wait_ld_regs(uint32_t *r) {
@@ -216,6 +249,15 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
   const int D = E.depth, dp = E.dp;
   const bool grad = a.need_grad != 0;
   const int nph = tc_num_phases(D, grad);
+  // The activations h_1..h_{D-1} that the adjoint pass needs stay in tensor memory after the
+  // accumulator columns (this rank's NS columns, BF16 pairs) when they fit, else in global
+  // scratch.
+  constexpr bool h_tmem = tc2_h_in_tmem(W, CS);
+  const uint32_t tcols_alloc = h_tmem ? 512u : static_cast<uint32_t>(TCOLS);
+  if (D > tc2_tmem_max_depth(W, CS)) {  // the launch picks a cluster size that fits; never here
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadArg);
+    return;
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -229,12 +271,12 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
     mbar_init(free_bar, CS > 1 ? CS - 1 : 1);
     mbar_init(part_bar, CS);
     mbar_init(free2_bar, CS > 1 ? CS - 1 : 1);
-    mbar_init(own_bar, 1);
+    mbar_init(own_bar, kTc2EpiThreads / 32);  // one arrive per epilogue warp
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
-                 "r"(static_cast<uint32_t>(TCOLS))
+                 "r"(tcols_alloc)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
@@ -471,8 +513,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         }
       }
       fence_proxy_async();
-      epi_sync();
-      if (t == 0) mbar_arrive(own_bar);  // the whole layer-1 operand is local
+      __syncwarp();
+      if (lane == 0) mbar_arrive(own_bar);  // the whole layer-1 operand is local
       bool ok = true;
       for (int p = 0; p < nph; ++p) {
         // while the second layer is in flight the chain does the evaluation-independent part
@@ -484,7 +526,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         // adjoint phases read the stored activation h_{l-1}: start loading its first chunk now
         const bool adj_phase = (p >= D) && (p != 2 * D - 1);
         const __nv_bfloat16 *hprev =
-            (adj_phase && valid)
+            (adj_phase && valid && !h_tmem)
                 ? E.scratch + static_cast<size_t>(row) * sstride + static_cast<size_t>(2 * D - p - 2) * W
                 : nullptr;
         uint4 hcur[4];
@@ -544,7 +586,12 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
             const int tcol = ch * CW + cc * 32;                     // TMEM column
             uint32_t raw[32];
             tmem_ld32_nowait(trow + tcol, raw);
+            // stored activation h_{l-1} of these columns (tensor-memory copy)
+            uint32_t hv16[16];
+            const bool ht = adj_phase && h_tmem;
+            if (ht) tmem_ld16_nowait(trow + TCOLS + (2 * D - p - 2) * (NS / 2) + (tcol >> 1), hv16);
             tmem_wait_ld_regs(raw);
+            if (ht) tmem_after_wait16(hv16);
             float aux[32];
             uint4 hnext[4];
             if (fwd) {
@@ -556,6 +603,12 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
                 aux[4 * u + 1] = b4.y;
                 aux[4 * u + 2] = b4.z;
                 aux[4 * u + 3] = b4.w;
+              }
+            } else if (ht) {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                aux[2 * i] = __uint_as_float(hv16[i] << 16);           // low half: even column
+                aux[2 * i + 1] = __uint_as_float(hv16[i] & 0xFFFF0000u);  // high half: odd column
               }
             } else {
               // stored activations of this chunk were loaded one chunk ahead; start the next one
@@ -607,13 +660,16 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
                 st_shared_v4(act_addr + kb * 16384 + sw128_off(r, jj), pk[4 * u], pk[4 * u + 1], pk[4 * u + 2],
                              pk[4 * u + 3]);
               }
-              if (hkeep) {
+              if (fwd && grad && !last_fwd && h_tmem) {
+                tmem_st16(trow + TCOLS + p * (NS / 2) + (tcol >> 1), pk);
+              } else if (hkeep) {
                 uint4 *dst = reinterpret_cast<uint4 *>(hkeep + gcol);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) dst[u] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
               }
             }
           }
+          if (fwd && grad && !last_fwd && h_tmem) tmem_wait_st();
           if (last_fwd) {
             // per-row partial of w_o . h_D over this rank's columns, gathered on rank 0
             if (ch > 0) red[(ch - 1) * 128 + r] = part;
@@ -628,10 +684,14 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
           }
         }
         if (distribute) {
+          // this warp's part of the own slice is written: the next layer's MMAs on the own K
+          // blocks may start (one arrive per warp)
           fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(own_bar);
+          if (CS > 1 && t == 0) mbar_expect_tx(actf_bar, (CS - 1) * SLICE_BYTES);  // the peers' slices
           if (kWarpSend) {
             // this warp's rows (32 q ..) of its K blocks, to every peer's buffer at the same place
-            __syncwarp();
             if (lane == 0 && ok)
               for (int kb2 = 0; kb2 < CW / 64; ++kb2) {
                 const uint32_t src = act_addr + static_cast<uint32_t>(col0 / 64 + kb2) * 16384 + q * 4096;
@@ -639,19 +699,13 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
                   if (pr != static_cast<int>(rank))
                     bulk_s2cluster(mapa(src, pr), src, 4096, mapa(actf_bar, pr));
               }
-          }
-          epi_sync();
-          if (t == 0) {
-            mbar_arrive(own_bar);  // own slice written
-            if (CS > 1) {
-              // (CS - 1) slices expected from the peers
-              mbar_expect_tx(actf_bar, (CS - 1) * SLICE_BYTES);
-              if (!kWarpSend && ok) {
-                const uint32_t off = static_cast<uint32_t>(rank) * SLICE_BYTES;  // slice = NS/64 K blocks
-                for (int pr = 0; pr < CS; ++pr)
-                  if (pr != static_cast<int>(rank))
-                    bulk_s2cluster(mapa(act_addr + off, pr), act_addr + off, SLICE_BYTES, mapa(actf_bar, pr));
-              }
+          } else if (CS > 1) {
+            epi_sync();
+            if (t == 0 && ok) {
+              const uint32_t off = static_cast<uint32_t>(rank) * SLICE_BYTES;  // slice = NS/64 K blocks
+              for (int pr = 0; pr < CS; ++pr)
+                if (pr != static_cast<int>(rank))
+                  bulk_s2cluster(mapa(act_addr + off, pr), act_addr + off, SLICE_BYTES, mapa(actf_bar, pr));
             }
           }
         }
@@ -702,7 +756,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
   if (CS > 1) cluster_sync_all();
   tc_fence_after();
   if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(static_cast<uint32_t>(TCOLS))
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tcols_alloc)
                  : "memory");
   }
 }

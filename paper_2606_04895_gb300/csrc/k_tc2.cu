@@ -5,6 +5,8 @@
 
 namespace bst {
 
+int tc2_cluster_size_for(int n_rows, int width);
+
 namespace {
 constexpr int kSmemCap = 232448;
 constexpr int kNumSMs = 152;
@@ -65,7 +67,15 @@ int tc2_max_active_clusters(int width, int cs, int depth) {
 
 // Split a layer across more CTAs while there are fewer 128-chain tiles than SMs.  The
 // environment variable BST_TC_CLUSTER (1, 2 or 4) overrides the choice (tuning).
-int tc2_cluster_size(int n_rows, int width) {
+int tc2_cluster_size(int n_rows, int width, int depth) {
+  int cs = tc2_cluster_size_for(n_rows, width);
+  // a smaller cluster keeps the stored activations in global scratch when they do not fit in
+  // tensor memory
+  while (cs > 1 && depth > tc2_tmem_max_depth(width, cs)) cs /= 2;
+  return cs;
+}
+
+int tc2_cluster_size_for(int n_rows, int width) {
   // every epilogue warp needs at least one 32-column chunk of its rank's slice
   const int cs_max = width / (32 * kTc2EQ);
   static const int forced = [] {

@@ -20,7 +20,7 @@ int simt_rows_per_tile(int precision, int width, int lik_kind);
 // cluster tcgen05 kernel: cs in {1, 2, 4}
 cudaError_t launch_emu_tc2(const StepArgs<float> &a, const Tc2Weights &w, cudaStream_t s);
 int tc2_stages(int width, int cs, int depth);
-int tc2_cluster_size(int n_rows, int width);
+int tc2_cluster_size(int n_rows, int width, int depth);
 
 // Weight preparation (k_aux.cu).
 // Fold whitening / standardisation into layer 1 (FP64 out): z-space (mode 0) or x-space (mode 1).

@@ -60,6 +60,22 @@ def test_emulator_loglike_parity(prec, d, width, depth):
     s.close()
 
 
+@pytest.mark.parametrize("depth", [7, 8])
+def test_bf16_deep_width512(depth):
+    """Depth 7 keeps the stored activations of a 4-CTA cluster in tensor memory; depth 8 no
+    longer fits there and runs on a smaller cluster with global scratch."""
+    e = emulator_case(8, 512, depth, out_s=20.0, out_m=100.0)
+    s = _sampler("bf16", e)
+    x = np.random.default_rng(3).uniform(-3, 3, (300, 8))
+    ll, g = s.grad_loglike(x)
+    ref = O.Model(8, emulator=e, bf16=True)
+    rl, rg = ref.loglike(x)
+    ll, g = ll.double().cpu().numpy(), g.double().cpu().numpy()
+    assert np.max(np.abs(ll - rl) / np.maximum(np.abs(rl), 1.0)) < 2e-3
+    assert rel_err(g, rg) < 2e-2
+    s.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 def test_loglike_edge_sizes(prec):
     e = emulator_case(8, 256, 2)
