@@ -199,6 +199,17 @@ StepArgs<R> make_args(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_st
   a.tgt.upper = static_cast<const R *>(h->up_r);
   a.tgt.gauss = h->gauss_d;
   a.tgt.any_gauss = h->any_gauss;
+  if (h->d <= 8) {
+    const int d = h->d;
+    for (int i = 0; i < d; ++i) {
+      if (h->mu.size() >= static_cast<size_t>(d)) a.t8_mu[i] = static_cast<R>(h->mu[i]);
+      if (h->L.size() >= static_cast<size_t>(d) * d)
+        for (int j = 0; j < d; ++j) a.t8_L[i * 8 + j] = static_cast<R>(h->L[static_cast<size_t>(i) * d + j]);
+      if (h->lower.size() >= static_cast<size_t>(d)) a.t8_lo[i] = static_cast<R>(h->lower[i]);
+      if (h->upper.size() >= static_cast<size_t>(d)) a.t8_up[i] = static_cast<R>(h->upper[i]);
+      if (h->gauss.size() >= static_cast<size_t>(d)) a.t8_gauss[i] = h->gauss[i];
+    }
+  }
   a.st.z = static_cast<R *>(h->z);
   a.st.g = static_cast<R *>(h->g);
   a.st.lp = static_cast<R *>(h->lp);

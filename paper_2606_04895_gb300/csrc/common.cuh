@@ -188,6 +188,11 @@ struct StepArgs {
   int wf_stride;
   R *xbuf;          // [n_rows][dp]
   int *status;
+  // d <= 8: the whitening (mu, L as an 8 x 8 row-major block), the box and the Gaussian-prior
+  // flags once more as kernel parameters, so register-resident chains read them through the
+  // constant cache (same working-precision values as tgt)
+  R t8_mu[8], t8_L[64], t8_lo[8], t8_up[8];
+  int t8_gauss[8];
 };
 
 // Per-chain work row: kDworkOffsetVecs vectors of dp reals (NUTS trajectory ends,

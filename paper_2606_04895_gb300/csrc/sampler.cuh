@@ -536,15 +536,16 @@ struct RegChain8 {
     prepped = have_xi = false;
   }
 
-  // x = mu + L v on the first d entries (same summation order as TargetView::to_x_prior)
-  static __device__ __forceinline__ void to_x(const TargetView<R> &t, const R *v, R *x) {
+  // x = mu + L v on the first d entries (same summation order as TargetView::to_x_prior); the
+  // whitening comes from the kernel-parameter copy (StepArgs::t8_*)
+  static __device__ __forceinline__ void to_x(const StepArgs<R> &a, const R *v, R *x) {
 #pragma unroll
     for (int i = 0; i < DB; ++i) {
       R acc = R(0);
-      if (i < t.d) {
-        acc = t.mu[i];
+      if (i < a.d) {
+        acc = a.t8_mu[i];
 #pragma unroll
-        for (int j = 0; j <= i; ++j) acc += t.L[i * t.d + j] * v[j];
+        for (int j = 0; j <= i; ++j) acc += a.t8_L[i * 8 + j] * v[j];
       }
       x[i] = acc;
     }
@@ -583,16 +584,15 @@ struct RegChain8 {
   // The part of post that does not depend on the evaluation in flight: x of the proposal and
   // its prior term, the accept uniform, and the noise of the next iteration's proposal.
   __device__ void prep(const StepArgs<R> &a, int c) {
-    const TargetView<R> &t = a.tgt;
     R xp[DB];
-    to_x(t, zp, xp);
+    to_x(a, zp, xp);
     inside = true;
     lpr = 0.0;
 #pragma unroll
     for (int i = 0; i < DB; ++i)
       if (i < a.d) {
-        if (!(xp[i] >= t.lower[i] && xp[i] <= t.upper[i])) inside = false;
-        if (t.any_gauss && t.gauss[i]) lpr -= 0.5 * static_cast<double>(xp[i]) * static_cast<double>(xp[i]);
+        if (!(xp[i] >= a.t8_lo[i] && xp[i] <= a.t8_up[i])) inside = false;
+        if (a.tgt.any_gauss && a.t8_gauss[i]) lpr -= 0.5 * static_cast<double>(xp[i]) * static_cast<double>(xp[i]);
       }
     u = draw_uniform<double>(a.seed, static_cast<uint32_t>(c), iter, kAccept, 0);
     lu32 = logf(static_cast<float>(u));
@@ -643,7 +643,7 @@ struct RegChain8 {
     prepped = false;
     R *q1 = xi, *g1 = gp, *z1 = zp;
     R xp[DB];
-    to_x(t, z1, xp);
+    to_x(a, z1, xp);
     const double lp1 = static_cast<double>(lle) + (inside ? lpr : -INFINITY) + t.logdet;
     if (t.any_gauss) {
 #pragma unroll
@@ -652,7 +652,7 @@ struct RegChain8 {
           R sg = 0;
 #pragma unroll
           for (int i = j; i < DB; ++i)
-            if (i < d && t.gauss[i]) sg -= t.L[i * d + j] * xp[i];
+            if (i < d && a.t8_gauss[i]) sg -= a.t8_L[i * 8 + j] * xp[i];
           g1[j] += sg;
         }
     }
@@ -706,7 +706,7 @@ struct RegChain8 {
       lp = static_cast<R>(lpnew);
       a.st.lp[c] = lp;
     } else {
-      to_x(t, z, x);  // x-space record of the kept position
+      to_x(a, z, x);  // x-space record of the kept position
     }
     acc_stat += static_cast<double>(p);
     n_acc += acc ? 1ull : 0ull;
@@ -740,7 +740,7 @@ struct RegChain8 {
     if (!prepped) prep(a, c);
     prepped = false;
     R xp[DB];
-    to_x(t, zp, xp);
+    to_x(a, zp, xp);
     // log pi_z(zp) and its gradient (logpi_eval)
     const double lpp = static_cast<double>(lle) + (inside ? lpr : -INFINITY) + t.logdet;
     if (mala && t.any_gauss) {
@@ -750,7 +750,7 @@ struct RegChain8 {
           R sg = 0;
 #pragma unroll
           for (int i = j; i < DB; ++i)
-            if (i < d && t.gauss[i]) sg -= t.L[i * d + j] * xp[i];
+            if (i < d && a.t8_gauss[i]) sg -= a.t8_L[i * 8 + j] * xp[i];
           gp[j] += sg;
         }
     }
