@@ -503,7 +503,27 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         free_pending = false;
       }
       // ---- layer-1 operand [z_hi | z_lo | z_hi | 0] from ze (written by rank 0's samplers)
-      {
+      if (fast && E.kb1 == 1) {
+        // dp == 16, d <= 8: chunks of 8 values are hi(z), 0, lo(z), 0 (this thread, ch 0) or
+        // hi(z), 0, 0, 0 (ch 1); z beyond d is zero in the staging buffer
+        const float4 za = *reinterpret_cast<const float4 *>(zbuf + r * 8);
+        const float4 zb = *reinterpret_cast<const float4 *>(zbuf + r * 8 + 4);
+        const float zv[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+        uint32_t hi2[4], lo2[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float h0 = __bfloat162float(__float2bfloat16_rn(zv[2 * u]));
+          const float h1 = __bfloat162float(__float2bfloat16_rn(zv[2 * u + 1]));
+          hi2[u] = pack_bf16x2(h0, h1);
+          lo2[u] = pack_bf16x2(zv[2 * u] - h0, zv[2 * u + 1] - h1);
+        }
+        const int j0 = 4 * ch;
+        st_shared_v4(act_addr + sw128_off(r, j0), hi2[0], hi2[1], hi2[2], hi2[3]);
+        st_shared_v4(act_addr + sw128_off(r, j0 + 1), 0u, 0u, 0u, 0u);
+        if (ch == 0) st_shared_v4(act_addr + sw128_off(r, j0 + 2), lo2[0], lo2[1], lo2[2], lo2[3]);
+        else st_shared_v4(act_addr + sw128_off(r, j0 + 2), 0u, 0u, 0u, 0u);
+        st_shared_v4(act_addr + sw128_off(r, j0 + 3), 0u, 0u, 0u, 0u);
+      } else {
         const float *zr = fast ? zbuf + r * 8 : a.st.ze + static_cast<size_t>(row) * a.st.ze_ld;
         const int nch = E.kb1 * 8;  // 16-byte chunks in the row; dp is a multiple of 16, so a
                                     // chunk (8 values) lies inside one segment
@@ -528,9 +548,12 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
       for (int p = 0; p < nph; ++p) {
         // while the second layer is in flight the chain does the evaluation-independent part
         // of its accept step and draws the next proposal's noise
-        if (p == 1 && fast && sampler && need) {
-          rc.prep(a, row);
-          rc.prep_next(a, row);
+        if (p == 1 && fast && sampler && valid) {
+          rc.record(a, row, row);  // the previous iteration's memory side, if still pending
+          if (need) {
+            rc.prep(a, row);
+            rc.prep_next(a, row);
+          }
         }
         // adjoint phases read the stored activation h_{l-1}: start loading its first chunk now
         const bool adj_phase = (p >= D) && (p != 2 * D - 1);
@@ -562,14 +585,10 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
             if (dp > 16) tmem_ld32_nowait(trow + 32, v1);
             tmem_wait_ld();
             if (rank == 0 && valid && fast) {
-              float *gout = a.st.gle + static_cast<size_t>(row) * a.st.gle_ld;
+              // (the register-resident chain takes the gradient from shared memory only)
 #pragma unroll
               for (int i = 0; i < RegChain8<float>::DB; ++i)
-                if (i < a.d) {
-                  const float gi = __uint_as_float(v0[i]) + __uint_as_float(v0[16 + i]);  // dp == 16
-                  rc.gp[i] = gi;
-                  gout[i] = gi;
-                }
+                if (i < a.d) rc.gp[i] = __uint_as_float(v0[i]) + __uint_as_float(v0[16 + i]);  // dp == 16
             } else if (rank == 0 && valid) {
               float *gout = a.st.gle + static_cast<size_t>(row) * a.st.gle_ld;
               for (int i = 0; i < a.d; ++i) {
@@ -748,8 +767,12 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         }
         epi_sync();
         bool done = false;
+        // the register-resident chains write their record while the next evaluation runs,
+        // unless the covariance accumulator reads it right away
+        const bool defer = !a.welford_on;
         if (sampler && need && !loglike)
-          done = fast ? (hmc ? rc.hmc_post(a, row, row, lle_v) : rc.post(a, row, row, lle_v, mala)) : chn.post(row, h);
+          done = fast ? (hmc ? rc.hmc_post(a, row, row, lle_v, defer) : rc.post(a, row, row, lle_v, mala, defer))
+                      : chn.post(row, h);
         if (sampler && !loglike && a.welford_on) {
           mask[r] = done ? 1 : 0;
           smp_sync();
@@ -759,6 +782,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArg
         }
       }
     }
+    if (fast && sampler && valid) rc.record(a, row, row);
     // the peers' release of the last phase: no copy or MMA arrive may still target this CTA
     if (free_pending) wait_free(free2_bar, free2_par);
   }

@@ -510,6 +510,9 @@ struct RegChain8 {
   unsigned long long n_acc, n_ev;
   float lu32;
   bool inside, prepped, have_xi;
+  // the last decision's memory side (record): pending, accepted, with gradient, step index
+  bool rec_pending, rec_acc, rec_grad;
+  int rec_step;
 
   __device__ void load(const StepArgs<R> &a, int c, R *zp_smem, R *gp_smem, R *xi_smem) {
     zp = zp_smem;
@@ -534,8 +537,23 @@ struct RegChain8 {
     e = static_cast<R>(a.eps);
     s = static_cast<R>(sqrt(2.0 * a.eps));
     prepped = have_xi = false;
+    rec_pending = rec_acc = rec_grad = false;
+    rec_step = 0;
   }
 
+  // dst[0..d) = v[0..d): one thread per chain writes its own row, so the stores do not coalesce
+  // across the warp; with d == 8 and a 16-byte aligned row two 16-byte stores do it.
+  static __device__ __forceinline__ void store_row(R *dst, const R *v, int d) {
+    if (sizeof(R) == 4 && d == 8 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+      float4 *q = reinterpret_cast<float4 *>(dst);
+      q[0] = make_float4(v[0], v[1], v[2], v[3]);
+      q[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < DB; ++i)
+        if (i < d) dst[i] = v[i];
+    }
+  }
   // x = mu + L v on the first d entries (same summation order as TargetView::to_x_prior); the
   // whitening comes from the kernel-parameter copy (StepArgs::t8_*)
   static __device__ __forceinline__ void to_x(const StepArgs<R> &a, const R *v, R *x) {
@@ -571,13 +589,9 @@ struct RegChain8 {
     if (steps >= a.n_steps) return false;
     if (!have_xi) normals(a, c, iter, xi);
     have_xi = false;
-    R *ze = a.st.ze + static_cast<size_t>(c) * a.dp;
 #pragma unroll
     for (int i = 0; i < DB; ++i)
-      if (i < a.d) {
-        zp[i] = mala ? z[i] + e * g[i] + s * xi[i] : z[i] + e * xi[i];
-        ze[i] = zp[i];
-      }
+      if (i < a.d) zp[i] = mala ? z[i] + e * g[i] + s * xi[i] : z[i] + e * xi[i];
     return true;
   }
 
@@ -623,29 +637,28 @@ struct RegChain8 {
         }
       h0 = -static_cast<double>(lp) + 0.5 * qq;
     }
-    R *ze = a.st.ze + static_cast<size_t>(c) * a.dp;
 #pragma unroll
     for (int i = 0; i < DB; ++i)
       if (i < a.d) {
         q1[i] += R(0.5) * e * g1[i];
         z1[i] += e * q1[i];
-        ze[i] = z1[i];
       }
     return true;
   }
   // HMC: close the leapfrog (gp holds grad logL at z1); after n_leapfrog of them, the
   // accept of hmc_post.  Returns whether the trajectory (an iteration) completed.
-  __device__ bool hmc_post(const StepArgs<R> &a, int c, int row, R lle) {
+  __device__ bool hmc_post(const StepArgs<R> &a, int c, int row, R lle, bool defer) {
     const TargetView<R> &t = a.tgt;
     const int d = a.d;
     const bool last = nlf + 1 >= a.n_leapfrog;
     if (!prepped) prep(a, c);
     prepped = false;
     R *q1 = xi, *g1 = gp, *z1 = zp;
-    R xp[DB];
-    to_x(a, z1, xp);
+    if (rec_pending) record(a, c, row);
     const double lp1 = static_cast<double>(lle) + (inside ? lpr : -INFINITY) + t.logdet;
     if (t.any_gauss) {
+      R xp[DB];
+      to_x(a, z1, xp);
 #pragma unroll
       for (int j = 0; j < DB; ++j)
         if (j < d) {
@@ -664,7 +677,6 @@ struct RegChain8 {
         qq += static_cast<double>(q1[i]) * q1[i];
       }
     n_ev += 1ull;
-    a.st.evals[c] = n_ev;
     nlf += 1;
     if (!last) return false;
     nlf = 0;
@@ -679,71 +691,69 @@ struct RegChain8 {
     else if (gap < -err) acc = false;
     else acc = log(u) < la;
     const float p = la32 >= 0.f ? 1.f : (la32 == la32 ? expf(la32) : 0.f);
-    return finish_step(a, c, row, acc, p, z1, g1, lp1, xp, true);
+    return finish_step(a, c, row, acc, p, z1, g1, lp1, true, defer);
   }
 
-  // Accept bookkeeping shared by the three kernels: state update (write-through), counters,
-  // iteration counter, sample record and Welford hand-off.  xnew = x of znew.
+  // End of an iteration, shared by the three kernels: the new state in registers (the next
+  // proposal needs only these), then record() writes it through: state, counters, iteration
+  // counter, sample record and Welford hand-off.  With `defer` the engine calls record()
+  // later, while the next evaluation is in flight (never with the covariance accumulator on,
+  // which reads the record right after the decision).
   __device__ bool finish_step(const StepArgs<R> &a, int c, int row, bool acc, float p, const R *znew,
-                              const R *gnew, double lpnew, const R *xnew, bool with_grad) {
-    const TargetView<R> &t = a.tgt;
-    const int d = a.d;
-    R *zc = a.st.z + static_cast<size_t>(c) * a.dp, *gc = a.st.g + static_cast<size_t>(c) * a.dp;
-    R x[DB];
+                              const R *gnew, double lpnew, bool with_grad, bool defer) {
     if (acc) {
 #pragma unroll
-      for (int i = 0; i < DB; ++i) {
-        x[i] = xnew[i];
-        if (i < d) {
+      for (int i = 0; i < DB; ++i)
+        if (i < a.d) {
           z[i] = znew[i];
-          zc[i] = z[i];
-          if (with_grad) {
-            g[i] = gnew[i];
-            gc[i] = g[i];
-          }
+          if (with_grad) g[i] = gnew[i];
         }
-      }
       lp = static_cast<R>(lpnew);
-      a.st.lp[c] = lp;
-    } else {
-      to_x(a, z, x);  // x-space record of the kept position
     }
     acc_stat += static_cast<double>(p);
     n_acc += acc ? 1ull : 0ull;
+    rec_acc = acc;
+    rec_grad = with_grad;
+    rec_step = steps;
+    iter += 1u;
+    steps += 1;
+    rec_pending = true;
+    if (!defer) record(a, c, row);
+    return true;
+  }
+  __device__ void record(const StepArgs<R> &a, int c, int row) {
+    if (!rec_pending) return;
+    rec_pending = false;
+    const int d = a.d;
+    R x[DB];
+    to_x(a, z, x);  // x-space record of the new position
+    if (rec_acc) {
+      store_row(a.st.z + static_cast<size_t>(c) * a.dp, z, d);
+      if (rec_grad) store_row(a.st.g + static_cast<size_t>(c) * a.dp, g, d);
+      a.st.lp[c] = lp;
+    }
     a.st.acc_stat[c] = acc_stat;
     a.st.accepts[c] = n_acc;
-    // finish: iteration counter, sample record, Welford hand-off
-    const int st = steps;
-    iter += 1u;
+    a.st.evals[c] = n_ev;
     a.st.iter[c] = iter;
-    if (a.samples && ((st + 1) % a.thin) == 0) {
-      R *dst = a.samples + (static_cast<size_t>(st / a.thin) * a.n_chains + c) * d;
-#pragma unroll
-      for (int i = 0; i < DB; ++i)
-        if (i < d) dst[i] = x[i];
-    }
-    if (a.welford_on) {
-      R *xb = a.xbuf + static_cast<size_t>(row) * a.dp;
-#pragma unroll
-      for (int i = 0; i < DB; ++i)
-        if (i < d) xb[i] = x[i];
-    }
-    steps = st + 1;
+    if (a.samples && ((rec_step + 1) % a.thin) == 0)
+      store_row(a.samples + (static_cast<size_t>(rec_step / a.thin) * a.n_chains + c) * d, x, d);
+    if (a.welford_on) store_row(a.xbuf + static_cast<size_t>(row) * a.dp, x, d);
     a.st.steps_done[c] = steps;
-    return true;
   }
 
   // lle = logL at zp; gp (MALA) holds grad logL at zp.  Returns true (an iteration completed).
-  __device__ bool post(const StepArgs<R> &a, int c, int row, R lle, bool mala) {
+  __device__ bool post(const StepArgs<R> &a, int c, int row, R lle, bool mala, bool defer) {
     const TargetView<R> &t = a.tgt;
     const int d = a.d;
+    if (rec_pending) record(a, c, row);
     if (!prepped) prep(a, c);
     prepped = false;
-    R xp[DB];
-    to_x(a, zp, xp);
     // log pi_z(zp) and its gradient (logpi_eval)
     const double lpp = static_cast<double>(lle) + (inside ? lpr : -INFINITY) + t.logdet;
     if (mala && t.any_gauss) {
+      R xp[DB];
+      to_x(a, zp, xp);
 #pragma unroll
       for (int j = 0; j < DB; ++j)
         if (j < d) {
@@ -808,8 +818,7 @@ struct RegChain8 {
       p = la32 >= 0.f ? 1.f : (la32 == la32 ? expf(la32) : 0.f);
     }
     n_ev += 1ull;
-    a.st.evals[c] = n_ev;
-    return finish_step(a, c, row, acc, p, zp, gp, lpp, xp, mala);
+    return finish_step(a, c, row, acc, p, zp, gp, lpp, mala, defer);
   }
 };
 
