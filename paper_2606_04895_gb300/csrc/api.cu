@@ -192,22 +192,18 @@ StepArgs<R> make_args(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_st
   a.seed = h->seed;
   a.need_grad = (mode == kModeMALA || mode == kModeHMC || mode == kModeNUTS || mode == kModeRefresh) ? 1 : 0;
   a.tgt.d = h->d;
-  a.tgt.mu = static_cast<const R *>(h->mu_r);
-  a.tgt.L = static_cast<const R *>(h->L_r);
   a.tgt.logdet = h->logdet;
-  a.tgt.lower = static_cast<const R *>(h->lo_r);
-  a.tgt.upper = static_cast<const R *>(h->up_r);
-  a.tgt.gauss = h->gauss_d;
   a.tgt.any_gauss = h->any_gauss;
-  if (h->d <= 8) {
+  {
+    // the working-precision values of the device copies (mu_r, L_r, lo_r, up_r, gauss_d)
     const int d = h->d;
     for (int i = 0; i < d; ++i) {
-      if (h->mu.size() >= static_cast<size_t>(d)) a.t8_mu[i] = static_cast<R>(h->mu[i]);
+      if (h->mu.size() >= static_cast<size_t>(d)) a.tgt.mu[i] = static_cast<R>(h->mu[i]);
       if (h->L.size() >= static_cast<size_t>(d) * d)
-        for (int j = 0; j < d; ++j) a.t8_L[i * 8 + j] = static_cast<R>(h->L[static_cast<size_t>(i) * d + j]);
-      if (h->lower.size() >= static_cast<size_t>(d)) a.t8_lo[i] = static_cast<R>(h->lower[i]);
-      if (h->upper.size() >= static_cast<size_t>(d)) a.t8_up[i] = static_cast<R>(h->upper[i]);
-      if (h->gauss.size() >= static_cast<size_t>(d)) a.t8_gauss[i] = h->gauss[i];
+        for (int j = 0; j < d; ++j) a.tgt.L[i * d + j] = static_cast<R>(h->L[static_cast<size_t>(i) * d + j]);
+      if (h->lower.size() >= static_cast<size_t>(d)) a.tgt.lower[i] = static_cast<R>(h->lower[i]);
+      if (h->upper.size() >= static_cast<size_t>(d)) a.tgt.upper[i] = static_cast<R>(h->upper[i]);
+      if (h->gauss.size() >= static_cast<size_t>(d)) a.tgt.gauss[i] = h->gauss[i];
     }
   }
   a.st.z = static_cast<R *>(h->z);

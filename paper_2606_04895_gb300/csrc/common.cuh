@@ -112,28 +112,39 @@ __device__ __forceinline__ void draw_normals(uint64_t seed, uint32_t chain, uint
   }
 }
 
-// Whitening (x = mu + L z) and prior (box, N(0,1) on flagged dims), device view.
+// Whitening (x = mu + L z) and prior (box, N(0,1) on flagged dims), device view.  The
+// values are copied into the kernel parameters (the step kernels take their StepArgs as a
+// __grid_constant__ parameter), so every thread reads them through the constant cache.
 template <typename R>
 struct TargetView {
   int d;
-  const R *mu;     // [d]
-  const R *L;      // [d][d] lower triangular
   double logdet;   // sum_i log L_ii
-  const R *lower;  // [d]
-  const R *upper;  // [d]
-  const int *gauss;  // [d]
   int any_gauss;
+  R mu[kMaxD];          // [d]
+  R L[kMaxD * kMaxD];   // [d][d] row-major (first d*d entries), lower triangular
+  R lower[kMaxD];       // [d]
+  R upper[kMaxD];       // [d]
+  int gauss[kMaxD];     // [d]
 
   // x = mu + L z; returns the log prior (0 / -inf / -x_g.x_g/2).
-  __device__ __forceinline__ double to_x_prior(const R *z, R *x) const {
+  // (z is read once into registers: the triangular product is unrolled over kMaxD with the
+  // same summation order as a plain loop over j <= i)
+  __device__ __noinline__ double to_x_prior(const R *z, R *x) const {
+    R zr[kMaxD];
+#pragma unroll
+    for (int j = 0; j < kMaxD; ++j) zr[j] = j < d ? z[j] : R(0);
     bool inside = true;
     double lp = 0.0;
-    for (int i = 0; i < d; ++i) {
-      R s = mu[i];
-      for (int j = 0; j <= i; ++j) s += L[i * d + j] * z[j];
-      x[i] = s;
-      if (!(s >= lower[i] && s <= upper[i])) inside = false;
-      if (any_gauss && gauss[i]) lp -= 0.5 * static_cast<double>(s) * static_cast<double>(s);
+#pragma unroll
+    for (int i = 0; i < kMaxD; ++i) {
+      if (i < d) {
+        R s = mu[i];
+#pragma unroll
+        for (int j = 0; j <= i; ++j) s += L[i * d + j] * zr[j];
+        x[i] = s;
+        if (!(s >= lower[i] && s <= upper[i])) inside = false;
+        if (any_gauss && gauss[i]) lp -= 0.5 * static_cast<double>(s) * static_cast<double>(s);
+      }
     }
     return inside ? lp : -INFINITY;
   }
@@ -188,11 +199,6 @@ struct StepArgs {
   int wf_stride;
   R *xbuf;          // [n_rows][dp]
   int *status;
-  // d <= 8: the whitening (mu, L as an 8 x 8 row-major block), the box and the Gaussian-prior
-  // flags once more as kernel parameters, so register-resident chains read them through the
-  // constant cache (same working-precision values as tgt)
-  R t8_mu[8], t8_L[64], t8_lo[8], t8_up[8];
-  int t8_gauss[8];
 };
 
 // Per-chain work row: kDworkOffsetVecs vectors of dp reals (NUTS trajectory ends,

@@ -373,7 +373,7 @@ __device__ void welford_tile(const StepArgs<R> &a, int row0, int nrows, const in
 // Chain-tile kernel: T rows per CTA, thread t < T owns row row0 + t.
 template <typename R, int T, class Engine, class Weights>
 __global__ void __launch_bounds__(kSimtThreads, 1)
-simt_chain_kernel(const StepArgs<R> a, const Weights W) {
+simt_chain_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ Weights W) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int mask[T];
   const int row0 = blockIdx.x * T;

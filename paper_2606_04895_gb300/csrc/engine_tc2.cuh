@@ -210,7 +210,8 @@ __device__ __forceinline__ void tmem_wait_ld_regs(uint32_t *r) {
 
 // ---------------------------------------------------------------- the kernel
 template <int W, int CS>
-__global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const StepArgs<float> a, const Tc2Weights E) {
+__global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_constant__ StepArgs<float> a,
+                                                                   const __grid_constant__ Tc2Weights E) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   constexpr int KBW = W / 64;           // K blocks of the hidden width
   constexpr int NS = W / CS;            // output columns of this rank

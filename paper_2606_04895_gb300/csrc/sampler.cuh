@@ -554,16 +554,15 @@ struct RegChain8 {
         if (i < d) dst[i] = v[i];
     }
   }
-  // x = mu + L v on the first d entries (same summation order as TargetView::to_x_prior); the
-  // whitening comes from the kernel-parameter copy (StepArgs::t8_*)
+  // x = mu + L v on the first d entries (same summation order as TargetView::to_x_prior)
   static __device__ __forceinline__ void to_x(const StepArgs<R> &a, const R *v, R *x) {
 #pragma unroll
     for (int i = 0; i < DB; ++i) {
       R acc = R(0);
       if (i < a.d) {
-        acc = a.t8_mu[i];
+        acc = a.tgt.mu[i];
 #pragma unroll
-        for (int j = 0; j <= i; ++j) acc += a.t8_L[i * 8 + j] * v[j];
+        for (int j = 0; j <= i; ++j) acc += a.tgt.L[i * a.d + j] * v[j];
       }
       x[i] = acc;
     }
@@ -605,8 +604,8 @@ struct RegChain8 {
 #pragma unroll
     for (int i = 0; i < DB; ++i)
       if (i < a.d) {
-        if (!(xp[i] >= a.t8_lo[i] && xp[i] <= a.t8_up[i])) inside = false;
-        if (a.tgt.any_gauss && a.t8_gauss[i]) lpr -= 0.5 * static_cast<double>(xp[i]) * static_cast<double>(xp[i]);
+        if (!(xp[i] >= a.tgt.lower[i] && xp[i] <= a.tgt.upper[i])) inside = false;
+        if (a.tgt.any_gauss && a.tgt.gauss[i]) lpr -= 0.5 * static_cast<double>(xp[i]) * static_cast<double>(xp[i]);
       }
     u = draw_uniform<double>(a.seed, static_cast<uint32_t>(c), iter, kAccept, 0);
     lu32 = logf(static_cast<float>(u));
@@ -665,7 +664,7 @@ struct RegChain8 {
           R sg = 0;
 #pragma unroll
           for (int i = j; i < DB; ++i)
-            if (i < d && a.t8_gauss[i]) sg -= a.t8_L[i * 8 + j] * xp[i];
+            if (i < d && a.tgt.gauss[i]) sg -= a.tgt.L[i * a.d + j] * xp[i];
           g1[j] += sg;
         }
     }
@@ -760,7 +759,7 @@ struct RegChain8 {
           R sg = 0;
 #pragma unroll
           for (int i = j; i < DB; ++i)
-            if (i < d && a.t8_gauss[i]) sg -= a.t8_L[i * 8 + j] * xp[i];
+            if (i < d && a.tgt.gauss[i]) sg -= a.tgt.L[i * a.d + j] * xp[i];
           gp[j] += sg;
         }
     }
