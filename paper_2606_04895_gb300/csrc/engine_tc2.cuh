@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
         {
           const uint4 *hp = hprev ? reinterpret_cast<const uint4 *>(hprev + col0) : nullptr;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) hcur[u] = hp ? hp[u] : make_uint4(0, 0, 0, 0);
+          for (int u = 0; u < 4; ++u) hcur[u] = hp ? __ldcs(hp + u) : make_uint4(0, 0, 0, 0);
         }
         const bool waited = mbar_wait(acc_bar, acc_par, a.status);
         acc_par ^= 1;
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
               const bool more = hprev && cc + 1 < CPW;
               const uint4 *hp = more ? reinterpret_cast<const uint4 *>(hprev + gcol + 32) : nullptr;
 #pragma unroll
-              for (int u = 0; u < 4; ++u) hnext[u] = more ? hp[u] : make_uint4(0, 0, 0, 0);
+              for (int u = 0; u < 4; ++u) hnext[u] = more ? __ldcs(hp + u) : make_uint4(0, 0, 0, 0);
               const __nv_bfloat16 *hh = reinterpret_cast<const __nv_bfloat16 *>(hcur);
 #pragma unroll
               for (int i = 0; i < 32; ++i) aux[i] = __bfloat162float(hh[i]);
@@ -694,9 +694,11 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
               if (fwd && grad && !last_fwd && h_tmem) {
                 tmem_st16(trow + TCOLS + p * (NS / 2) + (tcol >> 1), pk);
               } else if (hkeep) {
+                // streaming accesses: the stored activations are read once, by the adjoint
+                // pass, and should not displace the samplers' working set from L1
                 uint4 *dst = reinterpret_cast<uint4 *>(hkeep + gcol);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) dst[u] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+                for (int u = 0; u < 4; ++u) __stcs(dst + u, make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]));
               }
             }
           }
