@@ -76,7 +76,7 @@ struct bst_ctx {
   float *tb1[2] = {nullptr, nullptr}, *tb = nullptr, *two = nullptr;
   int kb1 = 1;
   void *scratch = nullptr;
-  size_t scratch_rows = 0;
+  size_t scratch_rows = 0, scratch_bytes = 0;
 
   // analytic likelihood
   int d_c = 0, H = 0, n_data = 0, linear = 0, has_N = 0;
@@ -275,6 +275,7 @@ Tc2Weights tc2_weights(bst_ctx *h, int fold, int n_rows) {
   w.out_m = static_cast<float>(h->out_m);
   w.out_s = static_cast<float>(h->out_s);
   w.scratch = static_cast<__nv_bfloat16 *>(h->scratch);
+  w.scratch_bytes = h->scratch_bytes;
   w.n_stages = tc2_stages(h->width, cs, h->depth);
   return w;
 }
@@ -298,14 +299,30 @@ AnaWeights<R> ana_weights(bst_ctx *h, int fold) {
 }
 
 // ------------------------------------------------------------------ weight preparation
+// Bytes of scratch a launch over `rows` evaluation rows needs: the adjoint's stored
+// activations, and (BF16) at least one slice image per CTA for the cluster exchange through
+// global memory (whole 128-row tiles).
+size_t scratch_bytes_for(const bst_ctx *h, size_t rows) {
+  const size_t el = (h->precision == BST_BF16) ? 2 : h->rs;
+  size_t bytes = rows * static_cast<size_t>(h->depth > 1 ? h->depth - 1 : 1) * h->width * el;
+  if (h->precision == BST_BF16) {
+    const size_t xchg = (rows + kTcRows - 1) / kTcRows * kTcRows * static_cast<size_t>(h->width) * 2;
+    if (xchg > bytes) bytes = xchg;
+  }
+  return bytes;
+}
+
 bst_status ensure_scratch(bst_ctx *h, size_t rows) {
   if (h->lik != BST_LIK_EMULATOR) return BST_OK;
   if (rows <= h->scratch_rows && h->scratch) return BST_OK;
   dfree(h, h->scratch);
-  const size_t el = (h->precision == BST_BF16) ? 2 : h->rs;
-  const size_t bytes = rows * static_cast<size_t>(h->depth > 1 ? h->depth - 1 : 1) * h->width * el;
+  h->scratch = nullptr;
+  h->scratch_rows = 0;
+  h->scratch_bytes = 0;
+  const size_t bytes = scratch_bytes_for(h, rows);
   BST_TRY(dalloc(h, &h->scratch, bytes));
   h->scratch_rows = rows;
+  h->scratch_bytes = bytes;
   return BST_OK;
 }
 
@@ -595,6 +612,7 @@ bst_status bst_set_emulator(bst_handle h, int depth, int width, const double *pa
       BST_TRY(dalloc(h, &h->swo, w * rs));
     }
     h->scratch_rows = 0;
+    h->scratch_bytes = 0;
     dfree(h, h->scratch);
     h->scratch = nullptr;
     // training state belongs to the old shape
@@ -806,7 +824,8 @@ static bst_status loglike_impl(bst_handle h, const void *theta, int m, void *log
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   BST_TRY(prepare(h, s));
   const int chunk = h->n > 65536 ? h->n : 65536;
-  if (need_grad) BST_TRY(ensure_scratch(h, chunk < m ? chunk : m));
+  // (the BF16 engine also needs the scratch for the cluster exchange of forward-only runs)
+  if (need_grad || h->precision == BST_BF16) BST_TRY(ensure_scratch(h, chunk < m ? chunk : m));
   const size_t rs = h->rs;
   for (int r0 = 0; r0 < m; r0 += chunk) {
     const int rows = (m - r0) < chunk ? (m - r0) : chunk;
@@ -1165,7 +1184,7 @@ extern "C" bst_status bst_grad_loglike_noalloc(bst_handle h, const void *theta_d
     const size_t el = (h->precision == BST_BF16) ? 2 : h->rs;
     row_bytes = static_cast<size_t>(h->depth > 1 ? h->depth - 1 : 1) * h->width * el;
     const size_t max_rows = kStaticScratchBytes / row_bytes;
-    if (static_cast<size_t>(m) > max_rows)
+    if (static_cast<size_t>(m) > max_rows || scratch_bytes_for(h, static_cast<size_t>(m)) > kStaticScratchBytes)
       return fail(BST_ERR_ARG, "bst_grad_loglike_noalloc: m = " + std::to_string(m) + " exceeds the " +
                                    std::to_string(max_rows) + " points the 16 MiB static scratch holds for this emulator");
   }
@@ -1204,6 +1223,7 @@ extern "C" bst_status bst_grad_loglike_noalloc(bst_handle h, const void *theta_d
     } else if (h->precision == BST_BF16) {
       Tc2Weights w = tc2_weights(h, 1, m);
       w.scratch = static_cast<__nv_bfloat16 *>(scratch);
+      w.scratch_bytes = kStaticScratchBytes;
       BST_CUDA(launch_emu_tc2(a, w, s));
     } else {
       EmuWeights<float> w = emu_weights<float>(h, 1);

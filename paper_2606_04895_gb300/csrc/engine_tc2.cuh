@@ -53,7 +53,8 @@ struct Tc2Weights {
   const float *b;     // [D-1][w]
   const float *wo;    // [w]
   float bo, out_m, out_s;
-  __nv_bfloat16 *scratch;  // [rows][D-1][w]
+  __nv_bfloat16 *scratch;  // [rows][D-1][w] stored activations, or the exchange images
+  size_t scratch_bytes;
   int n_stages;
 };
 
@@ -111,6 +112,19 @@ __device__ __forceinline__ void mma_commit_multicast(uint32_t bar, uint16_t mask
 }
 __device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;\n" ::"r"(addr), "f"(v) : "memory");
+}
+// Global -> shared copy delivered to the same shared-memory offset in every CTA of `mask`,
+// completion counted on the mbarrier at `bar`'s offset in each of them.
+__device__ __forceinline__ void bulk_g2s_multicast(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
+                                                   uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+      "%4;\n" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;\n" ::: "memory");
 }
 __device__ __forceinline__ void st_cluster_v4f(uint32_t addr, float x, float y, float z, float w) {
   asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(x), "f"(y), "f"(z), "f"(w)
@@ -263,8 +277,16 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
   // accumulator columns (this rank's NS columns, BF16 pairs) when they fit, else in global
   // scratch.
   constexpr bool h_tmem = tc2_h_in_tmem(W, CS);
+  // With the stored activations in tensor memory the global scratch is free: each CTA then
+  // also writes its slice of a layer output there (a byte image of its shared-memory slice)
+  // and every epilogue warp sends its part to the peers with one multicast global->shared
+  // copy instead of one shared->shared copy per peer.
+  constexpr bool kL2X = h_tmem && kWarpSend;
   const uint32_t tcols_alloc = h_tmem ? 512u : static_cast<uint32_t>(TCOLS);
-  if (D > tc2_tmem_max_depth(W, CS)) {  // the launch picks a cluster size that fits; never here
+  // the launch picks a cluster size whose stored activations fit, and sizes the scratch for
+  // the exchange images; never taken
+  if (D > tc2_tmem_max_depth(W, CS) ||
+      (kL2X && (E.scratch == nullptr || static_cast<size_t>(gridDim.x) * SLICE_BYTES > E.scratch_bytes))) {
     if (threadIdx.x == 0) set_status(a.status, kStatusBadArg);
     return;
   }
@@ -437,6 +459,9 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
     const int col0 = static_cast<int>(rank) * NS + ch * CW;  // first global column of this warp
     Chain<float> chn(a);
     const bool loglike = a.mode == kModeLoglike;
+    // this CTA's global image of its slice (kL2X) and the peers as a cluster mask
+    uint8_t *ximg = reinterpret_cast<uint8_t *>(E.scratch) + static_cast<size_t>(blockIdx.x) * SLICE_BYTES;
+    const uint16_t peer_mask_e = static_cast<uint16_t>(((1u << CS) - 1u) & ~(1u << rank));
     const bool mala = a.mode == kModeMALA, hmc = a.mode == kModeHMC;
     // MALA / MH / HMC with d <= 8 (padded to 16) keep the chain in the sampler thread's registers
     const bool fast = (mala || hmc || a.mode == kModeMH) && a.d <= RegChain8<float>::DB && dp == 16;
@@ -690,6 +715,9 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
                 const int jj = ((gcol & 63) >> 3) + u;
                 st_shared_v4(act_addr + kb * 16384 + sw128_off(r, jj), pk[4 * u], pk[4 * u + 1], pk[4 * u + 2],
                              pk[4 * u + 3]);
+                if (kL2X)
+                  *reinterpret_cast<uint4 *>(ximg + (kb - static_cast<int>(rank) * NOWN) * 16384 + sw128_off(r, jj)) =
+                      make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
               }
               if (fwd && grad && !last_fwd && h_tmem) {
                 tmem_st16(trow + TCOLS + p * (NS / 2) + (tcol >> 1), pk);
@@ -723,7 +751,19 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
           __syncwarp();
           if (lane == 0) mbar_arrive(own_bar);
           if (CS > 1 && t == 0) mbar_expect_tx(actf_bar, (CS - 1) * SLICE_BYTES);  // the peers' slices
-          if (kWarpSend) {
+          if (kL2X) {
+            // this warp's rows (32 q ..) of its K blocks, from the global image into every
+            // peer's buffer at the same place (one multicast copy per 4 KB)
+            fence_proxy_async_global();
+            __syncwarp();
+            if (lane == 0 && ok)
+              for (int kb2 = 0; kb2 < CW / 64; ++kb2) {
+                const int kbl = col0 / 64 + kb2;
+                bulk_g2s_multicast(act_addr + static_cast<uint32_t>(kbl) * 16384 + q * 4096,
+                                   ximg + (kbl - static_cast<int>(rank) * NOWN) * 16384 + q * 4096, 4096, actf_bar,
+                                   peer_mask_e);
+              }
+          } else if (kWarpSend) {
             // this warp's rows (32 q ..) of its K blocks, to every peer's buffer at the same place
             if (lane == 0 && ok)
               for (int kb2 = 0; kb2 < CW / 64; ++kb2) {
