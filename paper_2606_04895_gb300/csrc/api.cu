@@ -173,6 +173,8 @@ bst_status check_status(bst_ctx *h) {
 }
 
 // ------------------------------------------------------------------ argument assembly
+size_t act_bytes_for(const bst_ctx *h, size_t rows);
+size_t xchg_bytes_for(const bst_ctx *h, size_t rows);
 template <typename R>
 StepArgs<R> make_args(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_steps, void *samples) {
   StepArgs<R> a;
@@ -275,7 +277,12 @@ Tc2Weights tc2_weights(bst_ctx *h, int fold, int n_rows) {
   w.out_m = static_cast<float>(h->out_m);
   w.out_s = static_cast<float>(h->out_s);
   w.scratch = static_cast<__nv_bfloat16 *>(h->scratch);
-  w.scratch_bytes = h->scratch_bytes;
+  {
+    // the exchange images follow the stored activations of h->scratch_rows rows
+    const size_t ab = act_bytes_for(h, h->scratch_rows);
+    w.xchg = h->scratch ? static_cast<uint8_t *>(h->scratch) + ab : nullptr;
+    w.xchg_bytes = h->scratch_bytes > ab ? h->scratch_bytes - ab : 0;
+  }
   w.n_stages = tc2_stages(h->width, cs, h->depth);
   return w;
 }
@@ -300,17 +307,18 @@ AnaWeights<R> ana_weights(bst_ctx *h, int fold) {
 
 // ------------------------------------------------------------------ weight preparation
 // Bytes of scratch a launch over `rows` evaluation rows needs: the adjoint's stored
-// activations, and (BF16) at least one slice image per CTA for the cluster exchange through
-// global memory (whole 128-row tiles).
-size_t scratch_bytes_for(const bst_ctx *h, size_t rows) {
+// activations, then (BF16) one slice image per CTA for the cluster exchange through global
+// memory (whole 128-row tiles: 128 x width BF16 per tile), 256-byte aligned.
+size_t act_bytes_for(const bst_ctx *h, size_t rows) {
   const size_t el = (h->precision == BST_BF16) ? 2 : h->rs;
-  size_t bytes = rows * static_cast<size_t>(h->depth > 1 ? h->depth - 1 : 1) * h->width * el;
-  if (h->precision == BST_BF16) {
-    const size_t xchg = (rows + kTcRows - 1) / kTcRows * kTcRows * static_cast<size_t>(h->width) * 2;
-    if (xchg > bytes) bytes = xchg;
-  }
-  return bytes;
+  const size_t b = rows * static_cast<size_t>(h->depth > 1 ? h->depth - 1 : 1) * h->width * el;
+  return (b + 255) / 256 * 256;
 }
+size_t xchg_bytes_for(const bst_ctx *h, size_t rows) {
+  if (h->precision != BST_BF16) return 0;
+  return (rows + kTcRows - 1) / kTcRows * kTcRows * static_cast<size_t>(h->width) * 2;
+}
+size_t scratch_bytes_for(const bst_ctx *h, size_t rows) { return act_bytes_for(h, rows) + xchg_bytes_for(h, rows); }
 
 bst_status ensure_scratch(bst_ctx *h, size_t rows) {
   if (h->lik != BST_LIK_EMULATOR) return BST_OK;
@@ -1184,7 +1192,7 @@ extern "C" bst_status bst_grad_loglike_noalloc(bst_handle h, const void *theta_d
     const size_t el = (h->precision == BST_BF16) ? 2 : h->rs;
     row_bytes = static_cast<size_t>(h->depth > 1 ? h->depth - 1 : 1) * h->width * el;
     const size_t max_rows = kStaticScratchBytes / row_bytes;
-    if (static_cast<size_t>(m) > max_rows || scratch_bytes_for(h, static_cast<size_t>(m)) > kStaticScratchBytes)
+    if (static_cast<size_t>(m) > max_rows)
       return fail(BST_ERR_ARG, "bst_grad_loglike_noalloc: m = " + std::to_string(m) + " exceeds the " +
                                    std::to_string(max_rows) + " points the 16 MiB static scratch holds for this emulator");
   }
@@ -1223,7 +1231,13 @@ extern "C" bst_status bst_grad_loglike_noalloc(bst_handle h, const void *theta_d
     } else if (h->precision == BST_BF16) {
       Tc2Weights w = tc2_weights(h, 1, m);
       w.scratch = static_cast<__nv_bfloat16 *>(scratch);
-      w.scratch_bytes = kStaticScratchBytes;
+      // exchange images after the activations if they fit, else the shared->shared exchange
+      w.xchg = nullptr;
+      w.xchg_bytes = 0;
+      if (scratch_bytes_for(h, static_cast<size_t>(m)) <= kStaticScratchBytes) {
+        w.xchg = static_cast<uint8_t *>(scratch) + act_bytes_for(h, static_cast<size_t>(m));
+        w.xchg_bytes = kStaticScratchBytes - act_bytes_for(h, static_cast<size_t>(m));
+      }
       BST_CUDA(launch_emu_tc2(a, w, s));
     } else {
       EmuWeights<float> w = emu_weights<float>(h, 1);

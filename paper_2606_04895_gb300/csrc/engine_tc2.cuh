@@ -53,8 +53,9 @@ struct Tc2Weights {
   const float *b;     // [D-1][w]
   const float *wo;    // [w]
   float bo, out_m, out_s;
-  __nv_bfloat16 *scratch;  // [rows][D-1][w] stored activations, or the exchange images
-  size_t scratch_bytes;
+  __nv_bfloat16 *scratch;  // [rows][D-1][w] stored activations (unless in tensor memory)
+  uint8_t *xchg;           // [CTAs][128 x NS BF16] slice images of the cluster exchange
+  size_t xchg_bytes;
   int n_stages;
 };
 
@@ -223,7 +224,9 @@ __device__ __forceinline__ void tmem_wait_ld_regs(uint32_t *r) {
 }
 
 // ---------------------------------------------------------------- the kernel
-template <int W, int CS>
+// L2X: cluster exchange through global slice images and multicast copies (clusters of 4 with
+// room for the images), else direct shared->shared copies.
+template <int W, int CS, bool L2X>
 __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_constant__ StepArgs<float> a,
                                                                    const __grid_constant__ Tc2Weights E) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -277,16 +280,16 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
   // accumulator columns (this rank's NS columns, BF16 pairs) when they fit, else in global
   // scratch.
   constexpr bool h_tmem = tc2_h_in_tmem(W, CS);
-  // With the stored activations in tensor memory the global scratch is free: each CTA then
-  // also writes its slice of a layer output there (a byte image of its shared-memory slice)
-  // and every epilogue warp sends its part to the peers with one multicast global->shared
-  // copy instead of one shared->shared copy per peer.
-  constexpr bool kL2X = h_tmem && kWarpSend;
+  // In clusters of 4, given room for them (E.xchg), each CTA also writes its slice of a layer
+  // output to global memory (a byte image of its shared-memory slice) and every epilogue warp
+  // sends its part to the three peers with one multicast global->shared copy instead of one
+  // shared->shared copy per peer (with a single peer the direct copy is faster).
+  constexpr bool l2x = L2X && kWarpSend && CS == 4;
   const uint32_t tcols_alloc = h_tmem ? 512u : static_cast<uint32_t>(TCOLS);
   // the launch picks a cluster size whose stored activations fit, and sizes the scratch for
   // the exchange images; never taken
   if (D > tc2_tmem_max_depth(W, CS) ||
-      (kL2X && (E.scratch == nullptr || static_cast<size_t>(gridDim.x) * SLICE_BYTES > E.scratch_bytes))) {
+      (l2x && (E.xchg == nullptr || static_cast<size_t>(gridDim.x) * SLICE_BYTES > E.xchg_bytes))) {
     if (threadIdx.x == 0) set_status(a.status, kStatusBadArg);
     return;
   }
@@ -459,8 +462,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
     const int col0 = static_cast<int>(rank) * NS + ch * CW;  // first global column of this warp
     Chain<float> chn(a);
     const bool loglike = a.mode == kModeLoglike;
-    // this CTA's global image of its slice (kL2X) and the peers as a cluster mask
-    uint8_t *ximg = reinterpret_cast<uint8_t *>(E.scratch) + static_cast<size_t>(blockIdx.x) * SLICE_BYTES;
+    // this CTA's global image of its slice (l2x) and the peers as a cluster mask
+    uint8_t *ximg = E.xchg + static_cast<size_t>(blockIdx.x) * SLICE_BYTES;
     const uint16_t peer_mask_e = static_cast<uint16_t>(((1u << CS) - 1u) & ~(1u << rank));
     const bool mala = a.mode == kModeMALA, hmc = a.mode == kModeHMC;
     // MALA / MH / HMC with d <= 8 (padded to 16) keep the chain in the sampler thread's registers
@@ -715,7 +718,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
                 const int jj = ((gcol & 63) >> 3) + u;
                 st_shared_v4(act_addr + kb * 16384 + sw128_off(r, jj), pk[4 * u], pk[4 * u + 1], pk[4 * u + 2],
                              pk[4 * u + 3]);
-                if (kL2X)
+                if (l2x)
                   *reinterpret_cast<uint4 *>(ximg + (kb - static_cast<int>(rank) * NOWN) * 16384 + sw128_off(r, jj)) =
                       make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
               }
@@ -751,7 +754,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
           __syncwarp();
           if (lane == 0) mbar_arrive(own_bar);
           if (CS > 1 && t == 0) mbar_expect_tx(actf_bar, (CS - 1) * SLICE_BYTES);  // the peers' slices
-          if (kL2X) {
+          if (l2x) {
             // this warp's rows (32 q ..) of its K blocks, from the global image into every
             // peer's buffer at the same place (one multicast copy per 4 KB)
             fence_proxy_async_global();

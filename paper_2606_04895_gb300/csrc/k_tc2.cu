@@ -11,12 +11,12 @@ namespace {
 constexpr int kSmemCap = 232448;
 constexpr int kNumSMs = 152;
 
-template <int W, int CS>
+template <int W, int CS, bool L2X = false>
 cudaError_t launch_one(const StepArgs<float> &a, const Tc2Weights &w, cudaStream_t s) {
   const int tiles = (a.n_rows + kTcRows - 1) / kTcRows;
   if (tiles == 0) return cudaSuccess;
   const size_t smem = tc2_smem_bytes(W, CS, w.n_stages, w.depth);
-  auto k = tc2_chain_kernel<W, CS>;
+  auto k = tc2_chain_kernel<W, CS, L2X>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   if (CS > 1) {
@@ -58,8 +58,12 @@ int tc2_max_active_clusters(int width, int cs, int depth) {
   cfg.numAttrs = 1;
   int n = -1;
   const void *k = nullptr;
-  if (width == 512) k = cs == 4 ? (const void *)tc2_chain_kernel<512, 4> : cs == 2 ? (const void *)tc2_chain_kernel<512, 2> : (const void *)tc2_chain_kernel<512, 1>;
-  else k = cs == 4 ? (const void *)tc2_chain_kernel<256, 4> : cs == 2 ? (const void *)tc2_chain_kernel<256, 2> : (const void *)tc2_chain_kernel<256, 1>;
+  if (width == 512)
+    k = cs == 4 ? (const void *)tc2_chain_kernel<512, 4, true>
+                : cs == 2 ? (const void *)tc2_chain_kernel<512, 2, false> : (const void *)tc2_chain_kernel<512, 1, false>;
+  else
+    k = cs == 4 ? (const void *)tc2_chain_kernel<256, 4, false>
+                : cs == 2 ? (const void *)tc2_chain_kernel<256, 2, false> : (const void *)tc2_chain_kernel<256, 1, false>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(cfg.dynamicSmemBytes));
   if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) return -1;
   return n;
@@ -92,7 +96,7 @@ int tc2_cluster_size_for(int n_rows, int width) {
 
 cudaError_t launch_emu_tc2(const StepArgs<float> &a, const Tc2Weights &w, cudaStream_t s) {
   if (w.width == 512) {
-    if (w.cs == 4) return launch_one<512, 4>(a, w, s);
+    if (w.cs == 4) return w.xchg ? launch_one<512, 4, true>(a, w, s) : launch_one<512, 4, false>(a, w, s);
     if (w.cs == 2) return launch_one<512, 2>(a, w, s);
     return launch_one<512, 1>(a, w, s);
   }
