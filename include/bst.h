@@ -149,8 +149,9 @@ bst_status bst_grad_loglike(bst_handle h, const void *theta_dev, int m, void *lo
  * first call with a larger m than before grows the buffer in which the adjoint
  * keeps the emulator's hidden activations.  This call instead uses one
  * file-scope device array of 16 MiB (g_static_scratch) that every GPU which
- * loads the library holds until the process exits, and calls no cudaMalloc,
- * cudaFree or other allocating routine.
+ * loads the library holds until the process exits (for the activations and,
+ * where room remains, the BF16 engine's cluster-exchange images), and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
  * Arguments and results are those of bst_grad_loglike.  Limit: m times the
  * bytes kept per point, (depth - 1) x width x (2 for BF16, 4 for FP32, 8 for
  * FP64), must fit in 16 MiB (for example m <= 5461 for a BF16 8-512x4-1

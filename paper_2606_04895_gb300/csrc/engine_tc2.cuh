@@ -11,14 +11,16 @@
 //               per chain).
 //
 // Per layer every CTA holds the whole input activation (128 x W BF16, 128-byte-swizzled
-// K-major) in shared memory, multiplies it by its slice of the weights, runs the epilogue
-// on its NS columns, writes the BF16 result into its own activation buffer and copies that
-// slice into every peer's buffer with cp.async.bulk shared::cluster (completion counted on
-// the peer's mbarrier).  A peer's buffer is written only after the peer's MMAs of the layer
-// have finished reading it ("free" arrivals).  The output dot w_o . h_D is reduced across
-// the cluster in a fixed order on rank 0.  All waits are bounded by a time limit; a timeout
-// sets a status bit and every role leaves its loop; a cluster barrier precedes exit so no
-// CTA leaves while a peer may still touch its shared memory.
+// K-major) in shared memory, multiplies it by its slice of the weights (its own K blocks
+// first), runs the epilogue on its NS columns, writes the BF16 result into its own
+// activation buffer and copies that slice into every peer's buffer: in clusters of 4 through
+// a global image of the slice and one multicast global->shared bulk copy per 4 KB piece,
+// otherwise with shared->shared bulk copies (completion counted on the peer's mbarrier).  A
+// peer's buffer is written only after the peer's MMAs of the layer have finished reading it
+// ("free" arrivals).  The output dot w_o . h_D is reduced across the cluster in a fixed
+// order on rank 0.  All waits are bounded by a time limit; a timeout sets a status bit and
+// every role leaves its loop; a cluster barrier precedes exit so no CTA leaves while a peer
+// may still touch its shared memory.
 #pragma once
 
 #include "common.cuh"
