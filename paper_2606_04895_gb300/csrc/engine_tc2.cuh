@@ -97,6 +97,20 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
     }
   }
 }
+// Bounded wait that backs off between polls: for threads that wait while the tensor pipe
+// runs, whose shared-memory operand reads would otherwise compete with every poll.
+__device__ __forceinline__ bool mbar_wait_backoff(uint32_t bar, uint32_t parity, int *status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    __nanosleep(128);
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      set_status(status, kStatusTimeout);
+      return false;
+    }
+  }
+}
 __device__ __forceinline__ void bulk_s2cluster(uint32_t dst_cluster, uint32_t src_cta, uint32_t bytes,
                                                uint32_t bar_cluster) {
   asm volatile(
@@ -598,7 +612,10 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
 #pragma unroll
           for (int u = 0; u < 4; ++u) hcur[u] = hp ? __ldcs(hp + u) : make_uint4(0, 0, 0, 0);
         }
-        const bool waited = mbar_wait(acc_bar, acc_par, a.status);
+        // one poller per warp, backing off, while the MMAs of the phase run
+        int wok = 1;
+        if (lane == 0) wok = mbar_wait_backoff(acc_bar, acc_par, a.status) ? 1 : 0;
+        const bool waited = __shfl_sync(0xffffffffu, wok, 0) != 0;
         acc_par ^= 1;
         if (epi_or(!waited)) {
           ok = false;
