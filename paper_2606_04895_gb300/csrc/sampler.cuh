@@ -17,6 +17,71 @@
 
 namespace bst {
 
+// Per-chain vector loops over the state rows (global memory).  The rows are distinct, so the
+// parameters are restrict-qualified: the loads of one loop can all be in flight at once
+// instead of each waiting behind the previous iteration's stores.
+template <typename R>
+__device__ __forceinline__ void vcopy(R *__restrict__ dst, const R *__restrict__ src, int d) {
+#pragma unroll 4
+  for (int i = 0; i < d; ++i) dst[i] = src[i];
+}
+template <typename R>
+__device__ __forceinline__ void vcopy2(R *__restrict__ d0, const R *__restrict__ s0, R *__restrict__ d1,
+                                       const R *__restrict__ s1, int d) {
+#pragma unroll 4
+  for (int i = 0; i < d; ++i) {
+    d0[i] = s0[i];
+    d1[i] = s1[i];
+  }
+}
+// qh = qe + e/2 ge; zn = ze + e qh  (first half of a leapfrog step)
+template <typename R>
+__device__ __forceinline__ void half_kick_drift(R *__restrict__ qh, R *__restrict__ zn, const R *__restrict__ qe,
+                                                const R *__restrict__ ge, const R *__restrict__ zs, R e, int d) {
+#pragma unroll 4
+  for (int i = 0; i < d; ++i) {
+    qh[i] = qe[i] + R(0.5) * e * ge[i];
+    zn[i] = zs[i] + e * qh[i];
+  }
+}
+// second half: qend = qh + e/2 gn, zend = zn, gend = gn; returns |qend|^2 (FP64 sum)
+template <typename R>
+__device__ __forceinline__ double half_kick_store(R *__restrict__ zend, R *__restrict__ qend, R *__restrict__ gend,
+                                                  const R *__restrict__ qh, const R *__restrict__ zn,
+                                                  const R *__restrict__ gn, R e, int d) {
+  double qq = 0.0;
+#pragma unroll 4
+  for (int i = 0; i < d; ++i) {
+    const R qn = qh[i] + R(0.5) * e * gn[i];
+    qq += static_cast<double>(qn) * qn;
+    zend[i] = zn[i];
+    qend[i] = qn;
+    gend[i] = gn[i];
+  }
+  return qq;
+}
+
+// zp = zc + a u + b v
+template <typename R>
+__device__ __forceinline__ void vaxpby(R *__restrict__ zp, const R *__restrict__ zc, R a, const R *__restrict__ u, R b,
+                                       const R *__restrict__ v, int d) {
+#pragma unroll 4
+  for (int i = 0; i < d; ++i) zp[i] = zc[i] + a * u[i] + b * v[i];
+}
+// q1 += e/2 g1; z1 += e q1; zp = z1
+template <typename R>
+__device__ __forceinline__ void kick_drift_inplace(R *__restrict__ z1, R *__restrict__ q1, const R *__restrict__ g1,
+                                                   R *__restrict__ zp, R e, int d) {
+#pragma unroll 4
+  for (int i = 0; i < d; ++i) {
+    const R q = q1[i] + R(0.5) * e * g1[i];
+    const R z = z1[i] + e * q;
+    q1[i] = q;
+    z1[i] = z;
+    zp[i] = z;
+  }
+}
+
 template <typename R>
 struct Chain {
   const StepArgs<R> &a;
@@ -55,8 +120,7 @@ struct Chain {
     const double lpr = a.tgt.to_x_prior(ze(r), xo);
     const double lp = static_cast<double>(a.st.lle[r]) + lpr + a.tgt.logdet;
     if (gout) {
-      const R *ge = gle(r);
-      for (int i = 0; i < a.d; ++i) gout[i] = ge[i];
+      vcopy(gout, static_cast<const R *>(gle(r)), a.d);
       a.tgt.add_prior_grad(xo, gout);
     }
     return lp;
@@ -76,7 +140,12 @@ struct Chain {
     draw_normals<R>(a.seed, c, a.st.iter[c], kXi, a.d, xi);
     const R e = static_cast<R>(a.eps);
     R *zc = z(c), *zp = ze(c);
-    for (int i = 0; i < a.d; ++i) zp[i] = zc[i] + e * xi[i];
+    {
+      R *__restrict__ dst = zp;
+      const R *__restrict__ src = zc;
+#pragma unroll 4
+      for (int i = 0; i < a.d; ++i) dst[i] = src[i] + e * xi[i];
+    }
     return true;
   }
   __device__ bool mh_post(int c) const {
@@ -87,8 +156,7 @@ struct Chain {
     const double u = draw_uniform<double>(a.seed, c, it, kAccept, 0);
     const bool acc = log(u) < la;
     if (acc) {
-      R *zc = z(c), *zp = ze(c);
-      for (int i = 0; i < a.d; ++i) zc[i] = zp[i];
+      vcopy(z(c), static_cast<const R *>(ze(c)), a.d);
       a.st.lp[c] = static_cast<R>(lpp);
     }
     count(c, acc, la, 1);
@@ -103,8 +171,7 @@ struct Chain {
     R xi[kMaxD];
     draw_normals<R>(a.seed, c, a.st.iter[c], kXi, a.d, xi);
     const R e = static_cast<R>(a.eps), s = static_cast<R>(sqrt(2.0 * a.eps));
-    R *zc = z(c), *gc = g(c), *zp = ze(c);
-    for (int i = 0; i < a.d; ++i) zp[i] = zc[i] + e * gc[i] + s * xi[i];
+    vaxpby(ze(c), static_cast<const R *>(z(c)), e, static_cast<const R *>(g(c)), s, static_cast<const R *>(xi), a.d);
     return true;
   }
   __device__ bool mala_post(int c) const {
@@ -125,10 +192,7 @@ struct Chain {
     const double u = draw_uniform<double>(a.seed, c, it, kAccept, 0);
     const bool acc = log(u) < la;
     if (acc) {
-      for (int i = 0; i < a.d; ++i) {
-        zc[i] = zp[i];
-        gc[i] = gp[i];
-      }
+      vcopy2(zc, static_cast<const R *>(zp), gc, static_cast<const R *>(gp), a.d);
       a.st.lp[c] = static_cast<R>(lpp);
     }
     count(c, acc, la, 1);
@@ -150,21 +214,12 @@ struct Chain {
       R q[kMaxD];
       draw_normals<R>(a.seed, c, a.st.iter[c], kXi, a.d, q);
       double qq = 0.0;
-      R *zc = z(c), *gc = g(c);
-      for (int i = 0; i < a.d; ++i) {
-        qq += static_cast<double>(q[i]) * q[i];
-        z1[i] = zc[i];
-        g1[i] = gc[i];
-        q1[i] = q[i];
-      }
+      for (int i = 0; i < a.d; ++i) qq += static_cast<double>(q[i]) * q[i];
+      vcopy2(z1, static_cast<const R *>(z(c)), g1, static_cast<const R *>(g(c)), a.d);
+      vcopy(q1, static_cast<const R *>(q), a.d);
       dw[1] = -static_cast<double>(a.st.lp[c]) + 0.5 * qq;
     }
-    R *zp = ze(c);
-    for (int i = 0; i < a.d; ++i) {
-      q1[i] += R(0.5) * e * g1[i];
-      z1[i] += e * q1[i];
-      zp[i] = z1[i];
-    }
+    kick_drift_inplace(z1, q1, static_cast<const R *>(g1), ze(c), e, a.d);
     return true;
   }
   __device__ bool hmc_post(int c) const {
@@ -188,11 +243,7 @@ struct Chain {
     const double u = draw_uniform<double>(a.seed, c, it, kAccept, 0);
     const bool acc = log(u) < la;
     if (acc) {
-      R *zc = z(c), *gc = g(c);
-      for (int i = 0; i < a.d; ++i) {
-        zc[i] = z1[i];
-        gc[i] = g1[i];
-      }
+      vcopy2(z(c), static_cast<const R *>(z1), g(c), static_cast<const R *>(g1), a.d);
       a.st.lp[c] = static_cast<R>(lp1);
     }
     count(c, acc, la, 0);
@@ -226,11 +277,10 @@ struct Chain {
       R *zc = z(c), *gc = g(c);
       R *zm = wv(c, 0), *qm = wv(c, 1), *gm = wv(c, 2), *zp = wv(c, 3), *qp = wv(c, 4),
         *gp = wv(c, 5), *zs = wv(c, 6), *gs = wv(c, 7);
-      for (int i = 0; i < d; ++i) {
-        zm[i] = zp[i] = zs[i] = zc[i];
-        gm[i] = gp[i] = gs[i] = gc[i];
-        qm[i] = qp[i] = q0[i];
-      }
+      vcopy2(zm, static_cast<const R *>(zc), gm, static_cast<const R *>(gc), d);
+      vcopy2(zp, static_cast<const R *>(zc), gp, static_cast<const R *>(gc), d);
+      vcopy2(zs, static_cast<const R *>(zc), gs, static_cast<const R *>(gc), d);
+      vcopy2(qm, static_cast<const R *>(q0), qp, static_cast<const R *>(q0), d);
       dw[3] = 1.0;
       dw[4] = static_cast<double>(a.st.lp[c]);
       dw[5] = 0.0;
@@ -246,10 +296,7 @@ struct Chain {
     const R e = static_cast<R>(dw[7] * a.eps);
     R *ze_ = wv(c, back ? 0 : 3), *qe = wv(c, back ? 1 : 4), *ge = wv(c, back ? 2 : 5);
     R *qh = wv(c, 8), *zn = ze(c);
-    for (int i = 0; i < d; ++i) {
-      qh[i] = qe[i] + R(0.5) * e * ge[i];
-      zn[i] = ze_[i] + e * qh[i];
-    }
+    half_kick_drift(qh, zn, static_cast<const R *>(qe), static_cast<const R *>(ge), static_cast<const R *>(ze_), e, d);
     return true;
   }
 
@@ -264,14 +311,8 @@ struct Chain {
     const double lpn = logpi_eval(c, gn, x);
     R *qh = wv(c, 8), *zn = ze(c);
     R *zend = wv(c, back ? 0 : 3), *qend = wv(c, back ? 1 : 4), *gend = wv(c, back ? 2 : 5);
-    double qq = 0.0;
-    for (int i = 0; i < d; ++i) {
-      const R qn = qh[i] + R(0.5) * e * gn[i];
-      qq += static_cast<double>(qn) * qn;
-      zend[i] = zn[i];
-      qend[i] = qn;
-      gend[i] = gn[i];
-    }
+    const double qq = half_kick_store(zend, qend, gend, static_cast<const R *>(qh), static_cast<const R *>(zn),
+                                      static_cast<const R *>(gn), e, d);
     a.st.evals[c] += 1ull;
     dw[9] += 1.0;
     const int leaf = static_cast<int>(dw[9]);
@@ -319,11 +360,7 @@ struct Chain {
       // the subtree of this doubling is complete: progressive top-level selection
       const double ut = draw_uniform<double>(a.seed, c, it, kNutsTop, static_cast<uint32_t>(j));
       if (ut * dw[3] < node_n) {
-        R *zs = wv(c, 6), *gs = wv(c, 7);
-        for (int i = 0; i < d; ++i) {
-          zs[i] = cz[i];
-          gs[i] = cg[i];
-        }
+        vcopy2(wv(c, 6), cz, wv(c, 7), cg, d);
         dw[4] = clp;
         dw[11] = 1.0;
       }
@@ -346,16 +383,8 @@ struct Chain {
         *pcg = wv(c, 12 + 4 * lvl);
       const R *fz = first_src < 0 ? zend : wv(c, 9 + 4 * first_src);
       const R *fq = first_src < 0 ? qend : wv(c, 10 + 4 * first_src);
-      if (first_src != lvl)
-        for (int i = 0; i < d; ++i) {
-          pz[i] = fz[i];
-          pq[i] = fq[i];
-        }
-      if (cand_src != lvl)
-        for (int i = 0; i < d; ++i) {
-          pcz[i] = cz[i];
-          pcg[i] = cg[i];
-        }
+      if (first_src != lvl) vcopy2(pz, fz, pq, fq, d);
+      if (cand_src != lvl) vcopy2(pcz, cz, pcg, cg, d);
       dw[12 + lvl] = clp;
       dw[22 + lvl] = node_n;
       dw[8] = m_sub + 1;
@@ -402,9 +431,11 @@ struct Chain {
     const double t = uz * (a.aies_a - 1.0) + 1.0;
     const double Z = t * t / a.aies_a;
     dwork_ptr(i)[0] = Z;
-    const R *zi = z(i), *zj = z(jw);
-    R *y = ze(r);
+    const R *__restrict__ zi = z(i);
+    const R *__restrict__ zj = z(jw);
+    R *__restrict__ y = ze(r);
     const R Zr = static_cast<R>(Z);
+#pragma unroll 4
     for (int q = 0; q < a.d; ++q) y[q] = zj[q] + Zr * (zi[q] - zj[q]);
     return true;
   }
@@ -418,8 +449,7 @@ struct Chain {
     const double u = draw_uniform<double>(a.seed, i, it, kAccept, 0);
     const bool acc = log(u) < la;
     if (acc) {
-      R *zi = z(i), *y = ze(r);
-      for (int q = 0; q < a.d; ++q) zi[q] = y[q];
+      vcopy(z(i), static_cast<const R *>(ze(r)), a.d);
       a.st.lp[i] = static_cast<R>(lpy);
     }
     count(i, acc, la, 1);
