@@ -293,7 +293,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
   const bool grad = a.need_grad != 0;
   const int nph = tc_num_phases(D, grad);
   // The activations h_1..h_{D-1} that the adjoint pass needs stay in tensor memory after the
-  // accumulator columns (this rank's NS columns, BF16 pairs) when they fit, else in global
+  // accumulator columns (this rank's NS columns, BF16 pairs) in the configurations of
+  // tc2_h_in_tmem (the launch keeps the depth within tc2_tmem_max_depth), else in global
   // scratch.
   constexpr bool h_tmem = tc2_h_in_tmem(W, CS);
   // In clusters of 4, given room for them (E.xchg), each CTA also writes its slice of a layer
