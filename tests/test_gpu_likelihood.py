@@ -136,3 +136,20 @@ def test_init_chains_log_pi_and_gradient(prec):
     assert rel_err(st["grad"], rg) < {"fp64": 1e-9, "fp32": 1e-4, "bf16": 2e-2}[prec]
     assert np.all(st["iter"] == 0)
     s.close()
+
+
+@pytest.mark.parametrize("width", [256, 512])
+def test_bf16_two_cta_clusters(width):
+    """6000 points are 47 tiles of 128: the BF16 engine splits each layer over clusters of two
+    CTAs (per-warp shared->shared slice exchange; width 256 keeps the stored activations in
+    tensor memory, width 512 in global scratch)."""
+    e = emulator_case(8, width, 2, out_s=20.0, out_m=100.0)
+    s = _sampler("bf16", e)
+    x = np.random.default_rng(5).uniform(-3, 3, (6000, 8))
+    ll, g = s.grad_loglike(x)
+    ref = O.Model(8, emulator=e, bf16=True)
+    rl, rg = ref.loglike(x)
+    ll, g = ll.double().cpu().numpy(), g.double().cpu().numpy()
+    assert np.max(np.abs(ll - rl) / np.maximum(np.abs(rl), 1.0)) < 2e-3
+    assert rel_err(g, rg) < 2e-2
+    s.close()

@@ -134,10 +134,10 @@ def test_thinning_and_sample_shape():
     s.close()
 
 
-def _setup_gauss(prec, n, width, d=8, seed=11):
+def _setup_gauss(prec, n, width, d=8, seed=11, depth=3):
     """d = 8 with the last two dimensions under N(0, 1) priors (no box): exercises the prior
     terms of the register-resident BF16 chains (d <= 8)."""
-    e = emulator_case(d, width, 3, out_s=8.0, out_m=50.0)
+    e = emulator_case(d, width, depth, out_s=8.0, out_m=50.0)
     mu, L = whitening(d, 2, scale=0.4)
     lower, upper = np.full(d, -3.0), np.full(d, 3.0)
     lower[6:], upper[6:] = -1e30, 1e30
@@ -188,4 +188,16 @@ def test_bf16_register_chains_record_every_step(kernel, extra):
     mu, L = s.whitening()
     x_state = mu + st["z"] @ L.T
     assert np.max(np.abs(x_state - x[-1])) < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("width", [256, 512])
+def test_bf16_mala_two_cta_clusters(width):
+    """MALA with 6000 chains (clusters of two CTAs per 128-chain tile) against the oracle."""
+    n = 6000
+    s, m, z0 = _setup_gauss("bf16", n, width, depth=2)
+    out = torch.empty((1, n, 8), dtype=s.dtype, device="cuda")
+    s.step("mala", 1, eps=0.4, samples=out)
+    ref = O.run(m, "mala", z0, eps=0.4, n_steps=1, seed=11, trace=True)
+    _check("bf16", s, ref, out, "mala", n)
     s.close()
