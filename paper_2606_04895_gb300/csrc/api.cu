@@ -1025,6 +1025,8 @@ static bst_status train_setup(bst_handle h, int m) {
     BST_TRY(dalloc_t(h, &h->tw.Dn, mm * w));
     BST_TRY(dalloc_t(h, &h->tw.dout, mm));
     BST_TRY(dalloc_t(h, &h->tw.loss, 4));
+    const size_t fmax = w > static_cast<size_t>(h->d) ? w : static_cast<size_t>(h->d);
+    BST_TRY(dalloc_t(h, &h->tw.ws, static_cast<size_t>(kTrainSplits) * w * fmax));
     h->train_cap = m;
   }
   return BST_OK;

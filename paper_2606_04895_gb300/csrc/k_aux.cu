@@ -539,24 +539,29 @@ cudaError_t launch_ess_variogram_f64(const double *x, int n, int M, int d, int t
 //   EPI_TANH  : C = tanh(acc + bias[j])
 //   EPI_DTANH : C = acc * (1 - H[i][j]^2)
 enum { EPI_STORE = 0, EPI_TANH = 1, EPI_DTANH = 2 };
+// Split over K (gridDim.z slices of k_chunk, a multiple of kGK): slice z accumulates its
+// k range into its own output C + z * M * ldc (EPI_STORE only); sum_slices adds the slices in
+// slice order, so the result does not depend on scheduling.
 constexpr int kGT = 64, kGK = 16;
 __global__ void __launch_bounds__(256) gemm_f32_kernel(int M, int N, int K, const float *A, long long a_i,
                                                        long long a_k, const float *B, long long b_k, long long b_j,
                                                        float *C, int ldc, int epi, const float *bias, const float *H,
-                                                       int ldh) {
+                                                       int ldh, int k_chunk) {
   __shared__ float As[kGK][kGT + 4];
   __shared__ float Bs[kGK][kGT + 4];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
+  const int kbeg = blockIdx.z * k_chunk, kend = min(K, kbeg + k_chunk);
+  C += static_cast<size_t>(blockIdx.z) * M * ldc;
   float acc[4][4] = {};
   (void)acc;
-  for (int k0 = 0; k0 < K; k0 += kGK) {
+  for (int k0 = kbeg; k0 < kend; k0 += kGK) {
     for (int e = threadIdx.x; e < kGK * kGT; e += 256) {
       const int kk = e / kGT, ii = e % kGT;
       const int i = i0 + ii, k = k0 + kk;
-      As[kk][ii] = (i < M && k < K) ? A[i * a_i + k * a_k] : 0.f;
+      As[kk][ii] = (i < M && k < kend) ? A[i * a_i + k * a_k] : 0.f;
       const int j = j0 + ii;
-      Bs[kk][ii] = (j < N && k < K) ? B[k * b_k + j * b_j] : 0.f;
+      Bs[kk][ii] = (j < N && k < kend) ? B[k * b_k + j * b_j] : 0.f;
     }
     __syncthreads();
 #pragma unroll
@@ -591,9 +596,17 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(int M, int N, int K, cons
 }
 static void gemm_f32(int M, int N, int K, const float *A, long long a_i, long long a_k, const float *B, long long b_k,
                      long long b_j, float *C, int ldc, int epi, const float *bias, const float *H, int ldh,
-                     cudaStream_t s) {
-  dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT);
-  gemm_f32_kernel<<<grid, 256, 0, s>>>(M, N, K, A, a_i, a_k, B, b_k, b_j, C, ldc, epi, bias, H, ldh);
+                     cudaStream_t s, int splits = 1) {
+  const int k_chunk = ((K + splits - 1) / splits + kGK - 1) / kGK * kGK;
+  dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT, splits);
+  gemm_f32_kernel<<<grid, 256, 0, s>>>(M, N, K, A, a_i, a_k, B, b_k, b_j, C, ldc, epi, bias, H, ldh, k_chunk);
+}
+__global__ void sum_slices_kernel(const float *ws, int splits, size_t n, float *out) {
+  const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  float r = ws[i];
+  for (int z = 1; z < splits; ++z) r += ws[static_cast<size_t>(z) * n + i];
+  out[i] = r;
 }
 
 __global__ void standardise_kernel(const float *X, const float *m, const float *sd, int rows, int d, float *U) {
@@ -657,8 +670,11 @@ cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in
   for (int l = D; l >= 1; --l) {
     const int fan = (l == 1) ? d : w;
     const float *Hprev = (l == 1) ? tw.U : tw.H + static_cast<size_t>(l - 2) * m * w;
-    // g_W_l[k][j] = sum_i delta_l[i][k] Hprev[i][j]
-    gemm_f32(w, fan, m, dl, 1, w, Hprev, fan, 1, G + off_W(l, d, w), fan, EPI_STORE, nullptr, nullptr, 0, s);
+    // g_W_l[k][j] = sum_i delta_l[i][k] Hprev[i][j]  (the batch split in kTrainSplits slices: a
+    // w x fan product has too few output tiles to fill the GPU)
+    gemm_f32(w, fan, m, dl, 1, w, Hprev, fan, 1, tw.ws, fan, EPI_STORE, nullptr, nullptr, 0, s, kTrainSplits);
+    sum_slices_kernel<<<blocks_for(static_cast<size_t>(w) * fan, 256), 256, 0, s>>>(
+        tw.ws, kTrainSplits, static_cast<size_t>(w) * fan, G + off_W(l, d, w));
     colsum_kernel<<<blocks_for(w, 128), 128, 0, s>>>(dl, m, w, G + off_b(l, d, w));
     if (l > 1) {
       // delta_{l-1} = (delta_l W_l) (1 - H_{l-1}^2)

@@ -81,7 +81,9 @@ struct TrainWork {
   float *Dn;    // [m][w] adjoint buffer
   float *dout;  // [m]
   float *loss;  // [1]
+  float *ws;    // [kTrainSplits][w][w] partial weight gradients (split over the batch)
 };
+constexpr int kTrainSplits = 4;
 cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in_s, float out_m, float out_s, int d,
                               int D, int w, int m, const float *X, const float *chi2, float *G, TrainWork &tw,
                               cudaStream_t s);
