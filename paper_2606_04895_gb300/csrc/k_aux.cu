@@ -637,13 +637,23 @@ __global__ void train_head_kernel(const float *HD, const float *wo, const float 
   for (int k = lane; k < w; k += 32) delta[static_cast<size_t>(warp) * w + k] = g * wo[k] * (1.f - h[k] * h[k]);
 }
 
-// column sums: out[j] = sum_i X[i][j] (bias gradients); out_scalar = sum_i v[i]
+// column sums: out[j] = sum_i X[i][j] (bias gradients).  A block of 256 threads takes 32
+// columns; its 8 row groups sum interleaved rows (i = g, g + 8, ...) and the 8 partial sums
+// are added in group order, so the result does not depend on scheduling.
 __global__ void colsum_kernel(const float *X, int rows, int cols, float *out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= cols) return;
+  __shared__ float part[8][32];
+  const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + c;
   float s = 0.f;
-  for (int i = 0; i < rows; ++i) s += X[static_cast<size_t>(i) * cols + j];
-  out[j] = s;
+  if (j < cols)
+    for (int i = g; i < rows; i += 8) s += X[static_cast<size_t>(i) * cols + j];
+  part[g][c] = s;
+  __syncthreads();
+  if (g == 0 && j < cols) {
+    float t = part[0][c];
+    for (int q = 1; q < 8; ++q) t += part[q][c];
+    out[j] = t;
+  }
 }
 
 cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in_s, float out_m, float out_s, int d,
@@ -665,7 +675,7 @@ cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in
                                                                                out_s, m, w, tw.dout, tw.Dl, tw.loss);
   // g_wo[j] = sum_i dout_i H_D[i][j]  (1 x w = dout^T H_D) ; g_bo = sum_i dout_i
   gemm_f32(1, w, m, tw.dout, 0, 1, HD, w, 1, G + owo, w, EPI_STORE, nullptr, nullptr, 0, s);
-  colsum_kernel<<<1, 32, 0, s>>>(tw.dout, m, 1, G + owo + w);
+  colsum_kernel<<<1, 256, 0, s>>>(tw.dout, m, 1, G + owo + w);
   float *dl = tw.Dl, *dn = tw.Dn;
   for (int l = D; l >= 1; --l) {
     const int fan = (l == 1) ? d : w;
@@ -675,7 +685,7 @@ cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in
     gemm_f32(w, fan, m, dl, 1, w, Hprev, fan, 1, tw.ws, fan, EPI_STORE, nullptr, nullptr, 0, s, kTrainSplits);
     sum_slices_kernel<<<blocks_for(static_cast<size_t>(w) * fan, 256), 256, 0, s>>>(
         tw.ws, kTrainSplits, static_cast<size_t>(w) * fan, G + off_W(l, d, w));
-    colsum_kernel<<<blocks_for(w, 128), 128, 0, s>>>(dl, m, w, G + off_b(l, d, w));
+    colsum_kernel<<<blocks_for(w, 32), 256, 0, s>>>(dl, m, w, G + off_b(l, d, w));
     if (l > 1) {
       // delta_{l-1} = (delta_l W_l) (1 - H_{l-1}^2)
       gemm_f32(m, w, w, dl, w, 1, P + off_W(l, d, w), w, 1, dn, w, EPI_DTANH, nullptr, Hprev, w, s);
