@@ -547,31 +547,35 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(int M, int N, int K, cons
                                                        long long a_k, const float *B, long long b_k, long long b_j,
                                                        float *C, int ldc, int epi, const float *bias, const float *H,
                                                        int ldh, int k_chunk) {
-  __shared__ float As[kGK][kGT + 4];
-  __shared__ float Bs[kGK][kGT + 4];
+  __shared__ __align__(16) float As[kGK][kGT + 4];
+  __shared__ __align__(16) float Bs[kGK][kGT + 4];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int i0 = blockIdx.y * kGT, j0 = blockIdx.x * kGT;
   const int kbeg = blockIdx.z * k_chunk, kend = min(K, kbeg + k_chunk);
   C += static_cast<size_t>(blockIdx.z) * M * ldc;
   float acc[4][4] = {};
   (void)acc;
+  // staging loads run along whichever index of an operand is contiguous in memory
+  const bool a_kc = (a_k == 1), b_kc = (b_k == 1);
   for (int k0 = kbeg; k0 < kend; k0 += kGK) {
     for (int e = threadIdx.x; e < kGK * kGT; e += 256) {
-      const int kk = e / kGT, ii = e % kGT;
-      const int i = i0 + ii, k = k0 + kk;
-      As[kk][ii] = (i < M && k < kend) ? A[i * a_i + k * a_k] : 0.f;
-      const int j = j0 + ii;
-      Bs[kk][ii] = (j < N && k < kend) ? B[k * b_k + j * b_j] : 0.f;
+      {
+        const int kk = a_kc ? e % kGK : e / kGT, ii = a_kc ? e / kGK : e % kGT;
+        const int i = i0 + ii, k = k0 + kk;
+        As[kk][ii] = (i < M && k < kend) ? A[i * a_i + k * a_k] : 0.f;
+      }
+      {
+        const int kk = b_kc ? e % kGK : e / kGT, jj = b_kc ? e / kGK : e % kGT;
+        const int j = j0 + jj, k = k0 + kk;
+        Bs[kk][jj] = (j < N && k < kend) ? B[k * b_k + j * b_j] : 0.f;
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kGK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a[u] = As[kk][ty * 4 + u];
-        b[u] = Bs[kk][tx * 4 + u];
-      }
+      const float4 a4 = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+      const float4 b4 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+      const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
