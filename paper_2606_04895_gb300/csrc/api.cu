@@ -199,10 +199,11 @@ StepArgs<R> make_args(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_st
   {
     // the working-precision values of the device copies (mu_r, L_r, lo_r, up_r, gauss_d)
     const int d = h->d;
+    // (entries beyond d stay zero: the device loops run unrolled to 16 or 32 entries)
     for (int i = 0; i < d; ++i) {
       if (h->mu.size() >= static_cast<size_t>(d)) a.tgt.mu[i] = static_cast<R>(h->mu[i]);
       if (h->L.size() >= static_cast<size_t>(d) * d)
-        for (int j = 0; j < d; ++j) a.tgt.L[i * d + j] = static_cast<R>(h->L[static_cast<size_t>(i) * d + j]);
+        for (int j = 0; j < d; ++j) a.tgt.L[i * kMaxD + j] = static_cast<R>(h->L[static_cast<size_t>(i) * d + j]);
       if (h->lower.size() >= static_cast<size_t>(d)) a.tgt.lower[i] = static_cast<R>(h->lower[i]);
       if (h->upper.size() >= static_cast<size_t>(d)) a.tgt.upper[i] = static_cast<R>(h->upper[i]);
       if (h->gauss.size() >= static_cast<size_t>(d)) a.tgt.gauss[i] = h->gauss[i];
@@ -219,10 +220,12 @@ StepArgs<R> make_args(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_st
   a.st.ze = static_cast<R *>(h->ze);
   a.st.lle = static_cast<R *>(h->lle);
   a.st.gle = static_cast<R *>(h->gle);
-  a.st.ze_ld = h->dp;
-  a.st.gle_ld = h->dp;
+  // the chains' evaluation rows, gradients and work buffers are chain-blocked (ld 0)
+  a.st.ze_ld = 0;
+  a.st.gle_ld = 0;
   a.st.work = static_cast<R *>(h->work);
-  a.st.work_stride = h->work_stride;
+  a.st.dwork = reinterpret_cast<double *>(static_cast<R *>(h->work) +
+                                          static_cast<size_t>(kDworkOffsetVecs) * kMaxD * chains_padded(h->n));
   a.st.steps_done = h->steps_done;
   a.samples = static_cast<R *>(samples);
   a.welford_on = (h->welford_on && mode != kModeRefresh && mode != kModeLoglike) ? 1 : 0;
@@ -521,7 +524,9 @@ bst_status bst_create(bst_handle *out, const bst_config *cfg) {
   h->rs = (cfg->precision == BST_FP64) ? 8 : 4;
   h->kb1 = (3 * h->dp + 63) / 64;
   const size_t n = h->n, dp = h->dp, rs = h->rs;
-  h->work_stride = (rs == 8) ? work_stride_elems<double>(h->dp) : work_stride_elems<float>(h->dp);
+  // the general sampler code's per-chain buffers are chain-blocked over the padded chain count
+  const size_t np = chains_padded(h->n);
+  h->work_stride = static_cast<int>(rs == 8 ? work_elems_per_chain<double>() : work_elems_per_chain<float>());
   bst_status st = BST_OK;
   auto A = [&](void **p, size_t b) {
     if (st == BST_OK) st = dalloc(h, p, b);
@@ -529,10 +534,10 @@ bst_status bst_create(bst_handle *out, const bst_config *cfg) {
   A(&h->z, n * dp * rs);
   A(&h->g, n * dp * rs);
   A(&h->lp, n * rs);
-  A(&h->ze, n * dp * rs);
+  A(&h->ze, np * dp * rs);
   A(&h->lle, n * rs);
-  A(&h->gle, n * dp * rs);
-  A(&h->work, n * static_cast<size_t>(h->work_stride) * rs);
+  A(&h->gle, np * dp * rs);
+  A(&h->work, np * static_cast<size_t>(h->work_stride) * rs);
   A(&h->xbuf, n * dp * rs);
   A((void **)&h->iter, n * 4);
   A((void **)&h->acc_stat, n * 8);
@@ -769,7 +774,7 @@ bst_status bst_init_chains(bst_handle h, const double *theta0, const double *low
   BST_CUDA(cudaMemset(h->accepts, 0, nn * 8));
   BST_CUDA(cudaMemset(h->evals, 0, nn * 8));
   BST_CUDA(cudaMemset(h->divs, 0, nn * 8));
-  BST_CUDA(cudaMemset(h->work, 0, nn * h->work_stride * h->rs));
+  BST_CUDA(cudaMemset(h->work, 0, chains_padded(h->n) * h->work_stride * h->rs));
   BST_CUDA(cudaMemset(h->status, 0, 64));
   h->stage = 2;
   BST_TRY(refresh(h, 0));

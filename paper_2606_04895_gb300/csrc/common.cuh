@@ -115,48 +115,80 @@ __device__ __forceinline__ void draw_normals(uint64_t seed, uint32_t chain, uint
 // Whitening (x = mu + L z) and prior (box, N(0,1) on flagged dims), device view.  The
 // values are copied into the kernel parameters (the step kernels take their StepArgs as a
 // __grid_constant__ parameter), so every thread reads them through the constant cache.
+// Entries beyond d are zero (mu, L, bounds, flags), so loops unrolled past d add exact zeros.
 template <typename R>
 struct TargetView {
   int d;
   double logdet;   // sum_i log L_ii
   int any_gauss;
   R mu[kMaxD];          // [d]
-  R L[kMaxD * kMaxD];   // [d][d] row-major (first d*d entries), lower triangular
+  R L[kMaxD * kMaxD];   // L_ij at i * kMaxD + j, lower triangular
   R lower[kMaxD];       // [d]
   R upper[kMaxD];       // [d]
   int gauss[kMaxD];     // [d]
 
-  // x = mu + L z; returns the log prior (0 / -inf / -x_g.x_g/2).
-  // (z is read once into registers: the triangular product is unrolled over kMaxD with the
-  // same summation order as a plain loop over j <= i)
-  __device__ __noinline__ double to_x_prior(const R *z, R *x) const {
-    R zr[kMaxD];
+  // x = mu + L z over DM >= d entries; returns the log prior (0 / -inf outside the box /
+  // -x_g.x_g / 2 over the flagged dims, as four partial sums of R added in FP64).  XOUT stores
+  // x (DM entries); with grad, g[j] -= sum_{i >= j} L_ij x_g,i (the gradient of the Gaussian
+  // prior term through x = mu + L z, Algorithm 1).  Fully unrolled, so every element of mu and
+  // L is a constant-bank operand of its FMA.  x is accumulated column by column (z_j streamed,
+  // each x_i still summed over j in ascending order) and the gradient row by row, so about DM
+  // values are live at a time.
+  template <int DM, bool XOUT, class VZ, class VG>
+  __device__ __forceinline__ double eval(VZ z, R *x, VG g, bool grad) const {
+    R xs[DM];
 #pragma unroll
-    for (int j = 0; j < kMaxD; ++j) zr[j] = j < d ? z[j] : R(0);
+    for (int i = 0; i < DM; ++i) xs[i] = mu[i];
+#pragma unroll
+    for (int j = 0; j < DM; ++j) {
+      const R zj = j < d ? static_cast<R>(z[j]) : R(0);
+#pragma unroll
+      for (int i = j; i < DM; ++i) xs[i] += L[i * kMaxD + j] * zj;
+    }
+    R part[4] = {R(0), R(0), R(0), R(0)};
     bool inside = true;
-    double lp = 0.0;
 #pragma unroll
-    for (int i = 0; i < kMaxD; ++i) {
-      if (i < d) {
-        R s = mu[i];
+    for (int i = 0; i < DM; ++i) {
+      if (XOUT) x[i] = xs[i];
+      if (i < d && !(xs[i] >= lower[i] && xs[i] <= upper[i])) inside = false;
+      xs[i] = gauss[i] ? xs[i] : R(0);
+      part[i & 3] += xs[i] * xs[i];
+    }
+    if (grad && any_gauss) {
 #pragma unroll
-        for (int j = 0; j <= i; ++j) s += L[i * d + j] * zr[j];
-        x[i] = s;
-        if (!(s >= lower[i] && s <= upper[i])) inside = false;
-        if (any_gauss && gauss[i]) lp -= 0.5 * static_cast<double>(s) * static_cast<double>(s);
+      for (int j = 0; j < DM; ++j) {
+        R sg = R(0);
+#pragma unroll
+        for (int i = j; i < DM; ++i) sg += L[i * kMaxD + j] * xs[i];
+        if (j < d) g[j] -= sg;
       }
     }
+    const double lp = -0.5 * ((static_cast<double>(part[0]) + static_cast<double>(part[1])) +
+                              (static_cast<double>(part[2]) + static_cast<double>(part[3])));
     return inside ? lp : -INFINITY;
   }
-  // g += L^T (-x on Gaussian dims)
-  __device__ __forceinline__ void add_prior_grad(const R *x, R *g) const {
-    if (!any_gauss) return;
-    for (int j = 0; j < d; ++j) {
-      R s = 0;
-      for (int i = j; i < d; ++i)
-        if (gauss[i]) s -= L[i * d + j] * x[i];
-      g[j] += s;
+  // The same quantities with loops over d (FP64 state, where the loop overhead is small next
+  // to the arithmetic); the prior is summed in order.
+  template <bool XOUT, class VZ, class VG>
+  __device__ __forceinline__ double eval_loop(VZ z, R *x, VG g, bool grad) const {
+    R xg[kMaxD];
+    bool inside = true;
+    double lp = 0.0;
+    for (int i = 0; i < d; ++i) {
+      R s = mu[i];
+      for (int j = 0; j <= i; ++j) s += L[i * kMaxD + j] * z[j];
+      if (XOUT) x[i] = s;
+      if (!(s >= lower[i] && s <= upper[i])) inside = false;
+      xg[i] = gauss[i] ? s : R(0);
+      lp -= 0.5 * static_cast<double>(xg[i]) * static_cast<double>(xg[i]);
     }
+    if (grad && any_gauss)
+      for (int j = 0; j < d; ++j) {
+        R sg = R(0);
+        for (int i = j; i < d; ++i) sg += L[i * kMaxD + j] * xg[i];
+        g[j] -= sg;
+      }
+    return inside ? lp : -INFINITY;
   }
 };
 
@@ -169,12 +201,17 @@ struct ChainState {
   uint32_t *iter;
   double *acc_stat;
   unsigned long long *accepts, *evals, *divs;
-  R *ze;   // [n_rows][ze_ld] point to evaluate (z-space, or x-space in loglike mode)
-  R *lle;  // [n_rows]        logL at ze
-  R *gle;  // [n_rows][gle_ld] grad of logL at ze (w.r.t. ze)
+  // Point to evaluate (z-space, or x-space in loglike mode) and grad of logL there (w.r.t. ze):
+  // with ld > 0 row-major [n_rows][ld] (a caller's theta rows), with ld == 0 chain-blocked with
+  // dp elements per row (row_off / row_es below).
+  R *ze;
+  R *lle;  // [n_rows] logL at ze
+  R *gle;
   int ze_ld, gle_ld;
-  R *work;         // [n_chains][work_stride] per-kernel temporaries
-  int work_stride;
+  // Per-chain temporaries of the general sampler code, chain-blocked: kDworkOffsetVecs vectors
+  // of kMaxD reals (vector k, element i is element k * kMaxD + i), and kDworkDoubles doubles.
+  R *work;
+  double *dwork;
   int *steps_done;  // [n_chains] iterations completed in this launch
 };
 
@@ -201,13 +238,32 @@ struct StepArgs {
   int *status;
 };
 
-// Per-chain work row: kDworkOffsetVecs vectors of dp reals (NUTS trajectory ends,
-// selected point, per-level pending subtrees), then kDworkDoubles doubles.
+// Chain-blocked layout of the per-chain buffers of the general sampler code: chains in blocks
+// of kChainBlock; element e (of n_e per chain) of chain c at
+//     (c / kChainBlock) * kChainBlock * n_e + e * kChainBlock + c % kChainBlock,
+// so the threads of a warp (consecutive chains) touch one line per element, and an element
+// index known at compile time is an immediate offset.
+constexpr int kChainBlock = 32;
+__host__ __device__ __forceinline__ size_t blk_off(int c, int n_e) {
+  return static_cast<size_t>(c / kChainBlock) * kChainBlock * static_cast<size_t>(n_e) + (c % kChainBlock);
+}
+__host__ __device__ __forceinline__ size_t chains_padded(int n) {
+  return static_cast<size_t>((n + kChainBlock - 1) / kChainBlock) * kChainBlock;
+}
+// element 0 of row r of ze / gle and the element stride (ld > 0: row-major, else chain-blocked)
+__device__ __forceinline__ size_t row_off(int ld, int r, int dp) {
+  return ld > 0 ? static_cast<size_t>(r) * ld : blk_off(r, dp);
+}
+__device__ __forceinline__ int row_es(int ld) { return ld > 0 ? 1 : kChainBlock; }
+
+// Per-chain work: kDworkOffsetVecs vectors of kMaxD reals (NUTS trajectory ends, selected point,
+// per-level pending subtrees; HMC z1 q1 g1), then kDworkDoubles doubles; the buffer holds the
+// vectors of all (padded) chains, then their doubles.
 constexpr int kDworkOffsetVecs = 9 + 4 * kMaxDepthNuts;
 constexpr int kDworkDoubles = 32;
 template <typename R>
-constexpr int work_stride_elems(int dp) {
-  return kDworkOffsetVecs * dp + kDworkDoubles * static_cast<int>(sizeof(double) / sizeof(R));
+constexpr size_t work_elems_per_chain() {
+  return static_cast<size_t>(kDworkOffsetVecs) * kMaxD + kDworkDoubles * (sizeof(double) / sizeof(R));
 }
 
 // Welford tile record layout (doubles): n, mean[32], M2[32*32], batch count, batch mean[32],

@@ -154,7 +154,7 @@ struct EmuSimt {
     for (int idx = tid; idx < T * dp; idx += kThreads) {
       const int r = idx / dp, i = idx % dp;
       const int row = row0 + r;
-      bufB[r * lda1 + i] = (row < a.n_rows && i < a.d) ? a.st.ze[static_cast<size_t>(row) * a.st.ze_ld + i] : R(0);
+      bufB[r * lda1 + i] = (row < a.n_rows && i < a.d) ? a.st.ze[row_off(a.st.ze_ld, row, a.dp) + i * row_es(a.st.ze_ld)] : R(0);
     }
     __syncthreads();
     R *cur = bufA, *nxt = bufB;
@@ -230,7 +230,7 @@ struct EmuSimt {
       if (i >= a.d || row >= a.n_rows) continue;
       R s = 0;
       for (int k = 0; k < w; ++k) s += cur[r * lda + k] * E.W1[k * dp + i];
-      a.st.gle[static_cast<size_t>(row) * a.st.gle_ld + i] = s;
+      a.st.gle[row_off(a.st.gle_ld, row, a.dp) + i * row_es(a.st.gle_ld)] = s;
     }
     __syncthreads();
   }
@@ -253,8 +253,8 @@ struct AnaSimt {
     for (int r = warp; r < T; r += kThreads / 32) {
       const int row = row0 + r;
       if (row >= a.n_rows) continue;
-      const R *zr = a.st.ze + static_cast<size_t>(row) * a.st.ze_ld;
-      for (int i = lane; i < dp; i += 32) zsh[i] = (i < P.d) ? zr[i] : R(0);
+      const R *zr = a.st.ze + row_off(a.st.ze_ld, row, a.dp);
+      for (int i = lane; i < dp; i += 32) zsh[i] = (i < P.d) ? zr[i * row_es(a.st.ze_ld)] : R(0);
       __syncwarp();
       for (int k = lane; k < H; k += 32) {
         R s = P.cf[k];
@@ -306,7 +306,7 @@ struct AnaSimt {
           R gsum = 0;
           for (int k = 0; k < H; ++k) gsum += P.Bf[k * dp + lane] * ssh[k];
           if (P.has_N) gsum += sn;
-          a.st.gle[static_cast<size_t>(row) * a.st.gle_ld + lane] = gsum * P.inv_s2;
+          a.st.gle[row_off(a.st.gle_ld, row, a.dp) + lane * row_es(a.st.gle_ld)] = gsum * P.inv_s2;
         }
       }
       __syncwarp();
@@ -392,8 +392,8 @@ simt_chain_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__
       for (int h = 0; h < 2; ++h) a.st.steps_done[ch.aies_walker(row, h)] = 0;
     } else {
       a.st.steps_done[row] = 0;
-      if (a.mode == kModeHMC) ch.dwork_ptr(row)[0] = 0.0;
-      if (a.mode == kModeNUTS) ch.dwork_ptr(row)[0] = 1.0;
+      if (a.mode == kModeHMC) ch.dw(row)[0] = 0.0;
+      if (a.mode == kModeNUTS) ch.dw(row)[0] = 1.0;
     }
   }
   __syncthreads();

@@ -241,8 +241,10 @@ __device__ __forceinline__ void tmem_wait_ld_regs(uint32_t *r) {
 
 // ---------------------------------------------------------------- the kernel
 // L2X: cluster exchange through global slice images and multicast copies (clusters of 4 with
-// room for the images), else direct shared->shared copies.
-template <int W, int CS, bool L2X>
+// room for the images), else direct shared->shared copies.  RC: MALA / MH / HMC with d <= 8
+// (padded to 16), whose chains live in the sampler threads' registers (RegChain8); else the
+// general per-chain code (Chain) or loglike mode.
+template <int W, int CS, bool L2X, bool RC>
 __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_constant__ StepArgs<float> a,
                                                                    const __grid_constant__ Tc2Weights E) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -484,7 +486,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
     const uint16_t peer_mask_e = static_cast<uint16_t>(((1u << CS) - 1u) & ~(1u << rank));
     const bool mala = a.mode == kModeMALA, hmc = a.mode == kModeHMC;
     // MALA / MH / HMC with d <= 8 (padded to 16) keep the chain in the sampler thread's registers
-    const bool fast = (mala || hmc || a.mode == kModeMH) && a.d <= RegChain8<float>::DB && dp == 16;
+    constexpr bool fast = RC;
     RegChain8<float> rc;
     if (fast && sampler && valid) rc.load(a, row, zbuf + r * 8, gbuf + r * 8, xibuf + r * 8);
     if (sampler && valid && !loglike) {
@@ -492,8 +494,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
         for (int h = 0; h < 2; ++h) a.st.steps_done[chn.aies_walker(row, h)] = 0;
       } else {
         a.st.steps_done[row] = 0;
-        if (a.mode == kModeHMC) chn.dwork_ptr(row)[0] = 0.0;
-        if (a.mode == kModeNUTS) chn.dwork_ptr(row)[0] = 1.0;
+        if (a.mode == kModeHMC) chn.dw(row)[0] = 0.0;
+        if (a.mode == kModeNUTS) chn.dw(row)[0] = 1.0;
       }
     }
     epi_sync();
@@ -570,7 +572,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
         else st_shared_v4(act_addr + sw128_off(r, j0 + 2), 0u, 0u, 0u, 0u);
         st_shared_v4(act_addr + sw128_off(r, j0 + 3), 0u, 0u, 0u, 0u);
       } else {
-        const float *zr = fast ? zbuf + r * 8 : a.st.ze + static_cast<size_t>(row) * a.st.ze_ld;
+        const float *zr = fast ? zbuf + r * 8 : a.st.ze + row_off(a.st.ze_ld, row, a.dp);
+        const int zes = fast ? 1 : row_es(a.st.ze_ld);
         const int nch = E.kb1 * 8;  // 16-byte chunks in the row; dp is a multiple of 16, so a
                                     // chunk (8 values) lies inside one segment
         for (int j = ch * (nch / kTc2EQ); j < (ch + 1) * (nch / kTc2EQ); ++j) {
@@ -579,7 +582,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int i = i0 + u;
-            const float zval = (valid && seg < 3 && i < a.d) ? zr[i] : 0.f;
+            const float zval = (valid && seg < 3 && i < a.d) ? zr[i * zes] : 0.f;
             const float hi = __bfloat162float(__float2bfloat16_rn(zval));
             v[u] = (seg == 1) ? (zval - hi) : hi;
           }
@@ -639,12 +642,13 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
               for (int i = 0; i < RegChain8<float>::DB; ++i)
                 if (i < a.d) rc.gp[i] = __uint_as_float(v0[i]) + __uint_as_float(v0[16 + i]);  // dp == 16
             } else if (rank == 0 && valid) {
-              float *gout = a.st.gle + static_cast<size_t>(row) * a.st.gle_ld;
+              float *gout = a.st.gle + row_off(a.st.gle_ld, row, a.dp);
+              const int ges = row_es(a.st.gle_ld);
               for (int i = 0; i < a.d; ++i) {
                 const int j2 = dp + i;
                 const float hi = __uint_as_float(v0[i]);
                 const float lo = __uint_as_float(j2 < 32 ? v0[j2] : v1[j2 - 32]);
-                gout[i] = hi + lo;
+                gout[i * ges] = hi + lo;
               }
             }
           }

@@ -1,7 +1,7 @@
-// k_tc2.cu -- instantiations and launch wrappers of the cluster tcgen05 chain-tile kernel.
+// k_tc2.cu -- launch wrappers and configuration of the cluster tcgen05 chain-tile kernel.
 #include <cstdlib>
 
-#include "launch.h"
+#include "tc2_launch.cuh"
 
 namespace bst {
 
@@ -10,36 +10,16 @@ int tc2_cluster_size_for(int n_rows, int width);
 namespace {
 constexpr int kSmemCap = 232448;
 constexpr int kNumSMs = 152;
-
-template <int W, int CS, bool L2X = false>
-cudaError_t launch_one(const StepArgs<float> &a, const Tc2Weights &w, cudaStream_t s) {
-  const int tiles = (a.n_rows + kTcRows - 1) / kTcRows;
-  if (tiles == 0) return cudaSuccess;
-  const size_t smem = tc2_smem_bytes(W, CS, w.n_stages, w.depth);
-  auto k = tc2_chain_kernel<W, CS, L2X>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  if (CS > 1) {
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
-    if (e != cudaSuccess) return e;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(tiles * CS, 1, 1);
-  cfg.blockDim = dim3(kTc2Threads, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CS;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, k, a, w);
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
-}
 }  // namespace
+
+// one translation unit per instantiation (k_tc2_w*.cu)
+BST_TC2_DECLARE(w512_c4x)
+BST_TC2_DECLARE(w512_c4)
+BST_TC2_DECLARE(w512_c2)
+BST_TC2_DECLARE(w512_c1)
+BST_TC2_DECLARE(w256_c4)
+BST_TC2_DECLARE(w256_c2)
+BST_TC2_DECLARE(w256_c1)
 
 int tc2_stages(int width, int cs, int depth) { return tc2_stages_for(width, cs, depth, kSmemCap); }
 
@@ -59,11 +39,9 @@ int tc2_max_active_clusters(int width, int cs, int depth) {
   int n = -1;
   const void *k = nullptr;
   if (width == 512)
-    k = cs == 4 ? (const void *)tc2_chain_kernel<512, 4, true>
-                : cs == 2 ? (const void *)tc2_chain_kernel<512, 2, false> : (const void *)tc2_chain_kernel<512, 1, false>;
+    k = cs == 4 ? tc2_kernel_w512_c4x(true) : cs == 2 ? tc2_kernel_w512_c2(true) : tc2_kernel_w512_c1(true);
   else
-    k = cs == 4 ? (const void *)tc2_chain_kernel<256, 4, false>
-                : cs == 2 ? (const void *)tc2_chain_kernel<256, 2, false> : (const void *)tc2_chain_kernel<256, 1, false>;
+    k = cs == 4 ? tc2_kernel_w256_c4(true) : cs == 2 ? tc2_kernel_w256_c2(true) : tc2_kernel_w256_c1(true);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(cfg.dynamicSmemBytes));
   if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) return -1;
   return n;
@@ -95,15 +73,18 @@ int tc2_cluster_size_for(int n_rows, int width) {
 }
 
 cudaError_t launch_emu_tc2(const StepArgs<float> &a, const Tc2Weights &w, cudaStream_t s) {
+  // register-resident chains: MALA / MH / HMC with d <= 8 (padded to 16)
+  const bool rc = (a.mode == kModeMALA || a.mode == kModeMH || a.mode == kModeHMC) && a.d <= RegChain8<float>::DB &&
+                  a.dp == 16;
   if (w.width == 512) {
-    if (w.cs == 4) return w.xchg ? launch_one<512, 4, true>(a, w, s) : launch_one<512, 4, false>(a, w, s);
-    if (w.cs == 2) return launch_one<512, 2>(a, w, s);
-    return launch_one<512, 1>(a, w, s);
+    if (w.cs == 4) return w.xchg ? tc2_launch_w512_c4x(a, w, rc, s) : tc2_launch_w512_c4(a, w, rc, s);
+    if (w.cs == 2) return tc2_launch_w512_c2(a, w, rc, s);
+    return tc2_launch_w512_c1(a, w, rc, s);
   }
   if (w.width == 256) {
-    if (w.cs == 4) return launch_one<256, 4>(a, w, s);
-    if (w.cs == 2) return launch_one<256, 2>(a, w, s);
-    return launch_one<256, 1>(a, w, s);
+    if (w.cs == 4) return tc2_launch_w256_c4(a, w, rc, s);
+    if (w.cs == 2) return tc2_launch_w256_c2(a, w, rc, s);
+    return tc2_launch_w256_c1(a, w, rc, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -1,0 +1,6 @@
+// k_tc2_w256_c4.cu -- the cluster tcgen05 chain-tile kernel for width 256, clusters of 4 CTAs.
+#include "tc2_launch.cuh"
+
+namespace bst {
+BST_TC2_VARIANT(w256_c4, 256, 4, false)
+}  // namespace bst

@@ -6,106 +6,256 @@
 //     post(row)  -> Metropolis / Hamiltonian / tree bookkeeping    (accept)
 // so one likelihood evaluation of a whole tile of chains is in flight at a
 // time.  Everything here is per chain, O(d) or O(d^2), and runs on the threads
-// that own the chains; the log-acceptance ratios and Hamiltonian energies are
-// formed in FP64 from the working-precision state.
+// that own the chains.  Every decision (Metropolis accept, NUTS slice, Delta_max
+// and U-turn tests) is the one of the FP64 expression formed from the working-
+// precision state.  With FP32 state it is first taken in FP32, with a bound on
+// the FP32 rounding error of each side; only a comparison closer than its bound
+// is evaluated in FP64 (FP64 arithmetic runs at a small fraction of the FP32
+// rate on this part).
 //
 // Target in whitened coordinates (paper Sec. 2.2, Eq. (2.12), Algorithm 1):
 //     x = mu + L z,   log pi_z(z) = logL(x) + log prior(x) + sum_i log L_ii.
 #pragma once
 
+#include <stddef.h>
+
 #include "common.cuh"
 
 namespace bst {
 
-// Per-chain vector loops over the state rows (global memory).  The rows are distinct, so the
-// parameters are restrict-qualified: the loads of one loop can all be in flight at once
-// instead of each waiting behind the previous iteration's stores.
+// A per-chain vector with its element stride S known at compile time: S = 1 for a state row,
+// S = kChainBlock for the chain-blocked buffers (a warp's consecutive chains read one line per
+// element; every offset within a vector is an immediate).
+template <typename T, int S>
+struct Vec {
+  T *p;
+  __device__ __forceinline__ T &operator[](int i) const { return p[i * S]; }
+};
 template <typename R>
-__device__ __forceinline__ void vcopy(R *__restrict__ dst, const R *__restrict__ src, int d) {
-#pragma unroll 4
-  for (int i = 0; i < d; ++i) dst[i] = src[i];
+using Row = Vec<R, 1>;
+template <typename R>
+using Blk = Vec<R, kChainBlock>;
+
+// The vector loops run in chunks of kVc elements: a chunk is loaded before any of it is stored,
+// so its loads are in flight together (the vectors may alias as far as the compiler knows).
+// Accessors are Vec or a thread's array.
+constexpr int kVc = 8;
+
+template <typename R, class A>
+__device__ __forceinline__ void vload(const A &v, int i0, int n, R (&t)[kVc]) {
+#pragma unroll
+  for (int u = 0; u < kVc; ++u)
+    if (u < n) t[u] = v[i0 + u];
 }
-template <typename R>
-__device__ __forceinline__ void vcopy2(R *__restrict__ d0, const R *__restrict__ s0, R *__restrict__ d1,
-                                       const R *__restrict__ s1, int d) {
-#pragma unroll 4
-  for (int i = 0; i < d; ++i) {
-    d0[i] = s0[i];
-    d1[i] = s1[i];
+template <typename R, class A>
+__device__ __forceinline__ void vstore(const A &v, int i0, int n, const R (&t)[kVc]) {
+#pragma unroll
+  for (int u = 0; u < kVc; ++u)
+    if (u < n) v[i0 + u] = t[u];
+}
+
+template <typename R, class D, class S>
+__device__ __forceinline__ void vcopy(D dst, S src, int d) {
+#pragma unroll 1
+  for (int i0 = 0; i0 < d; i0 += kVc) {
+    const int n = min(kVc, d - i0);
+    R t[kVc];
+    vload(src, i0, n, t);
+    vstore(dst, i0, n, t);
   }
 }
-// qh = qe + e/2 ge; zn = ze + e qh  (first half of a leapfrog step)
-template <typename R>
-__device__ __forceinline__ void half_kick_drift(R *__restrict__ qh, R *__restrict__ zn, const R *__restrict__ qe,
-                                                const R *__restrict__ ge, const R *__restrict__ zs, R e, int d) {
-#pragma unroll 4
-  for (int i = 0; i < d; ++i) {
-    qh[i] = qe[i] + R(0.5) * e * ge[i];
-    zn[i] = zs[i] + e * qh[i];
+template <typename R, class D0, class S0, class D1, class S1>
+__device__ __forceinline__ void vcopy2(D0 d0, S0 s0, D1 d1, S1 s1, int d) {
+#pragma unroll 1
+  for (int i0 = 0; i0 < d; i0 += kVc) {
+    const int n = min(kVc, d - i0);
+    R t0[kVc], t1[kVc];
+    vload(s0, i0, n, t0);
+    vload(s1, i0, n, t1);
+    vstore(d0, i0, n, t0);
+    vstore(d1, i0, n, t1);
   }
 }
-// second half: qend = qh + e/2 gn, zend = zn, gend = gn; returns |qend|^2 (FP64 sum)
-template <typename R>
-__device__ __forceinline__ double half_kick_store(R *__restrict__ zend, R *__restrict__ qend, R *__restrict__ gend,
-                                                  const R *__restrict__ qh, const R *__restrict__ zn,
-                                                  const R *__restrict__ gn, R e, int d) {
-  double qq = 0.0;
-#pragma unroll 4
-  for (int i = 0; i < d; ++i) {
-    const R qn = qh[i] + R(0.5) * e * gn[i];
-    qq += static_cast<double>(qn) * qn;
-    zend[i] = zn[i];
-    qend[i] = qn;
-    gend[i] = gn[i];
+// qh = qe + e/2 ge; zn = zs + e qh  (first half of a leapfrog step)
+template <typename R, class QH, class ZN, class QE, class GE, class ZS>
+__device__ __forceinline__ void half_kick_drift(QH qh, ZN zn, QE qe, GE ge, ZS zs, R e, int d) {
+#pragma unroll 1
+  for (int i0 = 0; i0 < d; i0 += kVc) {
+    const int n = min(kVc, d - i0);
+    R q[kVc], g[kVc], z[kVc];
+    vload(qe, i0, n, q);
+    vload(ge, i0, n, g);
+    vload(zs, i0, n, z);
+#pragma unroll
+    for (int u = 0; u < kVc; ++u) {
+      q[u] = q[u] + R(0.5) * e * g[u];
+      z[u] = z[u] + e * q[u];
+    }
+    vstore(qh, i0, n, q);
+    vstore(zn, i0, n, z);
+  }
+}
+// second half: qend = qh + e/2 gn, zend = zn, gend = gn; returns |qend|^2 summed in R
+template <typename R, class ZE, class QE, class GE, class QH, class ZN, class GN>
+__device__ __forceinline__ R half_kick_store(ZE zend, QE qend, GE gend, QH qh, ZN zn, GN gn, R e, int d) {
+  R qq = R(0);
+#pragma unroll 1
+  for (int i0 = 0; i0 < d; i0 += kVc) {
+    const int n = min(kVc, d - i0);
+    R q[kVc], z[kVc], g[kVc];
+    vload(qh, i0, n, q);
+    vload(zn, i0, n, z);
+    vload(gn, i0, n, g);
+#pragma unroll
+    for (int u = 0; u < kVc; ++u) {
+      q[u] = q[u] + R(0.5) * e * g[u];
+      if (u < n) qq += q[u] * q[u];
+    }
+    vstore(zend, i0, n, z);
+    vstore(qend, i0, n, q);
+    vstore(gend, i0, n, g);
   }
   return qq;
 }
-
-// zp = zc + a u + b v
-template <typename R>
-__device__ __forceinline__ void vaxpby(R *__restrict__ zp, const R *__restrict__ zc, R a, const R *__restrict__ u, R b,
-                                       const R *__restrict__ v, int d) {
-#pragma unroll 4
-  for (int i = 0; i < d; ++i) zp[i] = zc[i] + a * u[i] + b * v[i];
+// dst = zc + a u (+ b v)
+template <typename R, class D, class ZC, class U>
+__device__ __forceinline__ void vaxpy(D dst, ZC zc, R a, U u, int d) {
+#pragma unroll 1
+  for (int i0 = 0; i0 < d; i0 += kVc) {
+    const int n = min(kVc, d - i0);
+    R t[kVc], w[kVc];
+    vload(zc, i0, n, t);
+    vload(u, i0, n, w);
+#pragma unroll
+    for (int k = 0; k < kVc; ++k) t[k] = t[k] + a * w[k];
+    vstore(dst, i0, n, t);
+  }
+}
+template <typename R, class D, class ZC, class U, class V>
+__device__ __forceinline__ void vaxpby(D dst, ZC zc, R a, U u, R b, V v, int d) {
+#pragma unroll 1
+  for (int i0 = 0; i0 < d; i0 += kVc) {
+    const int n = min(kVc, d - i0);
+    R t[kVc], w[kVc], x[kVc];
+    vload(zc, i0, n, t);
+    vload(u, i0, n, w);
+    vload(v, i0, n, x);
+#pragma unroll
+    for (int k = 0; k < kVc; ++k) t[k] = t[k] + a * w[k] + b * x[k];
+    vstore(dst, i0, n, t);
+  }
 }
 // q1 += e/2 g1; z1 += e q1; zp = z1
-template <typename R>
-__device__ __forceinline__ void kick_drift_inplace(R *__restrict__ z1, R *__restrict__ q1, const R *__restrict__ g1,
-                                                   R *__restrict__ zp, R e, int d) {
-#pragma unroll 4
-  for (int i = 0; i < d; ++i) {
-    const R q = q1[i] + R(0.5) * e * g1[i];
-    const R z = z1[i] + e * q;
-    q1[i] = q;
-    z1[i] = z;
-    zp[i] = z;
+template <typename R, class Z1, class Q1, class G1, class ZP>
+__device__ __forceinline__ void kick_drift_inplace(Z1 z1, Q1 q1, G1 g1, ZP zp, R e, int d) {
+#pragma unroll 1
+  for (int i0 = 0; i0 < d; i0 += kVc) {
+    const int n = min(kVc, d - i0);
+    R q[kVc], g[kVc], z[kVc];
+    vload(q1, i0, n, q);
+    vload(g1, i0, n, g);
+    vload(z1, i0, n, z);
+#pragma unroll
+    for (int u = 0; u < kVc; ++u) {
+      q[u] = q[u] + R(0.5) * e * g[u];
+      z[u] = z[u] + e * q[u];
+    }
+    vstore(q1, i0, n, q);
+    vstore(z1, i0, n, z);
+    vstore(zp, i0, n, z);
   }
+}
+
+// No U-turn between two trajectory points (Hoffman & Gelman 2014, Eq. (9) with identity mass):
+// sum_i v (a_i - b_i) p_i >= 0 and sum_i v (a_i - b_i) q_i >= 0, as FP64 sums of the products of
+// the working-precision values.  FP32 state: FP32 sums first, with the bound (d + 4) 2^-23 times
+// the sum of |terms| on their error (twice the recursive-summation bound); a sum within its
+// bound of zero sends the test to the FP64 loop.
+template <typename R, class VA, class VB, class VP, class VQ>
+__device__ __forceinline__ bool no_uturn(VA za, VB zb, VP p, VQ q, double v, int d) {
+  if constexpr (sizeof(R) == 4) {
+    const float vf = static_cast<float>(v);
+    float s1 = 0.f, s2 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 1
+    for (int i0 = 0; i0 < d; i0 += kVc) {
+      const int n = min(kVc, d - i0);
+      float A[kVc], B[kVc], P[kVc], Q[kVc];
+      vload(za, i0, n, A);
+      vload(zb, i0, n, B);
+      vload(p, i0, n, P);
+      vload(q, i0, n, Q);
+#pragma unroll
+      for (int u = 0; u < kVc; ++u)
+        if (u < n) {
+          const float dz = vf * (A[u] - B[u]);
+          const float t1 = dz * P[u], t2 = dz * Q[u];
+          s1 += t1;
+          s2 += t2;
+          a1 += fabsf(t1);
+          a2 += fabsf(t2);
+        }
+    }
+    const float k = static_cast<float>(d + 4) * 0x1p-23f;
+    const float e1 = k * a1, e2 = k * a2;
+    if (s1 > e1 && s2 > e2) return true;
+    if (s1 < -e1 || s2 < -e2) return false;
+  }
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = 0; i < d; ++i) {
+    const double dz = v * (static_cast<double>(za[i]) - zb[i]);
+    s1 += dz * p[i];
+    s2 += dz * q[i];
+  }
+  return s1 >= 0.0 && s2 >= 0.0;
 }
 
 template <typename R>
 struct Chain {
+  // FP32 state: FP32-first decisions (see the header)
+  static constexpr bool kF32 = sizeof(R) == 4;
   const StepArgs<R> &a;
   __device__ Chain(const StepArgs<R> &args) : a(args) {}
 
-  __device__ R *z(int c) const { return a.st.z + static_cast<size_t>(c) * a.dp; }
-  __device__ R *g(int c) const { return a.st.g + static_cast<size_t>(c) * a.dp; }
-  __device__ R *ze(int r) const { return a.st.ze + static_cast<size_t>(r) * a.dp; }
-  __device__ R *gle(int r) const { return a.st.gle + static_cast<size_t>(r) * a.dp; }
-  __device__ R *wv(int c, int k) const {
-    return a.st.work + static_cast<size_t>(c) * a.st.work_stride + static_cast<size_t>(k) * a.dp;
+  // state rows (row-major), then the chain-blocked evaluation rows and work buffers
+  __device__ Row<R> z(int c) const { return Row<R>{a.st.z + static_cast<size_t>(c) * a.dp}; }
+  __device__ Row<R> g(int c) const { return Row<R>{a.st.g + static_cast<size_t>(c) * a.dp}; }
+  __device__ Blk<R> ze(int r) const { return Blk<R>{a.st.ze + blk_off(r, a.dp)}; }
+  __device__ Blk<R> gle(int r) const { return Blk<R>{a.st.gle + blk_off(r, a.dp)}; }
+  __device__ Blk<R> wv(int c, int k) const {
+    return Blk<R>{a.st.work + blk_off(c, kDworkOffsetVecs * kMaxD) + k * (kMaxD * kChainBlock)};
   }
+  __device__ Blk<double> dw(int c) const { return Blk<double>{a.st.dwork + blk_off(c, kDworkDoubles)}; }
 
   static __device__ double accept_prob(double la) {
     if (!(la == la)) return 0.0;
     return la >= 0.0 ? 1.0 : exp(la);
   }
+  // min(1, alpha) from an FP32 log alpha: the acceptance statistic, which only feeds step-size
+  // adaptation
+  static __device__ float accept_prob32(float la) { return la >= 0.f ? 1.f : (la == la ? expf(la) : 0.f); }
+
+  // x = mu + L z, log prior and its gradient: FP32 state TargetView::eval unrolled to 8 or
+  // kMaxD entries (constant-bank operands), FP64 state plain loops over d
+  // (TargetView::eval_loop).  (Each kernel has two call sites: log pi in post(), the x-space
+  // record in finish().)
+  template <bool XOUT, class VZ, class VG>
+  __device__ __forceinline__ double prior(VZ zv, R *x, VG gadd, bool grad) const {
+    if constexpr (kF32) {
+      if (a.d <= 8) return a.tgt.template eval<8, XOUT>(zv, x, gadd, grad);
+      return a.tgt.template eval<kMaxD, XOUT>(zv, x, gadd, grad);
+    } else {
+      return a.tgt.template eval_loop<XOUT>(zv, x, gadd, grad);
+    }
+  }
 
   // x-space sample record and Welford hand-off after a chain finishes an iteration.
   __device__ void record(int c, int row, int step) const {
+    const bool smp = a.samples && ((step + 1) % a.thin) == 0;
+    if (!smp && !a.welford_on) return;
     const int d = a.d;
     R x[kMaxD];
-    a.tgt.to_x_prior(z(c), x);
-    if (a.samples && ((step + 1) % a.thin) == 0) {
+    prior<true>(z(c), x, static_cast<R *>(nullptr), false);
+    if (smp) {
       R *dst = a.samples + (static_cast<size_t>(step / a.thin) * a.n_chains + c) * d;
       for (int i = 0; i < d; ++i) dst[i] = x[i];
     }
@@ -115,139 +265,224 @@ struct Chain {
     }
   }
 
-  // log pi_z and grad log pi_z at the evaluated point of row r (x written to xo).
-  __device__ double logpi_eval(int r, R *gout, R *xo) const {
-    const double lpr = a.tgt.to_x_prior(ze(r), xo);
-    const double lp = static_cast<double>(a.st.lle[r]) + lpr + a.tgt.logdet;
-    if (gout) {
-      vcopy(gout, static_cast<const R *>(gle(r)), a.d);
-      a.tgt.add_prior_grad(xo, gout);
-    }
-    return lp;
+  // log pi_z and, with grad, grad log pi_z (into the thread's array gout) at the evaluated
+  // point of row r
+  __device__ double logpi(int r, bool grad, R *gout) const {
+    if (grad) vcopy<R>(gout, gle(r), a.d);
+    const double lpr = prior<false>(ze(r), static_cast<R *>(nullptr), gout, grad);
+    return static_cast<double>(a.st.lle[r]) + lpr + a.tgt.logdet;
   }
 
-  __device__ void count(int c, bool accepted, double la, int evals) const {
-    a.st.acc_stat[c] += accept_prob(la);
+  __device__ void count(int c, bool accepted, double stat, int evals) const {
+    a.st.acc_stat[c] += stat;
     a.st.accepts[c] += accepted ? 1ull : 0ull;
     a.st.evals[c] += static_cast<unsigned long long>(evals);
   }
 
+  // Metropolis decision log u < la for MH / MALA / AIES.  FP64 state: la64() and log u in FP64.
+  // FP32 state: la32 with the bound err on its rounding error (relative to la64()) against
+  // logf(u) (u has 25 significant bits; 2^-20 |log u| covers logf), FP64 only inside the bound.
+  template <class F>
+  __device__ __forceinline__ bool metropolis(int c, uint32_t it, float la32, float err, F la64,
+                                             double &stat) const {
+    if constexpr (kF32) {
+      const float u32 = draw_uniform<float>(a.seed, static_cast<uint32_t>(c), it, kAccept, 0);
+      const float lu32 = logf(u32);
+      const float gap = la32 - lu32;
+      const float e2 = err + 0x1p-20f * fabsf(lu32) + 0x1p-22f;
+      stat = static_cast<double>(accept_prob32(la32));
+      if (gap > e2) return true;
+      if (gap < -e2) return false;
+      return log(static_cast<double>(u32)) < la64();
+    } else {
+      const double la = la64();
+      stat = accept_prob(la);
+      return log(draw_uniform<double>(a.seed, static_cast<uint32_t>(c), it, kAccept, 0)) < la;
+    }
+  }
+
   // ---------------------------------------------------------------- MH
   // Random walk in whitened units: z' = z + eps xi.
-  __device__ bool mh_pre(int c) const {
+  __device__ __noinline__ bool mh_pre(int c) const {
     if (a.st.steps_done[c] >= a.n_steps) return false;
     R xi[kMaxD];
     draw_normals<R>(a.seed, c, a.st.iter[c], kXi, a.d, xi);
-    const R e = static_cast<R>(a.eps);
-    R *zc = z(c), *zp = ze(c);
-    {
-      R *__restrict__ dst = zp;
-      const R *__restrict__ src = zc;
-#pragma unroll 4
-      for (int i = 0; i < a.d; ++i) dst[i] = src[i] + e * xi[i];
-    }
+    vaxpy<R>(ze(c), z(c), static_cast<R>(a.eps), xi, a.d);
     return true;
   }
-  __device__ bool mh_post(int c) const {
-    R x[kMaxD];
-    const double lpp = logpi_eval(c, nullptr, x);
+  __device__ __noinline__ bool mh_post(int c, double lpp) const {
     const uint32_t it = a.st.iter[c];
-    const double la = lpp - static_cast<double>(a.st.lp[c]);
-    const double u = draw_uniform<double>(a.seed, c, it, kAccept, 0);
-    const bool acc = log(u) < la;
+    const double lpc = static_cast<double>(a.st.lp[c]);
+    bool acc;
+    double stat = 0.0;
+    if (lpp == -INFINITY) {
+      acc = false;  // log alpha = -inf (or NaN): the FP64 comparison is false
+    } else {
+      const float lpp32 = static_cast<float>(lpp), lp32 = static_cast<float>(lpc);
+      const float la32 = lpp32 - lp32;
+      const float err = 0x1p-22f * (3.f * (fabsf(lpp32) + fabsf(lp32)) + 4.f);
+      acc = metropolis(c, it, la32, err, [&] { return lpp - lpc; }, stat);
+    }
     if (acc) {
-      vcopy(z(c), static_cast<const R *>(ze(c)), a.d);
+      vcopy<R>(z(c), ze(c), a.d);
       a.st.lp[c] = static_cast<R>(lpp);
     }
-    count(c, acc, la, 1);
-    finish(c, c);
+    count(c, acc, stat, 1);
     return true;
   }
 
   // ---------------------------------------------------------------- MALA
   // Eq. (2.3): z' = z + eps grad + sqrt(2 eps) xi; q(a|b) = N(a; b + eps grad(b), 2 eps I).
-  __device__ bool mala_pre(int c) const {
+  __device__ __noinline__ bool mala_pre(int c) const {
     if (a.st.steps_done[c] >= a.n_steps) return false;
     R xi[kMaxD];
     draw_normals<R>(a.seed, c, a.st.iter[c], kXi, a.d, xi);
     const R e = static_cast<R>(a.eps), s = static_cast<R>(sqrt(2.0 * a.eps));
-    vaxpby(ze(c), static_cast<const R *>(z(c)), e, static_cast<const R *>(g(c)), s, static_cast<const R *>(xi), a.d);
+    vaxpby<R>(ze(c), z(c), e, g(c), s, xi, a.d);
     return true;
   }
-  __device__ bool mala_post(int c) const {
-    R x[kMaxD], gp[kMaxD];
-    const double lpp = logpi_eval(c, gp, x);
+  __device__ __noinline__ bool mala_post(int c, double lpp, const R *gp) const {
+    const int d = a.d;
     const uint32_t it = a.st.iter[c];
-    R *zc = z(c), *gc = g(c), *zp = ze(c);
+    const Row<R> zc = z(c), gc = g(c);
+    const Blk<R> zp = ze(c);
     const double e = a.eps;
-    double fwd = 0.0, rev = 0.0;
-    for (int i = 0; i < a.d; ++i) {
-      const double f = static_cast<double>(zp[i]) - zc[i] - e * gc[i];
-      const double r = static_cast<double>(zc[i]) - zp[i] - e * gp[i];
-      fwd += f * f;
-      rev += r * r;
+    const double lpc = static_cast<double>(a.st.lp[c]);
+    // log alpha = log pi(z') - log pi(z) + log q(z|z') - log q(z'|z), in FP64
+    auto la64 = [&] {
+      double fwd = 0.0, rev = 0.0;
+      for (int i = 0; i < d; ++i) {
+        const double f = static_cast<double>(zp[i]) - zc[i] - e * gc[i];
+        const double r = static_cast<double>(zc[i]) - zp[i] - e * gp[i];
+        fwd += f * f;
+        rev += r * r;
+      }
+      return lpp - lpc + (fwd - rev) / (4.0 * e);
+    };
+    bool acc;
+    double stat = 0.0;
+    if (kF32 && lpp == -INFINITY) {
+      acc = false;
+    } else if constexpr (kF32) {
+      // FP32 log alpha and its rounding bound (the sums of squares, e*g, the differences and
+      // the final combination, with a factor 4 of margin)
+      const float ef = static_cast<float>(e);
+      float fwd = 0.f, rev = 0.f, fab = 0.f, rab = 0.f;
+#pragma unroll 1
+      for (int i0 = 0; i0 < d; i0 += kVc) {
+        const int n = min(kVc, d - i0);
+        float P[kVc], Z[kVc], G[kVc], GP[kVc];
+        vload(zp, i0, n, P);
+        vload(zc, i0, n, Z);
+        vload(gc, i0, n, G);
+        vload(gp, i0, n, GP);
+#pragma unroll
+        for (int u = 0; u < kVc; ++u)
+          if (u < n) {
+            const float eg = ef * G[u], egp = ef * GP[u];
+            const float f = P[u] - Z[u] - eg;
+            const float r = Z[u] - P[u] - egp;
+            const float fa = fabsf(P[u]) + fabsf(Z[u]) + fabsf(eg);
+            const float ra = fabsf(Z[u]) + fabsf(P[u]) + fabsf(egp);
+            fwd += f * f;
+            rev += r * r;
+            fab += fa * fa;
+            rab += ra * ra;
+          }
+      }
+      const float inv4e = 0.25f / ef;
+      const float lpp32 = static_cast<float>(lpp), lp32 = static_cast<float>(lpc);
+      const float la32 = (lpp32 - lp32) + (fwd - rev) * inv4e;
+      const float err = 0x1p-22f * (static_cast<float>(d + 10) * (fab + rab) * inv4e +
+                                    3.f * (fabsf(lpp32) + fabsf(lp32)) + 4.f);
+      acc = metropolis(c, it, la32, err, la64, stat);
+    } else {
+      acc = metropolis(c, it, 0.f, 0.f, la64, stat);
     }
-    // log q(z|z') - log q(z'|z)
-    const double la = lpp - static_cast<double>(a.st.lp[c]) + (fwd - rev) / (4.0 * e);
-    const double u = draw_uniform<double>(a.seed, c, it, kAccept, 0);
-    const bool acc = log(u) < la;
     if (acc) {
-      vcopy2(zc, static_cast<const R *>(zp), gc, static_cast<const R *>(gp), a.d);
+      vcopy2<R>(zc, zp, gc, gp, d);
       a.st.lp[c] = static_cast<R>(lpp);
     }
-    count(c, acc, la, 1);
-    finish(c, c);
+    count(c, acc, stat, 1);
     return true;
   }
 
   // ---------------------------------------------------------------- HMC
   // Identity mass in whitened space (Eqs. (2.7)-(2.8)); leapfrog; accept on H0 - H1.
   // work vectors: 0 z1, 1 q1, 2 g1; dwork: 0 leapfrogs done, 1 H0.
-  __device__ double *dwork_ptr(int c) const;
-
-  __device__ bool hmc_pre(int c) const {
+  __device__ __noinline__ bool hmc_pre(int c) const {
     if (a.st.steps_done[c] >= a.n_steps) return false;
-    double *dw = dwork_ptr(c);
-    R *z1 = wv(c, 0), *q1 = wv(c, 1), *g1 = wv(c, 2);
+    const Blk<double> dwc = dw(c);
+    const Blk<R> z1 = wv(c, 0), q1 = wv(c, 1), g1 = wv(c, 2);
     const R e = static_cast<R>(a.eps);
-    if (dw[0] == 0.0) {
+    if (dwc[0] == 0.0) {
       R q[kMaxD];
       draw_normals<R>(a.seed, c, a.st.iter[c], kXi, a.d, q);
-      double qq = 0.0;
+      double qq = 0.0;  // once per trajectory: FP64
       for (int i = 0; i < a.d; ++i) qq += static_cast<double>(q[i]) * q[i];
-      vcopy2(z1, static_cast<const R *>(z(c)), g1, static_cast<const R *>(g(c)), a.d);
-      vcopy(q1, static_cast<const R *>(q), a.d);
-      dw[1] = -static_cast<double>(a.st.lp[c]) + 0.5 * qq;
+      vcopy2<R>(z1, z(c), g1, g(c), a.d);
+      vcopy<R>(q1, q, a.d);
+      dwc[1] = -static_cast<double>(a.st.lp[c]) + 0.5 * qq;
     }
-    kick_drift_inplace(z1, q1, static_cast<const R *>(g1), ze(c), e, a.d);
+    kick_drift_inplace<R>(z1, q1, g1, ze(c), e, a.d);
     return true;
   }
-  __device__ bool hmc_post(int c) const {
-    double *dw = dwork_ptr(c);
-    R *z1 = wv(c, 0), *q1 = wv(c, 1), *g1 = wv(c, 2);
-    R x[kMaxD];
-    const double lp1 = logpi_eval(c, g1, x);
+  __device__ __noinline__ bool hmc_post(int c, double lp1, const R *gl) const {
+    const int d = a.d;
+    const Blk<double> dwc = dw(c);
+    const Blk<R> q1 = wv(c, 1), g1 = wv(c, 2);
     const R e = static_cast<R>(a.eps);
-    double qq = 0.0;
-    for (int i = 0; i < a.d; ++i) {
-      q1[i] += R(0.5) * e * g1[i];
-      qq += static_cast<double>(q1[i]) * q1[i];
+    // q1 += e/2 g (closing the leapfrog); g1 = g, the gradient at z1
+    R qq = R(0);
+#pragma unroll 1
+    for (int i0 = 0; i0 < d; i0 += kVc) {
+      const int n = min(kVc, d - i0);
+      R q[kVc], gg[kVc];
+      vload(q1, i0, n, q);
+      vload(gl, i0, n, gg);
+#pragma unroll
+      for (int u = 0; u < kVc; ++u) {
+        q[u] = q[u] + R(0.5) * e * gg[u];
+        if (u < n) qq += q[u] * q[u];
+      }
+      vstore(q1, i0, n, q);
+      vstore(g1, i0, n, gg);
     }
-    dw[0] += 1.0;
+    const double nlf = dwc[0] + 1.0;
     a.st.evals[c] += 1ull;
-    if (dw[0] < a.n_leapfrog) return false;
-    dw[0] = 0.0;
-    const double H1 = -lp1 + 0.5 * qq;
-    const double la = dw[1] - H1;
+    if (nlf < a.n_leapfrog) {
+      dwc[0] = nlf;
+      return false;
+    }
+    dwc[0] = 0.0;
+    const double h0 = dwc[1];
     const uint32_t it = a.st.iter[c];
     const double u = draw_uniform<double>(a.seed, c, it, kAccept, 0);
-    const bool acc = log(u) < la;
+    const double lu = log(u);  // once per trajectory
+    // H1 = -log pi(z1) + |q1|^2 / 2; FP32 state: |q1|^2 in FP32 within (d + 4) 2^-24 |q1|^2
+    // of the FP64 sum, which is formed only when la is that close to log u
+    double la = h0 - (-lp1 + 0.5 * static_cast<double>(qq));
+    bool acc;
+    if (kF32 && la - lu > (d + 4) * 0x1p-24 * static_cast<double>(qq) +
+                              0x1p-50 * (fabs(h0) + fabs(lp1) + static_cast<double>(qq) + fabs(lu))) {
+      acc = true;
+    } else if (kF32 && la - lu < -((d + 4) * 0x1p-24 * static_cast<double>(qq) +
+                                   0x1p-50 * (fabs(h0) + fabs(lp1) + static_cast<double>(qq) + fabs(lu)))) {
+      acc = false;
+    } else {
+      if (kF32) {
+        double q2 = 0.0;
+        for (int i = 0; i < d; ++i) q2 += static_cast<double>(q1[i]) * q1[i];
+        la = h0 - (-lp1 + 0.5 * q2);
+      }
+      acc = lu < la;
+    }
+    const double stat = kF32 ? static_cast<double>(accept_prob32(static_cast<float>(la))) : accept_prob(la);
     if (acc) {
-      vcopy2(z(c), static_cast<const R *>(z1), g(c), static_cast<const R *>(g1), a.d);
+      vcopy2<R>(z(c), wv(c, 0), g(c), g1, d);
       a.st.lp[c] = static_cast<R>(lp1);
     }
-    count(c, acc, la, 0);
-    finish(c, c);
+    count(c, acc, stat, 0);
     return true;
   }
 
@@ -258,166 +493,163 @@ struct Chain {
   // probability n''/(n'+n''), U-turn check of the merged span) when their right
   // sibling completes.  work vectors: 0 zm 1 qm 2 gm 3 zp 4 qp 5 gp 6 zs 7 gs
   // 8 qh, level i: 9+4i first z, 10+4i first q, 11+4i cand z, 12+4i cand g.
-  // dwork: 0 new-iteration flag, 1 log u, 2 H0, 3 n, 4 lp of selected,
+  // dwork: 0 new-iteration flag, 1 log u - H0, 2 H0, 3 n, 4 lp of selected,
   // 5 acceptance-stat sum, 6 j, 7 v, 8 m_sub, 9 leaves, 10 diverged, 11 moved,
   // 12+i cand lp, 22+i node n.
-  __device__ bool nuts_pre(int c) const {
+  __device__ __noinline__ bool nuts_pre(int c) const {
     if (a.st.steps_done[c] >= a.n_steps) return false;
-    double *dw = dwork_ptr(c);
+    const Blk<double> dwc = dw(c);
     const int d = a.d;
     const uint32_t it = a.st.iter[c];
-    if (dw[0] != 0.0) {
+    if (dwc[0] != 0.0) {
       R q0[kMaxD];
       draw_normals<R>(a.seed, c, it, kXi, d, q0);
-      double qq = 0.0;
+      double qq = 0.0;  // once per iteration: FP64
       for (int i = 0; i < d; ++i) qq += static_cast<double>(q0[i]) * q0[i];
       const double H0 = -static_cast<double>(a.st.lp[c]) + 0.5 * qq;
-      dw[2] = H0;
-      dw[1] = log(draw_uniform<double>(a.seed, c, it, kAccept, 0)) - H0;
-      R *zc = z(c), *gc = g(c);
-      R *zm = wv(c, 0), *qm = wv(c, 1), *gm = wv(c, 2), *zp = wv(c, 3), *qp = wv(c, 4),
-        *gp = wv(c, 5), *zs = wv(c, 6), *gs = wv(c, 7);
-      vcopy2(zm, static_cast<const R *>(zc), gm, static_cast<const R *>(gc), d);
-      vcopy2(zp, static_cast<const R *>(zc), gp, static_cast<const R *>(gc), d);
-      vcopy2(zs, static_cast<const R *>(zc), gs, static_cast<const R *>(gc), d);
-      vcopy2(qm, static_cast<const R *>(q0), qp, static_cast<const R *>(q0), d);
-      dw[3] = 1.0;
-      dw[4] = static_cast<double>(a.st.lp[c]);
-      dw[5] = 0.0;
-      dw[6] = 0.0;
-      dw[7] = draw_uniform<double>(a.seed, c, it, kNutsDir, 0) < 0.5 ? -1.0 : 1.0;
-      dw[8] = 0.0;
-      dw[9] = 0.0;
-      dw[10] = 0.0;
-      dw[11] = 0.0;
-      dw[0] = 0.0;
+      dwc[2] = H0;
+      dwc[1] = log(draw_uniform<double>(a.seed, c, it, kAccept, 0)) - H0;
+      const Row<R> zc = z(c), gc = g(c);
+      vcopy2<R>(wv(c, 0), zc, wv(c, 2), gc, d);
+      vcopy2<R>(wv(c, 3), zc, wv(c, 5), gc, d);
+      vcopy2<R>(wv(c, 6), zc, wv(c, 7), gc, d);
+      vcopy2<R>(wv(c, 1), q0, wv(c, 4), q0, d);
+      dwc[3] = 1.0;
+      dwc[4] = static_cast<double>(a.st.lp[c]);
+      dwc[5] = 0.0;
+      dwc[6] = 0.0;
+      dwc[7] = draw_uniform<double>(a.seed, c, it, kNutsDir, 0) < 0.5 ? -1.0 : 1.0;
+      dwc[8] = 0.0;
+      dwc[9] = 0.0;
+      dwc[10] = 0.0;
+      dwc[11] = 0.0;
+      dwc[0] = 0.0;
     }
-    const bool back = dw[7] < 0.0;
-    const R e = static_cast<R>(dw[7] * a.eps);
-    R *ze_ = wv(c, back ? 0 : 3), *qe = wv(c, back ? 1 : 4), *ge = wv(c, back ? 2 : 5);
-    R *qh = wv(c, 8), *zn = ze(c);
-    half_kick_drift(qh, zn, static_cast<const R *>(qe), static_cast<const R *>(ge), static_cast<const R *>(ze_), e, d);
+    const bool back = dwc[7] < 0.0;
+    const R e = static_cast<R>(dwc[7] * a.eps);
+    half_kick_drift<R>(wv(c, 8), ze(c), wv(c, back ? 1 : 4), wv(c, back ? 2 : 5), wv(c, back ? 0 : 3), e, d);
     return true;
   }
 
-  __device__ bool nuts_post(int c) const {
-    double *dw = dwork_ptr(c);
+  // returns whether the iteration ends (nuts_finish follows)
+  __device__ bool nuts_leaf(int c, double lpn, const R *gn) const {
+    const Blk<double> dwc = dw(c);
     const int d = a.d;
     const uint32_t it = a.st.iter[c];
-    const bool back = dw[7] < 0.0;
-    const double v = dw[7];
+    const double v = dwc[7];
+    const bool back = v < 0.0;
     const R e = static_cast<R>(v * a.eps);
-    R x[kMaxD], gn[kMaxD];
-    const double lpn = logpi_eval(c, gn, x);
-    R *qh = wv(c, 8), *zn = ze(c);
-    R *zend = wv(c, back ? 0 : 3), *qend = wv(c, back ? 1 : 4), *gend = wv(c, back ? 2 : 5);
-    const double qq = half_kick_store(zend, qend, gend, static_cast<const R *>(qh), static_cast<const R *>(zn),
-                                      static_cast<const R *>(gn), e, d);
+    const Blk<R> zend = wv(c, back ? 0 : 3), qend = wv(c, back ? 1 : 4), gend = wv(c, back ? 2 : 5);
+    const R qq = half_kick_store<R>(zend, qend, gend, wv(c, 8), ze(c), gn, e, d);
     a.st.evals[c] += 1ull;
-    dw[9] += 1.0;
-    const int leaf = static_cast<int>(dw[9]);
-    const double Hl = -lpn + 0.5 * qq;
-    dw[5] += accept_prob(dw[2] - Hl);
-    const double log_u = dw[1];
-    const double nl = (log_u <= -Hl) ? 1.0 : 0.0;
-    const bool sl = log_u < kNutsDeltaMax - Hl;
+    const double leaves = dwc[9] + 1.0;
+    dwc[9] = leaves;
+    const int leaf = static_cast<int>(leaves);
+    const double log_u = dwc[1];
+    // H of the new leaf; FP32 state: |q|^2 in FP32, within errH of the FP64 H
+    double Hl = -lpn + 0.5 * static_cast<double>(qq);
+    bool nlb, sl;
+    {
+      const double t = log_u + Hl;
+      const double errH = kF32 ? (d + 4) * 0x1p-24 * static_cast<double>(qq) +
+                                     0x1p-50 * (fabs(lpn) + static_cast<double>(qq) + fabs(log_u) + kNutsDeltaMax)
+                               : 0.0;
+      const bool sure = kF32 && (t < -errH || t > errH) && (t < kNutsDeltaMax - errH || t > kNutsDeltaMax + errH);
+      if (sure) {
+        nlb = t < 0.0;
+        sl = t < kNutsDeltaMax;
+      } else {
+        if (kF32) {
+          double q2 = 0.0;
+          for (int i = 0; i < d; ++i) q2 += static_cast<double>(qend[i]) * qend[i];
+          Hl = -lpn + 0.5 * q2;
+        }
+        nlb = log_u <= -Hl;
+        sl = log_u < kNutsDeltaMax - Hl;
+      }
+    }
+    dwc[5] = dwc[5] + (kF32 ? static_cast<double>(accept_prob32(static_cast<float>(dwc[2] - Hl)))
+                            : accept_prob(dwc[2] - Hl));
+    const double nl = nlb ? 1.0 : 0.0;
     if (!sl) {
-      dw[10] = 1.0;
-      return nuts_finish(c);
+      dwc[10] = 1.0;
+      return true;
     }
     // current node = the new leaf; first = leaf, candidate = leaf
     int first_src = -1, cand_src = -1;
     double node_n = nl;
-    const int m_sub = static_cast<int>(dw[8]);
-    const int j = static_cast<int>(dw[6]);
+    const int m_sub = static_cast<int>(dwc[8]);
+    const int j = static_cast<int>(dwc[6]);
     int lvl = 0;
     while ((m_sub >> lvl) & 1) {
       // merge pending left sibling at level lvl with the node
-      const double ln = dw[22 + lvl];
+      const double ln = dwc[22 + lvl];
       const double u = draw_uniform<double>(a.seed, c, it, kNutsSel,
                                             static_cast<uint32_t>(8 * (leaf - 1) + lvl + 1));
       const double ntot = ln + node_n;
       const bool take_right = ntot > 0.0 && u * ntot < node_n;
       if (!take_right) cand_src = lvl;
       // U-turn check of the merged span [left.first .. leaf]
-      const R *fz = wv(c, 9 + 4 * lvl), *fq = wv(c, 10 + 4 * lvl);
-      double s1 = 0.0, s2 = 0.0;
-      for (int i = 0; i < d; ++i) {
-        const double dz = v * (static_cast<double>(zend[i]) - fz[i]);
-        s1 += dz * fq[i];
-        s2 += dz * qend[i];
-      }
+      const bool ok = no_uturn<R>(zend, wv(c, 9 + 4 * lvl), wv(c, 10 + 4 * lvl), qend, v, d);
       first_src = lvl;
       node_n = ntot;
       ++lvl;
-      if (!(s1 >= 0.0 && s2 >= 0.0)) return nuts_finish(c);
+      if (!ok) return true;
     }
     // candidate vectors of the node
-    const R *cz = cand_src < 0 ? zend : wv(c, 11 + 4 * cand_src);
-    const R *cg = cand_src < 0 ? gend : wv(c, 12 + 4 * cand_src);
-    const double clp = cand_src < 0 ? lpn : dw[12 + cand_src];
+    const Blk<R> cz = cand_src < 0 ? zend : wv(c, 11 + 4 * cand_src);
+    const Blk<R> cg = cand_src < 0 ? gend : wv(c, 12 + 4 * cand_src);
+    const double clp = cand_src < 0 ? lpn : dwc[12 + cand_src];
     if (lvl == j) {
       // the subtree of this doubling is complete: progressive top-level selection
       const double ut = draw_uniform<double>(a.seed, c, it, kNutsTop, static_cast<uint32_t>(j));
-      if (ut * dw[3] < node_n) {
-        vcopy2(wv(c, 6), cz, wv(c, 7), cg, d);
-        dw[4] = clp;
-        dw[11] = 1.0;
+      if (ut * dwc[3] < node_n) {
+        vcopy2<R>(wv(c, 6), cz, wv(c, 7), cg, d);
+        dwc[4] = clp;
+        dwc[11] = 1.0;
       }
-      dw[3] += node_n;
-      const R *zm = wv(c, 0), *qm = wv(c, 1), *zp = wv(c, 3), *qp = wv(c, 4);
-      double s1 = 0.0, s2 = 0.0;
-      for (int i = 0; i < d; ++i) {
-        const double dz = static_cast<double>(zp[i]) - zm[i];
-        s1 += dz * qm[i];
-        s2 += dz * qp[i];
-      }
+      dwc[3] = dwc[3] + node_n;
+      const bool ok = no_uturn<R>(wv(c, 3), wv(c, 0), wv(c, 1), wv(c, 4), 1.0, d);
       const int jn = j + 1;
-      dw[6] = jn;
-      if (!(s1 >= 0.0 && s2 >= 0.0) || jn >= a.max_depth) return nuts_finish(c);
-      dw[7] = draw_uniform<double>(a.seed, c, it, kNutsDir, static_cast<uint32_t>(jn)) < 0.5 ? -1.0 : 1.0;
-      dw[8] = 0.0;
+      dwc[6] = jn;
+      if (!ok || jn >= a.max_depth) return true;
+      dwc[7] = draw_uniform<double>(a.seed, c, it, kNutsDir, static_cast<uint32_t>(jn)) < 0.5 ? -1.0 : 1.0;
+      dwc[8] = 0.0;
     } else {
       // park the node as the pending left sibling at level lvl
-      R *pz = wv(c, 9 + 4 * lvl), *pq = wv(c, 10 + 4 * lvl), *pcz = wv(c, 11 + 4 * lvl),
-        *pcg = wv(c, 12 + 4 * lvl);
-      const R *fz = first_src < 0 ? zend : wv(c, 9 + 4 * first_src);
-      const R *fq = first_src < 0 ? qend : wv(c, 10 + 4 * first_src);
-      if (first_src != lvl) vcopy2(pz, fz, pq, fq, d);
-      if (cand_src != lvl) vcopy2(pcz, cz, pcg, cg, d);
-      dw[12 + lvl] = clp;
-      dw[22 + lvl] = node_n;
-      dw[8] = m_sub + 1;
+      const Blk<R> fz = first_src < 0 ? zend : wv(c, 9 + 4 * first_src);
+      const Blk<R> fq = first_src < 0 ? qend : wv(c, 10 + 4 * first_src);
+      if (first_src != lvl) vcopy2<R>(wv(c, 9 + 4 * lvl), fz, wv(c, 10 + 4 * lvl), fq, d);
+      if (cand_src != lvl) vcopy2<R>(wv(c, 11 + 4 * lvl), cz, wv(c, 12 + 4 * lvl), cg, d);
+      dwc[12 + lvl] = clp;
+      dwc[22 + lvl] = node_n;
+      dwc[8] = m_sub + 1;
     }
     return false;
   }
 
   __device__ bool nuts_finish(int c) const {
-    double *dw = dwork_ptr(c);
-    R *zc = z(c), *gc = g(c), *zs = wv(c, 6), *gs = wv(c, 7);
-    for (int i = 0; i < a.d; ++i) {
-      zc[i] = zs[i];
-      gc[i] = gs[i];
-    }
-    a.st.lp[c] = static_cast<R>(dw[4]);
-    const double leaves = dw[9];
-    a.st.acc_stat[c] += leaves > 0.0 ? dw[5] / leaves : 0.0;
-    a.st.accepts[c] += dw[11] != 0.0 ? 1ull : 0ull;
-    a.st.divs[c] += dw[10] != 0.0 ? 1ull : 0ull;
-    dw[0] = 1.0;
-    finish(c, c);
+    const Blk<double> dwc = dw(c);
+    vcopy2<R>(z(c), wv(c, 6), g(c), wv(c, 7), a.d);
+    a.st.lp[c] = static_cast<R>(dwc[4]);
+    const double leaves = dwc[9];
+    a.st.acc_stat[c] += leaves > 0.0 ? dwc[5] / leaves : 0.0;
+    a.st.accepts[c] += dwc[11] != 0.0 ? 1ull : 0ull;
+    a.st.divs[c] += dwc[10] != 0.0 ? 1ull : 0ull;
+    dwc[0] = 1.0;
     return true;
   }
+  __device__ __noinline__ bool nuts_post(int c, double lpn, const R *gn) const { return nuts_leaf(c, lpn, gn) && nuts_finish(c); }
 
   // ---------------------------------------------------------------- AIES
   // Goodman-Weare stretch move (Sec. 2.3): y = z_j + Z (z_i - z_j),
   // Z = (u (a - 1) + 1)^2 / a (Eq. (2.15)); accept with min(1, Z^(d-1) pi(y)/pi(z_i)).
-  // Row r moves walker k = r % (W/2) of half h of ensemble r / (W/2).
+  // Row r moves walker k = r % (W/2) of half h of ensemble r / (W/2).  dwork 0: Z.
   __device__ int aies_walker(int r, int h) const {
     const int half = a.aies_walkers / 2;
     return (r / half) * a.aies_walkers + h * half + (r % half);
   }
-  __device__ bool aies_pre(int r, int h) const {
+  __device__ __noinline__ bool aies_pre(int r, int h) const {
     const int i = aies_walker(r, h);
     if (a.st.steps_done[i] >= a.n_steps) return false;
     const int half = a.aies_walkers / 2;
@@ -429,47 +661,65 @@ struct Chain {
     const int jw = base + jj;
     const double uz = draw_uniform<double>(a.seed, i, it, kAiesZ, 0);
     const double t = uz * (a.aies_a - 1.0) + 1.0;
-    const double Z = t * t / a.aies_a;
-    dwork_ptr(i)[0] = Z;
-    const R *__restrict__ zi = z(i);
-    const R *__restrict__ zj = z(jw);
-    R *__restrict__ y = ze(r);
+    const double Z = a.aies_a == 2.0 ? t * t * 0.5 : t * t / a.aies_a;  // (x 0.5 is exact)
+    dw(i)[0] = Z;
+    const Row<R> zi = z(i), zj = z(jw);
+    const Blk<R> y = ze(r);
     const R Zr = static_cast<R>(Z);
-#pragma unroll 4
-    for (int q = 0; q < a.d; ++q) y[q] = zj[q] + Zr * (zi[q] - zj[q]);
+#pragma unroll 1
+    for (int q0 = 0; q0 < a.d; q0 += kVc) {
+      R A[kVc], B[kVc];
+#pragma unroll
+      for (int u = 0; u < kVc; ++u)
+        if (q0 + u < a.d) {
+          A[u] = zi[q0 + u];
+          B[u] = zj[q0 + u];
+        }
+#pragma unroll
+      for (int u = 0; u < kVc; ++u)
+        if (q0 + u < a.d) y[q0 + u] = B[u] + Zr * (A[u] - B[u]);
+    }
     return true;
   }
-  __device__ bool aies_post(int r, int h) const {
+  __device__ __noinline__ bool aies_post(int r, int h, double lpy) const {
     const int i = aies_walker(r, h);
-    R x[kMaxD];
-    const double lpy = logpi_eval(r, nullptr, x);
-    const double Z = dwork_ptr(i)[0];
-    const double la = (a.d - 1) * log(Z) + lpy - static_cast<double>(a.st.lp[i]);
+    const double Z = dw(i)[0];
+    const double lpc = static_cast<double>(a.st.lp[i]);
     const uint32_t it = a.st.iter[i];
-    const double u = draw_uniform<double>(a.seed, i, it, kAccept, 0);
-    const bool acc = log(u) < la;
+    const int d = a.d;
+    auto la64 = [&] { return (d - 1) * log(Z) + lpy - lpc; };
+    bool acc;
+    double stat = 0.0;
+    if (kF32 && lpy == -INFINITY) {
+      acc = false;
+    } else if constexpr (kF32) {
+      // logf(Z) to 2 ulp plus 2^-24 from rounding Z, times (d - 1); the FP32 sums to a factor 4
+      const float lz = logf(static_cast<float>(Z));
+      const float lpy32 = static_cast<float>(lpy), lp32 = static_cast<float>(lpc);
+      const float la32 = static_cast<float>(d - 1) * lz + (lpy32 - lp32);
+      const float err = static_cast<float>(d - 1) * (0x1p-21f * fabsf(lz) + 0x1p-22f) +
+                        0x1p-21f * (fabsf(lpy32) + fabsf(lp32) + static_cast<float>(d - 1) * fabsf(lz));
+      acc = metropolis(i, it, la32, err, la64, stat);
+    } else {
+      acc = metropolis(i, it, 0.f, 0.f, la64, stat);
+    }
     if (acc) {
-      vcopy(z(i), static_cast<const R *>(ze(r)), a.d);
+      vcopy<R>(z(i), ze(r), d);
       a.st.lp[i] = static_cast<R>(lpy);
     }
-    count(i, acc, la, 1);
-    finish(i, r);
+    count(i, acc, stat, 1);
     return true;
   }
 
   // ---------------------------------------------------------------- batch modes
   __device__ bool refresh_pre(int c) const {
     if (a.st.steps_done[c] >= 1) return false;
-    R *zc = z(c), *zp = ze(c);
-    for (int i = 0; i < a.d; ++i) zp[i] = zc[i];
+    vcopy<R>(ze(c), z(c), a.d);
     return true;
   }
-  __device__ bool refresh_post(int c) const {
-    R x[kMaxD], gp[kMaxD];
-    const double lp = logpi_eval(c, gp, x);
+  __device__ bool refresh_post(int c, double lp, const R *gp) const {
     a.st.lp[c] = static_cast<R>(lp);
-    R *gc = g(c);
-    for (int i = 0; i < a.d; ++i) gc[i] = gp[i];
+    vcopy<R>(g(c), gp, a.d);
     a.st.steps_done[c] = 1;
     return true;
   }
@@ -483,7 +733,10 @@ struct Chain {
   }
 
   // Dispatch. pre returns whether the row needs an evaluation; post returns whether
-  // the chain of the row completed an iteration (for the covariance accumulator).
+  // the chain of the row completed an iteration (for the covariance accumulator).  The
+  // per-kernel bodies are separate functions (__noinline__), so that their temporaries do not
+  // add up in the caller; log pi (and its gradient) and the record are evaluated here, where
+  // the whitening factor is read from the kernel parameters as constant-bank operands.
   __device__ bool pre(int row, int h) const {
     switch (a.mode) {
       case kModeMH: return mh_pre(row);
@@ -496,15 +749,27 @@ struct Chain {
     }
   }
   __device__ bool post(int row, int h) const {
+    // log pi (and its gradient) at the evaluated point, then the kernel's decision, then the
+    // end of the chain's iteration if it completed one
+    R gp[kMaxD];
+    const bool grad = a.mode != kModeMH && a.mode != kModeAIES;
+    const double lp = logpi(row, grad, gp);
+    int c = row;
+    bool done;
     switch (a.mode) {
-      case kModeMH: return mh_post(row);
-      case kModeMALA: return mala_post(row);
-      case kModeHMC: return hmc_post(row);
-      case kModeNUTS: return nuts_post(row);
-      case kModeAIES: return aies_post(row, h);
-      case kModeRefresh: return refresh_post(row);
+      case kModeMH: done = mh_post(row, lp); break;
+      case kModeMALA: done = mala_post(row, lp, gp); break;
+      case kModeHMC: done = hmc_post(row, lp, gp); break;
+      case kModeNUTS: done = nuts_post(row, lp, gp); break;
+      case kModeAIES:
+        c = aies_walker(row, h);
+        done = aies_post(row, h, lp);
+        break;
+      case kModeRefresh: return refresh_post(row, lp, gp);
       default: return false;
     }
+    if (done) finish(c, row);
+    return done;
   }
 };
 
@@ -592,7 +857,7 @@ struct RegChain8 {
       if (i < a.d) {
         acc = a.tgt.mu[i];
 #pragma unroll
-        for (int j = 0; j <= i; ++j) acc += a.tgt.L[i * a.d + j] * v[j];
+        for (int j = 0; j <= i; ++j) acc += a.tgt.L[i * kMaxD + j] * v[j];
       }
       x[i] = acc;
     }
@@ -694,7 +959,7 @@ struct RegChain8 {
           R sg = 0;
 #pragma unroll
           for (int i = j; i < DB; ++i)
-            if (i < d && a.tgt.gauss[i]) sg -= a.tgt.L[i * a.d + j] * xp[i];
+            if (i < d && a.tgt.gauss[i]) sg -= a.tgt.L[i * kMaxD + j] * xp[i];
           g1[j] += sg;
         }
     }
@@ -789,7 +1054,7 @@ struct RegChain8 {
           R sg = 0;
 #pragma unroll
           for (int i = j; i < DB; ++i)
-            if (i < d && a.tgt.gauss[i]) sg -= a.tgt.L[i * a.d + j] * xp[i];
+            if (i < d && a.tgt.gauss[i]) sg -= a.tgt.L[i * kMaxD + j] * xp[i];
           gp[j] += sg;
         }
     }
@@ -850,13 +1115,5 @@ struct RegChain8 {
     return finish_step(a, c, row, acc, p, zp, gp, lpp, mala, defer);
   }
 };
-
-// Double-precision per-chain scratch lives after the R vectors of the work row.
-template <typename R>
-__device__ double *Chain<R>::dwork_ptr(int c) const {
-  char *base = reinterpret_cast<char *>(a.st.work + static_cast<size_t>(c) * a.st.work_stride);
-  const size_t vec_bytes = static_cast<size_t>(kDworkOffsetVecs) * a.dp * sizeof(R);
-  return reinterpret_cast<double *>(base + vec_bytes);
-}
 
 }  // namespace bst

@@ -201,3 +201,62 @@ def test_bf16_mala_two_cta_clusters(width):
     ref = O.run(m, "mala", z0, eps=0.4, n_steps=1, seed=11, trace=True)
     _check("bf16", s, ref, out, "mala", n)
     s.close()
+
+
+def _setup27(prec, n, width=256, depth=2, seed=11):
+    """d = 27: six box-bounded dimensions and 21 nuisance dimensions under N(0, 1) priors, with
+    a dense whitening factor (the general sampler code: chain vectors in global memory,
+    FP32-first decisions)."""
+    d = 27
+    e = emulator_case(d, width, depth, out_s=8.0, out_m=50.0)
+    mu, L = whitening(d, 3, scale=0.3)
+    lower, upper = np.full(d, -3.0), np.full(d, 3.0)
+    lower[6:], upper[6:] = -1e30, 1e30
+    gauss = np.array([0] * 6 + [1] * 21, dtype=np.int32)
+    theta0 = mu + np.random.default_rng(6).normal(size=(n, d)) @ L.T
+    theta0[:, :6] = np.clip(theta0[:, :6], -2.9, 2.9)
+    s = make_emulator_sampler(prec, e, n, mu=mu, L=L, lower=lower, upper=upper, theta0=theta0, gauss=gauss,
+                              seed=seed)
+    m = oracle_emulator_model(e, mu=mu, L=L, lower=lower, upper=upper, gauss=gauss, bf16=(prec == "bf16"))
+    z0 = np.linalg.solve(L, (theta0 - mu).T).T
+    return s, m, z0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("kernel,eps,extra", [("mh", 0.6, {}), ("mala", 0.6, {}), ("hmc", 0.5, {"n_leapfrog": 4}),
+                                              ("nuts", 0.5, {}), ("aies", 0.0, {"aies_walkers": 64})])
+def test_27d_one_step_parity(prec, kernel, eps, extra):
+    n = 256  # four AIES ensembles of 64 walkers
+    s, m, z0 = _setup27(prec, n)
+    out = torch.empty((1, n, 27), dtype=s.dtype, device="cuda")
+    kw = {k: v for k, v in extra.items() if k != "aies_walkers"}
+    s.step(kernel, 1, eps=eps, samples=out, **kw)
+    ref = O.run(m, kernel, z0, eps=eps, n_steps=1, seed=11, trace=True, **extra)
+    _check(prec, s, ref, out, kernel, n, margin=1e-2 if (prec == "bf16" and kernel == "hmc") else MARGIN)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("kernel,eps,extra", [("mala", 0.6, {}), ("nuts", 0.5, {})])
+def test_27d_trajectories_and_counters(prec, kernel, eps, extra):
+    """Five iterations of the general code at d = 27: samples, counters and the final state
+    against the oracle run step by step."""
+    n, steps = 256, 5
+    s, m, z0 = _setup27(prec, n)
+    out = torch.full((steps, n, 27), float("nan"), dtype=s.dtype, device="cuda")
+    s.step(kernel, steps, eps=eps, samples=out, **extra)
+    ref = O.run(m, kernel, z0, eps=eps, n_steps=steps, seed=11, trace=True, **extra)
+    x = out.double().cpu().numpy()
+    assert np.isfinite(x).all()
+    same = np.all(np.abs(x - ref["samples"]) < 2e-3, axis=(0, 2))
+    assert same.mean() >= 0.9, same.mean()
+    st = s.get_state()
+    c = s.counters()
+    assert np.all(st["iter"] == steps)
+    assert np.array_equal(c["accepts"][same], ref["accepts"][same])
+    # a U-turn test that flips under BF16 rounding adds a doubling whose candidate need not be
+    # taken: the same samples can come with a different leapfrog count
+    assert np.mean(c["evals"][same] == ref["evals"][same]) >= 0.95
+    mu, L = s.whitening()
+    assert np.max(np.abs(mu + st["z"] @ L.T - x[-1])) < 1e-4
+    s.close()
