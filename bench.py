@@ -233,7 +233,9 @@ def extras(torch, device, seed, eps_mala, K):
     # NUTS and AIES on the 27-D nuisance-extended target, 16384 chains
     s = _emulator_target(27, 16384, "bf16", seed + 11, device, nuis=21)
     eps_n = dual_average_eps(s, "nuts", 0.3, n_iter=6, chunk=4, target=0.8)
-    it = 40
+    # one launch of 200 iterations per chain: a 128-chain tile runs until its slowest chain has
+    # finished (trees differ in size), so short launches leave rows idle at the end
+    it = 200
     x = torch.empty((it, 16384, 27), dtype=torch.float32, device="cuda")
     c0 = s.counters()["evals"].sum()
     t = time_steps(torch, s, "nuts", it, eps_n, samples=x)

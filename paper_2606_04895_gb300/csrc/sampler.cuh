@@ -509,11 +509,24 @@ struct Chain {
       const double H0 = -static_cast<double>(a.st.lp[c]) + 0.5 * qq;
       dwc[2] = H0;
       dwc[1] = log(draw_uniform<double>(a.seed, c, it, kAccept, 0)) - H0;
+      // both trajectory ends and the selected point start at (z, q0, g): one pass over z, g
       const Row<R> zc = z(c), gc = g(c);
-      vcopy2<R>(wv(c, 0), zc, wv(c, 2), gc, d);
-      vcopy2<R>(wv(c, 3), zc, wv(c, 5), gc, d);
-      vcopy2<R>(wv(c, 6), zc, wv(c, 7), gc, d);
-      vcopy2<R>(wv(c, 1), q0, wv(c, 4), q0, d);
+#pragma unroll 1
+      for (int i0 = 0; i0 < d; i0 += kVc) {
+        const int n = min(kVc, d - i0);
+        R tz[kVc], tg[kVc], tq[kVc];
+        vload(zc, i0, n, tz);
+        vload(gc, i0, n, tg);
+        vload(q0, i0, n, tq);
+        vstore(wv(c, 0), i0, n, tz);
+        vstore(wv(c, 3), i0, n, tz);
+        vstore(wv(c, 6), i0, n, tz);
+        vstore(wv(c, 2), i0, n, tg);
+        vstore(wv(c, 5), i0, n, tg);
+        vstore(wv(c, 7), i0, n, tg);
+        vstore(wv(c, 1), i0, n, tq);
+        vstore(wv(c, 4), i0, n, tq);
+      }
       dwc[3] = 1.0;
       dwc[4] = static_cast<double>(a.st.lp[c]);
       dwc[5] = 0.0;
@@ -535,17 +548,19 @@ struct Chain {
   __device__ bool nuts_leaf(int c, double lpn, const R *gn) const {
     const Blk<double> dwc = dw(c);
     const int d = a.d;
+    // the chain's scalars in one batch of loads, ahead of the leaf's vector stores
     const uint32_t it = a.st.iter[c];
-    const double v = dwc[7];
+    const unsigned long long n_ev = a.st.evals[c];
+    const double v = dwc[7], leaves = dwc[9] + 1.0, log_u = dwc[1], H0 = dwc[2], stat0 = dwc[5];
+    const int m_sub = static_cast<int>(dwc[8]);
+    const int j = static_cast<int>(dwc[6]);
     const bool back = v < 0.0;
     const R e = static_cast<R>(v * a.eps);
     const Blk<R> zend = wv(c, back ? 0 : 3), qend = wv(c, back ? 1 : 4), gend = wv(c, back ? 2 : 5);
     const R qq = half_kick_store<R>(zend, qend, gend, wv(c, 8), ze(c), gn, e, d);
-    a.st.evals[c] += 1ull;
-    const double leaves = dwc[9] + 1.0;
+    a.st.evals[c] = n_ev + 1ull;
     dwc[9] = leaves;
     const int leaf = static_cast<int>(leaves);
-    const double log_u = dwc[1];
     // H of the new leaf; FP32 state: |q|^2 in FP32, within errH of the FP64 H
     double Hl = -lpn + 0.5 * static_cast<double>(qq);
     bool nlb, sl;
@@ -568,8 +583,7 @@ struct Chain {
         sl = log_u < kNutsDeltaMax - Hl;
       }
     }
-    dwc[5] = dwc[5] + (kF32 ? static_cast<double>(accept_prob32(static_cast<float>(dwc[2] - Hl)))
-                            : accept_prob(dwc[2] - Hl));
+    dwc[5] = stat0 + (kF32 ? static_cast<double>(accept_prob32(static_cast<float>(H0 - Hl))) : accept_prob(H0 - Hl));
     const double nl = nlb ? 1.0 : 0.0;
     if (!sl) {
       dwc[10] = 1.0;
@@ -578,8 +592,6 @@ struct Chain {
     // current node = the new leaf; first = leaf, candidate = leaf
     int first_src = -1, cand_src = -1;
     double node_n = nl;
-    const int m_sub = static_cast<int>(dwc[8]);
-    const int j = static_cast<int>(dwc[6]);
     int lvl = 0;
     while ((m_sub >> lvl) & 1) {
       // merge pending left sibling at level lvl with the node
