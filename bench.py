@@ -295,7 +295,7 @@ def extras(torch, device, seed, eps_mala, K):
     return out
 
 
-def sweep(torch, device):
+def sweep(torch, device, points=None):
     """Throughput over chains x width x depth x dims x kernel x precision (reduced grid)."""
     pts = []
     for prec in ("bf16", "fp32", "fp64"):
@@ -316,15 +316,31 @@ def sweep(torch, device):
         pts.append(dict(prec="bf16", n=16384, d=d, width=512, depth=4, kernel="mala"))
     for k in ("mh", "hmc"):
         pts.append(dict(prec="bf16", n=16384, d=8, width=512, depth=4, kernel=k))
+    # the general sampler code: 27-D target with 21 N(0, 1) nuisance dimensions, every kernel
+    for k in ("mala", "mh", "hmc", "nuts", "aies"):
+        pts.append(dict(prec="bf16", n=16384, d=27, width=512, depth=4, kernel=k, nuis=21))
+    pts.append(dict(prec="fp32", n=16384, d=27, width=512, depth=4, kernel="mala", nuis=21))
+    if points:
+        # "key=value,key=value": keep the points that match every pair
+        want = dict(kv.split("=", 1) for kv in points.split(","))
+        pts = [p for p in pts if all(str(p.get(k)) == v for k, v in want.items())]
     burst, _, _, kind = peaks()
+    eps_of = {"mala": 0.3, "mh": 0.2, "hmc": 0.1, "nuts": 0.3, "aies": 0.0}
     for p in pts:
-        s = _emulator_target(p["d"], p["n"], p["prec"], 5, device, width=p["width"], depth=p["depth"])
+        s = _emulator_target(p["d"], p["n"], p["prec"], 5, device, width=p["width"], depth=p["depth"],
+                             nuis=p.get("nuis", 0))
         steps = max(3, min(200, int(2e11 / (p["n"] * 4 * n_params(p["d"], p["depth"], p["width"])))))
+        # NUTS: one launch of 200 iterations (a tile runs until its slowest chain is done);
+        # AIES: 100 ensemble updates
+        steps = {"nuts": 200, "aies": 100}.get(p["kernel"], steps)
         kw = {"n_leapfrog": 10} if p["kernel"] == "hmc" else {}
-        s.step(p["kernel"], 2, eps=0.1, stats=False, **kw)
-        t = time_steps(torch, s, p["kernel"], steps, 0.1, **kw)
-        evals = steps * p["n"] * (10 if p["kernel"] == "hmc" else 1)
-        fl = (2 if p["kernel"] == "mh" else 4) * (n_params(p["d"], p["depth"], p["width"]) - 1) * evals / t
+        eps = eps_of[p["kernel"]] if "nuis" in p else 0.1
+        s.step(p["kernel"], 2, eps=eps, stats=False, **kw)
+        c0 = int(s.counters()["evals"].sum())
+        t = time_steps(torch, s, p["kernel"], steps, eps, **kw)
+        evals = int(s.counters()["evals"].sum()) - c0
+        fwd_only = p["kernel"] in ("mh", "aies")
+        fl = (2 if fwd_only else 4) * (n_params(p["d"], p["depth"], p["width"]) - 1) * evals / t
         row = dict(p, evals_per_s=evals / t, tflops=fl / 1e12,
                    frac_bf16_peak=fl / 1e12 / burst if p["prec"] == "bf16" else None, steps=steps)
         print(json.dumps(row), flush=True)
@@ -340,6 +356,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="print one JSON line per point of the throughput grid")
+    ap.add_argument("--points", default=None, help="with --sweep: key=value[,key=value] filter, e.g. d=27")
     ap.add_argument("--quick", action="store_true",
                     help="skip the burn-in (fixed whitening and step size): three launches in total, "
                          "for profiler captures")
@@ -355,7 +372,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     if args.sweep:
-        sweep(torch, local)
+        sweep(torch, local, args.points)
         return 0
     dist = None
     global DIST
