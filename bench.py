@@ -43,6 +43,29 @@ def peaks():
     return 1900.0, 1700.0, 6800.0, "fallback"
 
 
+# DRAM traffic of the timed step-kernel launch (4096 chains, 8-512x4-1, MALA): one-pass ncu
+# captures (dram__bytes_read.sum + dram__bytes_write.sum) of K = 20 and K = 5000 launches,
+# 4.05 + 0.73 MB and 30.04 + 615.50 MB (profiles/tc2_chain_kernel_mala_4096x8_w512_cs4.md),
+# i.e. a fixed 2.2 MB plus 128.7 KB per MALA iteration (the x-space sample write, 131 KB per
+# iteration).  Valid for the kernel sources they were taken on; None once those change.
+TRAFFIC_SOURCES = ['include/bst.h', 'paper_2606_04895_gb300/csrc/common.cuh', 'paper_2606_04895_gb300/csrc/engine_tc.cuh', 'paper_2606_04895_gb300/csrc/engine_tc2.cuh', 'paper_2606_04895_gb300/csrc/sampler.cuh', 'paper_2606_04895_gb300/csrc/tc2_launch.cuh', 'paper_2606_04895_gb300/csrc/launch.h', 'paper_2606_04895_gb300/csrc/k_tc2_w512_c4x.cu']
+TRAFFIC_SOURCES_SHA256 = "296cbd61127eda3e"
+TRAFFIC_K, TRAFFIC_BYTES = (20, 5000), (4.05e6 + 0.73267e6, 30.04e6 + 615.50e6)
+
+
+def step_kernel_traffic(k):
+    """DRAM bytes of a k-iteration launch of the step kernel, or None (sources changed)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != TRAFFIC_SOURCES_SHA256:
+        return None
+    (k0, k1), (b0, b1) = TRAFFIC_K, TRAFFIC_BYTES
+    return b0 + (b1 - b0) * (k - k0) / (k1 - k0)
+
+
 def n_params(d, depth, width):
     return d * width + width + (depth - 1) * (width * width + width) + width + 1
 
@@ -429,7 +452,8 @@ def main():
         burst, sustained, hbm, kind = peaks()
         achieved = flops / dts[0] / 1e12
         out["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": burst, "unit": "TFLOP/s",
-                           "frac": achieved / burst, "traffic": None,
+                           "frac": achieved / burst, "traffic": step_kernel_traffic(K),
+                           "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                            "peak_kind": f"{kind} bf16 dense burst (cuBLAS)",
                            "algorithmic": "4P flop per logL+grad eval (forward 2P + adjoint 2P), P = 791040"}
         out["clocks"] = clk.summary()
