@@ -237,7 +237,8 @@ def test_27d_one_step_parity(prec, kernel, eps, extra):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-@pytest.mark.parametrize("kernel,eps,extra", [("mala", 0.6, {}), ("nuts", 0.5, {})])
+@pytest.mark.parametrize("kernel,eps,extra", [("mala", 0.6, {}), ("nuts", 0.5, {}), ("hmc", 0.4, {"n_leapfrog": 3}),
+                                              ("aies", 0.0, {})])
 def test_27d_trajectories_and_counters(prec, kernel, eps, extra):
     """Five iterations of the general code at d = 27: samples, counters and the final state
     against the oracle run step by step."""
@@ -259,4 +260,21 @@ def test_27d_trajectories_and_counters(prec, kernel, eps, extra):
     assert np.mean(c["evals"][same] == ref["evals"][same]) >= 0.95
     mu, L = s.whitening()
     assert np.max(np.abs(mu + st["z"] @ L.T - x[-1])) < 1e-4
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("kernel,eps,extra", [("mala", 0.6, {}), ("nuts", 0.5, {}), ("mh", 0.6, {})])
+def test_27d_ragged_chain_count(prec, kernel, eps, extra):
+    """200 chains: the last block of 32 chains of the chain-blocked buffers and the last
+    128-chain tile are partly empty."""
+    n = 200
+    s, m, z0 = _setup27(prec, n)
+    out = torch.empty((2, n, 27), dtype=s.dtype, device="cuda")
+    s.step(kernel, 2, eps=eps, samples=out, **extra)
+    ref = O.run(m, kernel, z0, eps=eps, n_steps=2, seed=11, trace=True, **extra)
+    x = out.double().cpu().numpy()
+    same = np.all(np.abs(x - ref["samples"]) < 2e-3, axis=(0, 2))
+    assert same.mean() >= 0.9, same.mean()
+    assert np.all(s.get_state()["iter"] == 2)
     s.close()
