@@ -45,12 +45,12 @@ def peaks():
 
 # DRAM traffic of the timed step-kernel launch (4096 chains, 8-512x4-1, MALA): one-pass ncu
 # captures (dram__bytes_read.sum + dram__bytes_write.sum) of K = 20 and K = 5000 launches,
-# 4.05 + 0.73 MB and 30.04 + 615.50 MB (profiles/tc2_chain_kernel_mala_4096x8_w512_cs4.md),
-# i.e. a fixed 2.2 MB plus 128.7 KB per MALA iteration (the x-space sample write, 131 KB per
+# 4.05 + 0.67 MB and 28.99 + 615.07 MB (profiles/tc2_chain_kernel_mala_4096x8_w512_cs4.md),
+# i.e. a fixed 2.3 MB plus 128.4 KB per MALA iteration (the x-space sample write, 131 KB per
 # iteration).  Valid for the kernel sources they were taken on; None once those change.
 TRAFFIC_SOURCES = ['include/bst.h', 'paper_2606_04895_gb300/csrc/common.cuh', 'paper_2606_04895_gb300/csrc/engine_tc.cuh', 'paper_2606_04895_gb300/csrc/engine_tc2.cuh', 'paper_2606_04895_gb300/csrc/sampler.cuh', 'paper_2606_04895_gb300/csrc/tc2_launch.cuh', 'paper_2606_04895_gb300/csrc/launch.h', 'paper_2606_04895_gb300/csrc/k_tc2_w512_c4x.cu']
-TRAFFIC_SOURCES_SHA256 = "296cbd61127eda3e"
-TRAFFIC_K, TRAFFIC_BYTES = (20, 5000), (4.05e6 + 0.73267e6, 30.04e6 + 615.50e6)
+TRAFFIC_SOURCES_SHA256 = "5911d9bb2155d67e"
+TRAFFIC_K, TRAFFIC_BYTES = (20, 5000), (4.05e6 + 0.66586e6, 28.99e6 + 615.07e6)
 
 
 def step_kernel_traffic(k):

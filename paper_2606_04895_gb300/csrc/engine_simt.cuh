@@ -371,15 +371,29 @@ __device__ void welford_tile(const StepArgs<R> &a, int row0, int nrows, const in
 
 // ------------------------------------------------------------------------------------------
 // Chain-tile kernel: T rows per CTA, thread t < T owns row row0 + t.
+// The per-chain sampler code as separate functions: inlined, its registers raised the
+// kernel's allocation (255 with spills) and slowed the emulator GEMM loop by ~15 %.
+template <typename R>
+__device__ __noinline__ bool simt_chain_pre(const StepArgs<R> &a, int row, int h) {
+  return Chain<R, false>(a).pre(row, h);
+}
+template <typename R>
+__device__ __noinline__ bool simt_chain_post(const StepArgs<R> &a, int row, int h) {
+  return Chain<R, false>(a).post(row, h);
+}
+
+// Launched with kSimtThreads threads.  Registers capped at 128: the emulator GEMM loop ran
+// fastest there (FP32 MALA, 4096 chains, 8-512x4-1: 711 us per round at 128, 739 at 168,
+// 898 at the 255 the compiler picks by itself).
 template <typename R, int T, class Engine, class Weights>
-__global__ void __launch_bounds__(kSimtThreads, 1)
+__global__ void __maxnreg__(128)
 simt_chain_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ Weights W) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int mask[T];
   const int row0 = blockIdx.x * T;
   const int tid = threadIdx.x;
   const bool owner = tid < T && row0 + tid < a.n_rows;
-  Chain<R> ch(a);
+  Chain<R, false> ch(a);
   const int row = row0 + tid;
   if (a.mode == kModeLoglike) {
     // ze / lle / gle point at the caller's theta, logL and gradient rows
@@ -399,11 +413,11 @@ simt_chain_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__
   __syncthreads();
   for (int ev = 0;; ++ev) {
     const int h = ev & 1;
-    const bool need = owner && ch.pre(row, h);
+    const bool need = owner && simt_chain_pre(a, row, h);
     if (!__syncthreads_or(need)) break;
     Engine::eval(W, a, row0, a.need_grad != 0, smem);
     bool done = false;
-    if (need) done = ch.post(row, h);
+    if (need) done = simt_chain_post(a, row, h);
     if (tid < T) mask[tid] = done ? 1 : 0;
     __syncthreads();
     if (a.welford_on && __syncthreads_or(done)) {

@@ -209,7 +209,9 @@ __device__ __forceinline__ bool no_uturn(VA za, VB zb, VP p, VQ q, double v, int
   return s1 >= 0.0 && s2 >= 0.0;
 }
 
-template <typename R>
+// U: unrolled whitening / prior for FP32 state (the tcgen05 kernel); the CUDA-core kernel,
+// whose time is all in its emulator GEMMs, takes the loop form, which needs far fewer registers.
+template <typename R, bool U = true>
 struct Chain {
   // FP32 state: FP32-first decisions (see the header)
   static constexpr bool kF32 = sizeof(R) == 4;
@@ -240,7 +242,7 @@ struct Chain {
   // record in finish().)
   template <bool XOUT, class VZ, class VG>
   __device__ __forceinline__ double prior(VZ zv, R *x, VG gadd, bool grad) const {
-    if constexpr (kF32) {
+    if constexpr (kF32 && U) {
       if (a.d <= 8) return a.tgt.template eval<8, XOUT>(zv, x, gadd, grad);
       return a.tgt.template eval<kMaxD, XOUT>(zv, x, gadd, grad);
     } else {
