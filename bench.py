@@ -256,15 +256,16 @@ def extras(torch, device, seed, eps_mala, K):
     # NUTS and AIES on the 27-D nuisance-extended target, 16384 chains
     s = _emulator_target(27, 16384, "bf16", seed + 11, device, nuis=21)
     eps_n = dual_average_eps(s, "nuts", 0.3, n_iter=6, chunk=4, target=0.8)
-    # one launch of 200 iterations per chain: a 128-chain tile runs until its slowest chain has
-    # finished (trees differ in size), so short launches leave rows idle at the end
-    it = 200
+    # one launch of 1000 iterations per chain: a 128-chain tile runs until its slowest chain has
+    # finished (trees differ in size), so short launches leave rows idle at the end (the idle
+    # tail grows like the square root of the iterations, the work like the iterations)
+    it = 1000
     x = torch.empty((it, 16384, 27), dtype=torch.float32, device="cuda")
     c0 = s.counters()["evals"].sum()
     t = time_steps(torch, s, "nuts", it, eps_n, samples=x)
     ev = s.counters()["evals"].sum() - c0
     ess = s.ess(x)
-    out["nuts_27d"] = {"chains": 16384, "iterations": it, "eps": eps_n, "evals_per_s": ev / t,
+    out["nuts_27d"] = {"chains": 16384, "iterations_per_launch": it, "eps": eps_n, "evals_per_s": ev / t,
                        "leapfrogs_per_iter": ev / (16384 * it), "min_ess_per_s": float(ess.min()) / t,
                        "tflops": 4.0 * P27 * ev / t / 1e12}
     s.close()
