@@ -47,20 +47,28 @@ def peaks():
 # captures (dram__bytes_read.sum + dram__bytes_write.sum) of K = 20 and K = 5000 launches,
 # 4.05 + 0.67 MB and 28.99 + 615.07 MB (profiles/tc2_chain_kernel_mala_4096x8_w512_cs4.md),
 # i.e. a fixed 2.3 MB plus 128.4 KB per MALA iteration (the x-space sample write, 131 KB per
-# iteration).  Valid for the kernel sources they were taken on; None once those change.
+# iteration).  Valid for the kernel code they were taken on (sources without comments);
+# None once that changes.
 TRAFFIC_SOURCES = ['include/bst.h', 'paper_2606_04895_gb300/csrc/common.cuh', 'paper_2606_04895_gb300/csrc/engine_tc.cuh', 'paper_2606_04895_gb300/csrc/engine_tc2.cuh', 'paper_2606_04895_gb300/csrc/sampler.cuh', 'paper_2606_04895_gb300/csrc/tc2_launch.cuh', 'paper_2606_04895_gb300/csrc/launch.h', 'paper_2606_04895_gb300/csrc/k_tc2_w512_c4x.cu']
-TRAFFIC_SOURCES_SHA256 = "5911d9bb2155d67e"
+TRAFFIC_SOURCES_SHA256 = "0e21f29cc60e7971"
 TRAFFIC_K, TRAFFIC_BYTES = (20, 5000), (4.05e6 + 0.66586e6, 28.99e6 + 615.07e6)
+
+
+def kernel_sources_digest():
+    """Hash of the step kernel's sources with comments and whitespace removed (code only)."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f)) as fh:
+            code = re.sub(r"//[^\n]*", "", fh.read())
+        h.update(" ".join(code.split()).encode())
+    return h.hexdigest()[:16]
 
 
 def step_kernel_traffic(k):
     """DRAM bytes of a k-iteration launch of the step kernel, or None (sources changed)."""
-    import hashlib
-    h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
-    if h.hexdigest()[:16] != TRAFFIC_SOURCES_SHA256:
+    if kernel_sources_digest() != TRAFFIC_SOURCES_SHA256:
         return None
     (k0, k1), (b0, b1) = TRAFFIC_K, TRAFFIC_BYTES
     return b0 + (b1 - b0) * (k - k0) / (k1 - k0)

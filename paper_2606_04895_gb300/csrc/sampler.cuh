@@ -863,7 +863,7 @@ struct RegChain8 {
         if (i < d) dst[i] = v[i];
     }
   }
-  // x = mu + L v on the first d entries (same summation order as TargetView::to_x_prior)
+  // x = mu + L v on the first d entries (same summation order as TargetView::eval)
   static __device__ __forceinline__ void to_x(const StepArgs<R> &a, const R *v, R *x) {
 #pragma unroll
     for (int i = 0; i < DB; ++i) {
