@@ -59,8 +59,6 @@ struct bst_ctx {
   std::vector<int> gauss;
   double logdet = 0.0;
   int any_gauss = 0;
-  void *mu_r = nullptr, *L_r = nullptr, *lo_r = nullptr, *up_r = nullptr;
-  int *gauss_d = nullptr;
   double *mu64 = nullptr, *L64 = nullptr, *mu64_new = nullptr, *L64_new = nullptr, *info64 = nullptr;
   double *stats64 = nullptr;  // [1 + kMaxD + kMaxD^2] Welford triple staging
 
@@ -197,9 +195,9 @@ StepArgs<R> make_args(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_st
   a.tgt.logdet = h->logdet;
   a.tgt.any_gauss = h->any_gauss;
   {
-    // the working-precision values of the device copies (mu_r, L_r, lo_r, up_r, gauss_d)
+    // whitening and prior in working precision, into the kernel parameters (entries beyond d
+    // stay zero: the device loops run unrolled to 8 or 32 entries)
     const int d = h->d;
-    // (entries beyond d stay zero: the device loops run unrolled to 16 or 32 entries)
     for (int i = 0; i < d; ++i) {
       if (h->mu.size() >= static_cast<size_t>(d)) a.tgt.mu[i] = static_cast<R>(h->mu[i]);
       if (h->L.size() >= static_cast<size_t>(d) * d)
@@ -455,8 +453,6 @@ bst_status set_target(bst_ctx *h, const double *mu, const double *L) {
     for (int j = 0; j <= i; ++j) h->L[i * d + j] = L[i * d + j];
   for (int i = 0; i < d; ++i) ld += std::log(std::fabs(h->L[i * d + i]));
   h->logdet = ld;
-  BST_TRY(upload_real(h, h->mu_r, h->mu.data(), d));
-  BST_TRY(upload_real(h, h->L_r, h->L.data(), static_cast<size_t>(d) * d));
   BST_CUDA(cudaMemcpy(h->mu64, h->mu.data(), d * 8, cudaMemcpyHostToDevice));
   BST_CUDA(cudaMemcpy(h->L64, h->L.data(), static_cast<size_t>(d) * d * 8, cudaMemcpyHostToDevice));
   h->weights_dirty = true;
@@ -546,11 +542,6 @@ bst_status bst_create(bst_handle *out, const bst_config *cfg) {
   A((void **)&h->divs, n * 8);
   A((void **)&h->steps_done, n * 4);
   A((void **)&h->status, 64);
-  A(&h->mu_r, kMaxD * rs);
-  A(&h->L_r, kMaxD * kMaxD * rs);
-  A(&h->lo_r, kMaxD * rs);
-  A(&h->up_r, kMaxD * rs);
-  A((void **)&h->gauss_d, kMaxD * 4);
   A((void **)&h->mu64, kMaxD * 8);
   A((void **)&h->L64, kMaxD * kMaxD * 8);
   A((void **)&h->mu64_new, kMaxD * 8);
@@ -755,9 +746,6 @@ bst_status bst_init_chains(bst_handle h, const double *theta0, const double *low
       h->gauss[i] = gauss[i] ? 1 : 0;
       h->any_gauss |= h->gauss[i];
     }
-  BST_TRY(upload_real(h, h->lo_r, h->lower.data(), d));
-  BST_TRY(upload_real(h, h->up_r, h->upper.data(), d));
-  BST_CUDA(cudaMemcpy(h->gauss_d, h->gauss.data(), d * 4, cudaMemcpyHostToDevice));
   // z0 = L^-1 (theta0 - mu), forward substitution in FP64, rows padded to dp
   std::vector<double> z(static_cast<size_t>(n) * h->dp, 0.0);
   for (int c = 0; c < n; ++c) {
