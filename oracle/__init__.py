@@ -312,5 +312,27 @@ def ess(samples):
     return out
 
 
+def r_minus_1(samples):
+    """Multivariate Gelman-Rubin statistic R - 1 (paper Sec. 4.1, the two displayed equations
+    there): B = covariance of the chain means (chains - 1 denominator), W = mean over chains of
+    the chain covariances (draws - 1 denominator), D = diag(sqrt(B_ii)), B~ = D^-1 B D^-1,
+    W~ = D^-1 W D^-1, R - 1 = max_i |lambda_i| over the eigenvalues of W~^-1 B~.
+    samples[n_draws][n_chains][d]; NaN when some B_ii is zero (the statistic is undefined)."""
+    S = _f64(samples)
+    n, M, d = S.shape
+    means = S.mean(axis=0)                                   # [M][d]
+    dm = means - means.mean(axis=0)
+    B = dm.T @ dm / (M - 1)
+    Y = S - means[None, :, :]                                # centred per chain
+    W = np.einsum("tci,tcj->ij", Y, Y) / ((n - 1) * M)
+    dB = np.sqrt(np.diag(B))
+    if np.any(dB == 0.0):
+        return float("nan")
+    Bt = B / np.outer(dB, dB)
+    Wt = W / np.outer(dB, dB)
+    lam = np.linalg.eigvals(np.linalg.solve(Wt, Bt))
+    return float(np.max(np.abs(lam)))
+
+
 def n_params(d, depth, width):
     return d * width + width + (depth - 1) * (width * width + width) + width + 1

@@ -1,0 +1,56 @@
+"""Pins of the oracle's multivariate Gelman-Rubin statistic R - 1 (paper Sec. 4.1)."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def test_one_dimension_worked_example():
+    # chains (0, 2) and (4, 6): chain means 1 and 5, B = 8 (chains - 1 denominator); chain
+    # variances 2 and 2, W = 2; R - 1 = B / W = 4
+    x = np.array([[[0.0], [4.0]], [[2.0], [6.0]]])  # [draws][chains][d]
+    assert O.r_minus_1(x) == pytest.approx(4.0, rel=1e-14)
+
+
+def test_two_dimension_worked_example():
+    # chain a: (0,0) (2,0) (0,2) (2,2); chain b: (4,1) (6,1) (4,3) (6,3)
+    # means (1,1) and (5,2): B = [[8, 2], [2, 0.5]] (rank one, eigenvalues 8.5 and 0)
+    # each chain: variances 4/3, no cross term: W = 4/3 I; R - 1 = 8.5 * 3/4 = 6.375
+    a = np.array([[0, 0], [2, 0], [0, 2], [2, 2]], float)
+    b = np.array([[4, 1], [6, 1], [4, 3], [6, 3]], float)
+    x = np.stack([a, b], axis=1)
+    assert O.r_minus_1(x) == pytest.approx(6.375, rel=1e-13)
+
+
+def test_equal_chain_means_give_zero_and_constant_dimension_gives_nan():
+    rng = np.random.default_rng(0)
+    base = rng.normal(size=(50, 1, 3))
+    x = np.concatenate([base, base[::-1]], axis=1)  # two chains, same draws reversed: same means
+    with np.errstate(invalid="ignore", divide="ignore"):
+        assert np.isnan(O.r_minus_1(x))  # B = 0: D is singular
+    y = rng.normal(size=(40, 6, 3))
+    y[:, :, 2] = 1.5  # a dimension with no spread at all
+    with np.errstate(invalid="ignore", divide="ignore"):
+        assert np.isnan(O.r_minus_1(y))
+
+
+def test_affine_invariance_and_chain_order():
+    # x -> A x + c maps W -> A W A^T and B -> A B A^T, so W^-1 B and the statistic are unchanged;
+    # the order of the chains does not enter
+    rng = np.random.default_rng(3)
+    n, M, d = 60, 9, 4
+    x = rng.normal(size=(n, M, d)) + rng.normal(size=(1, M, d)) * 0.3
+    A = rng.normal(size=(d, d)) + 2 * np.eye(d)
+    c = rng.normal(size=d)
+    r0 = O.r_minus_1(x)
+    assert r0 > 0
+    assert O.r_minus_1(x @ A.T + c) == pytest.approx(r0, rel=1e-9)
+    assert O.r_minus_1(x[:, rng.permutation(M), :]) == pytest.approx(r0, rel=1e-12)
+
+
+def test_well_mixed_chains_tend_to_zero():
+    # i.i.d. draws: B ~ W / n, so R - 1 shrinks like 1 / n
+    rng = np.random.default_rng(5)
+    r_short = O.r_minus_1(rng.normal(size=(100, 20, 3)))
+    r_long = O.r_minus_1(rng.normal(size=(10000, 20, 3)))
+    assert r_long < r_short and r_long < 0.01
