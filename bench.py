@@ -49,8 +49,8 @@ def peaks():
 # i.e. a fixed 2.3 MB plus 128.4 KB per MALA iteration (the x-space sample write, 131 KB per
 # iteration).  Valid for the kernel code they were taken on (sources without comments);
 # None once that changes.
-TRAFFIC_SOURCES = ['include/bst.h', 'paper_2606_04895_gb300/csrc/common.cuh', 'paper_2606_04895_gb300/csrc/engine_tc.cuh', 'paper_2606_04895_gb300/csrc/engine_tc2.cuh', 'paper_2606_04895_gb300/csrc/sampler.cuh', 'paper_2606_04895_gb300/csrc/tc2_launch.cuh', 'paper_2606_04895_gb300/csrc/launch.h', 'paper_2606_04895_gb300/csrc/k_tc2_w512_c4x.cu']
-TRAFFIC_SOURCES_SHA256 = "0e21f29cc60e7971"
+TRAFFIC_SOURCES = ['paper_2606_04895_gb300/csrc/common.cuh', 'paper_2606_04895_gb300/csrc/engine_tc.cuh', 'paper_2606_04895_gb300/csrc/engine_tc2.cuh', 'paper_2606_04895_gb300/csrc/sampler.cuh', 'paper_2606_04895_gb300/csrc/tc2_launch.cuh', 'paper_2606_04895_gb300/csrc/k_tc2_w512_c4x.cu']
+TRAFFIC_SOURCES_SHA256 = "940d555273b79f5d"
 TRAFFIC_K, TRAFFIC_BYTES = (20, 5000), (4.05e6 + 0.66586e6, 28.99e6 + 615.07e6)
 
 
@@ -275,6 +275,7 @@ def extras(torch, device, seed, eps_mala, K):
     ess = s.ess(x)
     out["nuts_27d"] = {"chains": 16384, "iterations_per_launch": it, "eps": eps_n, "evals_per_s": ev / t,
                        "leapfrogs_per_iter": ev / (16384 * it), "min_ess_per_s": float(ess.min()) / t,
+                       "r_minus_1": s.r_minus_1(x),
                        "tflops": 4.0 * P27 * ev / t / 1e12}
     s.close()
     s = _emulator_target(27, 16384, "bf16", seed + 12, device, nuis=21)
@@ -284,7 +285,7 @@ def extras(torch, device, seed, eps_mala, K):
     t = time_steps(torch, s, "aies", ka, 0.0, samples=x)
     ess = s.ess(x)
     out["aies_27d"] = {"walkers": 16384, "ensembles": 256, "steps": ka, "evals_per_s": ka * 16384 / t,
-                       "min_ess_per_s": float(ess.min()) / t, "tflops": 2.0 * P27 * ka * 16384 / t / 1e12}
+                       "min_ess_per_s": float(ess.min()) / t, "r_minus_1": s.r_minus_1(x), "tflops": 2.0 * P27 * ka * 16384 / t / 1e12}
     s.close()
     # MH (forward only) on the headline target
     s, _ = make_sampler("bf16", N_CHAINS, seed, device)
@@ -443,6 +444,7 @@ def main():
     acc = s.step("mala", 1, eps=eps)["accept_stat"]
     ess = s.ess(samples)
     min_ess_s = float(ess.min()) * world / dt
+    rm1 = s.r_minus_1(samples)  # convergence of the timed samples (Sec. 4.1), this rank's chains
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
            "ms_per_step": dt * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -453,7 +455,7 @@ def main():
                       "accept_stat": acc, "parallelism": f"dp{world} (independent chains per GPU)",
                       "l2": "flushed (256 MB write) before the timed launch; the 1.6 MB of BF16 weights are "
                             "L2-resident by design inside the persistent step loop"},
-           "min_ess_per_s": min_ess_s, "min_ess": float(ess.min()) * world}
+           "min_ess_per_s": min_ess_s, "min_ess": float(ess.min()) * world, "r_minus_1": rm1}
     if rank == 0:
         # roofline of the dominant kernel: the tcgen05 chain-tile kernel is the whole timed region
         P = n_params(D, DEPTH, WIDTH) - 1

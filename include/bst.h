@@ -232,6 +232,17 @@ bst_status bst_train_apply(bst_handle h, const float *grad_dev, double lr, doubl
  * type).  ess_out: host double[d].  Synchronises. */
 bst_status bst_ess(bst_handle h, const void *samples_dev, int n_draws, double *ess_out);
 
+/* Multivariate Gelman-Rubin statistic R - 1 (paper Sec. 4.1) of samples_dev
+ * real[n_draws][n_chains][d] (this handle's n_chains, d and real type): B = the
+ * covariance of the chain means (n_chains - 1 denominator), W = the mean of the
+ * chain covariances (n_draws - 1 denominator), both scaled by D = diag(sqrt(B_ii));
+ * *out = the largest |eigenvalue| of W~^-1 B~ (host double).  The cross products run
+ * on the device in FP64, the d x d algebra (Cholesky, Jacobi eigenvalues) on the
+ * host.  *out is NaN when some B_ii is zero or W is not positive definite (the
+ * statistic is undefined).  n_draws >= 2 and n_chains >= 2, else BST_ERR_ARG.
+ * Synchronises. */
+bst_status bst_r_minus_1(bst_handle h, const void *samples_dev, int n_draws, double *out);
+
 /* Block until all work of h on ``stream`` is done and check the device status. */
 bst_status bst_sync(bst_handle h, void *stream);
 

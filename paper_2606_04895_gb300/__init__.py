@@ -239,6 +239,14 @@ class Sampler:
         _lib.check(self.lib.bst_ess(self.h, C.c_void_p(samples.data_ptr()), samples.shape[0], _p(out)))
         return out
 
+    def r_minus_1(self, samples):
+        """Multivariate Gelman-Rubin R - 1 (Sec. 4.1) of samples[n_draws][n_chains][d] (NaN
+        when undefined)."""
+        self._check_dev(samples, (samples.shape[0], self.n, self.d))
+        out = np.zeros(1)
+        _lib.check(self.lib.bst_r_minus_1(self.h, C.c_void_p(samples.data_ptr()), samples.shape[0], _p(out)))
+        return float(out[0])
+
     def sync(self, stream=None):
         _lib.check(self.lib.bst_sync(self.h, _stream_ptr(stream)))
 

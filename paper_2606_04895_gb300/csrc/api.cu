@@ -104,6 +104,7 @@ struct bst_ctx {
   // host-side counter snapshot for per-call statistics
   int ess_tmp_cap = 0;
   double *ess_mean = nullptr, *ess_var = nullptr, *ess_V = nullptr;
+  double *rhat_part = nullptr;  // [blocks][d (d + 1) / 2] pooled cross products (R - 1)
 };
 
 namespace {
@@ -1071,6 +1072,136 @@ bst_status bst_train_apply(bst_handle h, const float *grad_dev, double lr, doubl
   h->p32_newer = true;
   h->weights_dirty = true;
   h->state_stale = true;
+  return BST_OK;
+}
+
+// Eigenvalues of the symmetric d x d matrix A (row-major; destroyed) by cyclic Jacobi
+// rotations (Golub & Van Loan, Matrix Computations, Sec. 8.5): each rotation zeroes one
+// off-diagonal pair; sweeps repeat until the off-diagonal mass is negligible.
+static void jacobi_eigenvalues(std::vector<double> &A, int d, std::vector<double> &ev) {
+  auto at = [&](int r, int c) -> double & { return A[static_cast<size_t>(r) * d + c]; };
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int r = 0; r < d; ++r)
+      for (int c = 0; c < d; ++c) {
+        tot += at(r, c) * at(r, c);
+        if (r != c) off += at(r, c) * at(r, c);
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < d - 1; ++p)
+      for (int q = p + 1; q < d; ++q) {
+        const double apq = at(p, q);
+        if (apq == 0.0) continue;
+        const double theta = (at(q, q) - at(p, p)) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < d; ++k) {  // columns p, q
+          const double akp = at(k, p), akq = at(k, q);
+          at(k, p) = c * akp - s * akq;
+          at(k, q) = s * akp + c * akq;
+        }
+        for (int k = 0; k < d; ++k) {  // rows p, q
+          const double apk = at(p, k), aqk = at(q, k);
+          at(p, k) = c * apk - s * aqk;
+          at(q, k) = s * apk + c * aqk;
+        }
+      }
+  }
+  ev.resize(d);
+  for (int r = 0; r < d; ++r) ev[r] = at(r, r);
+}
+
+bst_status bst_r_minus_1(bst_handle h, const void *samples_dev, int n_draws, double *out) {
+  if (!h || !samples_dev || !out) return fail(BST_ERR_ARG, "bst_r_minus_1: NULL argument");
+  if (n_draws < 2 || h->n < 2) return fail(BST_ERR_ARG, "bst_r_minus_1: need at least 2 draws and 2 chains");
+  BST_CUDA(cudaSetDevice(h->device));
+  const int M = h->n, d = h->d, n = n_draws;
+  const size_t md = static_cast<size_t>(M) * d;
+  const int nb = rhat_blocks(M), np = d * (d + 1) / 2;
+  if (!h->ess_mean) {
+    BST_TRY(dalloc_t(h, &h->ess_mean, md));
+    BST_TRY(dalloc_t(h, &h->ess_var, md));
+    BST_TRY(dalloc_t(h, &h->ess_V, static_cast<size_t>(d) * 32));
+  }
+  if (!h->rhat_part) BST_TRY(dalloc_t(h, &h->rhat_part, static_cast<size_t>(nb) * np));
+  // per-chain means, then the pooled within-chain cross products about them
+  if (h->rs == 8) {
+    BST_CUDA(launch_ess_moments_f64((const double *)samples_dev, n, M, d, h->ess_mean, h->ess_var, 0));
+    BST_CUDA(launch_rhat_cross_f64((const double *)samples_dev, n, M, d, h->ess_mean, h->rhat_part, 0));
+  } else {
+    BST_CUDA(launch_ess_moments_f32((const float *)samples_dev, n, M, d, h->ess_mean, h->ess_var, 0));
+    BST_CUDA(launch_rhat_cross_f32((const float *)samples_dev, n, M, d, h->ess_mean, h->rhat_part, 0));
+  }
+  std::vector<double> mean(md), part(static_cast<size_t>(nb) * np);
+  BST_CUDA(cudaMemcpy(mean.data(), h->ess_mean, md * 8, cudaMemcpyDeviceToHost));
+  BST_CUDA(cudaMemcpy(part.data(), h->rhat_part, part.size() * 8, cudaMemcpyDeviceToHost));
+  // W (blocks summed in order) and B
+  std::vector<double> W(static_cast<size_t>(d) * d), B(static_cast<size_t>(d) * d, 0.0), gm(d, 0.0);
+  for (int i = 0, p = 0; i < d; ++i)
+    for (int j = i; j < d; ++j, ++p) {
+      double sum = 0.0;
+      for (int b = 0; b < nb; ++b) sum += part[static_cast<size_t>(b) * np + p];
+      W[i * d + j] = W[j * d + i] = sum / (static_cast<double>(M) * (n - 1));
+    }
+  for (int c = 0; c < M; ++c)
+    for (int i = 0; i < d; ++i) gm[i] += mean[static_cast<size_t>(c) * d + i];
+  for (int i = 0; i < d; ++i) gm[i] /= M;
+  for (int c = 0; c < M; ++c)
+    for (int i = 0; i < d; ++i) {
+      const double ei = mean[static_cast<size_t>(c) * d + i] - gm[i];
+      for (int j = 0; j < d; ++j) B[i * d + j] += ei * (mean[static_cast<size_t>(c) * d + j] - gm[j]);
+    }
+  for (auto &v : B) v /= (M - 1);
+  // scaling by D = diag(sqrt(B_ii)), then eig(W~^-1 B~) = eig(L^-1 B~ L^-T) with W~ = L L^T
+  std::vector<double> dB(d);
+  for (int i = 0; i < d; ++i) {
+    dB[i] = std::sqrt(B[i * d + i]);
+    if (!(dB[i] > 0.0)) {
+      *out = NAN;
+      return BST_OK;
+    }
+  }
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      B[i * d + j] /= dB[i] * dB[j];
+      W[i * d + j] /= dB[i] * dB[j];
+    }
+  std::vector<double> Lc(static_cast<size_t>(d) * d, 0.0);
+  for (int j = 0; j < d; ++j) {
+    double s = W[j * d + j];
+    for (int k = 0; k < j; ++k) s -= Lc[j * d + k] * Lc[j * d + k];
+    if (!(s > 0.0)) {
+      *out = NAN;
+      return BST_OK;
+    }
+    Lc[j * d + j] = std::sqrt(s);
+    for (int i = j + 1; i < d; ++i) {
+      double t = W[i * d + j];
+      for (int k = 0; k < j; ++k) t -= Lc[i * d + k] * Lc[j * d + k];
+      Lc[i * d + j] = t / Lc[j * d + j];
+    }
+  }
+  auto lsolve = [&](const std::vector<double> &Rhs, std::vector<double> &X) {  // X = L^-1 Rhs
+    X = Rhs;
+    for (int col = 0; col < d; ++col)
+      for (int i = 0; i < d; ++i) {
+        double s = X[i * d + col];
+        for (int k = 0; k < i; ++k) s -= Lc[i * d + k] * X[k * d + col];
+        X[i * d + col] = s / Lc[i * d + i];
+      }
+  };
+  std::vector<double> Y, Yt(static_cast<size_t>(d) * d), Cm;
+  lsolve(B, Y);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) Yt[i * d + j] = Y[j * d + i];
+  lsolve(Yt, Cm);
+  for (int i = 0; i < d; ++i)  // symmetric up to rounding: use the symmetric part
+    for (int j = i + 1; j < d; ++j) Cm[i * d + j] = Cm[j * d + i] = 0.5 * (Cm[i * d + j] + Cm[j * d + i]);
+  std::vector<double> ev;
+  jacobi_eigenvalues(Cm, d, ev);
+  double r = 0.0;
+  for (double v : ev) r = std::fmax(r, std::fabs(v));
+  *out = r;
   return BST_OK;
 }
 

@@ -495,6 +495,56 @@ __global__ void ess_moments_kernel(const R *x, int n, int M, int d, double *mean
   mean[s] = m;
   var[s] = ss / (n - 1);
 }
+// ------------------------------------------------------------------------------------------
+// R - 1 (Sec. 4.1): pooled within-chain cross products S_ij = sum_c sum_t (x_tci - m_ci)(x_tcj - m_cj)
+// for the chains of one block (kRhatChains of them), FP64; one partial per block and pair
+// i <= j (pair p = i * d - i (i - 1) / 2 + j - i), summed over blocks in order on the host.
+constexpr int kRhatChains = 32;
+template <typename R>
+__global__ void __launch_bounds__(256) rhat_cross_kernel(const R *x, int n, int M, int d, const double *mean,
+                                                         double *partial) {
+  __shared__ double y[kRhatChains * kMaxD];
+  const int c0 = blockIdx.x * kRhatChains;
+  const int nc = min(kRhatChains, M - c0);
+  const int npairs = d * (d + 1) / 2;
+  double acc[3] = {0.0, 0.0, 0.0};  // pairs threadIdx.x + 256 k, k < 3 (npairs <= 528)
+  int pi[3], pj[3];
+  for (int k = 0; k < 3; ++k) {
+    int p = threadIdx.x + 256 * k, i = 0;
+    pi[k] = pj[k] = -1;
+    if (p < npairs) {
+      while (p >= d - i) {
+        p -= d - i;
+        ++i;
+      }
+      pi[k] = i;
+      pj[k] = i + p;
+    }
+  }
+  const size_t st = static_cast<size_t>(M) * d;
+  for (int t = 0; t < n; ++t) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * d; e += blockDim.x)
+      y[e] = static_cast<double>(x[t * st + static_cast<size_t>(c0) * d + e]) - mean[static_cast<size_t>(c0) * d + e];
+    __syncthreads();
+    for (int k = 0; k < 3; ++k)
+      if (pi[k] >= 0)
+        for (int c = 0; c < nc; ++c) acc[k] += y[c * d + pi[k]] * y[c * d + pj[k]];
+  }
+  for (int k = 0; k < 3; ++k)
+    if (pi[k] >= 0) partial[static_cast<size_t>(blockIdx.x) * npairs + threadIdx.x + 256 * k] = acc[k];
+}
+cudaError_t launch_rhat_cross_f32(const float *x, int n, int M, int d, const double *mean, double *partial,
+                                  cudaStream_t s) {
+  rhat_cross_kernel<float><<<(M + kRhatChains - 1) / kRhatChains, 256, 0, s>>>(x, n, M, d, mean, partial);
+  return cudaGetLastError();
+}
+cudaError_t launch_rhat_cross_f64(const double *x, int n, int M, int d, const double *mean, double *partial,
+                                  cudaStream_t s) {
+  rhat_cross_kernel<double><<<(M + kRhatChains - 1) / kRhatChains, 256, 0, s>>>(x, n, M, d, mean, partial);
+  return cudaGetLastError();
+}
+int rhat_blocks(int M) { return (M + kRhatChains - 1) / kRhatChains; }
 cudaError_t launch_ess_moments_f32(const float *x, int n, int M, int d, double *mean, double *var, cudaStream_t s) {
   ess_moments_kernel<float><<<blocks_for(static_cast<size_t>(M) * d, 128), 128, 0, s>>>(x, n, M, d, mean, var);
   return cudaGetLastError();

@@ -69,6 +69,11 @@ cudaError_t launch_remap_f64(double *z, int n, int d, int dp, const double *mu_o
 
 // ESS (k_aux.cu): per-(chain, dim) means and variances, then variograms per lag block.
 cudaError_t launch_ess_moments_f32(const float *x, int n, int M, int d, double *mean, double *var, cudaStream_t s);
+cudaError_t launch_rhat_cross_f32(const float *x, int n, int M, int d, const double *mean, double *partial,
+                                  cudaStream_t s);
+cudaError_t launch_rhat_cross_f64(const double *x, int n, int M, int d, const double *mean, double *partial,
+                                  cudaStream_t s);
+int rhat_blocks(int M);
 cudaError_t launch_ess_moments_f64(const double *x, int n, int M, int d, double *mean, double *var, cudaStream_t s);
 cudaError_t launch_ess_variogram_f32(const float *x, int n, int M, int d, int t0, int nt, double *V, cudaStream_t s);
 cudaError_t launch_ess_variogram_f64(const double *x, int n, int M, int d, int t0, int nt, double *V, cudaStream_t s);

@@ -201,3 +201,46 @@ def test_train_apply_equals_train_step():
         b.train_apply(g, lr=1e-3)
     assert np.array_equal(a.get_emulator(), b.get_emulator())
     a.close(); b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_r_minus_1_worked_example(prec):
+    """The hand-worked one-dimensional case of the oracle pins through the device path:
+    chains (0, 2) and (4, 6) give R - 1 = B / W = 8 / 2 = 4."""
+    from paper_2606_04895_gb300 import Sampler
+    s = Sampler(1, 2, precision=prec, likelihood="emulator")
+    x = torch.tensor([[[0.0], [4.0]], [[2.0], [6.0]]], dtype=s.dtype, device="cuda")
+    assert s.r_minus_1(x) == pytest.approx(4.0, rel=1e-12)
+    s.close()
+
+
+@pytest.mark.parametrize("prec,n_chains,d", [("fp64", 64, 6), ("fp32", 64, 6), ("fp32", 200, 27), ("fp64", 33, 27),
+                                             ("bf16", 300, 8)])
+def test_r_minus_1_matches_oracle(prec, n_chains, d):
+    """R - 1 of AR(1) chains with chain-dependent offsets (ragged chain counts: the device
+    blocks hold 32 chains) against the FP64 oracle on the same working-precision draws."""
+    from paper_2606_04895_gb300 import Sampler
+    s = Sampler(d, n_chains, precision=prec, likelihood="emulator")
+    rng = np.random.default_rng(4)
+    n = 300
+    A = rng.normal(size=(d, d)) / np.sqrt(d) + np.eye(d)
+    x = np.zeros((n, n_chains, d))
+    x[0] = rng.normal(size=(n_chains, d))
+    for t in range(1, n):
+        x[t] = 0.7 * x[t - 1] + rng.normal(size=(n_chains, d))
+    x = x @ A.T + 0.3 * rng.normal(size=(1, n_chains, d))
+    xt = torch.as_tensor(x, dtype=s.dtype, device="cuda")
+    r = s.r_minus_1(xt)
+    ref = O.r_minus_1(xt.double().cpu().numpy())
+    assert np.isfinite(ref) and ref > 0
+    assert r == pytest.approx(ref, rel=1e-8)
+    s.close()
+
+
+def test_r_minus_1_undefined_is_nan():
+    from paper_2606_04895_gb300 import Sampler
+    s = Sampler(3, 40, precision="fp32", likelihood="emulator")
+    x = torch.randn(50, 40, 3, device="cuda")
+    x[:, :, 1] = 2.0  # no spread in one dimension: B_11 = 0
+    assert np.isnan(s.r_minus_1(x))
+    s.close()
