@@ -334,5 +334,23 @@ def r_minus_1(samples):
     return float(np.max(np.abs(lam)))
 
 
+def quantiles(samples, q):
+    """Per-dimension quantiles of the pooled draws samples[n_draws][n_chains][d] at levels q
+    (linear interpolation between order statistics at rank (N - 1) q); out[d][len(q)]."""
+    S = _f64(samples)
+    flat = S.reshape(-1, S.shape[-1])
+    return np.quantile(flat, np.asarray(q, dtype=np.float64), axis=0).T.copy()
+
+
+def credible_metric(samples, alpha, true_lo, true_hi):
+    """Credible metric of Sec. 4.1 per dimension: (|hi - hi0| + |lo - lo0|) / (hi0 - lo0), with
+    lo, hi the equal-tailed credible limits at level alpha of the pooled draws (quantiles
+    (1 - alpha) / 2 and (1 + alpha) / 2) and lo0, hi0 the true limits."""
+    lo0 = _f64(true_lo)
+    hi0 = _f64(true_hi)
+    qs = quantiles(samples, [(1.0 - alpha) / 2.0, (1.0 + alpha) / 2.0])
+    return (np.abs(qs[:, 1] - hi0) + np.abs(qs[:, 0] - lo0)) / (hi0 - lo0)
+
+
 def n_params(d, depth, width):
     return d * width + width + (depth - 1) * (width * width + width) + width + 1

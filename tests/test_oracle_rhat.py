@@ -54,3 +54,25 @@ def test_well_mixed_chains_tend_to_zero():
     r_short = O.r_minus_1(rng.normal(size=(100, 20, 3)))
     r_long = O.r_minus_1(rng.normal(size=(10000, 20, 3)))
     assert r_long < r_short and r_long < 0.01
+
+
+def test_quantiles_of_an_arithmetic_sequence():
+    # the 101 draws 0, 1, ..., 100: the q-quantile is 100 q exactly (rank (N - 1) q); a second
+    # dimension holding 2 x + 1 has quantiles 200 q + 1
+    v = np.arange(101.0)
+    x = np.stack([v, 2 * v + 1], axis=-1).reshape(101, 1, 2)
+    q = [0.025, 0.16, 0.5, 0.84, 0.975]
+    out = O.quantiles(x, q)
+    assert np.allclose(out[0], 100 * np.array(q), rtol=0, atol=1e-12)
+    assert np.allclose(out[1], 200 * np.array(q) + 1, rtol=0, atol=1e-12)
+
+
+def test_credible_metric_worked_example():
+    # draws 0..100: the 68 % limits are 16 and 84; against true limits 20 and 80 the metric is
+    # (|84 - 80| + |16 - 20|) / (80 - 20) = 8 / 60
+    x = np.arange(101.0).reshape(101, 1, 1)
+    cm = O.credible_metric(x, 0.68, [20.0], [80.0])
+    assert cm[0] == pytest.approx(8.0 / 60.0, rel=1e-12)
+    # exact limits give zero; scaling draws and limits together leaves the metric unchanged
+    assert O.credible_metric(x, 0.68, [16.0], [84.0])[0] == pytest.approx(0.0, abs=1e-12)
+    assert O.credible_metric(3 * x, 0.68, [60.0], [240.0])[0] == pytest.approx(8.0 / 60.0, rel=1e-12)
