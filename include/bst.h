@@ -243,6 +243,23 @@ bst_status bst_ess(bst_handle h, const void *samples_dev, int n_draws, double *e
  * Synchronises. */
 bst_status bst_r_minus_1(bst_handle h, const void *samples_dev, int n_draws, double *out);
 
+/* Per-dimension quantiles of the pooled draws samples_dev real[n_draws][n_chains][d]
+ * (this handle's n_chains, d and real type) at the levels q[0..nq) in [0, 1], 1 <= nq
+ * <= 8: linear interpolation between the order statistics at ranks floor(h) and
+ * floor(h) + 1, h = (N - 1) q, N = n_draws n_chains (the order statistics are exact:
+ * radix select on the device).  out: host double[d][nq].  Draws must be finite.
+ * Synchronises. */
+bst_status bst_quantiles(bst_handle h, const void *samples_dev, int n_draws, const double *q, int nq,
+                         double *out);
+
+/* Credible metric (paper Sec. 4.1) per dimension at credible level alpha in (0, 1):
+ * (|hi - true_hi| + |lo - true_lo|) / (true_hi - true_lo), lo and hi the equal-tailed
+ * limits of the pooled draws (quantiles (1 - alpha) / 2 and (1 + alpha) / 2, as in
+ * bst_quantiles).  true_lo, true_hi, out: host double[d]; true_hi > true_lo.
+ * Synchronises. */
+bst_status bst_credible_metric(bst_handle h, const void *samples_dev, int n_draws, double alpha,
+                               const double *true_lo, const double *true_hi, double *out);
+
 /* Block until all work of h on ``stream`` is done and check the device status. */
 bst_status bst_sync(bst_handle h, void *stream);
 

@@ -247,6 +247,25 @@ class Sampler:
         _lib.check(self.lib.bst_r_minus_1(self.h, C.c_void_p(samples.data_ptr()), samples.shape[0], _p(out)))
         return float(out[0])
 
+    def quantiles(self, samples, q):
+        """Per-dimension quantiles of the pooled draws samples[n_draws][n_chains][d]; [d][len(q)]."""
+        self._check_dev(samples, (samples.shape[0], self.n, self.d))
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        out = np.zeros((self.d, q.size))
+        _lib.check(self.lib.bst_quantiles(self.h, C.c_void_p(samples.data_ptr()), samples.shape[0], _p(q), q.size,
+                                          _p(out)))
+        return out
+
+    def credible_metric(self, samples, alpha, true_lo, true_hi):
+        """Credible metric of Sec. 4.1 per dimension against the true limits."""
+        self._check_dev(samples, (samples.shape[0], self.n, self.d))
+        lo = np.ascontiguousarray(true_lo, dtype=np.float64)
+        hi = np.ascontiguousarray(true_hi, dtype=np.float64)
+        out = np.zeros(self.d)
+        _lib.check(self.lib.bst_credible_metric(self.h, C.c_void_p(samples.data_ptr()), samples.shape[0], float(alpha),
+                                                _p(lo), _p(hi), _p(out)))
+        return out
+
     def sync(self, stream=None):
         _lib.check(self.lib.bst_sync(self.h, _stream_ptr(stream)))
 

@@ -105,6 +105,8 @@ struct bst_ctx {
   int ess_tmp_cap = 0;
   double *ess_mean = nullptr, *ess_var = nullptr, *ess_V = nullptr;
   double *rhat_part = nullptr;  // [blocks][d (d + 1) / 2] pooled cross products (R - 1)
+  void *qsel_prefix = nullptr;    // [d][2 kMaxQuantiles] radix-select prefixes (quantiles)
+  unsigned int *qsel_hist = nullptr;  // [d][2 kMaxQuantiles][16]
 };
 
 namespace {
@@ -1202,6 +1204,106 @@ bst_status bst_r_minus_1(bst_handle h, const void *samples_dev, int n_draws, dou
   double r = 0.0;
   for (double v : ev) r = std::fmax(r, std::fabs(v));
   *out = r;
+  return BST_OK;
+}
+
+// Quantiles of the pooled draws per dimension: order statistics by radix select on the
+// device (qsel_hist_kernel), the key of each rank fixed 4 bits per pass from the most
+// significant digit; then linear interpolation between ranks floor(h) and floor(h) + 1,
+// h = (N - 1) q, in FP64.
+constexpr int kMaxQuantiles = 8;
+extern "C++" {
+template <typename R, typename K>
+static bst_status quantiles_impl(bst_ctx *h, const R *x, int n_draws, const double *q, int nq, double *out) {
+  const int d = h->d, M = h->n;
+  const size_t N = static_cast<size_t>(n_draws) * M;
+  const int jpd = 2 * nq, nj = d * jpd;
+  if (!h->qsel_prefix) {
+    BST_TRY(dalloc(h, &h->qsel_prefix, static_cast<size_t>(kMaxD) * 2 * kMaxQuantiles * 8));
+    BST_TRY(dalloc(h, reinterpret_cast<void **>(&h->qsel_hist), static_cast<size_t>(kMaxD) * 2 * kMaxQuantiles * 16 * 4));
+  }
+  std::vector<K> prefix(nj, K(0));
+  std::vector<unsigned long long> rank(nj);
+  std::vector<double> frac(static_cast<size_t>(d) * nq);
+  for (int qd = 0; qd < d; ++qd)
+    for (int k = 0; k < nq; ++k) {
+      const double hpos = (static_cast<double>(N) - 1.0) * q[k];
+      unsigned long long lo = static_cast<unsigned long long>(std::floor(hpos));
+      if (lo > N - 1) lo = N - 1;
+      const unsigned long long hi = lo + 1 < N ? lo + 1 : N - 1;
+      rank[qd * jpd + 2 * k] = lo;
+      rank[qd * jpd + 2 * k + 1] = hi;
+      frac[static_cast<size_t>(qd) * nq + k] = hpos - static_cast<double>(lo);
+    }
+  std::vector<unsigned int> hist(static_cast<size_t>(nj) * 16);
+  const int bits = 8 * static_cast<int>(sizeof(K));
+  for (int shift = bits - 4; shift >= 0; shift -= 4) {
+    BST_CUDA(cudaMemcpy(h->qsel_prefix, prefix.data(), nj * sizeof(K), cudaMemcpyHostToDevice));
+    BST_CUDA(cudaMemset(h->qsel_hist, 0, static_cast<size_t>(nj) * 16 * 4));
+    if (sizeof(R) == 8)
+      BST_CUDA(launch_qsel_hist_f64(reinterpret_cast<const double *>(x), N * d, d, jpd,
+                                    static_cast<const unsigned long long *>(h->qsel_prefix), shift, h->qsel_hist, 0));
+    else
+      BST_CUDA(launch_qsel_hist_f32(reinterpret_cast<const float *>(x), N * d, d, jpd,
+                                    static_cast<const uint32_t *>(h->qsel_prefix), shift, h->qsel_hist, 0));
+    BST_CUDA(cudaMemcpy(hist.data(), h->qsel_hist, hist.size() * 4, cudaMemcpyDeviceToHost));
+    for (int j = 0; j < nj; ++j) {  // the digit whose bin holds the job's remaining rank
+      unsigned long long below = 0;
+      int b = 0;
+      for (; b < 15; ++b) {
+        const unsigned long long cnt = hist[static_cast<size_t>(j) * 16 + b];
+        if (rank[j] < below + cnt) break;
+        below += cnt;
+      }
+      rank[j] -= below;
+      prefix[j] |= static_cast<K>(b) << shift;
+    }
+  }
+  for (int qd = 0; qd < d; ++qd)
+    for (int k = 0; k < nq; ++k) {
+      double v[2];
+      for (int e = 0; e < 2; ++e) {  // key -> value
+        const K key = prefix[qd * jpd + 2 * k + e];
+        const K top = K(1) << (8 * sizeof(K) - 1);
+        const K b = (key & top) ? (key & ~top) : ~key;
+        if (sizeof(K) == 8) {
+          double dv;
+          std::memcpy(&dv, &b, 8);
+          v[e] = dv;
+        } else {
+          float fv;
+          std::memcpy(&fv, &b, 4);
+          v[e] = fv;
+        }
+      }
+      out[static_cast<size_t>(qd) * nq + k] = v[0] + frac[static_cast<size_t>(qd) * nq + k] * (v[1] - v[0]);
+    }
+  return BST_OK;
+}
+}  // extern "C++"
+
+bst_status bst_quantiles(bst_handle h, const void *samples_dev, int n_draws, const double *q, int nq, double *out) {
+  if (!h || !samples_dev || !q || !out) return fail(BST_ERR_ARG, "bst_quantiles: NULL argument");
+  if (n_draws < 1 || nq < 1 || nq > kMaxQuantiles) return fail(BST_ERR_ARG, "bst_quantiles: need n_draws >= 1 and 1 <= nq <= 8");
+  for (int k = 0; k < nq; ++k)
+    if (!(q[k] >= 0.0 && q[k] <= 1.0)) return fail(BST_ERR_ARG, "bst_quantiles: levels must lie in [0, 1]");
+  BST_CUDA(cudaSetDevice(h->device));
+  if (h->rs == 8) return quantiles_impl<double, unsigned long long>(h, static_cast<const double *>(samples_dev), n_draws, q, nq, out);
+  return quantiles_impl<float, uint32_t>(h, static_cast<const float *>(samples_dev), n_draws, q, nq, out);
+}
+
+bst_status bst_credible_metric(bst_handle h, const void *samples_dev, int n_draws, double alpha, const double *true_lo,
+                               const double *true_hi, double *out) {
+  if (!h || !samples_dev || !true_lo || !true_hi || !out) return fail(BST_ERR_ARG, "bst_credible_metric: NULL argument");
+  if (!(alpha > 0.0 && alpha < 1.0)) return fail(BST_ERR_ARG, "bst_credible_metric: alpha must lie in (0, 1)");
+  const int d = h->d;
+  for (int i = 0; i < d; ++i)
+    if (!(true_hi[i] > true_lo[i])) return fail(BST_ERR_ARG, "bst_credible_metric: need true_hi > true_lo");
+  const double q[2] = {(1.0 - alpha) / 2.0, (1.0 + alpha) / 2.0};
+  std::vector<double> lim(static_cast<size_t>(d) * 2);
+  BST_TRY(bst_quantiles(h, samples_dev, n_draws, q, 2, lim.data()));
+  for (int i = 0; i < d; ++i)
+    out[i] = (std::fabs(lim[2 * i + 1] - true_hi[i]) + std::fabs(lim[2 * i] - true_lo[i])) / (true_hi[i] - true_lo[i]);
   return BST_OK;
 }
 

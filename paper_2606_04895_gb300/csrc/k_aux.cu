@@ -545,6 +545,64 @@ cudaError_t launch_rhat_cross_f64(const double *x, int n, int M, int d, const do
   return cudaGetLastError();
 }
 int rhat_blocks(int M) { return (M + kRhatChains - 1) / kRhatChains; }
+
+// ------------------------------------------------------------------------------------------
+// Quantiles of the pooled draws per dimension by radix select (exact order statistics).  A
+// value's key is its order-preserving unsigned image; pass by pass (4-bit digits, most
+// significant first) every job (one rank of one dimension; the jobs of dimension q are
+// q * jpd .. q * jpd + jpd - 1) histograms the next digit of the keys that match its prefix.
+template <typename R>
+struct SelKey;
+template <>
+struct SelKey<float> {
+  using K = uint32_t;
+  static __device__ __forceinline__ K of(float v) {
+    const uint32_t b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+  }
+};
+template <>
+struct SelKey<double> {
+  using K = unsigned long long;
+  static __device__ __forceinline__ K of(double v) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+  }
+};
+template <typename R>
+__global__ void qsel_hist_kernel(const R *x, size_t n_elems, int d, int jpd, const typename SelKey<R>::K *prefix,
+                                 int shift, unsigned int *hist) {
+  using K = typename SelKey<R>::K;
+  extern __shared__ unsigned int qh[];  // [d * jpd][16]
+  const int njobs = d * jpd;
+  for (int i = threadIdx.x; i < njobs * 16; i += blockDim.x) qh[i] = 0u;
+  __syncthreads();
+  const int top = shift + 4;  // bits at and above `top` are fixed by the prefix
+  const K hi_mask = top >= static_cast<int>(8 * sizeof(K)) ? K(0) : (~K(0) << top);
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n_elems;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int q = static_cast<int>(e % static_cast<size_t>(d));
+    const K key = SelKey<R>::of(x[e]);
+    const unsigned digit = static_cast<unsigned>((key >> shift) & K(15));
+    for (int j = q * jpd; j < (q + 1) * jpd; ++j)
+      if ((key & hi_mask) == prefix[j]) atomicAdd(&qh[j * 16 + digit], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < njobs * 16; i += blockDim.x)
+    if (qh[i]) atomicAdd(&hist[i], qh[i]);
+}
+cudaError_t launch_qsel_hist_f32(const float *x, size_t n_elems, int d, int jpd, const uint32_t *prefix, int shift,
+                                 unsigned int *hist, cudaStream_t s) {
+  const size_t smem = static_cast<size_t>(d) * jpd * 16 * sizeof(unsigned int);
+  qsel_hist_kernel<float><<<1216, 256, smem, s>>>(x, n_elems, d, jpd, prefix, shift, hist);
+  return cudaGetLastError();
+}
+cudaError_t launch_qsel_hist_f64(const double *x, size_t n_elems, int d, int jpd, const unsigned long long *prefix,
+                                 int shift, unsigned int *hist, cudaStream_t s) {
+  const size_t smem = static_cast<size_t>(d) * jpd * 16 * sizeof(unsigned int);
+  qsel_hist_kernel<double><<<1216, 256, smem, s>>>(x, n_elems, d, jpd, prefix, shift, hist);
+  return cudaGetLastError();
+}
 cudaError_t launch_ess_moments_f32(const float *x, int n, int M, int d, double *mean, double *var, cudaStream_t s) {
   ess_moments_kernel<float><<<blocks_for(static_cast<size_t>(M) * d, 128), 128, 0, s>>>(x, n, M, d, mean, var);
   return cudaGetLastError();

@@ -244,3 +244,36 @@ def test_r_minus_1_undefined_is_nan():
     x[:, :, 1] = 2.0  # no spread in one dimension: B_11 = 0
     assert np.isnan(s.r_minus_1(x))
     s.close()
+
+
+@pytest.mark.parametrize("prec,n_chains,d,n_draws", [("fp32", 64, 6, 301), ("fp64", 33, 27, 120), ("bf16", 300, 8, 77),
+                                                      ("fp32", 16384, 27, 40)])
+def test_quantiles_match_oracle(prec, n_chains, d, n_draws):
+    """Exact order statistics (radix select) against numpy's on the same working-precision
+    draws: negative values, ties (a coarse grid in one dimension), the extreme levels 0 and 1."""
+    from paper_2606_04895_gb300 import Sampler
+    s = Sampler(d, n_chains, precision=prec, likelihood="emulator")
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=(n_draws, n_chains, d)) * np.linspace(0.1, 3.0, d) - 0.5
+    x[:, :, 0] = np.round(x[:, :, 0] * 4) / 4  # many ties
+    xt = torch.as_tensor(x, dtype=s.dtype, device="cuda")
+    q = [0.0, 0.025, 0.16, 0.5, 0.84, 0.975, 1.0]
+    out = s.quantiles(xt, q)
+    ref = O.quantiles(xt.double().cpu().numpy(), q)
+    assert np.allclose(out, ref, rtol=1e-12, atol=1e-12)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_credible_metric_matches_oracle(prec):
+    from paper_2606_04895_gb300 import Sampler
+    d, n_chains, n = 5, 96, 200
+    s = Sampler(d, n_chains, precision=prec, likelihood="emulator")
+    x = np.random.default_rng(8).normal(size=(n, n_chains, d)) * 2.0 + 1.0
+    xt = torch.as_tensor(x, dtype=s.dtype, device="cuda")
+    lo0, hi0 = np.full(d, 1.0 - 2.0), np.full(d, 1.0 + 2.0)  # the true 68 % limits, about +-1 sd
+    for alpha in (0.68, 0.95):
+        cm = s.credible_metric(xt, alpha, lo0, hi0)
+        ref = O.credible_metric(xt.double().cpu().numpy(), alpha, lo0, hi0)
+        assert np.allclose(cm, ref, rtol=1e-10, atol=1e-12)
+    s.close()
