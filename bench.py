@@ -309,6 +309,28 @@ def extras(torch, device, seed, eps_mala, K):
     out["analytic_fp32"] = {"evals_per_s": ka * N_CHAINS / t, "min_ess_per_s": float(a.ess(x).min()) / t,
                             "flop_per_eval": 4 * 256 * (32 + 8)}
     a.close()
+    # convergence metrics of Sec. 4.1 against a known truth: the linear 6-D target, whose
+    # posterior is exactly Gaussian (closed-form mean and covariance), MALA on 4096 chains
+    tl = S.target(6, linear=True, seed=0, n_data=64)
+    J = tl["A"] @ tl["B"]
+    pcov = np.linalg.inv(J.T @ J / tl["sigma"] ** 2)
+    pmean = pcov @ (J.T @ (tl["data"] - tl["A"] @ tl["c"])) / tl["sigma"] ** 2
+    psd = np.sqrt(np.diag(pcov))
+    lin = learn.analytic_sampler(tl, n_chains=N_CHAINS, precision="fp32", seed=seed)
+    lin.init_chains(pmean + 3.0 * S.chains_init(N_CHAINS, 6, seed=4) @ np.linalg.cholesky(pcov).T, tl["lower"],
+                    tl["upper"], mu=pmean, L=np.linalg.cholesky(pcov))
+    lin.step("mala", 400, eps=0.5, stats=False)
+    kl = 2000
+    x = torch.empty((kl, N_CHAINS, 6), dtype=torch.float32, device="cuda")
+    t = time_steps(torch, lin, "mala", kl, 0.5, samples=x)
+    out["metrics_linear_6d"] = {
+        "chains": N_CHAINS, "steps": kl, "evals_per_s": kl * N_CHAINS / t, "r_minus_1": lin.r_minus_1(x),
+        "credible_metric_68": float(lin.credible_metric(x, 0.68, pmean - 0.994457883 * psd,
+                                                        pmean + 0.994457883 * psd).max()),
+        "credible_metric_95": float(lin.credible_metric(x, 0.95, pmean - 1.959963985 * psd,
+                                                        pmean + 1.959963985 * psd).max()),
+        "truth": "closed-form Gaussian posterior of the linear target"}
+    lin.close()
     # training throughput of the hand-written FP32 training kernels (batch 4096, 8-512x4-1)
     s, _ = make_sampler("bf16", 8, seed, device)
     X = torch.rand((4096, D), device="cuda") * 6 - 3

@@ -98,3 +98,28 @@ def test_bf16_emulator_chains_cover_their_target():
     (m1, s1), (m2, s2) = res["bf16"], res["fp64"]
     z = (m1 - m2) / np.sqrt(s1 ** 2 + s2 ** 2)
     assert np.all(np.abs(z) < 5), z
+
+
+def test_convergence_metrics_on_sampler_output():
+    """R - 1 and the credible metric (Sec. 4.1) of MALA draws on the linear target against its
+    exact Gaussian posterior: near zero after mixing; R - 1 large for dispersed, unmixed starts."""
+    from paper_2606_04895_gb300 import Sampler
+    t, mean, cov = _closed_form()
+    Lp = np.linalg.cholesky(cov)
+    sd = np.sqrt(np.diag(cov))
+    n, steps = 256, 2000
+    s = Sampler(6, n, precision="fp32", likelihood="analytic", seed=23)
+    s.set_analytic(t["A"], t["B"], t["c"], t["data"], t["sigma"], linear=True)
+    theta0 = mean + 4.0 * S.chains_init(n, 6, seed=4) @ Lp.T
+    s.init_chains(theta0, t["lower"], t["upper"], mu=mean, L=Lp)
+    first = torch.empty((3, n, 6), dtype=s.dtype, device="cuda")
+    s.step("mala", 3, eps=0.5, samples=first)
+    assert s.r_minus_1(first) > 1.0  # three steps from dispersed starts: not mixed
+    out = torch.empty((steps, n, 6), dtype=s.dtype, device="cuda")
+    s.step("mala", steps, eps=0.5, samples=out)
+    x = out[steps // 5:].contiguous()
+    assert s.r_minus_1(x) < 0.02
+    for alpha, z in ((0.68, 0.994457883), (0.95, 1.959963985)):  # Phi^-1((1 + alpha) / 2)
+        cm = s.credible_metric(x, alpha, mean - z * sd, mean + z * sd)
+        assert np.all(cm < 0.1), cm
+    s.close()
