@@ -200,6 +200,14 @@ bst_status bst_set_state(bst_handle h, const double *z, const double *logp, cons
                          const uint32_t *iter);
 /* Current whitening (mu[d], L[d][d]); synchronises. */
 bst_status bst_get_whitening(bst_handle h, double *mu, double *L);
+
+/* Replace the whitening x = mu + L z (Algorithm 1) of initialised chains: mu host double[d],
+ * L host double[d][d] row-major, lower triangular with a positive diagonal (the upper
+ * triangle is ignored).  Every chain keeps its x (z is remapped), layer 1 is refolded and
+ * log pi and its gradient are recomputed.  Per-dimension step multipliers m (a step of
+ * eps m_i along whitened direction i) are the whitening L diag(m).  BST_ERR_ARG for a
+ * non-finite mu or an invalid L, BST_ERR_STATE before bst_init_chains.  Synchronises. */
+bst_status bst_set_whitening(bst_handle h, const double *mu, const double *L);
 /* Per-chain counters since bst_init_chains (host arrays, each n_chains long,
  * any may be NULL).  Synchronises. */
 bst_status bst_get_counters(bst_handle h, int64_t *accepts, int64_t *evals, int64_t *divergences,

@@ -239,6 +239,17 @@ class Sampler:
         _lib.check(self.lib.bst_ess(self.h, C.c_void_p(samples.data_ptr()), samples.shape[0], _p(out)))
         return out
 
+    def set_whitening(self, mu, L):
+        """New whitening x = mu + L z for the chains (their x is kept; z remapped)."""
+        mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(self.d)
+        L = np.ascontiguousarray(L, dtype=np.float64).reshape(self.d, self.d)
+        _lib.check(self.lib.bst_set_whitening(self.h, _p(mu), _p(L)))
+
+    def set_step_multipliers(self, m):
+        """Step sizes eps m_i along the whitened directions: the whitening L diag(m)."""
+        mu, L = self.whitening()
+        self.set_whitening(mu, L * np.asarray(m, dtype=np.float64)[None, :])
+
     def r_minus_1(self, samples):
         """Multivariate Gelman-Rubin R - 1 (Sec. 4.1) of samples[n_draws][n_chains][d] (NaN
         when undefined)."""

@@ -931,6 +931,34 @@ bst_status bst_adapt_cov(bst_handle h, double jitter0, double *mu_out, double *L
   return check_status(h);
 }
 
+bst_status bst_set_whitening(bst_handle h, const double *mu, const double *L) {
+  if (!h || !mu || !L) return fail(BST_ERR_ARG, "bst_set_whitening: NULL argument");
+  if (h->stage < 2) return fail(BST_ERR_STATE, "bst_set_whitening: call bst_init_chains first");
+  const int d = h->d;
+  for (int i = 0; i < d; ++i) {
+    if (!std::isfinite(mu[i]) || !(L[i * d + i] > 0.0) || !std::isfinite(L[i * d + i]))
+      return fail(BST_ERR_ARG, "bst_set_whitening: mu must be finite and L lower triangular with positive diagonal");
+    for (int j = 0; j < i; ++j)
+      if (!std::isfinite(L[i * d + j])) return fail(BST_ERR_ARG, "bst_set_whitening: L not finite");
+  }
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_CUDA(cudaDeviceSynchronize());
+  BST_TRY(check_status(h));
+  std::vector<double> Ll(static_cast<size_t>(d) * d, 0.0);  // lower triangle only
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j <= i; ++j) Ll[i * d + j] = L[i * d + j];
+  BST_CUDA(cudaMemcpy(h->mu64_new, mu, d * 8, cudaMemcpyHostToDevice));
+  BST_CUDA(cudaMemcpy(h->L64_new, Ll.data(), static_cast<size_t>(d) * d * 8, cudaMemcpyHostToDevice));
+  // keep x fixed: z_new = L_new^-1 (mu_old + L_old z_old - mu_new), as after adaptation
+  if (h->rs == 8) BST_CUDA(launch_remap_f64((double *)h->z, h->n, d, h->dp, h->mu64, h->L64, h->mu64_new, h->L64_new, 0));
+  else BST_CUDA(launch_remap_f32((float *)h->z, h->n, d, h->dp, h->mu64, h->L64, h->mu64_new, h->L64_new, 0));
+  BST_CUDA(cudaDeviceSynchronize());
+  BST_TRY(set_target(h, mu, Ll.data()));
+  BST_TRY(refresh(h, 0));
+  BST_CUDA(cudaDeviceSynchronize());
+  return check_status(h);
+}
+
 bst_status bst_get_state(bst_handle h, double *z, double *logp, double *grad, uint32_t *iter) {
   if (!h) return fail(BST_ERR_ARG, "bst_get_state: NULL handle");
   if (h->stage < 2) return fail(BST_ERR_STATE, "bst_get_state: no chain state");

@@ -277,3 +277,33 @@ def test_credible_metric_matches_oracle(prec):
         ref = O.credible_metric(xt.double().cpu().numpy(), alpha, lo0, hi0)
         assert np.allclose(cm, ref, rtol=1e-10, atol=1e-12)
     s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("fp32", 2e-5)])
+def test_set_whitening_keeps_x_and_shifts_log_pi_by_log_det(prec, tol):
+    """A new whitening keeps every chain's x; log pi_z changes by log|det L_new| - log|det L_old|
+    (Algorithm 1), and grad_z by L_new^T L_old^-T."""
+    from paper_2606_04895_gb300 import BstError
+    s, e, mu, L, lo, up = _small(prec, n=96)
+    st0 = s.get_state()
+    x0 = mu + st0["z"] @ L.T
+    rng = np.random.default_rng(11)
+    mu2 = mu + 0.05 * rng.normal(size=mu.size)
+    L2 = np.tril(0.3 * rng.normal(size=L.shape)) + np.diag(np.full(mu.size, 0.6))
+    s.set_whitening(mu2, L2)
+    st1 = s.get_state()
+    m, Lw = s.whitening()
+    assert np.allclose(m, mu2) and np.allclose(Lw, L2)
+    x1 = mu2 + st1["z"] @ L2.T
+    assert np.max(np.abs(x1 - x0)) < tol * 10
+    fin = np.isfinite(st0["logp"])
+    dld = np.sum(np.log(np.diag(L2))) - np.sum(np.log(np.diag(L)))
+    assert np.allclose(st1["logp"][fin] - st0["logp"][fin], dld, rtol=0, atol=tol * max(1.0, np.abs(st0["logp"]).max()))
+    gx = np.linalg.solve(L.T, st0["grad"].T).T  # grad_x = L^-T grad_z
+    assert np.allclose(st1["grad"][fin], (gx @ L2)[fin], rtol=0, atol=tol * 10 * max(1.0, np.abs(gx @ L2).max()))
+    # step multipliers are the whitening L diag(m)
+    s.set_step_multipliers(np.arange(1, mu.size + 1))
+    assert np.allclose(s.whitening()[1], L2 * np.arange(1, mu.size + 1)[None, :])
+    with pytest.raises(BstError):
+        s.set_whitening(mu2, np.zeros_like(L2))
+    s.close()
