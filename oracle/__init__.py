@@ -35,6 +35,8 @@ MH, MALA, HMC, NUTS, AIES = 0, 1, 2, 3, 4
 KERNELS = {"mh": MH, "mala": MALA, "hmc": HMC, "nuts": NUTS, "aies": AIES}
 LIK_EMULATOR, LIK_ANALYTIC = 0, 1
 P_XI, P_ACCEPT, P_NUTS_DIR, P_NUTS_SEL, P_NUTS_TOP, P_AIES_PARTNER, P_AIES_Z = 1, 2, 3, 4, 5, 6, 7
+P_INIT = 8  # initial walker positions
+INIT_REPEATED, INIT_UNIFORM, INIT_GAUSSIAN = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -332,6 +334,25 @@ def r_minus_1(samples):
     Wt = W / np.outer(dB, dB)
     lam = np.linalg.eigvals(np.linalg.solve(Wt, Bt))
     return float(np.max(np.abs(lam)))
+
+
+def draw_positions(strategy, seed, n, d, *, center=None, Lc=None, lower=None, upper=None):
+    """Initial walker positions (the initialisation strategies of Sec. 3.1): REPEATED every
+    chain at `center`; UNIFORM lower + (upper - lower) u with u the uniforms 0..d-1 of stream
+    (chain, 0, P_INIT); GAUSSIAN center + Lc xi with xi the normals 0..d-1 of that stream.
+    Returns theta[n][d]."""
+    out = np.zeros((n, d))
+    for c in range(n):
+        if strategy == INIT_REPEATED:
+            out[c] = _f64(center)
+        elif strategy == INIT_UNIFORM:
+            u = np.array([uniform(seed, c, 0, P_INIT, i) for i in range(d)])
+            out[c] = _f64(lower) + (_f64(upper) - _f64(lower)) * u
+        elif strategy == INIT_GAUSSIAN:
+            out[c] = _f64(center) + _f64(Lc) @ normals(seed, c, 0, P_INIT, d)
+        else:
+            raise ValueError("unknown strategy")
+    return out
 
 
 def quantiles(samples, q):

@@ -76,3 +76,24 @@ def test_credible_metric_worked_example():
     # exact limits give zero; scaling draws and limits together leaves the metric unchanged
     assert O.credible_metric(x, 0.68, [16.0], [84.0])[0] == pytest.approx(0.0, abs=1e-12)
     assert O.credible_metric(3 * x, 0.68, [60.0], [240.0])[0] == pytest.approx(8.0 / 60.0, rel=1e-12)
+
+
+def test_initial_positions_of_each_strategy():
+    """Sec. 3.1 initialisation strategies: repeated = the centre exactly; uniform draws inside
+    the box with the uniform law's mean and variance; Gaussian draws with covariance Lc Lc^T."""
+    n, d = 20000, 3
+    c = np.array([0.5, -1.0, 2.0])
+    rep = O.draw_positions(O.INIT_REPEATED, 7, 5, d, center=c)
+    assert np.array_equal(rep, np.tile(c, (5, 1)))
+    lo, hi = np.array([-3.0, 0.0, 1.0]), np.array([3.0, 1.0, 5.0])
+    u = O.draw_positions(O.INIT_UNIFORM, 7, n, d, lower=lo, upper=hi)
+    assert np.all(u > lo) and np.all(u < hi)
+    se = (hi - lo) / np.sqrt(12 * n)
+    assert np.all(np.abs(u.mean(axis=0) - (lo + hi) / 2) < 5 * se)
+    assert np.allclose(u.var(axis=0), (hi - lo) ** 2 / 12, rtol=0.05)
+    Lc = np.array([[1.0, 0, 0], [0.5, 2.0, 0], [-0.3, 0.2, 0.5]])
+    g = O.draw_positions(O.INIT_GAUSSIAN, 7, n, d, center=c, Lc=Lc)
+    assert np.allclose(g.mean(axis=0), c, atol=5 * np.sqrt(np.diag(Lc @ Lc.T) / n))
+    assert np.allclose(np.cov(g, rowvar=False), Lc @ Lc.T, atol=0.08)
+    # a chain's draw depends on the seed and on its index only
+    assert np.array_equal(O.draw_positions(O.INIT_UNIFORM, 7, 3, d, lower=lo, upper=hi), u[:3])
