@@ -201,6 +201,16 @@ bst_status bst_set_state(bst_handle h, const double *z, const double *logp, cons
 /* Current whitening (mu[d], L[d][d]); synchronises. */
 bst_status bst_get_whitening(bst_handle h, double *mu, double *L);
 
+/* Initial walker positions by one of the strategies of Sec. 3.1, drawn on the device from
+ * this handle's counter-based random streams (stream (chain, 0, 8)), FP64: REPEATED every
+ * chain at center; UNIFORM lower + (upper - lower) u (finite bounds, upper > lower);
+ * GAUSSIAN center + Lc xi, xi ~ N(0, I) (Lc host double[d][d] row-major).  theta_out: host
+ * double[n_chains][d], to pass to bst_init_chains.  A chain's draw depends only on the seed
+ * and its index.  Synchronises. */
+typedef enum { BST_INIT_REPEATED = 0, BST_INIT_UNIFORM = 1, BST_INIT_GAUSSIAN = 2 } bst_init_strategy;
+bst_status bst_draw_positions(bst_handle h, int strategy, const double *center, const double *Lc,
+                              const double *lower, const double *upper, double *theta_out);
+
 /* Replace the whitening x = mu + L z (Algorithm 1) of initialised chains: mu host double[d],
  * L host double[d][d] row-major, lower triangular with a positive diagonal (the upper
  * triangle is ignored).  Every chain keeps its x (z is remapped), layer 1 is refolded and

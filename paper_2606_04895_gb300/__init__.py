@@ -239,6 +239,20 @@ class Sampler:
         _lib.check(self.lib.bst_ess(self.h, C.c_void_p(samples.data_ptr()), samples.shape[0], _p(out)))
         return out
 
+    INIT_STRATEGIES = {"repeated": 0, "uniform": 1, "gaussian": 2}
+
+    def draw_positions(self, strategy, *, center=None, L=None, lower=None, upper=None):
+        """Initial positions theta[n_chains][d] by a strategy of Sec. 3.1 ("repeated",
+        "uniform" in [lower, upper], "gaussian" center + L xi), drawn on the device."""
+        def arr(v, shape):
+            return None if v is None else np.ascontiguousarray(v, dtype=np.float64).reshape(shape)
+        c, Lc, lo, up = arr(center, self.d), arr(L, (self.d, self.d)), arr(lower, self.d), arr(upper, self.d)
+        out = np.zeros((self.n, self.d))
+        ptr = lambda v: None if v is None else _p(v)
+        _lib.check(self.lib.bst_draw_positions(self.h, self.INIT_STRATEGIES[strategy], ptr(c), ptr(Lc), ptr(lo),
+                                               ptr(up), _p(out)))
+        return out
+
     def set_whitening(self, mu, L):
         """New whitening x = mu + L z for the chains (their x is kept; z remapped)."""
         mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(self.d)

@@ -105,6 +105,7 @@ struct bst_ctx {
   int ess_tmp_cap = 0;
   double *ess_mean = nullptr, *ess_var = nullptr, *ess_V = nullptr;
   double *rhat_part = nullptr;  // [blocks][d (d + 1) / 2] pooled cross products (R - 1)
+  double *init_par = nullptr, *init_theta = nullptr;  // initial positions: parameters, [n][d] draws
   void *qsel_prefix = nullptr;    // [d][2 kMaxQuantiles] radix-select prefixes (quantiles)
   unsigned int *qsel_hist = nullptr;  // [d][2 kMaxQuantiles][16]
 };
@@ -929,6 +930,46 @@ bst_status bst_adapt_cov(bst_handle h, double jitter0, double *mu_out, double *L
   if (L_out) std::memcpy(L_out, L.data(), static_cast<size_t>(d) * d * 8);
   if (jitter_used) *jitter_used = info[1];
   return check_status(h);
+}
+
+bst_status bst_draw_positions(bst_handle h, int strategy, const double *center, const double *Lc, const double *lower,
+                              const double *upper, double *theta_out) {
+  if (!h || !theta_out) return fail(BST_ERR_ARG, "bst_draw_positions: NULL argument");
+  const int n = h->n, d = h->d;
+  std::vector<double> par(static_cast<size_t>(3 + kMaxD) * kMaxD, 0.0);
+  if (strategy == BST_INIT_REPEATED || strategy == BST_INIT_GAUSSIAN) {
+    if (!center) return fail(BST_ERR_ARG, "bst_draw_positions: center required");
+    for (int i = 0; i < d; ++i) {
+      if (!std::isfinite(center[i])) return fail(BST_ERR_ARG, "bst_draw_positions: center not finite");
+      par[i] = center[i];
+    }
+  }
+  if (strategy == BST_INIT_UNIFORM) {
+    if (!lower || !upper) return fail(BST_ERR_ARG, "bst_draw_positions: bounds required");
+    for (int i = 0; i < d; ++i) {
+      if (!std::isfinite(lower[i]) || !std::isfinite(upper[i]) || !(upper[i] > lower[i]))
+        return fail(BST_ERR_ARG, "bst_draw_positions: need finite bounds with upper > lower");
+      par[kMaxD + i] = lower[i];
+      par[2 * kMaxD + i] = upper[i];
+    }
+  }
+  if (strategy == BST_INIT_GAUSSIAN) {
+    if (!Lc) return fail(BST_ERR_ARG, "bst_draw_positions: Lc required");
+    for (int i = 0; i < d * d; ++i) {
+      if (!std::isfinite(Lc[i])) return fail(BST_ERR_ARG, "bst_draw_positions: Lc not finite");
+      par[3 * kMaxD + i] = Lc[i];
+    }
+  }
+  if (strategy < BST_INIT_REPEATED || strategy > BST_INIT_GAUSSIAN) return fail(BST_ERR_ARG, "bst_draw_positions: unknown strategy");
+  BST_CUDA(cudaSetDevice(h->device));
+  if (!h->init_par) {
+    BST_TRY(dalloc_t(h, &h->init_par, par.size()));
+    BST_TRY(dalloc_t(h, &h->init_theta, static_cast<size_t>(n) * d));
+  }
+  BST_CUDA(cudaMemcpy(h->init_par, par.data(), par.size() * 8, cudaMemcpyHostToDevice));
+  BST_CUDA(launch_init_positions(strategy, h->seed, n, d, h->init_par, h->init_theta, 0));
+  BST_CUDA(cudaMemcpy(theta_out, h->init_theta, static_cast<size_t>(n) * d * 8, cudaMemcpyDeviceToHost));
+  return BST_OK;
 }
 
 bst_status bst_set_whitening(bst_handle h, const double *mu, const double *L) {

@@ -29,6 +29,7 @@ enum Purpose : uint32_t {
   kNutsTop = 5,      // top-level progressive selection
   kAiesPartner = 6,  // partner walker
   kAiesZ = 7         // stretch factor
+  // (8: initial walker positions, drawn by init_positions_kernel)
 };
 
 // Launch modes of the chain-tile kernels.

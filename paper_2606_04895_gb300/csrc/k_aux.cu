@@ -496,6 +496,39 @@ __global__ void ess_moments_kernel(const R *x, int n, int M, int d, double *mean
   var[s] = ss / (n - 1);
 }
 // ------------------------------------------------------------------------------------------
+// Initial walker positions (the initialisation strategies of Sec. 3.1), one thread per chain, in
+// FP64 from stream (chain, 0, kInit): 0 every chain at `center`; 1 lower + (upper - lower) u with
+// the uniforms 0..d-1; 2 center + Lc xi with the normals 0..d-1 (Lc row-major d x d).  par holds
+// center, lower, upper (kMaxD each) and Lc (kMaxD x kMaxD).
+constexpr uint32_t kInit = 8;  // Philox purpose of the initial positions (after those of common.cuh)
+__global__ void init_positions_kernel(int strategy, uint64_t seed, int n, int d, const double *par, double *theta) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const double *center = par, *lower = par + kMaxD, *upper = par + 2 * kMaxD, *Lc = par + 3 * kMaxD;
+  double *out = theta + static_cast<size_t>(c) * d;
+  if (strategy == 1) {
+    for (int i = 0; i < d; ++i)
+      out[i] = lower[i] + (upper[i] - lower[i]) * draw_uniform<double>(seed, static_cast<uint32_t>(c), 0u, kInit,
+                                                                      static_cast<uint32_t>(i));
+  } else if (strategy == 2) {
+    double xi[kMaxD];
+    draw_normals<double>(seed, static_cast<uint32_t>(c), 0u, kInit, d, xi);
+    for (int i = 0; i < d; ++i) {
+      double s = center[i];
+      for (int j = 0; j < d; ++j) s += Lc[i * d + j] * xi[j];
+      out[i] = s;
+    }
+  } else {
+    for (int i = 0; i < d; ++i) out[i] = center[i];
+  }
+}
+cudaError_t launch_init_positions(int strategy, uint64_t seed, int n, int d, const double *par, double *theta,
+                                  cudaStream_t s) {
+  init_positions_kernel<<<blocks_for(static_cast<size_t>(n), 128), 128, 0, s>>>(strategy, seed, n, d, par, theta);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
 // R - 1 (Sec. 4.1): pooled within-chain cross products S_ij = sum_c sum_t (x_tci - m_ci)(x_tcj - m_cj)
 // for the chains of one block (kRhatChains of them), FP64; one partial per block and pair
 // i <= j (pair p = i * d - i (i - 1) / 2 + j - i), summed over blocks in order on the host.

@@ -74,6 +74,8 @@ cudaError_t launch_rhat_cross_f32(const float *x, int n, int M, int d, const dou
 cudaError_t launch_rhat_cross_f64(const double *x, int n, int M, int d, const double *mean, double *partial,
                                   cudaStream_t s);
 int rhat_blocks(int M);
+cudaError_t launch_init_positions(int strategy, uint64_t seed, int n, int d, const double *par, double *theta,
+                                  cudaStream_t s);
 cudaError_t launch_qsel_hist_f32(const float *x, size_t n_elems, int d, int jpd, const uint32_t *prefix, int shift,
                                  unsigned int *hist, cudaStream_t s);
 cudaError_t launch_qsel_hist_f64(const double *x, size_t n_elems, int d, int jpd, const unsigned long long *prefix,

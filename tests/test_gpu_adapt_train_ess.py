@@ -307,3 +307,26 @@ def test_set_whitening_keeps_x_and_shifts_log_pi_by_log_det(prec, tol):
     with pytest.raises(BstError):
         s.set_whitening(mu2, np.zeros_like(L2))
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_draw_positions_match_oracle(prec):
+    """Initial positions of the three strategies of Sec. 3.1 drawn on the device against the
+    oracle's draws from the same Philox streams (uniform draws bit for bit; Gaussian to
+    rounding of the Box-Muller transcendentals), then usable by init_chains."""
+    from paper_2606_04895_gb300 import BstError, Sampler
+    d, n, seed = 5, 300, 21
+    s = Sampler(d, n, precision=prec, likelihood="emulator", seed=seed)
+    c = np.array([0.3, -0.2, 1.0, 0.0, -1.5])
+    lo, hi = np.full(d, -3.0), np.array([3.0, 2.0, 3.0, 1.0, 0.5])
+    Lc = np.tril(np.random.default_rng(2).normal(size=(d, d))) * 0.3 + 0.5 * np.eye(d)
+    rep = s.draw_positions("repeated", center=c)
+    assert np.array_equal(rep, np.tile(c, (n, 1)))
+    u = s.draw_positions("uniform", lower=lo, upper=hi)
+    assert np.array_equal(u, O.draw_positions(O.INIT_UNIFORM, seed, n, d, lower=lo, upper=hi))
+    g = s.draw_positions("gaussian", center=c, L=Lc)
+    ref = O.draw_positions(O.INIT_GAUSSIAN, seed, n, d, center=c, Lc=Lc)
+    assert np.max(np.abs(g - ref)) < 1e-12
+    with pytest.raises(BstError):
+        s.draw_positions("uniform", lower=hi, upper=lo)
+    s.close()
