@@ -330,3 +330,18 @@ def test_draw_positions_match_oracle(prec):
     with pytest.raises(BstError):
         s.draw_positions("uniform", lower=hi, upper=lo)
     s.close()
+
+
+def test_burn_in_driver_adapts_whitening_and_step_size():
+    """The burn-in driver on the library: two adaptation iterations change the whitening, and
+    the adapted step size gives an acceptance statistic near the 0.65 target."""
+    from paper_2606_04895_gb300 import driver
+    s, e, mu, L, lo, up = _small("fp32", n=128)
+    _, L0 = s.whitening()
+    eps, hist = driver.burn_in(s, "mala", eps0=0.2, n_iter=2, adapt_steps=200, chunk=40, cov_steps=200)
+    _, L1 = s.whitening()
+    assert np.isfinite(eps) and eps > 0 and len(hist) == 2
+    assert not np.allclose(L1, L0)
+    st = s.step("mala", 200, eps=eps)
+    assert 0.3 < st["accept_stat"] < 0.95, st
+    s.close()
