@@ -6,7 +6,7 @@ paper Sec. 1 and Sec. 4: a neural-network likelihood that replaces the
 parameter-to-likelihood pipeline) is then fitted with the library's own
 forward / backward / Adam kernels (bst_train_step): MSE on the standardised
 chi^2, Adam (Kingma & Ba) on FP32 master weights, batches of 4096.  The
-analytic likelihood stays available as the judge of the emulator's error
+analytic likelihood stays available to measure the emulator's error
 along sampled chains.
 
 Only argument marshalling and batching happen here; every evaluation,
