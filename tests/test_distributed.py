@@ -99,3 +99,52 @@ def test_two_rank_adaptation_and_reductions():
         assert np.allclose(g, 1.5)
     # bit-identical on both ranks
     assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][2], res[1][2])
+
+
+class _FakeAcceptance:
+    """A stand-in sampler whose acceptance statistic falls with eps at a rank-dependent rate."""
+
+    def __init__(self, rate, n):
+        self.rate, self.n = rate, n
+
+    def step(self, kernel, n_steps, *, eps, stats=True, **kw):
+        return {"accept_stat": float(np.exp(-eps / self.rate))} if stats else None
+
+
+def _driver_worker(rank, world, port, q):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2606_04895_gb300 import distributed as D
+    from paper_2606_04895_gb300 import driver
+    s = _FakeAcceptance(0.4 + 0.2 * rank, 64 * (rank + 1))
+    eps = driver.dual_average_eps(s, "mala", 0.5, n_iter=150, chunk=20, target=0.65,
+                                  mean_accept=lambda st, chunk: D.mean_accept(st, s.n, chunk))
+    q.put((rank, eps))
+    dist.destroy_process_group()
+
+
+def test_two_rank_step_size_adaptation_agrees():
+    """The burn-in driver's dual averaging on the acceptance statistic pooled over ranks gives
+    every rank the same step size, the one of the chain-weighted mean acceptance curve."""
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_driver_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted([q.get(timeout=120) for _ in ps], key=lambda t: t[0])
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][1] == res[1][1]
+    # the pooled curve (64 chains at rate 0.4, 128 at rate 0.6) crosses 0.65 at eps*
+    f = lambda e: (64 * np.exp(-e / 0.4) + 128 * np.exp(-e / 0.6)) / 192 - 0.65
+    lo, hi = 0.0, 2.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if f(mid) > 0 else (lo, mid)
+    assert res[0][1] == pytest.approx(lo, rel=0.06)
