@@ -36,6 +36,7 @@ KERNELS = {"mh": MH, "mala": MALA, "hmc": HMC, "nuts": NUTS, "aies": AIES}
 LIK_EMULATOR, LIK_ANALYTIC = 0, 1
 P_XI, P_ACCEPT, P_NUTS_DIR, P_NUTS_SEL, P_NUTS_TOP, P_AIES_PARTNER, P_AIES_Z = 1, 2, 3, 4, 5, 6, 7
 P_INIT = 8  # initial walker positions
+P_SWD = 9  # sliced-Wasserstein projection directions
 INIT_REPEATED, INIT_UNIFORM, INIT_GAUSSIAN = 0, 1, 2
 
 
@@ -353,6 +354,45 @@ def draw_positions(strategy, seed, n, d, *, center=None, Lc=None, lower=None, up
         else:
             raise ValueError("unknown strategy")
     return out
+
+
+def w1_1d(a, b):
+    """1-D Wasserstein-1 distance of two empirical distributions: the integral over t in (0, 1)
+    of |F^-1(t) - G^-1(t)|, the quantile functions being steps at multiples of 1/len(a) and
+    1/len(b); exact, by walking the merged breakpoints of the two sorted samples."""
+    a = np.sort(_f64(a).ravel())
+    b = np.sort(_f64(b).ravel())
+    na, nb = len(a), len(b)
+    i = j = 0
+    t = 0.0
+    total = 0.0
+    while i < na and j < nb:
+        ta, tb = (i + 1) / na, (j + 1) / nb
+        t_next = min(ta, tb)
+        total += (t_next - t) * abs(a[i] - b[j])
+        t = t_next
+        if ta <= t_next:
+            i += 1
+        if tb <= t_next:
+            j += 1
+    return total
+
+
+def swd_directions(seed, n_proj, d):
+    """Projection directions of the sliced Wasserstein distance: direction k is the normals
+    0..d-1 of stream (k, 0, P_SWD), normalised (uniform on the sphere); the same set is reused
+    for every comparison, as in Sec. 4.1."""
+    u = np.array([normals(seed, k, 0, P_SWD, d) for k in range(n_proj)])
+    return u / np.linalg.norm(u, axis=1, keepdims=True)
+
+
+def sliced_wasserstein(P, Q, *, n_proj=500, seed=0):
+    """Sliced Wasserstein distance (Sec. 4.1): the mean over the projection directions u_k of
+    the 1-D Wasserstein-1 distance between the projections P u_k and Q u_k (P[n][d], Q[m][d])."""
+    P = _f64(P).reshape(-1, np.shape(P)[-1])
+    Q = _f64(Q).reshape(-1, np.shape(Q)[-1])
+    U = swd_directions(seed, n_proj, P.shape[1])
+    return float(np.mean([w1_1d(P @ u, Q @ u) for u in U]))
 
 
 def quantiles(samples, q):

@@ -97,3 +97,39 @@ def test_initial_positions_of_each_strategy():
     assert np.allclose(np.cov(g, rowvar=False), Lc @ Lc.T, atol=0.08)
     # a chain's draw depends on the seed and on its index only
     assert np.array_equal(O.draw_positions(O.INIT_UNIFORM, 7, 3, d, lower=lo, upper=hi), u[:3])
+
+
+def test_w1_worked_examples():
+    # equal sizes: mean |sorted difference|
+    assert O.w1_1d([0.0, 3.0], [1.0, 1.0]) == pytest.approx((1.0 + 2.0) / 2, rel=1e-15)
+    # {0, 1} against {0, 0.5, 1}: the quantile functions differ by 1/2 on (1/3, 2/3): 1/6
+    assert O.w1_1d([0.0, 1.0], [0.0, 0.5, 1.0]) == pytest.approx(1.0 / 6.0, rel=1e-14)
+    # a shift by c moves every quantile by c
+    x = np.random.default_rng(1).normal(size=37)
+    assert O.w1_1d(x, x + 0.75) == pytest.approx(0.75, rel=1e-12)
+    # symmetric, zero on identical samples
+    y = np.random.default_rng(2).normal(size=53)
+    assert O.w1_1d(x, y) == pytest.approx(O.w1_1d(y, x), rel=1e-12)
+    assert O.w1_1d(y, y[::-1]) == 0.0
+
+
+def test_sliced_wasserstein_of_a_shift_and_of_identical_sets():
+    rng = np.random.default_rng(3)
+    P = rng.normal(size=(400, 4))
+    c = np.array([0.5, -1.0, 0.0, 2.0])
+    U = O.swd_directions(9, 64, 4)
+    assert np.allclose(np.linalg.norm(U, axis=1), 1.0)
+    # a shift by c: every projected quantile moves by c.u, so the distance is mean |c.u|
+    assert O.sliced_wasserstein(P, P + c, n_proj=64, seed=9) == pytest.approx(np.mean(np.abs(U @ c)), rel=1e-10)
+    assert O.sliced_wasserstein(P, P[::-1], n_proj=64, seed=9) == pytest.approx(0.0, abs=1e-15)
+    # directions uniform on the sphere S^3: E|u_i| = Gamma(2) / (sqrt(pi) Gamma(5/2)) = 4 / (3 pi)
+    big = O.swd_directions(9, 4000, 4)
+    assert np.abs(big).mean(axis=0) == pytest.approx(np.full(4, 4.0 / (3.0 * np.pi)), rel=0.04)
+
+
+def test_w1_against_scipy_for_unequal_sizes():
+    scipy_stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(4)
+    for na, nb in [(1, 1), (5, 3), (64, 100), (257, 31)]:
+        a, b = rng.normal(size=na), rng.gamma(2.0, size=nb)
+        assert O.w1_1d(a, b) == pytest.approx(scipy_stats.wasserstein_distance(a, b), rel=1e-12)
