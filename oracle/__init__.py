@@ -358,24 +358,18 @@ def draw_positions(strategy, seed, n, d, *, center=None, Lc=None, lower=None, up
 
 def w1_1d(a, b):
     """1-D Wasserstein-1 distance of two empirical distributions: the integral over t in (0, 1)
-    of |F^-1(t) - G^-1(t)|, the quantile functions being steps at multiples of 1/len(a) and
-    1/len(b); exact, by walking the merged breakpoints of the two sorted samples."""
+    of |F^-1(t) - G^-1(t)|.  With na, nb values the quantile functions step at multiples of
+    1/na and 1/nb; over the common denominator na nb the breakpoints are the integers T = i nb
+    and j na, and on the interval ending at T the quantile functions take the sorted values of
+    ranks ceil(T / nb) - 1 and ceil(T / na) - 1 (integer arithmetic: exact interval ends)."""
     a = np.sort(_f64(a).ravel())
     b = np.sort(_f64(b).ravel())
     na, nb = len(a), len(b)
-    i = j = 0
-    t = 0.0
-    total = 0.0
-    while i < na and j < nb:
-        ta, tb = (i + 1) / na, (j + 1) / nb
-        t_next = min(ta, tb)
-        total += (t_next - t) * abs(a[i] - b[j])
-        t = t_next
-        if ta <= t_next:
-            i += 1
-        if tb <= t_next:
-            j += 1
-    return total
+    T = np.union1d(np.arange(1, na + 1, dtype=np.int64) * nb, np.arange(1, nb + 1, dtype=np.int64) * na)
+    ia = (T + nb - 1) // nb - 1
+    ib = (T + na - 1) // na - 1
+    width = np.diff(np.concatenate(([0], T))) / (float(na) * float(nb))
+    return float(np.sum(width * np.abs(a[ia] - b[ib])))
 
 
 def swd_directions(seed, n_proj, d):

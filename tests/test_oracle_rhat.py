@@ -133,3 +133,24 @@ def test_w1_against_scipy_for_unequal_sizes():
     for na, nb in [(1, 1), (5, 3), (64, 100), (257, 31)]:
         a, b = rng.normal(size=na), rng.gamma(2.0, size=nb)
         assert O.w1_1d(a, b) == pytest.approx(scipy_stats.wasserstein_distance(a, b), rel=1e-12)
+
+
+def test_w1_equal_sizes_is_mean_sorted_difference_and_matches_transport_lp():
+    """Equal sizes: the mean absolute difference of the sorted samples (Sec. 4.1).  Unequal tiny
+    sizes: the optimal-transport linear program solved by brute force (scipy's LP solver)."""
+    rng = np.random.default_rng(5)
+    a, b = rng.normal(size=64), rng.exponential(size=64)
+    assert O.w1_1d(a, b) == pytest.approx(np.mean(np.abs(np.sort(a) - np.sort(b))), rel=1e-13)
+    optimize = pytest.importorskip("scipy.optimize")
+    a, b = rng.normal(size=4), rng.normal(size=6) + 0.4
+    na, nb = len(a), len(b)
+    cost = np.abs(a[:, None] - b[None, :]).ravel()
+    A_eq = np.zeros((na + nb, na * nb))
+    for i in range(na):
+        A_eq[i, i * nb:(i + 1) * nb] = 1.0
+    for j in range(nb):
+        A_eq[na + j, j::nb] = 1.0
+    b_eq = np.concatenate([np.full(na, 1.0 / na), np.full(nb, 1.0 / nb)])
+    lp = optimize.linprog(cost, A_eq=A_eq, b_eq=b_eq, bounds=(0, None), method="highs")
+    assert lp.success
+    assert O.w1_1d(a, b) == pytest.approx(lp.fun, rel=1e-9)
