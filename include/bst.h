@@ -278,6 +278,17 @@ bst_status bst_quantiles(bst_handle h, const void *samples_dev, int n_draws, con
 bst_status bst_credible_metric(bst_handle h, const void *samples_dev, int n_draws, double alpha,
                                const double *true_lo, const double *true_hi, double *out);
 
+/* Sliced Wasserstein distance (paper Sec. 4.1) between the pooled draws samples_dev
+ * real[n_draws][n_chains][d] and a reference set ref_dev real[n_ref][d] (both device memory,
+ * this handle's real type): the mean over n_proj directions u_k of the 1-D Wasserstein-1
+ * distance between the projections {x . u_k}, the 1-D distance being the integral of the
+ * absolute difference of the two empirical quantile functions (sizes may differ).  Direction
+ * k is the normals 0..d-1 of Philox stream (k, 0, 9) under `seed`, normalised, so a fixed
+ * seed reuses one set of directions for every comparison.  FP64 arithmetic; *out: host
+ * double.  n_draws n_chains + n_ref <= 2^27; draws must be finite.  Synchronises. */
+bst_status bst_sliced_wasserstein(bst_handle h, const void *samples_dev, int n_draws, const void *ref_dev,
+                                  long long n_ref, int n_proj, unsigned long long seed, double *out);
+
 /* Block until all work of h on ``stream`` is done and check the device status. */
 bst_status bst_sync(bst_handle h, void *stream);
 

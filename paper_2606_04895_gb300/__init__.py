@@ -291,6 +291,18 @@ class Sampler:
                                                 _p(lo), _p(hi), _p(out)))
         return out
 
+    def sliced_wasserstein(self, samples, reference, n_proj=500, seed=0):
+        """Sliced Wasserstein distance of Sec. 4.1 between the pooled draws samples[n_draws][n][d]
+        and reference[n_ref][d] (both CUDA tensors of this sampler's dtype), over n_proj
+        directions fixed by `seed`."""
+        self._check_dev(samples, (samples.shape[0], self.n, self.d))
+        self._check_dev(reference, (reference.shape[0], self.d))
+        out = C.c_double(0.0)
+        _lib.check(self.lib.bst_sliced_wasserstein(self.h, C.c_void_p(samples.data_ptr()), samples.shape[0],
+                                                   C.c_void_p(reference.data_ptr()), reference.shape[0], int(n_proj),
+                                                   int(seed), C.byref(out)))
+        return out.value
+
     def sync(self, stream=None):
         _lib.check(self.lib.bst_sync(self.h, _stream_ptr(stream)))
 

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI declared in include/bst.h: handle, validation, device memory of the
 // library-owned state, weight preparation and the launches of the sampling kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1373,6 +1374,79 @@ bst_status bst_credible_metric(bst_handle h, const void *samples_dev, int n_draw
   BST_TRY(bst_quantiles(h, samples_dev, n_draws, q, 2, lim.data()));
   for (int i = 0; i < d; ++i)
     out[i] = (std::fabs(lim[2 * i + 1] - true_hi[i]) + std::fabs(lim[2 * i] - true_lo[i])) / (true_hi[i] - true_lo[i]);
+  return BST_OK;
+}
+
+// Sliced Wasserstein distance: directions, then per chunk of directions the projections of the
+// draws and the reference set side by side (segment 2k: draws, 2k + 1: reference), a
+// segmented sort and the per-direction 1-D distances; the mean over directions on the host.
+constexpr long long kSwdChunkElems = 1LL << 27;  // projected values per chunk (1 GiB in FP64)
+extern "C++" {
+namespace {
+struct DevScratch {  // call-local device buffer, freed on every return path
+  void *p = nullptr;
+  DevScratch() = default;
+  DevScratch(const DevScratch &) = delete;
+  DevScratch &operator=(const DevScratch &) = delete;
+  ~DevScratch() {
+    if (p) cudaFree(p);
+  }
+  template <typename T>
+  T *as() const {
+    return static_cast<T *>(p);
+  }
+};
+}  // namespace
+}  // extern "C++"
+
+bst_status bst_sliced_wasserstein(bst_handle h, const void *samples_dev, int n_draws, const void *ref_dev,
+                                  long long n_ref, int n_proj, unsigned long long seed, double *out) {
+  if (!h || !samples_dev || !ref_dev || !out) return fail(BST_ERR_ARG, "bst_sliced_wasserstein: NULL argument");
+  if (n_draws < 1 || n_ref < 1 || n_proj < 1)
+    return fail(BST_ERR_ARG, "bst_sliced_wasserstein: need n_draws, n_ref and n_proj >= 1");
+  const long long n = static_cast<long long>(n_draws) * h->n, m = n_ref, nm = n + m;
+  if (nm > kSwdChunkElems) return fail(BST_ERR_ARG, "bst_sliced_wasserstein: at most 2^27 draws and reference points");
+  BST_CUDA(cudaSetDevice(h->device));
+  const int d = h->d;
+  const int kc = static_cast<int>(std::min<long long>(n_proj, kSwdChunkElems / nm));
+  DevScratch U, proj, sorted, offs, w1, temp;
+  BST_CUDA(cudaMalloc(&U.p, static_cast<size_t>(n_proj) * d * 8));
+  BST_CUDA(cudaMalloc(&proj.p, static_cast<size_t>(kc) * nm * 8));
+  BST_CUDA(cudaMalloc(&sorted.p, static_cast<size_t>(kc) * nm * 8));
+  BST_CUDA(cudaMalloc(&offs.p, (2 * static_cast<size_t>(kc) + 1) * sizeof(int)));
+  BST_CUDA(cudaMalloc(&w1.p, static_cast<size_t>(n_proj) * 8));
+  std::vector<int> o(2 * static_cast<size_t>(kc) + 1);
+  for (int k = 0; k < kc; ++k) {
+    o[2 * k] = static_cast<int>(k * nm);
+    o[2 * k + 1] = static_cast<int>(k * nm + n);
+  }
+  o[2 * kc] = static_cast<int>(kc * nm);
+  BST_CUDA(cudaMemcpy(offs.p, o.data(), o.size() * sizeof(int), cudaMemcpyHostToDevice));
+  size_t temp_bytes = 0;
+  BST_CUDA(swd_sort_segments(nullptr, temp_bytes, proj.as<double>(), sorted.as<double>(), static_cast<int>(kc * nm),
+                             2 * kc, offs.as<int>(), 0));
+  BST_CUDA(cudaMalloc(&temp.p, temp_bytes > 0 ? temp_bytes : 1));
+  BST_CUDA(launch_swd_directions(seed, n_proj, d, U.as<double>(), 0));
+  for (int k0 = 0; k0 < n_proj; k0 += kc) {
+    const int nk = std::min(kc, n_proj - k0);
+    const double *Uk = U.as<double>() + static_cast<size_t>(k0) * d;
+    if (h->rs == 8) {
+      BST_CUDA(launch_swd_project_f64(static_cast<const double *>(samples_dev), n, d, Uk, nk, proj.as<double>(), nm, 0));
+      BST_CUDA(launch_swd_project_f64(static_cast<const double *>(ref_dev), m, d, Uk, nk, proj.as<double>() + n, nm, 0));
+    } else {
+      BST_CUDA(launch_swd_project_f32(static_cast<const float *>(samples_dev), n, d, Uk, nk, proj.as<double>(), nm, 0));
+      BST_CUDA(launch_swd_project_f32(static_cast<const float *>(ref_dev), m, d, Uk, nk, proj.as<double>() + n, nm, 0));
+    }
+    size_t tb = temp_bytes;
+    BST_CUDA(swd_sort_segments(temp.p, tb, proj.as<double>(), sorted.as<double>(), static_cast<int>(nk * nm), 2 * nk,
+                               offs.as<int>(), 0));
+    BST_CUDA(launch_swd_w1(sorted.as<double>(), n, m, nk, w1.as<double>() + k0, 0));
+  }
+  std::vector<double> w(n_proj);
+  BST_CUDA(cudaMemcpy(w.data(), w1.p, static_cast<size_t>(n_proj) * 8, cudaMemcpyDeviceToHost));
+  double sum = 0.0;
+  for (double v : w) sum += v;
+  *out = sum / n_proj;
   return BST_OK;
 }
 

@@ -81,6 +81,18 @@ cudaError_t launch_qsel_hist_f32(const float *x, size_t n_elems, int d, int jpd,
 cudaError_t launch_qsel_hist_f64(const double *x, size_t n_elems, int d, int jpd, const unsigned long long *prefix,
                                  int shift, unsigned int *hist, cudaStream_t s);
 cudaError_t launch_ess_moments_f64(const double *x, int n, int M, int d, double *mean, double *var, cudaStream_t s);
+
+// Sliced Wasserstein distance (k_swd.cu), FP64: directions U[n_proj][d]; projections
+// out[kk * ld + i] = X_i . U_kk; per-segment sorting (offsets[n_segments + 1], temp_bytes
+// queried with temp = nullptr); per-direction 1-D W1 of the sorted pair (a: n values, then b: m).
+cudaError_t launch_swd_directions(uint64_t seed, int n_proj, int d, double *U, cudaStream_t s);
+cudaError_t launch_swd_project_f32(const float *X, long long n_rows, int d, const double *U, int nk, double *out,
+                                   long long ld, cudaStream_t s);
+cudaError_t launch_swd_project_f64(const double *X, long long n_rows, int d, const double *U, int nk, double *out,
+                                   long long ld, cudaStream_t s);
+cudaError_t swd_sort_segments(void *temp, size_t &temp_bytes, const double *in, double *out, int n_items,
+                              int n_segments, const int *offsets, cudaStream_t s);
+cudaError_t launch_swd_w1(const double *sorted, long long n, long long m, int nk, double *w1, cudaStream_t s);
 cudaError_t launch_ess_variogram_f32(const float *x, int n, int M, int d, int t0, int nt, double *V, cudaStream_t s);
 cudaError_t launch_ess_variogram_f64(const double *x, int n, int M, int d, int t0, int nt, double *V, cudaStream_t s);
 

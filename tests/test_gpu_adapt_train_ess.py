@@ -345,3 +345,60 @@ def test_burn_in_driver_adapts_whitening_and_step_size():
     st = s.step("mala", 200, eps=eps)
     assert 0.3 < st["accept_stat"] < 0.95, st
     s.close()
+
+
+@pytest.mark.parametrize("prec,n_chains,d,n_draws,n_ref,n_proj", [
+    ("fp32", 64, 6, 31, 1000, 64),   # unequal sizes
+    ("fp64", 33, 27, 20, 660, 37),   # equal sizes, 27-D
+    ("fp32", 40, 1, 5, 77, 7),       # d = 1: projections +-x, many ties within and across the sets
+    ("fp64", 3, 2, 1, 1, 5),         # three draws against one reference point
+])
+def test_sliced_wasserstein_matches_oracle(prec, n_chains, d, n_draws, n_ref, n_proj):
+    """Sliced Wasserstein distance (Sec. 4.1) against the oracle on the same working-precision
+    values: the device integrates |F_a - F_b| over x on the merged sorted projections, the
+    oracle |F^-1 - G^-1| over t."""
+    from paper_2606_04895_gb300 import Sampler
+    s = Sampler(d, n_chains, precision=prec, likelihood="emulator")
+    rng = np.random.default_rng(12)
+    x = rng.normal(size=(n_draws, n_chains, d)) * np.linspace(0.5, 2.0, d)
+    r = rng.standard_t(5, size=(n_ref, d)) + 0.3
+    if d == 1:
+        x, r = np.round(x * 2) / 2, np.round(r * 2) / 2
+    xt = torch.as_tensor(x, dtype=s.dtype, device="cuda")
+    rt = torch.as_tensor(r, dtype=s.dtype, device="cuda")
+    got = s.sliced_wasserstein(xt, rt, n_proj=n_proj, seed=5)
+    ref = O.sliced_wasserstein(xt.double().cpu().numpy().reshape(-1, d), rt.double().cpu().numpy(), n_proj=n_proj,
+                               seed=5)
+    assert ref > 0
+    assert got == pytest.approx(ref, rel=1e-9)
+    assert s.sliced_wasserstein(xt, xt.reshape(-1, d).flip(0).contiguous(), n_proj=n_proj, seed=5) == 0.0
+    s.close()
+
+
+def test_sliced_wasserstein_of_a_shift_over_several_sorting_chunks():
+    """60,000 projected values per direction and 3,000 directions exceed one sorting chunk
+    (2^27 values): the distance between a set and its shift by c is mean_k |c . u_k| exactly,
+    u_k the oracle's directions."""
+    from paper_2606_04895_gb300 import Sampler
+    d, n_chains, n_draws = 5, 1000, 30
+    s = Sampler(d, n_chains, precision="fp64", likelihood="emulator")
+    rng = np.random.default_rng(13)
+    x = rng.normal(size=(n_draws, n_chains, d))
+    c = np.array([0.5, -1.0, 0.25, 2.0, 0.0])
+    xt = torch.as_tensor(x, dtype=torch.float64, device="cuda")
+    qt = torch.as_tensor(x.reshape(-1, d) + c, dtype=torch.float64, device="cuda")
+    got = s.sliced_wasserstein(xt, qt, n_proj=3000, seed=3)
+    U = O.swd_directions(3, 3000, d)
+    assert got == pytest.approx(float(np.mean(np.abs(U @ c))), rel=1e-10)
+    s.close()
+
+
+def test_sliced_wasserstein_rejects_bad_arguments():
+    from paper_2606_04895_gb300 import BstError, Sampler
+    s = Sampler(3, 8, precision="fp32", likelihood="emulator")
+    x = torch.zeros(2, 8, 3, device="cuda")
+    with pytest.raises(BstError):
+        s.sliced_wasserstein(x, torch.zeros(4, 3, device="cuda"), n_proj=0)
+    with pytest.raises(BstError):
+        s.sliced_wasserstein(x, torch.zeros(4, 2, device="cuda"))
+    s.close()
