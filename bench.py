@@ -257,6 +257,31 @@ def _emulator_target(d, n, precision, seed, device, width=WIDTH, depth=DEPTH, nu
     return s
 
 
+def swd_leg(torch, s, x, pmean, pcov, n_keep=25, n_ref=100_000, n_proj=500, seed=0):
+    """Sliced Wasserstein distance (Sec. 4.1) of the last n_keep draws of every chain (x[n][chains][d],
+    CUDA, the sampler's dtype) against n_ref exact draws of the Gaussian posterior N(pmean, pcov),
+    over n_proj directions; beside it the noise floor (an exact sample of the same size against the
+    same reference) and the host time of one (synchronising) library call."""
+    d = len(pmean)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    Lc = torch.as_tensor(np.linalg.cholesky(pcov), dtype=torch.float64, device="cuda")
+    mu = torch.as_tensor(pmean, dtype=torch.float64, device="cuda")
+
+    def exact(*shape):
+        z = torch.randn((*shape, d), generator=g, dtype=torch.float64, device="cuda")
+        return (mu + z @ Lc.T).to(x.dtype).contiguous()
+
+    ref, tail = exact(n_ref), x[-n_keep:].contiguous()
+    floor = s.sliced_wasserstein(exact(*tail.shape[:2]), ref, n_proj=n_proj, seed=seed)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    v = s.sliced_wasserstein(tail, ref, n_proj=n_proj, seed=seed)
+    dt = time.perf_counter() - t0
+    return {"value": v, "noise_floor": floor, "seconds": dt, "draws": tail.shape[0] * tail.shape[1],
+            "reference": n_ref, "directions": n_proj}
+
+
 def extras(torch, device, seed, eps_mala, K):
     """Other samplers / targets / paths at their configurations (reported beside the headline)."""
     out = {}
@@ -329,7 +354,8 @@ def extras(torch, device, seed, eps_mala, K):
                                                         pmean + 0.994457883 * psd).max()),
         "credible_metric_95": float(lin.credible_metric(x, 0.95, pmean - 1.959963985 * psd,
                                                         pmean + 1.959963985 * psd).max()),
-        "truth": "closed-form Gaussian posterior of the linear target"}
+        "truth": "closed-form Gaussian posterior of the linear target",
+        "sliced_wasserstein": swd_leg(torch, lin, x, pmean, pcov)}
     lin.close()
     # training throughput of the hand-written FP32 training kernels (batch 4096, 8-512x4-1)
     s, _ = make_sampler("bf16", 8, seed, device)

@@ -402,3 +402,20 @@ def test_sliced_wasserstein_rejects_bad_arguments():
     with pytest.raises(BstError):
         s.sliced_wasserstein(x, torch.zeros(4, 2, device="cuda"))
     s.close()
+
+
+def test_sliced_wasserstein_at_the_comparison_scale():
+    """The comparison scale of Sec. 4.1 (500 directions, 100,000 reference points) with 100 draws
+    of 1,000 chains of a 27-D target in FP32: a set against its shift by c gives mean_k |c . u_k|."""
+    from paper_2606_04895_gb300 import Sampler
+    d, n_chains, n_draws = 27, 1000, 100
+    s = Sampler(d, n_chains, precision="fp32", likelihood="emulator")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(14)
+    xt = torch.randn((n_draws, n_chains, d), generator=g, device="cuda")
+    c = np.linspace(-1.0, 1.0, d)
+    qt = (xt.reshape(-1, d) + torch.as_tensor(c, dtype=torch.float32, device="cuda")).contiguous()
+    got = s.sliced_wasserstein(xt, qt, n_proj=500, seed=0)
+    U = O.swd_directions(0, 500, d)
+    assert got == pytest.approx(float(np.mean(np.abs(U @ c))), rel=2e-5)
+    s.close()
