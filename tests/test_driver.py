@@ -52,3 +52,23 @@ def test_burn_in_with_pooled_callbacks():
                                mean_accept=lambda st, chunk: 0.65)
     assert seen == ["pooled"] and hist[0]["jitter"] is None
     assert not any(c[0] == "adapt_cov" for c in s.calls)
+
+
+def test_initial_whitening_is_the_box_centre_and_scaled_widths():
+    mu, L = driver.initial_whitening([-1.0, 0.0, 10.0], [3.0, 0.5, 30.0], frac=0.25)
+    assert np.array_equal(mu, [1.0, 0.25, 20.0])
+    assert np.array_equal(L, np.diag([1.0, 0.125, 5.0]))
+    with pytest.raises(ValueError):
+        driver.initial_whitening([0.0, 1.0], [1.0, 1.0])
+    with pytest.raises(ValueError):
+        driver.initial_whitening([0.0], [1.0], frac=0.0)
+
+
+def test_aies_burn_in_is_one_long_run_in_bounded_launches():
+    s = FakeSampler()
+    s.step = lambda kernel, n, stats=True, **kw: s.calls.append((kernel, n, stats))
+    assert driver.aies_burn_in(s, 20000, chunk=6000) == 20000
+    assert s.calls == [("aies", 6000, False)] * 3 + [("aies", 2000, False)]
+    assert driver.aies_burn_in(s, 0) == 0
+    with pytest.raises(ValueError):
+        driver.burn_in(FakeSampler(), "aies")
