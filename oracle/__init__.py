@@ -31,8 +31,8 @@ _SO = os.path.join(_BUILD, "liborc.so")
 _lock = threading.Lock()
 _lib = None
 
-MH, MALA, HMC, NUTS, AIES = 0, 1, 2, 3, 4
-KERNELS = {"mh": MH, "mala": MALA, "hmc": HMC, "nuts": NUTS, "aies": AIES}
+MH, MALA, HMC, NUTS, AIES, AIES_DE = 0, 1, 2, 3, 4, 5
+KERNELS = {"mh": MH, "mala": MALA, "hmc": HMC, "nuts": NUTS, "aies": AIES, "aies_de": AIES_DE}
 LIK_EMULATOR, LIK_ANALYTIC = 0, 1
 P_XI, P_ACCEPT, P_NUTS_DIR, P_NUTS_SEL, P_NUTS_TOP, P_AIES_PARTNER, P_AIES_Z = 1, 2, 3, 4, 5, 6, 7
 P_INIT = 8  # initial walker positions
@@ -70,7 +70,7 @@ class _StepParams(C.Structure):
     _fields_ = [
         ("kernel", C.c_int), ("eps", C.c_double), ("n_leapfrog", C.c_int), ("n_steps", C.c_int),
         ("max_depth", C.c_int), ("aies_a", C.c_double), ("aies_walkers", C.c_int),
-        ("seed", C.c_uint64),
+        ("seed", C.c_uint64), ("de_sigma", C.c_double),
     ]
 
 
@@ -217,8 +217,9 @@ def leapfrog(model: Model, z, q, g, eps, n):
 
 
 def run(model: Model, kernel, z, *, eps, n_steps, seed, n_leapfrog=10, max_depth=8, aies_a=2.0,
-        aies_walkers=64, iter0=None, lp=None, g=None, record=True, trace=False):
-    """Run n_steps of a sampler on all chains from whitened positions z[n][d].
+        aies_walkers=64, de_sigma=0.1, iter0=None, lp=None, g=None, record=True, trace=False):
+    """Run n_steps of a sampler on all chains from whitened positions z[n][d].  de_sigma: the
+    standard deviation of eta in the differential-evolution move (not given in Sec. 2.3).
 
     Returns a dict with the final state, per-chain counters and (optionally) the
     x-space samples [n_steps][n][d] and per-step decision traces."""
@@ -237,7 +238,7 @@ def run(model: Model, kernel, z, *, eps, n_steps, seed, n_leapfrog=10, max_depth
     evals = np.zeros(n, dtype=np.int64)
     div = np.zeros(n, dtype=np.int64)
     p = _StepParams(kernel=k, eps=eps, n_leapfrog=n_leapfrog, n_steps=n_steps, max_depth=max_depth,
-                    aies_a=aies_a, aies_walkers=aies_walkers, seed=seed)
+                    aies_a=aies_a, aies_walkers=aies_walkers, seed=seed, de_sigma=de_sigma)
     samples = np.zeros((n_steps, n, d)) if record else None
     t = _Trace()
     out = {}

@@ -21,7 +21,8 @@
  *  - NUTS: Hoffman & Gelman (2014) Algorithm 3 (slice variable, doubling in a
  *    random direction, U-turn test, progressive top-level selection), as
  *    described in Sec. 2.1.
- *  - AIES: Goodman & Weare (2010) stretch move, Sec. 2.3, Eqs. (2.13)-(2.15).
+ *  - AIES: Goodman & Weare (2010) stretch move, Sec. 2.3, Eqs. (2.13)-(2.15);
+ *    the differential-evolution move of Sec. 2.3 (after Eq. (2.15)).
  *  - Covariance adaptation: pooled covariance, Cholesky factorisation with
  *    diagonal regularisation (Sec. 3.2); Chan, Golub & LeVeque (1979) merge.
  *  - Adam: Kingma & Ba (2015), Algorithm 1.
@@ -603,7 +604,13 @@ static void record(const orc_model *m, const orc_trace *tr, int n_chains, int t,
  * S0 moves using partners drawn uniformly from S1, then S1 using the updated S0.
  * y = z_j + Z (z_i - z_j), Z = (u (a - 1) + 1)^2 / a (Eq. (2.15));
  * accept with probability min(1, Z^(d-1) pi(y) / pi(z_i)).  Because x = mu + L z is
- * affine, this is the same move as in x-space.                                  */
+ * affine, this is the same move as in x-space.
+ * Differential-evolution move (Sec. 2.3, after Eq. (2.15)), same halves and order:
+ * y = z_i + gamma (z_j - z_k) with j != k uniform in the other half and
+ * gamma = (1 + eta) 2.38 / sqrt(2 d), eta ~ N(0, de_sigma^2); the proposal is symmetric,
+ * so accept with probability min(1, pi(y) / pi(z_i)).  j is uniform 0 of the partner
+ * stream, k uniform 1 over the other half - 1 walkers (skipping j), eta the first
+ * normal of the stretch-factor stream.                                           */
 static void aies_run(const orc_model *m, const orc_step_params *p, int n_chains, double *z,
                      double *lp, double *g, uint32_t *iter, double *accept_stat, int64_t *accepts,
                      int64_t *evals, const orc_trace *tr) {
@@ -624,11 +631,28 @@ static void aies_run(const orc_model *m, const orc_step_params *p, int n_chains,
           int jj = (int)(up * half);
           if (jj > half - 1) jj = half - 1;
           const int jw = oth + jj;
-          double uz = orc_uniform(p->seed, (uint32_t)i, it, ORC_P_AIES_Z, 0);
-          double Z = (uz * (a - 1.0) + 1.0) * (uz * (a - 1.0) + 1.0) / a;
-          for (int q = 0; q < d; ++q) y[q] = z[(size_t)jw * d + q] + Z * (z[(size_t)i * d + q] - z[(size_t)jw * d + q]);
-          double lpy = orc_logpost_z(m, y, NULL, NULL);
-          double la = (d - 1) * log(Z) + lpy - lp[i];
+          double lpy, la;
+          if (p->kernel == ORC_AIES_DE) {
+            double uk = orc_uniform(p->seed, (uint32_t)i, it, ORC_P_AIES_PARTNER, 1);
+            int kk = (int)(uk * (half - 1));
+            if (kk > half - 2) kk = half - 2;
+            if (kk >= jj) ++kk;
+            const int kw = oth + kk;
+            double eta;
+            orc_normals(p->seed, (uint32_t)i, it, ORC_P_AIES_Z, 1, &eta);
+            const double gamma = (1.0 + p->de_sigma * eta) * 2.38 / sqrt(2.0 * d);
+            for (int q = 0; q < d; ++q)
+              y[q] = z[(size_t)i * d + q] + gamma * (z[(size_t)jw * d + q] - z[(size_t)kw * d + q]);
+            lpy = orc_logpost_z(m, y, NULL, NULL);
+            la = lpy - lp[i];
+          } else {
+            double uz = orc_uniform(p->seed, (uint32_t)i, it, ORC_P_AIES_Z, 0);
+            double Z = (uz * (a - 1.0) + 1.0) * (uz * (a - 1.0) + 1.0) / a;
+            for (int q = 0; q < d; ++q)
+              y[q] = z[(size_t)jw * d + q] + Z * (z[(size_t)i * d + q] - z[(size_t)jw * d + q]);
+            lpy = orc_logpost_z(m, y, NULL, NULL);
+            la = (d - 1) * log(Z) + lpy - lp[i];
+          }
           double u = orc_uniform(p->seed, (uint32_t)i, it, ORC_P_ACCEPT, 0);
           step_out o;
           memset(&o, 0, sizeof(o));
@@ -656,8 +680,9 @@ int orc_run(const orc_model *m, const orc_step_params *p, int n_chains, double *
             double *g, uint32_t *iter, double *accept_stat, int64_t *accepts, int64_t *evals,
             int64_t *divergences, const orc_trace *tr) {
   const int d = m->d;
-  if (p->kernel == ORC_AIES) {
+  if (p->kernel == ORC_AIES || p->kernel == ORC_AIES_DE) {
     if (p->aies_walkers < 2 || p->aies_walkers % 2 || n_chains % p->aies_walkers) return -1;
+    if (p->kernel == ORC_AIES_DE && (p->aies_walkers < 4 || !(p->de_sigma >= 0.0))) return -1;
     aies_run(m, p, n_chains, z, lp, g, iter, accept_stat, accepts, evals, tr);
     return 0;
   }

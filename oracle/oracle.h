@@ -31,7 +31,7 @@ enum {
   ORC_P_AIES_Z = 7       /* AIES stretch factor                         */
 };
 
-enum { ORC_MH = 0, ORC_MALA = 1, ORC_HMC = 2, ORC_NUTS = 3, ORC_AIES = 4 };
+enum { ORC_MH = 0, ORC_MALA = 1, ORC_HMC = 2, ORC_NUTS = 3, ORC_AIES = 4, ORC_AIES_DE = 5 };
 enum { ORC_LIK_EMULATOR = 0, ORC_LIK_ANALYTIC = 1 };
 
 /* Target model: likelihood + prior + whitening (x = mu + L z). */
@@ -78,7 +78,7 @@ void orc_logpost_batch(const orc_model *m, int n, const double *z, double *lp, d
 /* ---- samplers ---- */
 double orc_leapfrog(const orc_model *m, double *z, double *q, double *g, double eps, int n);
 typedef struct {
-  int kernel;        /* ORC_MH .. ORC_AIES                     */
+  int kernel;        /* ORC_MH .. ORC_AIES_DE                  */
   double eps;        /* step size                              */
   int n_leapfrog;    /* HMC L                                  */
   int n_steps;       /* iterations per chain                   */
@@ -86,6 +86,7 @@ typedef struct {
   double aies_a;     /* stretch parameter a                    */
   int aies_walkers;  /* walkers per ensemble (even)            */
   uint64_t seed;
+  double de_sigma;   /* DE move: standard deviation of eta     */
 } orc_step_params;
 
 typedef struct {

@@ -203,3 +203,89 @@ def test_mala_proposal_reduces_to_gaussian_kernel():
     r = O.run(m, "mala", z0, eps=1e-6, n_steps=3, seed=1, trace=True)
     assert np.all(r["accept"] == 1)
     assert np.all(np.abs(r["log_alpha"]) < 1e-3)
+
+
+# ---- differential-evolution move (Sec. 2.3, after Eq. (2.15)) ----
+
+def test_aies_de_closed_form_posterior():
+    t, mean, cov = _linear_problem()
+    Lp = np.linalg.cholesky(cov)
+    m = _model(t, np.zeros(6), np.eye(6))
+    n_ens = 32
+    x0 = mean + S.chains_init(n_ens * 64, 6, seed=9) @ Lp.T
+    steps = 800
+    r = O.run(m, "aies_de", x0, eps=0.0, n_steps=steps, seed=4, aies_walkers=64, de_sigma=0.1)
+    keep = r["samples"][steps // 4:]
+    ens = keep.reshape(keep.shape[0], n_ens, 64, 6).transpose(0, 2, 1, 3).reshape(-1, n_ens, 6)
+    _check_moments(ens, mean, cov)
+    assert 0.1 < r["accepts"].sum() / (n_ens * 64 * steps) < 0.9
+
+
+def _flat_1d():
+    e = S.emulator(1, width=8, depth=1, seed=0)
+    W, b, wo, bo = S.unpack_emulator(e)
+    flat = dict(e, params=S.pack_emulator([np.zeros_like(W[0])], b, np.zeros_like(wo), 0.0))
+    return O.Model(1, emulator=flat, lower=[-1000.0], upper=[1000.0])
+
+
+def test_aies_de_partner_law():
+    """d = 1, flat target, de_sigma = 0: the moving half at 1, the other half at 0..31.  Every
+    move is accepted and y - 1 = gamma0 (p_j - p_k), gamma0 = 2.38 / sqrt(2): the difference
+    j - k is never 0 (two distinct partners) and takes delta with probability
+    (32 - |delta|) / (32 * 31) (an ordered pair of distinct walkers, uniform)."""
+    m = _flat_1d()
+    n_ens, W_ = 400, 64
+    z0 = np.zeros((n_ens * W_, 1))
+    for e_ in range(n_ens):
+        z0[e_ * W_: e_ * W_ + 32, 0] = 1.0
+        z0[e_ * W_ + 32: (e_ + 1) * W_, 0] = np.arange(32)
+    r = O.run(m, "aies_de", z0, eps=0.0, n_steps=1, seed=22, aies_walkers=W_, de_sigma=0.0)
+    y = np.concatenate([r["samples"][0, e_ * W_: e_ * W_ + 32, 0] for e_ in range(n_ens)])
+    D = (y - 1.0) / (2.38 / np.sqrt(2.0))
+    Di = np.rint(D)
+    assert np.allclose(D, Di, atol=1e-9)
+    assert np.all(Di != 0) and np.abs(Di).max() <= 31
+    deltas = np.arange(-31, 32)
+    deltas = deltas[deltas != 0]
+    expect = (32 - np.abs(deltas)) / (32 * 31) * D.size
+    obs = np.array([(Di == dl).sum() for dl in deltas])
+    assert stats.chisquare(obs, expect).pvalue > 1e-4
+
+
+def test_aies_de_gamma_law():
+    """d = 1, flat target, de_sigma = 0.3: the other half has 16 walkers at 0 and 16 at 1, so
+    (y - 1) / gamma0 is exactly 0 with probability 2 * 16 * 15 / (32 * 31) and otherwise
+    +-(1 + eta), eta ~ N(0, 0.3^2)."""
+    m = _flat_1d()
+    n_ens, W_, sig = 600, 64, 0.3
+    z0 = np.zeros((n_ens * W_, 1))
+    for e_ in range(n_ens):
+        z0[e_ * W_: e_ * W_ + 32, 0] = 1.0
+        z0[e_ * W_ + 48: (e_ + 1) * W_, 0] = 1.0
+    r = O.run(m, "aies_de", z0, eps=0.0, n_steps=1, seed=23, aies_walkers=W_, de_sigma=sig)
+    y = np.concatenate([r["samples"][0, e_ * W_: e_ * W_ + 32, 0] for e_ in range(n_ens)])
+    v = (y - 1.0) / (2.38 / np.sqrt(2.0))
+    zero = v == 0.0
+    p0 = 2 * 16 * 15 / (32 * 31)
+    assert abs(zero.mean() - p0) < 5 * np.sqrt(p0 * (1 - p0) / v.size)
+    mix = lambda u: 0.5 * stats.norm.cdf(u, 1.0, sig) + 0.5 * stats.norm.cdf(u, -1.0, sig)
+    assert stats.kstest(v[~zero], mix).pvalue > 1e-4
+
+
+def test_aies_de_affine_invariance_and_argument_checks():
+    t, mean, cov = _linear_problem()
+    rng = np.random.default_rng(5)
+    Mx = np.tril(rng.normal(size=(6, 6))) * 0.3 + np.eye(6)
+    bvec = rng.normal(size=6) * 0.1
+    m1 = _model(t, np.zeros(6), np.eye(6))
+    m2 = _model(t, bvec, Mx)
+    x0 = mean + S.chains_init(128, 6, seed=3) @ np.linalg.cholesky(cov).T
+    z0 = np.linalg.solve(Mx, (x0 - bvec).T).T
+    r1 = O.run(m1, "aies_de", x0, eps=0.0, n_steps=50, seed=14)
+    r2 = O.run(m2, "aies_de", z0, eps=0.0, n_steps=50, seed=14)
+    assert np.array_equal(r1["accepts"], r2["accepts"])
+    assert np.allclose(r1["samples"], r2["samples"], rtol=1e-9, atol=1e-9)
+    with pytest.raises(ValueError):
+        O.run(m1, "aies_de", x0[:2], eps=0.0, n_steps=1, seed=1, aies_walkers=2)  # needs 2 partners
+    with pytest.raises(ValueError):
+        O.run(m1, "aies_de", x0, eps=0.0, n_steps=1, seed=1, de_sigma=-1.0)
