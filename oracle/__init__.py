@@ -31,8 +31,9 @@ _SO = os.path.join(_BUILD, "liborc.so")
 _lock = threading.Lock()
 _lib = None
 
-MH, MALA, HMC, NUTS, AIES, AIES_DE = 0, 1, 2, 3, 4, 5
-KERNELS = {"mh": MH, "mala": MALA, "hmc": HMC, "nuts": NUTS, "aies": AIES, "aies_de": AIES_DE}
+MH, MALA, HMC, NUTS, AIES, AIES_DE, NUTS_MULTINOMIAL = 0, 1, 2, 3, 4, 5, 6
+KERNELS = {"mh": MH, "mala": MALA, "hmc": HMC, "nuts": NUTS, "aies": AIES, "aies_de": AIES_DE,
+           "nuts_multinomial": NUTS_MULTINOMIAL}
 LIK_EMULATOR, LIK_ANALYTIC = 0, 1
 P_XI, P_ACCEPT, P_NUTS_DIR, P_NUTS_SEL, P_NUTS_TOP, P_AIES_PARTNER, P_AIES_Z = 1, 2, 3, 4, 5, 6, 7
 P_INIT = 8  # initial walker positions

@@ -20,7 +20,9 @@
  *    (Eqs. (2.7)-(2.8)), leapfrog integrator, Metropolis accept on Delta H.
  *  - NUTS: Hoffman & Gelman (2014) Algorithm 3 (slice variable, doubling in a
  *    random direction, U-turn test, progressive top-level selection), as
- *    described in Sec. 2.1.
+ *    described in Sec. 2.1; the multinomial variant (Betancourt 2017, "A
+ *    Conceptual Introduction to Hamiltonian Monte Carlo", Appendix A) draws the
+ *    point from the trajectory with weights exp(-H) instead of a slice.
  *  - AIES: Goodman & Weare (2010) stretch move, Sec. 2.3, Eqs. (2.13)-(2.15);
  *    the differential-evolution move of Sec. 2.3 (after Eq. (2.15)).
  *  - Covariance adaptation: pooled covariance, Cholesky factorisation with
@@ -426,6 +428,7 @@ typedef struct {
   int diverged;
   double H0;
   double acc_sum;   /* sum over leaves of min(1, exp(H0 - H))       */
+  int multinomial;  /* weights exp(H0 - H) instead of the slice      */
 } nuts_ctx;
 
 typedef struct {
@@ -434,10 +437,15 @@ typedef struct {
   double *zc, *gc;        /* candidate theta' and its gradient          */
   double lpc;
   double n;               /* n'  */
+  double lw;              /* multinomial: log of the summed leaf weights exp(H0 - H) */
   int s;                  /* s'  */
 } nuts_tree;
 
 static double *nalloc(int d) { return (double *)malloc(sizeof(double) * (size_t)d); }
+static double log_add_exp(double a, double b) {
+  const double hi = a > b ? a : b, lo = a > b ? b : a;
+  return hi + log1p(exp(lo - hi));
+}
 static void tree_alloc(nuts_tree *t, int d) {
   t->zm = nalloc(d); t->qm = nalloc(d); t->gm = nalloc(d);
   t->zp = nalloc(d); t->qp = nalloc(d); t->gp = nalloc(d);
@@ -475,8 +483,15 @@ static void build_tree(nuts_ctx *c, const double *z, const double *q, const doub
     for (int i = 0; i < d; ++i) q1[i] += 0.5 * e * g1[i];
     c->leaf++;
     const double H = -lp1 + 0.5 * dot(d, q1, q1);
-    out->n = (c->log_u <= -H) ? 1.0 : 0.0;
-    out->s = (c->log_u < NUTS_DELTA_MAX - H) ? 1 : 0;
+    if (c->multinomial) {
+      /* weight exp(H0 - H); divergent when the energy error exceeds Delta_max */
+      out->lw = c->H0 - H;
+      out->n = 0.0;
+      out->s = (H - c->H0 < NUTS_DELTA_MAX) ? 1 : 0;
+    } else {
+      out->n = (c->log_u <= -H) ? 1.0 : 0.0;
+      out->s = (c->log_u < NUTS_DELTA_MAX - H) ? 1 : 0;
+    }
     if (!out->s) c->diverged = 1;
     c->acc_sum += accept_prob(c->H0 - H);
     memcpy(out->zm, z1, sizeof(double) * (size_t)d);
@@ -507,11 +522,20 @@ static void build_tree(nuts_ctx *c, const double *z, const double *q, const doub
     memcpy(out->gp, t2.gp, sizeof(double) * (size_t)d);
   }
   if (t2.s) {
-    /* with probability n'' / (n' + n''), take the candidate of the second half */
+    /* with probability n'' / (n' + n'') (multinomial: w'' / (w' + w'')), take the
+     * candidate of the second half */
     const double ntot = out->n + t2.n;
     const double u =
         orc_uniform(c->p->seed, c->chain, c->it, ORC_P_NUTS_SEL, (uint32_t)(8 * (c->leaf - 1) + j));
-    if (ntot > 0.0 && u * ntot < t2.n) {
+    int take;
+    if (c->multinomial) {
+      const double lw_tot = log_add_exp(out->lw, t2.lw);
+      take = u < exp(t2.lw - lw_tot);
+      out->lw = lw_tot;
+    } else {
+      take = ntot > 0.0 && u * ntot < t2.n;
+    }
+    if (take) {
       memcpy(out->zc, t2.zc, sizeof(double) * (size_t)d);
       memcpy(out->gc, t2.gc, sizeof(double) * (size_t)d);
       out->lpc = t2.lpc;
@@ -529,6 +553,7 @@ static void nuts_step(const orc_model *m, const orc_step_params *p, uint32_t cha
   const int d = m->d;
   nuts_ctx c;
   c.m = m; c.p = p; c.chain = chain; c.it = it; c.leaf = 0; c.diverged = 0; c.acc_sum = 0.0;
+  c.multinomial = (p->kernel == ORC_NUTS_MULTINOMIAL);
   double *q0 = nalloc(d);
   orc_normals(p->seed, chain, it, ORC_P_XI, d, q0);
   c.H0 = -(*lp) + 0.5 * dot(d, q0, q0);
@@ -544,6 +569,7 @@ static void nuts_step(const orc_model *m, const orc_step_params *p, uint32_t cha
   memcpy(zs, z, sizeof(double) * (size_t)d); memcpy(gs, g, sizeof(double) * (size_t)d);
   double lps = *lp;
   double n = 1.0;
+  double lw = 0.0; /* multinomial: log weight of the trajectory so far (the start: exp(0)) */
   int s = 1, j = 0;
   nuts_tree t;
   tree_alloc(&t, d);
@@ -562,15 +588,17 @@ static void nuts_step(const orc_model *m, const orc_step_params *p, uint32_t cha
       memcpy(gp, t.gp, sizeof(double) * (size_t)d);
     }
     if (t.s) {
-      /* with probability min(1, n'/n), move to the new subtree's candidate */
+      /* with probability min(1, n'/n) (multinomial: min(1, w'/w)), move to the new
+       * subtree's candidate */
       double ut = orc_uniform(p->seed, chain, it, ORC_P_NUTS_TOP, (uint32_t)j);
-      if (ut * n < t.n) {
+      if (c.multinomial ? (ut < exp(t.lw - lw)) : (ut * n < t.n)) {
         memcpy(zs, t.zc, sizeof(double) * (size_t)d);
         memcpy(gs, t.gc, sizeof(double) * (size_t)d);
         lps = t.lpc;
       }
     }
     n += t.n;
+    if (c.multinomial && t.s) lw = log_add_exp(lw, t.lw);
     s = t.s && no_uturn(d, zm, qm, zp, qp);
     j++;
   }
@@ -712,6 +740,7 @@ int orc_run(const orc_model *m, const orc_step_params *p, int n_chains, double *
           as = accept_prob(o.log_alpha);
           break;
         case ORC_NUTS:
+        case ORC_NUTS_MULTINOMIAL:
           nuts_step(m, p, (uint32_t)c, it, zc, &lp[c], gc, &o, &as);
           evals[c] += o.nleaf;
           divergences[c] += o.diverged;

@@ -31,7 +31,8 @@ enum {
   ORC_P_AIES_Z = 7       /* AIES stretch factor                         */
 };
 
-enum { ORC_MH = 0, ORC_MALA = 1, ORC_HMC = 2, ORC_NUTS = 3, ORC_AIES = 4, ORC_AIES_DE = 5 };
+enum { ORC_MH = 0, ORC_MALA = 1, ORC_HMC = 2, ORC_NUTS = 3, ORC_AIES = 4, ORC_AIES_DE = 5,
+       ORC_NUTS_MULTINOMIAL = 6 };
 enum { ORC_LIK_EMULATOR = 0, ORC_LIK_ANALYTIC = 1 };
 
 /* Target model: likelihood + prior + whitening (x = mu + L z). */
@@ -78,7 +79,7 @@ void orc_logpost_batch(const orc_model *m, int n, const double *z, double *lp, d
 /* ---- samplers ---- */
 double orc_leapfrog(const orc_model *m, double *z, double *q, double *g, double eps, int n);
 typedef struct {
-  int kernel;        /* ORC_MH .. ORC_AIES_DE                  */
+  int kernel;        /* ORC_MH .. ORC_NUTS_MULTINOMIAL         */
   double eps;        /* step size                              */
   int n_leapfrog;    /* HMC L                                  */
   int n_steps;       /* iterations per chain                   */

@@ -1,5 +1,6 @@
 """Pins for the oracle's samplers (paper Sec. 2): closed-form posterior moments
-of the linear theory map, leapfrog reversibility / volume preservation and the
+of the linear theory map (every kernel, including the multinomial NUTS variant and the
+differential-evolution move), leapfrog reversibility / volume preservation and the
 O(eps^2) energy error of HMC, reversibility of MH on a two-state coarse
 graining, the stretch-factor law of AIES (Eq. (2.15) against g(z) of
 Eq. (2.14)) and its affine invariance."""
@@ -50,6 +51,9 @@ def _check_moments(samples, mean, cov, nsig=5.0):
     # top-level selection probabilities matter
     ("nuts", 1.3, 3000, {"max_depth": 8}),
     ("hmc", 0.9, 1500, {"n_leapfrog": 3}),
+    # multinomial NUTS: trajectory points weighted by exp(-H), at a small and a large step
+    ("nuts_multinomial", 0.35, 1000, {"max_depth": 8}),
+    ("nuts_multinomial", 1.3, 3000, {"max_depth": 8}),
 ])
 def test_closed_form_posterior(kernel, eps, steps, extra):
     t, mean, cov = _linear_problem()
