@@ -45,3 +45,41 @@ def test_host_side_argument_errors():
     assert L.bst_step(None, 0, 0.1, 1, 1, None, None, None) == _lib.ERR_ARG
     assert L.bst_sync(None, None) == _lib.ERR_ARG
     L.bst_destroy(None)
+
+
+def test_ctypes_mirrors_match_the_header_layout(tmp_path):
+    """The binding's ctypes structures and enum values against the C compiler's view of
+    include/bst.h (sizes, field offsets, enum values), so the two cannot drift apart."""
+    import shutil
+    import subprocess
+    from paper_2606_04895_gb300 import _lib
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    cfg_fields = [f for f, _ in _lib.Config._fields_]
+    st_fields = [f for f, _ in _lib.StepStats._fields_]
+    kernels = ["BST_MH", "BST_MALA", "BST_HMC", "BST_NUTS", "BST_AIES"]
+    statuses = ["BST_OK", "BST_ERR_ARG", "BST_ERR_STATE", "BST_ERR_CUDA", "BST_ERR_NOT_PD", "BST_ERR_TIMEOUT",
+                "BST_ERR_NONFINITE", "BST_ERR_UNSUPPORTED"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bst.h"', "int main(void) {",
+             '  printf("cfg %zu\\n", sizeof(bst_config));', '  printf("st %zu\\n", sizeof(bst_step_stats));']
+    lines += [f'  printf("cfg.{f} %zu\\n", offsetof(bst_config, {f}));' for f in cfg_fields]
+    lines += [f'  printf("st.{f} %zu\\n", offsetof(bst_step_stats, {f}));' for f in st_fields]
+    lines += [f'  printf("{k} %d\\n", (int){k});' for k in kernels + statuses]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    assert int(got["cfg"]) == C.sizeof(_lib.Config)
+    assert int(got["st"]) == C.sizeof(_lib.StepStats)
+    for f in cfg_fields:
+        assert int(got[f"cfg.{f}"]) == getattr(_lib.Config, f).offset, f
+    for f in st_fields:
+        assert int(got[f"st.{f}"]) == getattr(_lib.StepStats, f).offset, f
+    for k in kernels:
+        assert int(got[k]) == getattr(_lib, k[4:]), k
+    for sname in statuses:
+        assert int(got[sname]) == getattr(_lib, sname[4:]), sname
