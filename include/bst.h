@@ -261,6 +261,19 @@ bst_status bst_ess(bst_handle h, const void *samples_dev, int n_draws, double *e
  * Synchronises. */
 bst_status bst_r_minus_1(bst_handle h, const void *samples_dev, int n_draws, double *out);
 
+/* The two halves of bst_r_minus_1, for chains spread over several handles (ranks):
+ * bst_r_minus_1_parts computes, on the device, every chain's mean (chain_means: host
+ * double[n_chains][d]) and the pooled within-chain cross products
+ * S = sum_c sum_t (x_tc - m_c)(x_tc - m_c)^T (S: host double[d][d]) of samples_dev
+ * (n_draws >= 2; synchronises).  bst_r_minus_1_combine is host-only (no device, no handle):
+ * from the means of all n_chains chains and the sum of every part's S it forms
+ * W = S / (n_chains (n_draws - 1)), B = the covariance of the chain means, and R - 1 as in
+ * bst_r_minus_1 (NaN where that is NaN).  Needs n_chains >= 2, n_draws >= 2, 1 <= d <= 32. */
+bst_status bst_r_minus_1_parts(bst_handle h, const void *samples_dev, int n_draws, double *chain_means,
+                               double *S);
+bst_status bst_r_minus_1_combine(int n_chains, int n_draws, int d, const double *chain_means, const double *S,
+                                 double *out);
+
 /* Per-dimension quantiles of the pooled draws samples_dev real[n_draws][n_chains][d]
  * (this handle's n_chains, d and real type) at the levels q[0..nq) in [0, 1], 1 <= nq
  * <= 8: linear interpolation between the order statistics at ranks floor(h) and

@@ -23,7 +23,7 @@ from . import _lib
 from ._lib import AIES, BF16, FP32, FP64, HMC, LIK_ANALYTIC, LIK_EMULATOR, MALA, MH, NUTS, BstError
 
 __all__ = ["Sampler", "Results", "BstError", "EmulatorLogL", "emulator_logl", "KERNELS", "PRECISIONS",
-           "n_params"]
+           "n_params", "r_minus_1_combine"]
 
 KERNELS = {"mh": MH, "mala": MALA, "hmc": HMC, "nuts": NUTS, "aies": AIES}
 PRECISIONS = {"bf16": BF16, "fp32": FP32, "fp64": FP64}
@@ -272,6 +272,16 @@ class Sampler:
         _lib.check(self.lib.bst_r_minus_1(self.h, C.c_void_p(samples.data_ptr()), samples.shape[0], _p(out)))
         return float(out[0])
 
+    def r_minus_1_parts(self, samples):
+        """This handle's share of R - 1: (chain means [n][d], pooled within-chain cross products
+        S [d][d]) of samples[n_draws][n_chains][d], for `r_minus_1_combine` over several handles."""
+        self._check_dev(samples, (samples.shape[0], self.n, self.d))
+        means = np.zeros((self.n, self.d))
+        S = np.zeros((self.d, self.d))
+        _lib.check(self.lib.bst_r_minus_1_parts(self.h, C.c_void_p(samples.data_ptr()), samples.shape[0], _p(means),
+                                                _p(S)))
+        return means, S
+
     def quantiles(self, samples, q):
         """Per-dimension quantiles of the pooled draws samples[n_draws][n_chains][d]; [d][len(q)]."""
         self._check_dev(samples, (samples.shape[0], self.n, self.d))
@@ -340,6 +350,20 @@ class EmulatorLogL(torch.autograd.Function):
         (theta,) = ctx.saved_tensors
         _, g = ctx.sampler.grad_loglike(theta.detach())
         return grad_out.to(g.dtype)[:, None] * g, None
+
+
+def r_minus_1_combine(n_draws, chain_means, S):
+    """R - 1 (Sec. 4.1) from the chain means of all chains (concatenated over handles,
+    [n_chains][d]) and the sum of their within-chain cross products S [d][d] (host-side
+    library call; needs no device)."""
+    means = np.ascontiguousarray(chain_means, dtype=np.float64)
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    n_chains, d = means.shape
+    if S.shape != (d, d):
+        raise BstError(_lib.ERR_ARG, f"S must be {d} x {d}")
+    out = np.zeros(1)
+    _lib.check(_lib.load().bst_r_minus_1_combine(int(n_chains), int(n_draws), int(d), _p(means), _p(S), _p(out)))
+    return float(out[0])
 
 
 def emulator_logl(theta, sampler):

@@ -1183,9 +1183,14 @@ static void jacobi_eigenvalues(std::vector<double> &A, int d, std::vector<double
   for (int r = 0; r < d; ++r) ev[r] = at(r, r);
 }
 
-bst_status bst_r_minus_1(bst_handle h, const void *samples_dev, int n_draws, double *out) {
-  if (!h || !samples_dev || !out) return fail(BST_ERR_ARG, "bst_r_minus_1: NULL argument");
-  if (n_draws < 2 || h->n < 2) return fail(BST_ERR_ARG, "bst_r_minus_1: need at least 2 draws and 2 chains");
+// R - 1 in two parts, so that ranks holding different chains can pool it: the device part
+// gives every chain's mean and the pooled within-chain cross products
+// S = sum_c sum_t (x_tc - m_c)(x_tc - m_c)^T (per-block partials summed in block order); the
+// host part forms W = S / (M (n - 1)), B from the chain means, and the eigenvalue problem.
+bst_status bst_r_minus_1_parts(bst_handle h, const void *samples_dev, int n_draws, double *chain_means,
+                               double *S_out) {
+  if (!h || !samples_dev || !chain_means || !S_out) return fail(BST_ERR_ARG, "bst_r_minus_1_parts: NULL argument");
+  if (n_draws < 2) return fail(BST_ERR_ARG, "bst_r_minus_1_parts: need at least 2 draws");
   BST_CUDA(cudaSetDevice(h->device));
   const int M = h->n, d = h->d, n = n_draws;
   const size_t md = static_cast<size_t>(M) * d;
@@ -1204,17 +1209,29 @@ bst_status bst_r_minus_1(bst_handle h, const void *samples_dev, int n_draws, dou
     BST_CUDA(launch_ess_moments_f32((const float *)samples_dev, n, M, d, h->ess_mean, h->ess_var, 0));
     BST_CUDA(launch_rhat_cross_f32((const float *)samples_dev, n, M, d, h->ess_mean, h->rhat_part, 0));
   }
-  std::vector<double> mean(md), part(static_cast<size_t>(nb) * np);
-  BST_CUDA(cudaMemcpy(mean.data(), h->ess_mean, md * 8, cudaMemcpyDeviceToHost));
+  std::vector<double> part(static_cast<size_t>(nb) * np);
+  BST_CUDA(cudaMemcpy(chain_means, h->ess_mean, md * 8, cudaMemcpyDeviceToHost));
   BST_CUDA(cudaMemcpy(part.data(), h->rhat_part, part.size() * 8, cudaMemcpyDeviceToHost));
-  // W (blocks summed in order) and B
-  std::vector<double> W(static_cast<size_t>(d) * d), B(static_cast<size_t>(d) * d, 0.0), gm(d, 0.0);
   for (int i = 0, p = 0; i < d; ++i)
     for (int j = i; j < d; ++j, ++p) {
       double sum = 0.0;
       for (int b = 0; b < nb; ++b) sum += part[static_cast<size_t>(b) * np + p];
-      W[i * d + j] = W[j * d + i] = sum / (static_cast<double>(M) * (n - 1));
+      S_out[i * d + j] = S_out[j * d + i] = sum;
     }
+  return BST_OK;
+}
+
+bst_status bst_r_minus_1_combine(int n_chains, int n_draws, int d, const double *chain_means, const double *S,
+                                 double *out) {
+  if (!chain_means || !S || !out) return fail(BST_ERR_ARG, "bst_r_minus_1_combine: NULL argument");
+  if (n_chains < 2 || n_draws < 2 || d < 1 || d > kMaxD)
+    return fail(BST_ERR_ARG, "bst_r_minus_1_combine: need n_chains >= 2, n_draws >= 2 and 1 <= d <= 32");
+  const int M = n_chains, n = n_draws;
+  const double *mean = chain_means;
+  // W and B
+  std::vector<double> W(static_cast<size_t>(d) * d), B(static_cast<size_t>(d) * d, 0.0), gm(d, 0.0);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) W[i * d + j] = S[i * d + j] / (static_cast<double>(M) * (n - 1));
   for (int c = 0; c < M; ++c)
     for (int i = 0; i < d; ++i) gm[i] += mean[static_cast<size_t>(c) * d + i];
   for (int i = 0; i < d; ++i) gm[i] /= M;
@@ -1275,6 +1292,14 @@ bst_status bst_r_minus_1(bst_handle h, const void *samples_dev, int n_draws, dou
   for (double v : ev) r = std::fmax(r, std::fabs(v));
   *out = r;
   return BST_OK;
+}
+
+bst_status bst_r_minus_1(bst_handle h, const void *samples_dev, int n_draws, double *out) {
+  if (!h || !samples_dev || !out) return fail(BST_ERR_ARG, "bst_r_minus_1: NULL argument");
+  if (n_draws < 2 || h->n < 2) return fail(BST_ERR_ARG, "bst_r_minus_1: need at least 2 draws and 2 chains");
+  std::vector<double> means(static_cast<size_t>(h->n) * h->d), S(static_cast<size_t>(h->d) * h->d);
+  BST_TRY(bst_r_minus_1_parts(h, samples_dev, n_draws, means.data(), S.data()));
+  return bst_r_minus_1_combine(h->n, n_draws, h->d, means.data(), S.data(), out);
 }
 
 // Quantiles of the pooled draws per dimension: order statistics by radix select on the

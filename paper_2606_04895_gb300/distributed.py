@@ -9,7 +9,9 @@ sampling step needs no communication (weak scaling).  Two things cross ranks:
   all-gathered and every rank merges them in rank order with the library's
   pairwise merge, so all ranks adapt to the same whitening bit for bit;
 * step-size adaptation uses the mean acceptance statistic over all chains
-  (an all-reduce of two numbers).
+  (an all-reduce of two numbers);
+* R - 1 over all chains (Sec. 4.1) gathers every rank's chain means and within-chain cross
+  products.
 
 Data-parallel emulator training averages the per-rank gradients
 (all-reduce) before the Adam update.
@@ -61,6 +63,33 @@ def adapt_cov(sampler, jitter0=1e-10, group=None):
     for n, mean, M2 in triples:
         sampler.welford_merge(n, mean, M2)
     return sampler.adapt_cov(jitter0)
+
+
+def pooled_r_minus_1(chain_means, S, n_draws: int, group=None) -> float:
+    """R - 1 (Sec. 4.1) over every rank's chains from each rank's part (its chain means and
+    within-chain cross products, `Sampler.r_minus_1_parts`): the means are all-gathered in rank
+    order, the cross products all-gathered and summed in rank order, so every rank computes
+    the same value.  Ranks may hold different numbers of chains."""
+    from . import r_minus_1_combine
+    means = np.ascontiguousarray(chain_means, dtype=np.float64)
+    m_local, d = means.shape
+    dev = _device_for(group)
+    world = dist.get_world_size(group)
+    counts = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in range(world)]
+    dist.all_gather(counts, torch.tensor([m_local], dtype=torch.int64, device=dev), group=group)
+    counts = [int(c.item()) for c in counts]
+    m_max = max(counts)
+    mine = torch.zeros((m_max * d + d * d,), dtype=torch.float64, device=dev)
+    mine[: m_local * d] = torch.as_tensor(means.ravel(), dtype=torch.float64, device=dev)
+    mine[m_max * d:] = torch.as_tensor(np.asarray(S, dtype=np.float64).ravel(), dtype=torch.float64, device=dev)
+    outs = [torch.empty_like(mine) for _ in range(world)]
+    dist.all_gather(outs, mine, group=group)
+    all_means, S_sum = [], np.zeros((d, d))
+    for c, o in zip(counts, outs):
+        v = o.cpu().numpy()
+        all_means.append(v[: c * d].reshape(c, d))
+        S_sum = S_sum + v[m_max * d:].reshape(d, d)
+    return r_minus_1_combine(n_draws, np.concatenate(all_means), S_sum)
 
 
 def mean_accept(stats: dict, n_chains_local: int, n_steps: int, group=None) -> float:

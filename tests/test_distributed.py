@@ -148,3 +148,53 @@ def test_two_rank_step_size_adaptation_agrees():
         mid = 0.5 * (lo + hi)
         lo, hi = (mid, hi) if f(mid) > 0 else (lo, mid)
     assert res[0][1] == pytest.approx(lo, rel=0.06)
+
+
+def _rhat_draws(rank):
+    """AR(1) chains with chain offsets; rank r holds 40 + 24 r chains of 150 draws in 4-D."""
+    rng = np.random.default_rng(300 + rank)
+    n, M, d = 150, 40 + 24 * rank, 4
+    x = np.zeros((n, M, d))
+    x[0] = rng.normal(size=(M, d))
+    for t in range(1, n):
+        x[t] = 0.6 * x[t - 1] + rng.normal(size=(M, d))
+    return x + 0.4 * rng.normal(size=(1, M, d)) + rank * 0.1
+
+
+def _parts(x):
+    """A handle's R - 1 part computed in numpy: chain means and within-chain cross products."""
+    m = x.mean(axis=0)
+    dev = x - m
+    return m, np.einsum("tca,tcb->ab", dev, dev)
+
+
+def _rhat_worker(rank, world, port, q):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2606_04895_gb300 import distributed as D
+    m, S = _parts(_rhat_draws(rank))
+    q.put((rank, D.pooled_r_minus_1(m, S, 150)))
+    dist.destroy_process_group()
+
+
+def test_two_rank_pooled_r_minus_1():
+    """R - 1 over both ranks' chains (different chain counts per rank) from the gathered parts:
+    the same number on both ranks, equal to the oracle's R - 1 of all draws together."""
+    import oracle as O
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_rhat_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    res = sorted([q.get(timeout=120) for _ in ps], key=lambda t: t[0])
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][1] == res[1][1]
+    allx = np.concatenate([_rhat_draws(r) for r in range(2)], axis=1)
+    assert res[0][1] == pytest.approx(O.r_minus_1(allx), rel=1e-10)
