@@ -822,9 +822,10 @@ bst_status bst_step(bst_handle h, int kernel, double eps, int n_leapfrog, int n_
 
 static bst_status loglike_impl(bst_handle h, const void *theta, int m, void *logl, void *grad, void *stream,
                                int need_grad) {
-  if (!h || (m > 0 && (!theta || !logl || (need_grad && !grad)))) return fail(BST_ERR_ARG, "bst_loglike: NULL argument");
-  if (h->stage < 1) return fail(BST_ERR_STATE, "bst_loglike: set a likelihood first");
-  if (m < 0) return fail(BST_ERR_ARG, "bst_loglike: m must be >= 0");
+  const std::string fn = need_grad ? "bst_grad_loglike" : "bst_loglike";
+  if (!h || (m > 0 && (!theta || !logl || (need_grad && !grad)))) return fail(BST_ERR_ARG, fn + ": NULL argument");
+  if (h->stage < 1) return fail(BST_ERR_STATE, fn + ": set a likelihood first");
+  if (m < 0) return fail(BST_ERR_ARG, fn + ": m must be >= 0");
   if (m == 0) return BST_OK;
   BST_CUDA(cudaSetDevice(h->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);

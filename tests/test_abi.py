@@ -83,3 +83,20 @@ def test_ctypes_mirrors_match_the_header_layout(tmp_path):
         assert int(got[k]) == getattr(_lib, k[4:]), k
     for sname in statuses:
         assert int(got[sname]) == getattr(_lib, sname[4:]), sname
+
+
+def test_every_entry_point_rejects_a_null_handle():
+    """Each call that takes a handle returns BST_ERR_ARG for a NULL one, before any device
+    work, and names itself in the error message."""
+    from paper_2606_04895_gb300 import _lib
+    L = _lib.load()
+    skip = {"bst_version", "bst_last_error", "bst_create", "bst_destroy", "bst_r_minus_1_combine"}
+    ints = (C.c_int, C.c_longlong, C.c_ulonglong, C.c_uint32, C.c_uint64)
+    for name in _lib.SYMBOLS:
+        if name in skip:
+            continue
+        f = getattr(L, name)
+        args = [0 if t in ints else 0.0 if t is C.c_double else None for t in f.argtypes]
+        assert f(*args) == _lib.ERR_ARG, name
+        assert L.bst_last_error().decode().startswith(name + ":"), (name, L.bst_last_error())
+    L.bst_destroy(None)  # a no-op
