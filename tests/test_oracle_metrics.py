@@ -1,4 +1,6 @@
-"""Pins of the oracle's multivariate Gelman-Rubin statistic R - 1 (paper Sec. 4.1)."""
+"""Pins of the oracle's convergence metrics (paper Sec. 4.1: multivariate R - 1, quantiles and the
+credible metric, the 1-D Wasserstein-1 distance and the sliced Wasserstein distance) and of the
+initial walker positions (Sec. 3.1)."""
 import numpy as np
 import pytest
 
