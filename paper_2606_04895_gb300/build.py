@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], check=True)
+    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"], check=True)
     os.replace(tmp, LIB)
     return LIB
 

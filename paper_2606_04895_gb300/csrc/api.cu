@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "launch.h"
 
 using namespace bst;
@@ -34,6 +36,14 @@ bst_status fail(bst_status s, const std::string &m) {
   } while (0)
 
 int pad16(int d) { return ((d + 15) / 16) * 16; }
+
+// A named range on the calling thread for timeline tools (NVTX; a no-op when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 }  // namespace
 
@@ -573,6 +583,7 @@ void bst_destroy(bst_handle h) {
 
 bst_status bst_set_emulator(bst_handle h, int depth, int width, const double *params, const double *in_m,
                             const double *in_s, double out_m, double out_s) {
+  NvtxRange nvtx_("bst_set_emulator");
   if (!h || !params || !in_m || !in_s) return fail(BST_ERR_ARG, "bst_set_emulator: NULL argument");
   if (h->lik != BST_LIK_EMULATOR) return fail(BST_ERR_STATE, "bst_set_emulator: handle was created for the analytic likelihood");
   if (depth < 1 || depth > 8) return fail(BST_ERR_ARG, "bst_set_emulator: depth must be in 1..8");
@@ -727,6 +738,7 @@ bst_status bst_set_analytic(bst_handle h, int d_c, int n_hidden, int n_data, con
 
 bst_status bst_init_chains(bst_handle h, const double *theta0, const double *lower, const double *upper,
                            const int *gauss, const double *mu, const double *L) {
+  NvtxRange nvtx_("bst_init_chains");
   if (!h || !theta0 || !lower || !upper || !mu || !L) return fail(BST_ERR_ARG, "bst_init_chains: NULL argument");
   if (h->stage < 1) return fail(BST_ERR_STATE, "bst_init_chains: set a likelihood first");
   const int d = h->d, n = h->n;
@@ -777,6 +789,7 @@ bst_status bst_init_chains(bst_handle h, const double *theta0, const double *low
 
 bst_status bst_step(bst_handle h, int kernel, double eps, int n_leapfrog, int n_steps, void *samples_dev,
                     void *stream, bst_step_stats *stats) {
+  NvtxRange nvtx_("bst_step");
   if (!h) return fail(BST_ERR_ARG, "bst_step: NULL handle");
   if (h->stage < 2) return fail(BST_ERR_STATE, "bst_step: call bst_init_chains first");
   if (kernel < BST_MH || kernel > BST_AIES) return fail(BST_ERR_ARG, "bst_step: unknown kernel");
@@ -822,6 +835,7 @@ bst_status bst_step(bst_handle h, int kernel, double eps, int n_leapfrog, int n_
 
 static bst_status loglike_impl(bst_handle h, const void *theta, int m, void *logl, void *grad, void *stream,
                                int need_grad) {
+  NvtxRange nvtx_(need_grad ? "bst_grad_loglike" : "bst_loglike");
   const std::string fn = need_grad ? "bst_grad_loglike" : "bst_loglike";
   if (!h || (m > 0 && (!theta || !logl || (need_grad && !grad)))) return fail(BST_ERR_ARG, fn + ": NULL argument");
   if (h->stage < 1) return fail(BST_ERR_STATE, fn + ": set a likelihood first");
@@ -861,6 +875,7 @@ bst_status bst_welford_reset(bst_handle h) {
 }
 
 bst_status bst_welford_add(bst_handle h, const void *x_dev, int m, void *stream) {
+  NvtxRange nvtx_("bst_welford_add");
   if (!h || (m > 0 && !x_dev)) return fail(BST_ERR_ARG, "bst_welford_add: NULL argument");
   if (m < 0) return fail(BST_ERR_ARG, "bst_welford_add: m must be >= 0");
   if (m == 0) return BST_OK;
@@ -905,6 +920,7 @@ bst_status bst_welford_merge(bst_handle h, double n, const double *mean, const d
 }
 
 bst_status bst_adapt_cov(bst_handle h, double jitter0, double *mu_out, double *L_out, double *jitter_used) {
+  NvtxRange nvtx_("bst_adapt_cov");
   if (!h) return fail(BST_ERR_ARG, "bst_adapt_cov: NULL handle");
   if (h->stage < 2) return fail(BST_ERR_STATE, "bst_adapt_cov: call bst_init_chains first");
   if (!(jitter0 > 0.0)) return fail(BST_ERR_ARG, "bst_adapt_cov: jitter0 must be positive");
@@ -936,6 +952,7 @@ bst_status bst_adapt_cov(bst_handle h, double jitter0, double *mu_out, double *L
 
 bst_status bst_draw_positions(bst_handle h, int strategy, const double *center, const double *Lc, const double *lower,
                               const double *upper, double *theta_out) {
+  NvtxRange nvtx_("bst_draw_positions");
   if (!h || !theta_out) return fail(BST_ERR_ARG, "bst_draw_positions: NULL argument");
   const int n = h->n, d = h->d;
   std::vector<double> par(static_cast<size_t>(3 + kMaxD) * kMaxD, 0.0);
@@ -975,6 +992,7 @@ bst_status bst_draw_positions(bst_handle h, int strategy, const double *center, 
 }
 
 bst_status bst_set_whitening(bst_handle h, const double *mu, const double *L) {
+  NvtxRange nvtx_("bst_set_whitening");
   if (!h || !mu || !L) return fail(BST_ERR_ARG, "bst_set_whitening: NULL argument");
   if (h->stage < 2) return fail(BST_ERR_STATE, "bst_set_whitening: call bst_init_chains first");
   const int d = h->d;
@@ -1101,6 +1119,7 @@ static bst_status train_setup(bst_handle h, int m) {
 
 bst_status bst_train_grad(bst_handle h, const float *X_dev, const float *chi2_dev, int m, float *grad_dev,
                           float *loss_dev, void *stream) {
+  NvtxRange nvtx_("bst_train_grad");
   if (!h || !X_dev || !chi2_dev || !grad_dev) return fail(BST_ERR_ARG, "bst_train_grad: NULL argument");
   BST_CUDA(cudaSetDevice(h->device));
   BST_TRY(train_setup(h, m));
@@ -1113,6 +1132,7 @@ bst_status bst_train_grad(bst_handle h, const float *X_dev, const float *chi2_de
 
 bst_status bst_train_step(bst_handle h, const float *X_dev, const float *chi2_dev, int m, double lr, double beta1,
                           double beta2, double adam_eps, float *loss_dev, void *stream) {
+  NvtxRange nvtx_("bst_train_step");
   if (!h || !X_dev || !chi2_dev) return fail(BST_ERR_ARG, "bst_train_step: NULL argument");
   if (!(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(adam_eps > 0.0))
     return fail(BST_ERR_ARG, "bst_train_step: bad Adam hyper-parameters");
@@ -1133,6 +1153,7 @@ bst_status bst_train_step(bst_handle h, const float *X_dev, const float *chi2_de
 
 bst_status bst_train_apply(bst_handle h, const float *grad_dev, double lr, double beta1, double beta2,
                            double adam_eps, void *stream) {
+  NvtxRange nvtx_("bst_train_apply");
   if (!h || !grad_dev) return fail(BST_ERR_ARG, "bst_train_apply: NULL argument");
   if (!(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(adam_eps > 0.0))
     return fail(BST_ERR_ARG, "bst_train_apply: bad Adam hyper-parameters");
@@ -1190,6 +1211,7 @@ static void jacobi_eigenvalues(std::vector<double> &A, int d, std::vector<double
 // host part forms W = S / (M (n - 1)), B from the chain means, and the eigenvalue problem.
 bst_status bst_r_minus_1_parts(bst_handle h, const void *samples_dev, int n_draws, double *chain_means,
                                double *S_out) {
+  NvtxRange nvtx_("bst_r_minus_1_parts");
   if (!h || !samples_dev || !chain_means || !S_out) return fail(BST_ERR_ARG, "bst_r_minus_1_parts: NULL argument");
   if (n_draws < 2) return fail(BST_ERR_ARG, "bst_r_minus_1_parts: need at least 2 draws");
   BST_CUDA(cudaSetDevice(h->device));
@@ -1379,6 +1401,7 @@ static bst_status quantiles_impl(bst_ctx *h, const R *x, int n_draws, const doub
 }  // extern "C++"
 
 bst_status bst_quantiles(bst_handle h, const void *samples_dev, int n_draws, const double *q, int nq, double *out) {
+  NvtxRange nvtx_("bst_quantiles");
   if (!h || !samples_dev || !q || !out) return fail(BST_ERR_ARG, "bst_quantiles: NULL argument");
   if (n_draws < 1 || nq < 1 || nq > kMaxQuantiles) return fail(BST_ERR_ARG, "bst_quantiles: need n_draws >= 1 and 1 <= nq <= 8");
   for (int k = 0; k < nq; ++k)
@@ -1427,6 +1450,7 @@ struct DevScratch {  // call-local device buffer, freed on every return path
 
 bst_status bst_sliced_wasserstein(bst_handle h, const void *samples_dev, int n_draws, const void *ref_dev,
                                   long long n_ref, int n_proj, unsigned long long seed, double *out) {
+  NvtxRange nvtx_("bst_sliced_wasserstein");
   if (!h || !samples_dev || !ref_dev || !out) return fail(BST_ERR_ARG, "bst_sliced_wasserstein: NULL argument");
   if (n_draws < 1 || n_ref < 1 || n_proj < 1)
     return fail(BST_ERR_ARG, "bst_sliced_wasserstein: need n_draws, n_ref and n_proj >= 1");
@@ -1477,6 +1501,7 @@ bst_status bst_sliced_wasserstein(bst_handle h, const void *samples_dev, int n_d
 }
 
 bst_status bst_ess(bst_handle h, const void *samples_dev, int n_draws, double *ess_out) {
+  NvtxRange nvtx_("bst_ess");
   if (!h || !samples_dev || !ess_out) return fail(BST_ERR_ARG, "bst_ess: NULL argument");
   if (n_draws < 4) return fail(BST_ERR_ARG, "bst_ess: need at least 4 draws");
   BST_CUDA(cudaSetDevice(h->device));
