@@ -44,11 +44,10 @@ def peaks():
 
 
 # DRAM traffic of the timed step-kernel launch (4096 chains, 8-512x4-1, MALA): one-pass ncu
-# captures (dram__bytes_read.sum + dram__bytes_write.sum) of K = 20 and K = 5000 launches,
-# 4.05 + 0.67 MB and 28.99 + 615.07 MB (profiles/tc2_chain_kernel_mala_4096x8_w512_cs4.md),
-# i.e. a fixed 2.3 MB plus 128.4 KB per MALA iteration (the x-space sample write, 131 KB per
-# iteration).  Valid for the kernel code they were taken on (sources without comments);
-# None once that changes.
+# captures (dram__bytes_read.sum + dram__bytes_write.sum) of launches of two lengths, fitted
+# as a fixed part plus a part per MALA iteration (the x-space sample write is 131 KB per
+# iteration).  Valid for the kernel code they were taken on (sources without comments); None
+# once that changes.
 TRAFFIC_SOURCES = ['paper_2606_04895_gb300/csrc/common.cuh', 'paper_2606_04895_gb300/csrc/engine_tc.cuh', 'paper_2606_04895_gb300/csrc/engine_tc2.cuh', 'paper_2606_04895_gb300/csrc/sampler.cuh', 'paper_2606_04895_gb300/csrc/tc2_launch.cuh', 'paper_2606_04895_gb300/csrc/k_tc2_w512_c4x.cu']
 TRAFFIC_SOURCES_SHA256 = "940d555273b79f5d"
 TRAFFIC_K, TRAFFIC_BYTES = (20, 5000), (4.05e6 + 0.66586e6, 28.99e6 + 615.07e6)

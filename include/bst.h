@@ -99,6 +99,20 @@ bst_status bst_set_emulator(bst_handle h, int depth, int width, const double *pa
  * (host, FP64, same layout as bst_set_emulator).  Synchronises. */
 bst_status bst_get_emulator(bst_handle h, double *params);
 
+/* Output transform of the emulator (the paper defers the emulator's design to
+ * CLiENT, Sec. 4; this is the reading used here).  BST_OUT_LINEAR (the default
+ * after bst_set_emulator): chi2 = out_s * out + out_m.  BST_OUT_LOG:
+ * chi2 = floor + exp(out_s * out + out_m), i.e. the network predicts the
+ * standardised log(chi2 - floor), which resolves the posterior region of a
+ * chi2 that spans orders of magnitude over the prior box; the gradient is
+ * d logL / dx = -(1/2) exp(out_s * out + out_m) out_s d out / dx.  Applies to
+ * every evaluation and to training (bst_train_*: the regression target is
+ * (log(chi2 - floor) - out_m) / out_s, with chi2 - floor clamped to >= 1e-30).
+ * Call after bst_set_emulator (which resets it to BST_OUT_LINEAR).
+ * Errors: BST_ERR_ARG (unknown kind, non-finite floor), BST_ERR_STATE (no emulator). */
+typedef enum { BST_OUT_LINEAR = 0, BST_OUT_LOG = 1 } bst_out_kind;
+bst_status bst_set_emulator_output(bst_handle h, int kind, double floor);
+
 /* Analytic likelihood: f(x) = A tanh(B x_c + c) + N x_n (tanh -> identity if
  * linear), logL = -|data - f(x)|^2 / (2 sigma^2); x_c = x[0:d_c], x_n = x[d_c:d].
  * A[n_data][n_hidden], B[n_hidden][d_c], c[n_hidden], N[n_data][d - d_c] (NULL
@@ -149,16 +163,18 @@ bst_status bst_grad_loglike(bst_handle h, const void *theta_dev, int m, void *lo
  * first call with a larger m than before grows the buffer in which the adjoint
  * keeps the emulator's hidden activations.  This call instead uses one
  * file-scope device array of 16 MiB (g_static_scratch) that every GPU which
- * loads the library holds until the process exits (for the activations and,
- * where room remains, the BF16 engine's cluster-exchange images), and calls no
- * cudaMalloc, cudaFree or other allocating routine.
+ * loads the library holds until the process exits (for the activations), and
+ * calls no cudaMalloc, cudaFree or other allocating routine.
  * Arguments and results are those of bst_grad_loglike.  Limit: m times the
  * bytes kept per point, (depth - 1) x width x (2 for BF16, 4 for FP32, 8 for
  * FP64), must fit in 16 MiB (for example m <= 5461 for a BF16 8-512x4-1
  * emulator); a larger m returns BST_ERR_ARG and launches nothing.
  * The first call on each device looks the array's device address up with
  * cudaGetSymbolAddress (the device must be current, which the call ensures);
- * make that first call before any stream capture.  Every call on a device
+ * make that first call before any stream capture.  The first call after new
+ * weights (bst_set_emulator, bst_train_apply) converts them for the device and
+ * synchronises the stream, as the first evaluation call of any kind does; make
+ * that call outside stream capture too.  Every call on a device
  * shares the one array and overwrites what the previous call left there
  * (nothing in it needs to start at zero), so calls whose work overlaps on the
  * GPU -- on different streams, or from different handles -- race; order them

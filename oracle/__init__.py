@@ -64,6 +64,7 @@ class _Model(C.Structure):
         ("bf16", C.c_int),
         ("lower", C.c_void_p), ("upper", C.c_void_p), ("gauss", C.c_void_p),
         ("mu", C.c_void_p), ("L", C.c_void_p),
+        ("out_log", C.c_int), ("out_floor", C.c_double),
     ]
 
 
@@ -110,7 +111,7 @@ def lib():
             L.orc_cholesky_jitter.argtypes = [i, vp, d, vp, vp]
             L.orc_cholesky_jitter.restype = i
             L.orc_remap_z.argtypes = [i, i, vp, vp, vp, vp, vp]
-            L.orc_train_loss_grad.argtypes = [i, i, i, vp, vp, vp, d, d, i, vp, vp, vp]
+            L.orc_train_loss_grad.argtypes = [i, i, i, vp, vp, vp, d, d, i, d, i, vp, vp, vp]
             L.orc_train_loss_grad.restype = d
             L.orc_adam.argtypes = [i, vp, vp, vp, vp, i, d, d, d, d]
             L.orc_ess.argtypes = [i, i, i, vp, vp]
@@ -179,6 +180,7 @@ class Model:
             self._keep += [P, in_m, in_s]
             s.params, s.in_m, s.in_s = _ptr(P), _ptr(in_m), _ptr(in_s)
             s.out_m, s.out_s = float(e["out_m"]), float(e["out_s"])
+            s.out_log, s.out_floor = int(e.get("out_log", 0)), float(e.get("out_floor", 0.0))
             s.bf16 = int(bf16)
         lower = _f64(np.full(d, -np.inf) if lower is None else lower)
         upper = _f64(np.full(d, np.inf) if upper is None else upper)
@@ -293,11 +295,12 @@ def remap_z(mu_old, L_old, mu_new, L_new, z):
 
 
 # --------------------------------------------------------------------------- training
-def train_loss_grad(d, depth, width, params, in_m, in_s, out_m, out_s, X, chi2):
+def train_loss_grad(d, depth, width, params, in_m, in_s, out_m, out_s, X, chi2, out_log=0, out_floor=0.0):
     P = _f64(params); X = _f64(X); y = _f64(chi2)
     g = np.zeros_like(P)
     loss = lib().orc_train_loss_grad(d, depth, width, _ptr(P), _ptr(_f64(in_m)), _ptr(_f64(in_s)),
-                                     float(out_m), float(out_s), X.shape[0], _ptr(X), _ptr(y), _ptr(g))
+                                     float(out_m), float(out_s), int(out_log), float(out_floor), X.shape[0],
+                                     _ptr(X), _ptr(y), _ptr(g))
     return loss, g
 
 

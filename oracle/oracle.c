@@ -153,7 +153,9 @@ static double analytic_logl(const orc_model *m, const double *x, double *grad) {
 }
 
 /* Emulator: u = (x - m_in)/s_in; h_1 = tanh(W_1 u + b_1); h_l = tanh(W_l h_{l-1} + b_l);
- * out = w_o . h_D + b_o; chi2_hat = out_s out + out_m; logL = -chi2_hat / 2.
+ * out = w_o . h_D + b_o; chi2_hat = out_s out + out_m (linear output) or
+ * out_floor + exp(out_s out + out_m) (log output); logL = -chi2_hat / 2.  The gradient of
+ * the log output is that of the linear one times exp(out_s out + out_m) (chain rule).
  * BF16 mode: operands of the hidden-to-hidden products (W_2..W_D, h_1..h_{D-1})
  * and every adjoint vector delta_1..delta_D are rounded to bfloat16; the input
  * layer, the output layer and all sums are exact.                            */
@@ -195,7 +197,9 @@ static double emulator_logl(const orc_model *m, const double *x, double *grad) {
   const double *hD = h + (size_t)(D - 1) * w;
   double out = bo;
   for (int k = 0; k < w; ++k) out += wo[k] * hD[k];
-  const double chi2 = m->out_s * out + m->out_m;
+  const double arg = m->out_s * out + m->out_m;
+  const double tfac = m->out_log ? exp(arg) : 1.0; /* d chi2_hat / d arg */
+  const double chi2 = m->out_log ? m->out_floor + tfac : arg;
 
   if (grad) {
     double *dl = (double *)malloc(sizeof(double) * (size_t)w);
@@ -221,7 +225,7 @@ static double emulator_logl(const orc_model *m, const double *x, double *grad) {
     for (int j = 0; j < d; ++j) {
       double s = 0.0;
       for (int k = 0; k < w; ++k) s += W[1][k * d + j] * dl[k];
-      grad[j] = s / m->in_s[j];
+      grad[j] = s / m->in_s[j] * tfac;
     }
     free(dl);
     free(dn);
@@ -857,11 +861,14 @@ void orc_remap_z(int d, int n, const double *mu_old, const double *L_old, const 
 /* Emulator training                                                        */
 /* ------------------------------------------------------------------------ */
 
-/* Loss = mean_i (out_i - y_i)^2 with y_i = (chi2_i - out_m) / out_s (standardised chi^2).
- * grad (same layout as params) = d loss / d params, by reverse-mode differentiation. */
+/* Loss = mean_i (out_i - y_i)^2 with y_i = (t(chi2_i) - out_m) / out_s (the standardised
+ * regression target), t(c) = c for the linear output and log(max(c - out_floor, 1e-30)) for
+ * the log output.  grad (same layout as params) = d loss / d params, by reverse-mode
+ * differentiation. */
 double orc_train_loss_grad(int d, int D, int w, const double *P, const double *in_m,
-                           const double *in_s, double out_m, double out_s, int mb, const double *X,
-                           const double *chi2, double *grad) {
+                           const double *in_s, double out_m, double out_s, int out_log,
+                           double out_floor, int mb, const double *X, const double *chi2,
+                           double *grad) {
   size_t np = (size_t)d * w + w + (size_t)(D - 1) * ((size_t)w * w + w) + w + 1;
   memset(grad, 0, sizeof(double) * np);
   double loss = 0.0;
@@ -891,7 +898,8 @@ double orc_train_loss_grad(int d, int D, int w, const double *P, const double *i
     const double *hD = h + (size_t)D * w;
     double out = P[off_bo];
     for (int k = 0; k < w; ++k) out += P[off_wo + k] * hD[k];
-    const double y = (chi2[i] - out_m) / out_s;
+    const double tc = out_log ? log(fmax(chi2[i] - out_floor, 1e-30)) : chi2[i];
+    const double y = (tc - out_m) / out_s;
     const double r = out - y;
     loss += r * r;
     const double dout = 2.0 * r / mb;

@@ -96,10 +96,13 @@ class Sampler:
         self.close()
 
     # ------------------------------------------------------------------ likelihoods
-    def set_emulator(self, params, depth, width, in_m, in_s, out_m=0.0, out_s=1.0):
+    def set_emulator(self, params, depth, width, in_m, in_s, out_m=0.0, out_s=1.0, out_log=0, out_floor=0.0):
+        """out_log = 1: chi2 = out_floor + exp(out_s out + out_m) (bst_set_emulator_output)."""
         P, m, s = _f64(params), _f64(in_m), _f64(in_s)
         _lib.check(self.lib.bst_set_emulator(self.h, int(depth), int(width), _p(P), _p(m), _p(s),
                                              float(out_m), float(out_s)))
+        if out_log:
+            _lib.check(self.lib.bst_set_emulator_output(self.h, 1, float(out_floor)))
         self.depth, self.width = int(depth), int(width)
 
     def get_emulator(self):

@@ -19,7 +19,7 @@ LIK_EMULATOR, LIK_ANALYTIC = range(2)
 
 # Every symbol include/bst.h declares.
 SYMBOLS = [
-    "bst_version", "bst_last_error", "bst_create", "bst_destroy", "bst_set_emulator", "bst_get_emulator",
+    "bst_version", "bst_last_error", "bst_create", "bst_destroy", "bst_set_emulator", "bst_get_emulator", "bst_set_emulator_output",
     "bst_set_analytic", "bst_init_chains", "bst_step", "bst_loglike", "bst_grad_loglike", "bst_welford_reset",
     "bst_welford_add", "bst_adapt_cov", "bst_get_state", "bst_set_state", "bst_get_whitening", "bst_get_counters",
     "bst_train_step", "bst_train_grad", "bst_ess", "bst_draw_positions", "bst_set_whitening", "bst_r_minus_1", "bst_r_minus_1_parts", "bst_r_minus_1_combine", "bst_quantiles", "bst_credible_metric", "bst_sliced_wasserstein", "bst_sync", "bst_grad_loglike_noalloc",
@@ -72,6 +72,7 @@ def load(build_if_missing: bool = True):
         L.bst_destroy.restype = None
         L.bst_set_emulator.argtypes = [h, i, i, vp, vp, vp, d, d]
         L.bst_get_emulator.argtypes = [h, vp]
+        L.bst_set_emulator_output.argtypes = [h, i, d]
         L.bst_set_analytic.argtypes = [h, i, i, i, vp, vp, vp, vp, vp, d, i]
         L.bst_init_chains.argtypes = [h, vp, vp, vp, vp, vp, vp]
         L.bst_step.argtypes = [h, i, d, i, i, vp, vp, C.POINTER(StepStats)]

@@ -78,6 +78,8 @@ struct bst_ctx {
   size_t nparams = 0;
   double *P64 = nullptr, *in_m64 = nullptr, *in_s64 = nullptr;
   double out_m = 0.0, out_s = 1.0, bo = 0.0;
+  int out_log = 0;       // bst_out_kind
+  double out_floor = 0.0;
   double *W1f[2] = {nullptr, nullptr}, *b1f[2] = {nullptr, nullptr};  // [0] z-space, [1] x-space
   void *sW1T[2] = {nullptr, nullptr}, *sW1[2] = {nullptr, nullptr}, *sb1[2] = {nullptr, nullptr};
   void *sWT = nullptr, *sW = nullptr, *sb = nullptr, *swo = nullptr;
@@ -265,6 +267,8 @@ EmuWeights<R> emu_weights(bst_ctx *h, int fold) {
   w.bo = static_cast<R>(h->bo);
   w.out_m = static_cast<R>(h->out_m);
   w.out_s = static_cast<R>(h->out_s);
+  w.out_log = h->out_log;
+  w.out_floor = static_cast<R>(h->out_floor);
   w.scratch = static_cast<R *>(h->scratch);
   return w;
 }
@@ -292,6 +296,8 @@ Tc2Weights tc2_weights(bst_ctx *h, int fold, int n_rows) {
   w.bo = static_cast<float>(h->bo);
   w.out_m = static_cast<float>(h->out_m);
   w.out_s = static_cast<float>(h->out_s);
+  w.out_log = h->out_log;
+  w.out_floor = static_cast<float>(h->out_floor);
   w.scratch = static_cast<__nv_bfloat16 *>(h->scratch);
   {
     // the exchange images follow the stored activations of h->scratch_rows rows
@@ -643,6 +649,8 @@ bst_status bst_set_emulator(bst_handle h, int depth, int width, const double *pa
   BST_CUDA(cudaMemcpy(h->in_s64, in_s, d * 8, cudaMemcpyHostToDevice));
   h->out_m = out_m;
   h->out_s = out_s;
+  h->out_log = 0;
+  h->out_floor = 0.0;
   h->bo = params[np - 1];
   h->p32_newer = false;
   if (h->P32) {
@@ -674,6 +682,17 @@ bst_status bst_get_emulator(bst_handle h, double *params) {
   BST_CUDA(cudaDeviceSynchronize());
   BST_CUDA(cudaMemcpy(params, h->P64, h->nparams * 8, cudaMemcpyDeviceToHost));
   h->bo = params[h->nparams - 1];
+  return BST_OK;
+}
+
+bst_status bst_set_emulator_output(bst_handle h, int kind, double floor) {
+  if (!h) return fail(BST_ERR_ARG, "bst_set_emulator_output: NULL handle");
+  if (h->lik != BST_LIK_EMULATOR || !h->P64) return fail(BST_ERR_STATE, "bst_set_emulator_output: no emulator set");
+  if (kind != BST_OUT_LINEAR && kind != BST_OUT_LOG) return fail(BST_ERR_ARG, "bst_set_emulator_output: unknown kind");
+  if (!std::isfinite(floor)) return fail(BST_ERR_ARG, "bst_set_emulator_output: non-finite floor");
+  h->out_log = kind == BST_OUT_LOG ? 1 : 0;
+  h->out_floor = floor;
+  h->state_stale = true;
   return BST_OK;
 }
 
@@ -1125,7 +1144,7 @@ bst_status bst_train_grad(bst_handle h, const float *X_dev, const float *chi2_de
   BST_TRY(train_setup(h, m));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   BST_CUDA(launch_train_grad(h->P32, h->in_m32, h->in_s32, static_cast<float>(h->out_m), static_cast<float>(h->out_s),
-                             h->d, h->depth, h->width, m, X_dev, chi2_dev, grad_dev, h->tw, s));
+                             h->out_log, static_cast<float>(h->out_floor), h->d, h->depth, h->width, m, X_dev, chi2_dev, grad_dev, h->tw, s));
   if (loss_dev) BST_CUDA(cudaMemcpyAsync(loss_dev, h->tw.loss, 4, cudaMemcpyDeviceToDevice, s));
   return BST_OK;
 }
@@ -1140,7 +1159,7 @@ bst_status bst_train_step(bst_handle h, const float *X_dev, const float *chi2_de
   BST_TRY(train_setup(h, m));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   BST_CUDA(launch_train_grad(h->P32, h->in_m32, h->in_s32, static_cast<float>(h->out_m), static_cast<float>(h->out_s),
-                             h->d, h->depth, h->width, m, X_dev, chi2_dev, h->G32, h->tw, s));
+                             h->out_log, static_cast<float>(h->out_floor), h->d, h->depth, h->width, m, X_dev, chi2_dev, h->G32, h->tw, s));
   if (loss_dev) BST_CUDA(cudaMemcpyAsync(loss_dev, h->tw.loss, 4, cudaMemcpyDeviceToDevice, s));
   h->adam_t += 1;
   BST_CUDA(launch_adam(h->P32, h->G32, h->m1, h->m2, h->nparams, h->adam_t, static_cast<float>(lr),
@@ -1604,6 +1623,7 @@ bst_status static_scratch_address(int dev, void **out) {
 
 extern "C" bst_status bst_grad_loglike_noalloc(bst_handle h, const void *theta_dev, int m, void *logl_dev,
                                                void *grad_dev, void *stream) {
+  NvtxRange nvtx_("bst_grad_loglike_noalloc");
   if (!h || (m > 0 && (!theta_dev || !logl_dev || !grad_dev)))
     return fail(BST_ERR_ARG, "bst_grad_loglike_noalloc: NULL argument");
   if (h->stage < 1) return fail(BST_ERR_STATE, "bst_grad_loglike_noalloc: set a likelihood first");

@@ -27,6 +27,8 @@ struct EmuWeights {
   const R *b;    // [D-1][w]
   const R *wo;   // [w]
   R bo, out_m, out_s;
+  int out_log;   // chi2 = out_floor + exp(out_s out + out_m) instead of out_s out + out_m
+  R out_floor;
   R *scratch;    // [rows][D-1][w] hidden activations h_1..h_{D-1} kept for the adjoint
 };
 
@@ -185,7 +187,9 @@ struct EmuSimt {
       cur = nxt;
       nxt = t;
     }
-    // output: out = wo . h_D + bo; logL = -(out_s out + out_m) / 2   (one warp per row)
+    // output: out = wo . h_D + bo; logL = -chi2 / 2 with chi2 = out_s out + out_m (linear output)
+    // or out_floor + exp(out_s out + out_m) (log output), one warp per row; outv[r] keeps
+    // d chi2 / d(out_s out + out_m) (1, or the exponential) for the adjoint's seed
     const int warp = tid >> 5, lane = tid & 31;
     for (int r = warp; r < T; r += kThreads / 32) {
       R s = 0;
@@ -193,21 +197,24 @@ struct EmuSimt {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) {
-        outv[r] = s;
+        const R arg = E.out_s * (s + E.bo) + E.out_m;
+        const R t = E.out_log ? exp(arg) : R(1);
+        outv[r] = t;
         const int row = row0 + r;
-        if (row < a.n_rows) a.st.lle[row] = R(-0.5) * (E.out_s * (s + E.bo) + E.out_m);
+        if (row < a.n_rows) a.st.lle[row] = R(-0.5) * (E.out_log ? E.out_floor + t : arg);
       }
     }
     if (!need_grad) {
       __syncthreads();
       return;
     }
-    // delta_D = (-out_s / 2) wo (1 - h_D^2), in place
+    // delta_D = (-out_s / 2) t_r wo (1 - h_D^2), in place
     const R c0 = R(-0.5) * E.out_s;
+    __syncthreads();
     for (int idx = tid; idx < T * w; idx += kThreads) {
       const int r = idx / w, n = idx % w;
       const R h = cur[r * lda + n];
-      cur[r * lda + n] = c0 * E.wo[n] * (R(1) - h * h);
+      cur[r * lda + n] = (c0 * outv[r]) * E.wo[n] * (R(1) - h * h);
     }
     __syncthreads();
     // delta_{l-1} = (W_l^T delta_l) (1 - h_{l-1}^2), l = D..2

@@ -14,7 +14,7 @@
 // K-major) in shared memory, multiplies it by its slice of the weights (its own K blocks
 // first), runs the epilogue on its NS columns, writes the BF16 result into its own
 // activation buffer and copies that slice into every peer's buffer: in clusters of 4 through
-// a global image of the slice and one multicast global->shared bulk copy per 4 KB piece,
+// a global image of the slice and one global->shared bulk copy per peer and 4 KB piece,
 // otherwise with shared->shared bulk copies (completion counted on the peer's mbarrier).  A
 // peer's buffer is written only after the peer's MMAs of the layer have finished reading it
 // ("free" arrivals).  The output dot w_o . h_D is reduced across the cluster in a fixed
@@ -55,6 +55,8 @@ struct Tc2Weights {
   const float *b;     // [D-1][w]
   const float *wo;    // [w]
   float bo, out_m, out_s;
+  int out_log;        // chi2 = out_floor + exp(out_s out + out_m) instead of out_s out + out_m
+  float out_floor;
   __nv_bfloat16 *scratch;  // [rows][D-1][w] stored activations (unless in tensor memory)
   uint8_t *xchg;           // [CTAs][128 x NS BF16] slice images of the cluster exchange
   size_t xchg_bytes;
@@ -129,16 +131,6 @@ __device__ __forceinline__ void mma_commit_multicast(uint32_t bar, uint16_t mask
 }
 __device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;\n" ::"r"(addr), "f"(v) : "memory");
-}
-// Global -> shared copy delivered to the same shared-memory offset in every CTA of `mask`,
-// completion counted on the mbarrier at `bar`'s offset in each of them.
-__device__ __forceinline__ void bulk_g2s_multicast(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
-                                                   uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
-      "%4;\n" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar), "h"(mask)
-      : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;\n" ::: "memory");
@@ -240,8 +232,8 @@ __device__ __forceinline__ void tmem_wait_ld_regs(uint32_t *r) {
 }
 
 // ---------------------------------------------------------------- the kernel
-// L2X: cluster exchange through global slice images and multicast copies (clusters of 4 with
-// room for the images), else direct shared->shared copies.  RC: MALA / MH / HMC with d <= 8
+// L2X: cluster exchange through global slice images and global->shared copies into each peer
+// (clusters of 4 with room for the images), else direct shared->shared copies.  RC: MALA / MH / HMC with d <= 8
 // (padded to 16), whose chains live in the sampler threads' registers (RegChain8); else the
 // general per-chain code (Chain) or loglike mode.
 template <int W, int CS, bool L2X, bool RC>
@@ -300,9 +292,9 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
   // scratch.
   constexpr bool h_tmem = tc2_h_in_tmem(W, CS);
   // In clusters of 4, given room for them (E.xchg), each CTA also writes its slice of a layer
-  // output to global memory (a byte image of its shared-memory slice) and every epilogue warp
-  // sends its part to the three peers with one multicast global->shared copy instead of one
-  // shared->shared copy per peer (with a single peer the direct copy is faster).
+  // output to global memory (a byte image of its shared-memory slice, which stays in L2) and
+  // every epilogue warp sends its part to each of the three peers with a global->shared bulk
+  // copy instead of a shared->shared copy (with a single peer the direct copy is faster).
   constexpr bool l2x = L2X && kWarpSend && CS == 4;
   const uint32_t tcols_alloc = h_tmem ? 512u : static_cast<uint32_t>(TCOLS);
   // the launch picks a cluster size whose stored activations fit, and sizes the scratch for
@@ -481,9 +473,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
     const int col0 = static_cast<int>(rank) * NS + ch * CW;  // first global column of this warp
     Chain<float> chn(a);
     const bool loglike = a.mode == kModeLoglike;
-    // this CTA's global image of its slice (l2x) and the peers as a cluster mask
+    // this CTA's global image of its slice (l2x)
     uint8_t *ximg = E.xchg + static_cast<size_t>(blockIdx.x) * SLICE_BYTES;
-    const uint16_t peer_mask_e = static_cast<uint16_t>(((1u << CS) - 1u) & ~(1u << rank));
     const bool mala = a.mode == kModeMALA, hmc = a.mode == kModeHMC;
     // MALA / MH / HMC with d <= 8 (padded to 16) keep the chain in the sampler thread's registers
     constexpr bool fast = RC;
@@ -780,15 +771,16 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
           if (CS > 1 && t == 0) mbar_expect_tx(actf_bar, (CS - 1) * SLICE_BYTES);  // the peers' slices
           if (l2x) {
             // this warp's rows (32 q ..) of its K blocks, from the global image into every
-            // peer's buffer at the same place (one multicast copy per 4 KB)
+            // peer's buffer at the same place (one copy per peer and 4 KB, read from L2)
             fence_proxy_async_global();
             __syncwarp();
             if (lane == 0 && ok)
               for (int kb2 = 0; kb2 < CW / 64; ++kb2) {
                 const int kbl = col0 / 64 + kb2;
-                bulk_g2s_multicast(act_addr + static_cast<uint32_t>(kbl) * 16384 + q * 4096,
-                                   ximg + (kbl - static_cast<int>(rank) * NOWN) * 16384 + q * 4096, 4096, actf_bar,
-                                   peer_mask_e);
+                const uint32_t dst = act_addr + static_cast<uint32_t>(kbl) * 16384 + q * 4096;
+                const uint8_t *src = ximg + (kbl - static_cast<int>(rank) * NOWN) * 16384 + q * 4096;
+                for (int pr = 0; pr < CS; ++pr)
+                  if (pr != static_cast<int>(rank)) bulk_g2s(mapa(dst, pr), src, 4096, mapa(actf_bar, pr));
               }
           } else if (kWarpSend) {
             // this warp's rows (32 q ..) of its K blocks, to every peer's buffer at the same place
@@ -832,7 +824,25 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
         if (sampler && valid && got) {
           float s_out = 0.f;
           for (int pr = 0; pr < CS; ++pr) s_out += partial[pr * 128 + r];
-          lle_v = -0.5f * (E.out_s * (s_out + E.bo) + E.out_m);
+          const float arg = E.out_s * (s_out + E.bo) + E.out_m;
+          if (E.out_log) {
+            // log output: chi2 = floor + t, t = exp(arg); the adjoint ran with the linear
+            // output's seed, so the gradient takes the factor t (d chi2 / d arg)
+            const float tx = expf(arg);
+            lle_v = -0.5f * (E.out_floor + tx);
+            if (grad) {
+              if (fast) {
+#pragma unroll
+                for (int i = 0; i < RegChain8<float>::DB; ++i) rc.gp[i] *= tx;
+              } else {
+                float *gout = a.st.gle + row_off(a.st.gle_ld, row, a.dp);
+                const int ges = row_es(a.st.gle_ld);
+                for (int i = 0; i < a.d; ++i) gout[i * ges] *= tx;
+              }
+            }
+          } else {
+            lle_v = -0.5f * arg;
+          }
           a.st.lle[row] = lle_v;
         }
         epi_sync();

@@ -761,10 +761,12 @@ __global__ void standardise_kernel(const float *X, const float *m, const float *
   U[i] = (X[i] - m[j]) / sd[j];
 }
 
-// out = wo . h_D + bo;  r = out - (chi2 - out_m)/out_s;  loss += r^2 / m;  dout = 2 r / m;
-// delta_D = dout wo (1 - h_D^2).  One warp per row.
+// out = wo . h_D + bo;  r = out - (t(chi2) - out_m)/out_s;  loss += r^2 / m;  dout = 2 r / m;
+// delta_D = dout wo (1 - h_D^2).  t(chi2) = chi2 (linear output) or log(max(chi2 - floor, 1e-30))
+// (log output).  One warp per row.
 __global__ void train_head_kernel(const float *HD, const float *wo, const float *bo_ptr, const float *chi2, float out_m,
-                                  float out_s, int m, int w, float *dout, float *delta, float *loss) {
+                                  float out_s, int out_log, float out_floor, int m, int w, float *dout, float *delta,
+                                  float *loss) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= m) return;
   const float *h = HD + static_cast<size_t>(warp) * w;
@@ -772,7 +774,8 @@ __global__ void train_head_kernel(const float *HD, const float *wo, const float 
   for (int k = lane; k < w; k += 32) s += wo[k] * h[k];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  const float y = (chi2[warp] - out_m) / out_s;
+  const float tc = out_log ? logf(fmaxf(chi2[warp] - out_floor, 1e-30f)) : chi2[warp];
+  const float y = (tc - out_m) / out_s;
   const float r = s + *bo_ptr - y;
   const float g = 2.f * r / m;
   if (lane == 0) {
@@ -801,9 +804,9 @@ __global__ void colsum_kernel(const float *X, int rows, int cols, float *out) {
   }
 }
 
-cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in_s, float out_m, float out_s, int d,
-                              int D, int w, int m, const float *X, const float *chi2, float *G, TrainWork &tw,
-                              cudaStream_t s) {
+cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in_s, float out_m, float out_s,
+                              int out_log, float out_floor, int d, int D, int w, int m, const float *X,
+                              const float *chi2, float *G, TrainWork &tw, cudaStream_t s) {
   cudaMemsetAsync(tw.loss, 0, sizeof(float), s);
   standardise_kernel<<<blocks_for(static_cast<size_t>(m) * d, 256), 256, 0, s>>>(X, in_m, in_s, m, d, tw.U);
   // forward: H_l = tanh(H_{l-1} W_l^T + b_l)
@@ -817,7 +820,8 @@ cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in
   const float *HD = tw.H + static_cast<size_t>(D - 1) * m * w;
   const size_t owo = off_wo(d, D, w);
   train_head_kernel<<<blocks_for(static_cast<size_t>(m) * 32, 256), 256, 0, s>>>(HD, P + owo, P + owo + w, chi2, out_m,
-                                                                               out_s, m, w, tw.dout, tw.Dl, tw.loss);
+                                                                               out_s, out_log, out_floor, m, w,
+                                                                               tw.dout, tw.Dl, tw.loss);
   // g_wo[j] = sum_i dout_i H_D[i][j]  (1 x w = dout^T H_D) ; g_bo = sum_i dout_i
   gemm_f32(1, w, m, tw.dout, 0, 1, HD, w, 1, G + owo, w, EPI_STORE, nullptr, nullptr, 0, s);
   colsum_kernel<<<1, 256, 0, s>>>(tw.dout, m, 1, G + owo + w);

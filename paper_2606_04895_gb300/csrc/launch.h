@@ -107,9 +107,9 @@ struct TrainWork {
   float *ws;    // [kTrainSplits][w][w] partial weight gradients (split over the batch)
 };
 constexpr int kTrainSplits = 4;
-cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in_s, float out_m, float out_s, int d,
-                              int D, int w, int m, const float *X, const float *chi2, float *G, TrainWork &tw,
-                              cudaStream_t s);
+cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in_s, float out_m, float out_s,
+                              int out_log, float out_floor, int d, int D, int w, int m, const float *X,
+                              const float *chi2, float *G, TrainWork &tw, cudaStream_t s);
 cudaError_t launch_adam(float *P, const float *G, float *m1, float *m2, size_t n, int t, float lr, float b1,
                         float b2, float eps, cudaStream_t s);
 cudaError_t launch_zero(void *p, size_t bytes, cudaStream_t s);

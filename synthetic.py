@@ -114,7 +114,7 @@ def target(d=6, *, linear=False, seed=0, sigma=0.1, n_data=None, sterile=None, n
 
 
 def emulator(d, *, width=512, depth=4, seed=5, in_m=None, in_s=None, out_m=0.0, out_s=1.0,
-             bias_scale=0.1):
+             bias_scale=0.1, out_log=0, out_floor=0.0):
     """Seeded tanh-MLP weights: W_l ~ N(0, 1/fan_in), small random biases.
 
     Flat layout: W1[w][d] b1[w] (W_l[w][w] b_l[w])_{l=2..D} wo[w] bo."""
@@ -132,6 +132,7 @@ def emulator(d, *, width=512, depth=4, seed=5, in_m=None, in_s=None, out_m=0.0, 
         "in_m": np.zeros(d) if in_m is None else np.asarray(in_m, float),
         "in_s": np.full(d, np.sqrt(3.0)) if in_s is None else np.asarray(in_s, float),
         "out_m": float(out_m), "out_s": float(out_s),
+        "out_log": int(out_log), "out_floor": float(out_floor),
     }
 
 

@@ -97,6 +97,29 @@ def test_training_gradient_matches_oracle():
     s.close()
 
 
+def test_training_gradient_log_output_matches_oracle():
+    """Log output (regression target log(chi2 - floor), standardised): loss and parameter gradient
+    of bst_train_grad against the FP64 oracle on the FP32-rounded inputs."""
+    from paper_2606_04895_gb300 import Sampler
+    d, D, w = 8, 3, 256
+    e = S.emulator(d, width=w, depth=D, seed=3, out_m=3.0, out_s=1.5, out_log=1, out_floor=240.0)
+    s = Sampler(d, 8, precision="fp32", likelihood="emulator")
+    s.set_emulator(e["params"], D, w, e["in_m"], e["in_s"], e["out_m"], e["out_s"], out_log=1,
+                   out_floor=e["out_floor"])
+    X = np.random.default_rng(0).uniform(-3, 3, (777, d))
+    y = 241.0 + np.exp(3.0 + 1.5 * np.random.default_rng(1).normal(size=777))
+    loss, g = s.train_grad(torch.as_tensor(X, dtype=torch.float32, device="cuda"),
+                           torch.as_tensor(y, dtype=torch.float32, device="cuda"))
+    Xf = X.astype(np.float32).astype(np.float64)
+    yf = y.astype(np.float32).astype(np.float64)
+    Pf = e["params"].astype(np.float32).astype(np.float64)
+    lref, gref = O.train_loss_grad(d, D, w, Pf, e["in_m"], e["in_s"], e["out_m"], e["out_s"], Xf, yf,
+                                   out_log=1, out_floor=e["out_floor"])
+    assert abs(loss.item() - lref) / lref < 1e-4
+    assert rel_err(g.cpu().numpy(), gref) < 1e-3
+    s.close()
+
+
 def test_training_reduces_loss_and_updates_sampling_weights():
     from paper_2606_04895_gb300 import Sampler
     d, D, w = 4, 2, 256

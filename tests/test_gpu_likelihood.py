@@ -60,6 +60,42 @@ def test_emulator_loglike_parity(prec, d, width, depth):
     s.close()
 
 
+@pytest.mark.parametrize("d,width,depth", [(8, 512, 4), (27, 512, 2), (6, 256, 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_emulator_log_output_parity(prec, d, width, depth):
+    """Log output chi2 = floor + exp(out_s out + out_m): logL and gradient against the oracle
+    (the BF16 path against the oracle's BF16 rounding mode), for loglike / grad_loglike and for
+    the register-resident and general chains' initial log pi and gradient."""
+    e = emulator_case(d, width, depth, out_s=1.2, out_m=2.5)
+    e = dict(e, out_log=1, out_floor=200.0)
+    from paper_2606_04895_gb300 import Sampler
+    s = Sampler(d, 300, precision=prec, likelihood="emulator", seed=1)
+    s.set_emulator(e["params"], depth, width, e["in_m"], e["in_s"], e["out_m"], e["out_s"], out_log=1,
+                   out_floor=e["out_floor"])
+    x = np.random.default_rng(4).uniform(-3, 3, (300, d))
+    ll, g = s.grad_loglike(x)
+    ll0 = s.loglike(x)
+    ll, g, ll0 = ll.double().cpu().numpy(), g.double().cpu().numpy(), ll0.double().cpu().numpy()
+    rl, rg = O.Model(d, emulator=e, bf16=(prec == "bf16")).loglike(x)
+    tl, tg = {"fp64": (1e-10, 1e-9), "fp32": (1e-5, 1e-4), "bf16": (2e-3, 2e-2)}[prec]
+    for v in (ll, ll0):
+        assert np.max(np.abs(v - rl) / np.maximum(np.abs(rl), 1.0)) < tl
+    assert rel_err(g, rg) < tg
+    # chains' initial log pi and gradient (whitened) through the step kernels' refresh
+    mu, L = whitening(d, seed=2)
+    lower, upper = np.full(d, -3.0), np.full(d, 3.0)
+    z0 = np.random.default_rng(5).normal(size=(300, d)) * 0.8
+    th0 = mu + z0 @ L.T
+    s.init_chains(th0, lower, upper, mu=mu, L=L)
+    st = s.get_state()
+    m = O.Model(d, emulator=e, lower=lower, upper=upper, mu=mu, L=L, bf16=(prec == "bf16"))
+    lp_ref, g_ref = m.logpost(np.linalg.solve(L, (th0 - mu).T).T)
+    ok = np.isfinite(lp_ref)
+    assert np.max(np.abs(st["logp"][ok] - lp_ref[ok]) / np.maximum(np.abs(lp_ref[ok]), 1.0)) < tl
+    assert rel_err(st["grad"][ok], g_ref[ok]) < tg
+    s.close()
+
+
 @pytest.mark.parametrize("depth", [7, 8])
 def test_bf16_deep_width512(depth):
     """Depth 7 keeps the stored activations of a 4-CTA cluster in tensor memory; depth 8 no

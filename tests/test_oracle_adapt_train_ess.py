@@ -89,6 +89,39 @@ def test_training_loss_is_mse_on_standardised_chi2():
     assert g[-1] == pytest.approx(2 * np.mean(0.4 - ys), rel=1e-14)
 
 
+def test_training_loss_log_output():
+    """Log output: the regression target is (log(chi2 - floor) - out_m) / out_s; with every weight
+    zero but b_o the loss is the mean squared difference to it, and the gradient of b_o is twice
+    the mean residual.  Labels below the floor are clamped to 1e-30 above it."""
+    d, D, w = 3, 2, 8
+    e = S.emulator(d, width=w, depth=D, seed=1)
+    P = np.zeros_like(e["params"]); P[-1] = 0.4
+    X = np.random.default_rng(0).normal(size=(6, d))
+    y = np.array([5.0, 7.0, 12.0, 100.0, 4.5, 3.0])
+    loss, g = O.train_loss_grad(d, D, w, P, e["in_m"], e["in_s"], 1.0, 2.0, X, y, out_log=1, out_floor=4.0)
+    ys = (np.log(np.maximum(y - 4.0, 1e-30)) - 1.0) / 2.0
+    assert loss == pytest.approx(np.mean((0.4 - ys) ** 2), rel=1e-14)
+    assert g[-1] == pytest.approx(2 * np.mean(0.4 - ys), rel=1e-14)
+
+
+def test_training_gradient_finite_differences_log_output():
+    d, D, w = 4, 3, 16
+    e = S.emulator(d, width=w, depth=D, seed=1)
+    P = e["params"]
+    X = np.random.default_rng(0).uniform(-3, 3, (9, d))
+    y = np.random.default_rng(1).normal(size=9) * 5 + 30
+    kw = dict(out_log=1, out_floor=12.0)
+    loss, g = O.train_loss_grad(d, D, w, P, e["in_m"], e["in_s"], 2.5, 0.5, X, y, **kw)
+    idx = np.random.default_rng(2).choice(P.size, 30, replace=False)
+    for i in idx:
+        h = 1e-6
+        Pp = P.copy(); Pp[i] += h
+        Pm = P.copy(); Pm[i] -= h
+        lp, _ = O.train_loss_grad(d, D, w, Pp, e["in_m"], e["in_s"], 2.5, 0.5, X, y, **kw)
+        lm, _ = O.train_loss_grad(d, D, w, Pm, e["in_m"], e["in_s"], 2.5, 0.5, X, y, **kw)
+        assert g[i] == pytest.approx((lp - lm) / (2 * h), rel=1e-5, abs=1e-9)
+
+
 def test_adam_first_step_closed_form():
     p = np.array([1.0, -2.0, 0.5])
     g = np.array([0.3, -4.0, 1e-3])

@@ -162,3 +162,43 @@ def test_gaussian_nuisance_prior_term():
     assert lp[0] - ll[0] == pytest.approx(-0.5 * np.sum(x[6:] ** 2), rel=1e-12)
     assert np.allclose(g[0, 6:] - gl[0, 6:], -x[6:], rtol=1e-12)
     assert np.allclose(g[0, :6], gl[0, :6], rtol=1e-12)
+
+
+def test_emulator_log_output_gradient_finite_differences():
+    """Log output (chi2 = floor + exp(out_s out + out_m)): the returned gradient against
+    central differences of the returned logL."""
+    e = S.emulator(8, width=64, depth=4, seed=9, out_s=1.5, out_m=2.0, out_log=1, out_floor=250.0)
+    m = O.Model(8, emulator=e)
+    x = np.random.default_rng(5).uniform(-2, 2, 8)
+    _, g = m.loglike(x)
+    fd = _fd_grad(lambda v: m.loglike(v, grad=False)[0], x)
+    assert np.allclose(g[0], fd, rtol=1e-6, atol=1e-8)
+
+
+def test_emulator_log_output_matches_torch_autograd():
+    """The log output is exp of the linear output's standardised value, shifted by the floor:
+    logL_log = -(floor + exp(-2 logL_lin')) / 2 with logL_lin' the linear-output logL at
+    out_m, out_s; torch autograd of that expression gives the gradient."""
+    d, width, depth = 6, 32, 3
+    e = S.emulator(d, width=width, depth=depth, seed=4, out_m=1.0, out_s=0.5, out_log=1, out_floor=-3.0)
+    m = O.Model(d, emulator=e)
+    x = np.random.default_rng(0).uniform(-2, 2, (7, d))
+    lp, g = m.loglike(x)
+    lin = dict(e, out_log=0)
+    logl_lin, X = _torch_emulator(lin, x)  # -(out_s out + out_m) / 2
+    logl = -0.5 * (e["out_floor"] + torch.exp(-2.0 * logl_lin))
+    (gt,) = torch.autograd.grad(logl.sum(), X)
+    assert np.allclose(lp, logl.detach().numpy(), rtol=1e-12, atol=1e-12)
+    assert np.allclose(g, gt.numpy(), rtol=1e-10, atol=1e-12)
+
+
+def test_emulator_log_output_constant_network():
+    """All weights zero: out = wo . tanh(b_D) + bo is constant, so chi2 = floor + exp(out_s out + out_m)
+    everywhere and the gradient is zero."""
+    d, w, D = 5, 16, 2
+    e = S.emulator(d, width=w, depth=D, seed=1, out_m=0.3, out_s=2.0, out_log=1, out_floor=10.0)
+    W, b, wo, bo = S.unpack_emulator(e)
+    ez = dict(e, params=S.pack_emulator([np.zeros_like(Wl) for Wl in W], b, wo, 0.2))
+    lp, g = O.Model(d, emulator=ez).loglike(np.random.default_rng(0).normal(size=(3, d)))
+    out = wo @ np.tanh(b[-1]) + 0.2
+    assert np.allclose(lp, -0.5 * (10.0 + np.exp(2.0 * out + 0.3)), rtol=1e-14) and np.all(g == 0)
