@@ -19,7 +19,7 @@
  *  - ``stream`` is a cudaStream_t (NULL = the legacy default stream).  Work is
  *    enqueued asynchronously unless a call says it synchronises.
  *  - Element type of real-valued device buffers ("real"): float for handles of
- *    precision BST_BF16 and BST_FP32, double for BST_FP64.
+ *    precision BST_BF16, BST_FP16 and BST_FP32, double for BST_FP64.
  *  - Call order: bst_create -> bst_set_emulator | bst_set_analytic ->
  *    bst_init_chains -> { bst_step, bst_adapt_cov, ... }*.  Out of order ->
  *    BST_ERR_STATE.  The library owns only small persistent state (chain
@@ -50,13 +50,16 @@ typedef enum {
 } bst_status;
 
 typedef enum { BST_MH = 0, BST_MALA = 1, BST_HMC = 2, BST_NUTS = 3, BST_AIES = 4 } bst_kernel;
-typedef enum { BST_BF16 = 0, BST_FP32 = 1, BST_FP64 = 2 } bst_precision;
+/* BST_BF16 / BST_FP16: emulator on the tcgen05 tensor cores with BF16 (8 significant bits) or
+ * FP16 (11 significant bits, same rate) weights and activations, FP32 accumulation; FP32 chain
+ * state.  BST_FP32 / BST_FP64: CUDA-core paths (the plain precisions). */
+typedef enum { BST_BF16 = 0, BST_FP32 = 1, BST_FP64 = 2, BST_FP16 = 3 } bst_precision;
 typedef enum { BST_LIK_EMULATOR = 0, BST_LIK_ANALYTIC = 1 } bst_lik_kind;
 
 typedef struct {
   int d;              /* parameter dimension, 1..32                                   */
   int n_chains;       /* chains (AIES: a multiple of 4 * aies_walkers)                */
-  int precision;      /* bst_precision; BF16 requires an emulator                     */
+  int precision;      /* bst_precision; BF16 / FP16 require an emulator               */
   int lik_kind;       /* bst_lik_kind                                                 */
   uint64_t seed;      /* Philox4x32-10 key                                            */
   int max_depth;      /* NUTS doublings per iteration (1..10; 0 -> 8)                 */
@@ -89,7 +92,7 @@ void bst_destroy(bst_handle h);
  *   u = (x - in_m) / in_s;  h_1 = tanh(W_1 u + b_1);  h_l = tanh(W_l h_{l-1} + b_l);
  *   out = w_o . h_D + b_o;  chi2 = out_s * out + out_m;  logL = -chi2 / 2.
  * params (host, FP64, copied): W_1[width][d] b_1[width] (W_l[width][width] b_l[width])
- * for l = 2..depth, then w_o[width], b_o.  width in {256, 512} for BF16, any
+ * for l = 2..depth, then w_o[width], b_o.  width in {256, 512} for BF16 / FP16, any
  * multiple of 64 up to 1024 for FP32 (up to 512 for FP64); depth 1..8.
  * Errors: BST_ERR_ARG, BST_ERR_UNSUPPORTED, BST_ERR_NONFINITE (non-finite weight). */
 bst_status bst_set_emulator(bst_handle h, int depth, int width, const double *params,
@@ -166,7 +169,7 @@ bst_status bst_grad_loglike(bst_handle h, const void *theta_dev, int m, void *lo
  * loads the library holds until the process exits (for the activations), and
  * calls no cudaMalloc, cudaFree or other allocating routine.
  * Arguments and results are those of bst_grad_loglike.  Limit: m times the
- * bytes kept per point, (depth - 1) x width x (2 for BF16, 4 for FP32, 8 for
+ * bytes kept per point, (depth - 1) x width x (2 for BF16 / FP16, 4 for FP32, 8 for
  * FP64), must fit in 16 MiB (for example m <= 5461 for a BF16 8-512x4-1
  * emulator); a larger m returns BST_ERR_ARG and launches nothing.
  * The first call on each device looks the array's device address up with

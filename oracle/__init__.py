@@ -96,6 +96,8 @@ def lib():
             L.orc_normals.argtypes = [u64, u32, u32, u32, i, vp]
             L.orc_bf16_round.argtypes = [d]
             L.orc_bf16_round.restype = d
+            L.orc_fp16_round.argtypes = [d]
+            L.orc_fp16_round.restype = d
             L.orc_loglike.argtypes = [vp, vp, vp]
             L.orc_loglike.restype = d
             L.orc_loglike_batch.argtypes = [vp, i, vp, vp, vp]
@@ -150,12 +152,16 @@ def bf16_round(v):
     return lib().orc_bf16_round(float(v))
 
 
+def fp16_round(v):
+    return lib().orc_fp16_round(float(v))
+
+
 # --------------------------------------------------------------------------- model
 class Model:
     """Owns the numpy arrays behind an ``orc_model`` (keeps them alive)."""
 
     def __init__(self, d, *, lik="emulator", lower=None, upper=None, gauss=None, mu=None, L=None,
-                 analytic=None, emulator=None, bf16=False):
+                 analytic=None, emulator=None, bf16=False, fp16=False):
         self._keep = []
         s = _Model()
         s.d = d
@@ -181,7 +187,7 @@ class Model:
             s.params, s.in_m, s.in_s = _ptr(P), _ptr(in_m), _ptr(in_s)
             s.out_m, s.out_s = float(e["out_m"]), float(e["out_s"])
             s.out_log, s.out_floor = int(e.get("out_log", 0)), float(e.get("out_floor", 0.0))
-            s.bf16 = int(bf16)
+            s.bf16 = 2 if fp16 else int(bool(bf16))
         lower = _f64(np.full(d, -np.inf) if lower is None else lower)
         upper = _f64(np.full(d, np.inf) if upper is None else upper)
         mu = _f64(np.zeros(d) if mu is None else mu)

@@ -109,6 +109,23 @@ double orc_bf16_round(double v) {
   return ldexp(r, e - 8);
 }
 
+/* Round to the nearest IEEE 754 binary16 value (11 significant bits, exponent range
+ * 2^-14 .. 2^15, subnormals in steps of 2^-24), ties to even; |v| >= 65520 gives inf. */
+double orc_fp16_round(double v) {
+  if (v == 0.0 || !isfinite(v)) return v;
+  const double a = fabs(v);
+  if (a >= 65520.0) return v > 0 ? INFINITY : -INFINITY;
+  if (a < ldexp(1.0, -14)) return ldexp(nearbyint(ldexp(v, 24)), -24);
+  int e;
+  double m = frexp(v, &e);         /* v = m 2^e, 0.5 <= |m| < 1 */
+  return ldexp(nearbyint(ldexp(m, 11)), e - 11);
+}
+
+/* Operand rounding of the emulation modes: 1 BF16, 2 FP16, else exact. */
+static double oround(double v, int mode) {
+  return mode == 1 ? orc_bf16_round(v) : (mode == 2 ? orc_fp16_round(v) : v);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Likelihoods                                                              */
 /* ------------------------------------------------------------------------ */
@@ -158,7 +175,10 @@ static double analytic_logl(const orc_model *m, const double *x, double *grad) {
  * the log output is that of the linear one times exp(out_s out + out_m) (chain rule).
  * BF16 mode: operands of the hidden-to-hidden products (W_2..W_D, h_1..h_{D-1})
  * and every adjoint vector delta_1..delta_D are rounded to bfloat16; the input
- * layer, the output layer and all sums are exact.                            */
+ * layer, the output layer and all sums are exact.  FP16 mode rounds the same
+ * operands to binary16, and seeds the adjoint with -w_o (1 - h_D^2) / 2 (without
+ * out_s, which scales the input gradient instead: the tensor-core engine keeps
+ * the FP16 adjoint vectors away from the range limit that way).               */
 static double emulator_logl(const orc_model *m, const double *x, double *grad) {
   const int d = m->d, D = m->depth, w = m->width, bf = m->bf16;
   const double *P = m->params;
@@ -186,13 +206,13 @@ static double emulator_logl(const orc_model *m, const double *x, double *grad) {
         const double *hp = h + (size_t)(l - 2) * w;
         for (int j = 0; j < w; ++j) {
           double wkj = W[l][(size_t)k * w + j];
-          a += (bf ? orc_bf16_round(wkj) : wkj) * hp[j];
+          a += oround(wkj, bf) * hp[j];
         }
       }
       hl[k] = tanh(a);
     }
     if (bf && l < D)
-      for (int k = 0; k < w; ++k) hl[k] = orc_bf16_round(hl[k]);
+      for (int k = 0; k < w; ++k) hl[k] = oround(hl[k], bf);
   }
   const double *hD = h + (size_t)(D - 1) * w;
   double out = bo;
@@ -204,10 +224,11 @@ static double emulator_logl(const orc_model *m, const double *x, double *grad) {
   if (grad) {
     double *dl = (double *)malloc(sizeof(double) * (size_t)w);
     double *dn = (double *)malloc(sizeof(double) * (size_t)w);
-    const double c = -0.5 * m->out_s; /* d logL / d out */
+    const double c = (bf == 2) ? -0.5 : -0.5 * m->out_s; /* d logL / d out (FP16: without out_s) */
+    const double gscale = tfac * ((bf == 2) ? m->out_s : 1.0);
     for (int k = 0; k < w; ++k) {
       dl[k] = c * wo[k] * (1.0 - hD[k] * hD[k]);
-      if (bf) dl[k] = orc_bf16_round(dl[k]);
+      if (bf) dl[k] = oround(dl[k], bf);
     }
     for (int l = D; l >= 2; --l) {
       const double *hp = h + (size_t)(l - 2) * w;
@@ -215,17 +236,17 @@ static double emulator_logl(const orc_model *m, const double *x, double *grad) {
         double s = 0.0;
         for (int k = 0; k < w; ++k) {
           double wkj = W[l][(size_t)k * w + j];
-          s += (bf ? orc_bf16_round(wkj) : wkj) * dl[k];
+          s += oround(wkj, bf) * dl[k];
         }
         dn[j] = s * (1.0 - hp[j] * hp[j]);
-        if (bf) dn[j] = orc_bf16_round(dn[j]);
+        if (bf) dn[j] = oround(dn[j], bf);
       }
       memcpy(dl, dn, sizeof(double) * (size_t)w);
     }
     for (int j = 0; j < d; ++j) {
       double s = 0.0;
       for (int k = 0; k < w; ++k) s += W[1][k * d + j] * dl[k];
-      grad[j] = s / m->in_s[j] * tfac;
+      grad[j] = s / m->in_s[j] * gscale;
     }
     free(dl);
     free(dn);

@@ -55,7 +55,7 @@ typedef struct {
   const double *params;
   const double *in_m, *in_s;  /* input standardisation u = (x - m)/s       */
   double out_m, out_s;        /* chi2_hat = out_s * out + out_m            */
-  int bf16;                   /* 1: BF16 operand-rounding emulation mode   */
+  int bf16;                   /* operand-rounding emulation: 1 BF16, 2 FP16 */
   /* prior: hard box on every dim; N(0,1) on dims with gauss[i] != 0       */
   const double *lower, *upper;
   const int *gauss;           /* [d] or NULL                               */
@@ -69,6 +69,7 @@ typedef struct {
 } orc_model;
 
 /* ---- Philox4x32-10 and the draws built on it ---- */
+double orc_fp16_round(double v);
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_uniform(uint64_t seed, uint32_t chain, uint32_t iter, uint32_t purpose, uint32_t idx);
 void orc_normals(uint64_t seed, uint32_t chain, uint32_t iter, uint32_t purpose, int n, double *out);

@@ -20,13 +20,13 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import AIES, BF16, FP32, FP64, HMC, LIK_ANALYTIC, LIK_EMULATOR, MALA, MH, NUTS, BstError
+from ._lib import AIES, BF16, FP16, FP32, FP64, HMC, LIK_ANALYTIC, LIK_EMULATOR, MALA, MH, NUTS, BstError
 
 __all__ = ["Sampler", "Results", "BstError", "EmulatorLogL", "emulator_logl", "KERNELS", "PRECISIONS",
            "n_params", "r_minus_1_combine"]
 
 KERNELS = {"mh": MH, "mala": MALA, "hmc": HMC, "nuts": NUTS, "aies": AIES}
-PRECISIONS = {"bf16": BF16, "fp32": FP32, "fp64": FP64}
+PRECISIONS = {"bf16": BF16, "fp16": FP16, "fp32": FP32, "fp64": FP64}
 
 
 def n_params(d, depth, width):

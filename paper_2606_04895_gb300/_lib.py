@@ -14,7 +14,7 @@ OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_NOT_PD, ERR_TIMEOUT, ERR_NONFINITE, ERR_UN
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_STATE", "ERR_CUDA", "ERR_NOT_PD", "ERR_TIMEOUT", "ERR_NONFINITE",
                 "ERR_UNSUPPORTED"]
 MH, MALA, HMC, NUTS, AIES = range(5)
-BF16, FP32, FP64 = range(3)
+BF16, FP32, FP64, FP16 = range(4)
 LIK_EMULATOR, LIK_ANALYTIC = range(2)
 
 # Every symbol include/bst.h declares.

@@ -177,6 +177,10 @@ bst_status download_real(bst_ctx *h, double *dst, const void *src, size_t n) {
   return BST_OK;
 }
 
+// The tensor-core engine serves BF16 and FP16 operands (same kernels, operand type a flag).
+bool tc_engine(const bst_ctx *h) { return h->precision == BST_BF16 || h->precision == BST_FP16; }
+int is_f16(const bst_ctx *h) { return h->precision == BST_FP16 ? 1 : 0; }
+
 bst_status check_status(bst_ctx *h) {
   int st = 0;
   BST_CUDA(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -298,6 +302,7 @@ Tc2Weights tc2_weights(bst_ctx *h, int fold, int n_rows) {
   w.out_s = static_cast<float>(h->out_s);
   w.out_log = h->out_log;
   w.out_floor = static_cast<float>(h->out_floor);
+  w.f16 = is_f16(h);
   w.scratch = static_cast<__nv_bfloat16 *>(h->scratch);
   {
     // the exchange images follow the stored activations of h->scratch_rows rows
@@ -332,12 +337,12 @@ AnaWeights<R> ana_weights(bst_ctx *h, int fold) {
 // activations, then (BF16) one slice image per CTA for the cluster exchange through global
 // memory (whole 128-row tiles: 128 x width BF16 per tile), 256-byte aligned.
 size_t act_bytes_for(const bst_ctx *h, size_t rows) {
-  const size_t el = (h->precision == BST_BF16) ? 2 : h->rs;
+  const size_t el = (tc_engine(h)) ? 2 : h->rs;
   const size_t b = rows * static_cast<size_t>(h->depth > 1 ? h->depth - 1 : 1) * h->width * el;
   return (b + 255) / 256 * 256;
 }
 size_t xchg_bytes_for(const bst_ctx *h, size_t rows) {
-  if (h->precision != BST_BF16) return 0;
+  if (!tc_engine(h)) return 0;
   return (rows + kTcRows - 1) / kTcRows * kTcRows * static_cast<size_t>(h->width) * 2;
 }
 size_t scratch_bytes_for(const bst_ctx *h, size_t rows) { return act_bytes_for(h, rows) + xchg_bytes_for(h, rows); }
@@ -380,19 +385,19 @@ bst_status prepare(bst_ctx *h, cudaStream_t s) {
         for (int ci = 0; ci < 3; ++ci) {
           const int cs = 1 << ci, ns = w / cs, tr = ns < 256 ? ns : 256;
           for (int rk = 0; rk < cs; ++rk)
-            BST_CUDA(launch_pack_tc2_l1(h->W1f[f], dp, h->kb1, rk, ns, tr,
+            BST_CUDA(launch_pack_tc2_l1(h->W1f[f], dp, h->kb1, rk, ns, tr, is_f16(h),
                                         h->tl1[f][ci] + static_cast<size_t>(rk) * ns * h->kb1 * 128, s));
         }
-        BST_CUDA(launch_pack_tc_g1(h->W1f[f], dp, w, h->tg1[f], s));
+        BST_CUDA(launch_pack_tc_g1(h->W1f[f], dp, w, is_f16(h), h->tg1[f], s));
         BST_CUDA(launch_cast_f32(h->b1f[f], h->tb1[f], w, s));
       }
     }
-    if (h->precision == BST_BF16) {
+    if (tc_engine(h)) {
       for (int ci = 0; ci < 3; ++ci) {
         const int cs = 1 << ci, ns = w / cs, tr = ns < 256 ? ns : 256;
         const size_t stride = 2 * static_cast<size_t>(D > 1 ? D - 1 : 0) * ns * w * 2;
         for (int rk = 0; rk < cs; ++rk)
-          BST_CUDA(launch_pack_tc2_hidden(h->P64, d, D, w, rk, ns, tr, h->thid[ci] + rk * stride, s));
+          BST_CUDA(launch_pack_tc2_hidden(h->P64, d, D, w, rk, ns, tr, is_f16(h), h->thid[ci] + rk * stride, s));
       }
       for (int l = 2; l <= D; ++l) {
         const size_t ob = static_cast<size_t>(d) * w + w + static_cast<size_t>(l - 2) * (static_cast<size_t>(w) * w + w) +
@@ -450,7 +455,7 @@ bst_status run(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_steps, vo
       a.st.gle_ld = h->d;
     }
     if (h->lik == BST_LIK_ANALYTIC) BST_CUDA(launch_ana_simt_f32(a, ana_weights<float>(h, fold), s));
-    else if (h->precision == BST_BF16) BST_CUDA(launch_emu_tc2(a, tc2_weights(h, fold, a.n_rows), s));
+    else if (tc_engine(h)) BST_CUDA(launch_emu_tc2(a, tc2_weights(h, fold, a.n_rows), s));
     else BST_CUDA(launch_emu_simt_f32(a, emu_weights<float>(h, fold), s));
   }
   return BST_OK;
@@ -512,11 +517,11 @@ bst_status bst_create(bst_handle *out, const bst_config *cfg) {
   *out = nullptr;
   if (cfg->d < 1 || cfg->d > kMaxD) return fail(BST_ERR_ARG, "bst_create: d must be in 1..32");
   if (cfg->n_chains < 1) return fail(BST_ERR_ARG, "bst_create: n_chains must be >= 1");
-  if (cfg->precision < BST_BF16 || cfg->precision > BST_FP64) return fail(BST_ERR_ARG, "bst_create: precision");
+  if (cfg->precision < BST_BF16 || cfg->precision > BST_FP16) return fail(BST_ERR_ARG, "bst_create: precision");
   if (cfg->lik_kind != BST_LIK_EMULATOR && cfg->lik_kind != BST_LIK_ANALYTIC)
     return fail(BST_ERR_ARG, "bst_create: lik_kind");
-  if (cfg->precision == BST_BF16 && cfg->lik_kind != BST_LIK_EMULATOR)
-    return fail(BST_ERR_UNSUPPORTED, "bst_create: BF16 precision needs the emulator likelihood");
+  if ((cfg->precision == BST_BF16 || cfg->precision == BST_FP16) && cfg->lik_kind != BST_LIK_EMULATOR)
+    return fail(BST_ERR_UNSUPPORTED, "bst_create: BF16 / FP16 precision needs the emulator likelihood");
   const int md = cfg->max_depth ? cfg->max_depth : 8;
   if (md < 1 || md > kMaxDepthNuts) return fail(BST_ERR_ARG, "bst_create: max_depth must be in 1..10");
   const int wk = cfg->aies_walkers ? cfg->aies_walkers : 64;
@@ -594,7 +599,7 @@ bst_status bst_set_emulator(bst_handle h, int depth, int width, const double *pa
   if (h->lik != BST_LIK_EMULATOR) return fail(BST_ERR_STATE, "bst_set_emulator: handle was created for the analytic likelihood");
   if (depth < 1 || depth > 8) return fail(BST_ERR_ARG, "bst_set_emulator: depth must be in 1..8");
   if (width < 256 || width % 256) return fail(BST_ERR_UNSUPPORTED, "bst_set_emulator: width must be a multiple of 256");
-  if (h->precision == BST_BF16 && width > 512) return fail(BST_ERR_UNSUPPORTED, "bst_set_emulator: BF16 width must be 256 or 512");
+  if (tc_engine(h) && width > 512) return fail(BST_ERR_UNSUPPORTED, "bst_set_emulator: BF16 / FP16 width must be 256 or 512");
   if (h->precision == BST_FP64 && width > 512) return fail(BST_ERR_UNSUPPORTED, "bst_set_emulator: FP64 width must be <= 512");
   if (width > 1024) return fail(BST_ERR_UNSUPPORTED, "bst_set_emulator: width must be <= 1024");
   const int d = h->d;
@@ -617,7 +622,7 @@ bst_status bst_set_emulator(bst_handle h, int depth, int width, const double *pa
       BST_TRY(dalloc_t(h, &h->W1f[f], w * dp));
       BST_TRY(dalloc_t(h, &h->b1f[f], w));
     }
-    if (h->precision == BST_BF16) {
+    if (tc_engine(h)) {
       for (int f = 0; f < 2; ++f) {
         for (int ci = 0; ci < 3; ++ci) BST_TRY(dalloc(h, (void **)&h->tl1[f][ci], w * h->kb1 * 128));
         BST_TRY(dalloc(h, (void **)&h->tg1[f], (w / 64) * 2 * dp * 128));
@@ -817,7 +822,7 @@ bst_status bst_step(bst_handle h, int kernel, double eps, int n_leapfrog, int n_
   if (kernel == BST_HMC && n_leapfrog < 1) return fail(BST_ERR_ARG, "bst_step: n_leapfrog must be >= 1");
   if (kernel == BST_AIES) {
     const int half = h->walkers / 2;
-    const int tile = (h->precision == BST_BF16) ? kTcRows : simt_rows_per_tile(h->precision, h->width, h->lik);  // chains per tile
+    const int tile = (tc_engine(h)) ? kTcRows : simt_rows_per_tile(h->precision, h->width, h->lik);  // chains per tile
     if (h->n % h->walkers) return fail(BST_ERR_ARG, "bst_step: AIES needs n_chains to be a multiple of aies_walkers");
     if (tile % half) return fail(BST_ERR_UNSUPPORTED, "bst_step: AIES ensemble halves must not span chain tiles");
   }
@@ -865,7 +870,7 @@ static bst_status loglike_impl(bst_handle h, const void *theta, int m, void *log
   BST_TRY(prepare(h, s));
   const int chunk = h->n > 65536 ? h->n : 65536;
   // (the BF16 engine also needs the scratch for the cluster exchange of forward-only runs)
-  if (need_grad || h->precision == BST_BF16) BST_TRY(ensure_scratch(h, chunk < m ? chunk : m));
+  if (need_grad || tc_engine(h)) BST_TRY(ensure_scratch(h, chunk < m ? chunk : m));
   const size_t rs = h->rs;
   for (int r0 = 0; r0 < m; r0 += chunk) {
     const int rows = (m - r0) < chunk ? (m - r0) : chunk;
@@ -1631,7 +1636,7 @@ extern "C" bst_status bst_grad_loglike_noalloc(bst_handle h, const void *theta_d
   if (m == 0) return BST_OK;
   size_t row_bytes = 0;  // activation bytes the adjoint keeps per evaluated point
   if (h->lik == BST_LIK_EMULATOR) {
-    const size_t el = (h->precision == BST_BF16) ? 2 : h->rs;
+    const size_t el = (tc_engine(h)) ? 2 : h->rs;
     row_bytes = static_cast<size_t>(h->depth > 1 ? h->depth - 1 : 1) * h->width * el;
     const size_t max_rows = kStaticScratchBytes / row_bytes;
     if (static_cast<size_t>(m) > max_rows)
@@ -1670,7 +1675,7 @@ extern "C" bst_status bst_grad_loglike_noalloc(bst_handle h, const void *theta_d
     a.st.gle_ld = h->d;
     if (h->lik == BST_LIK_ANALYTIC) {
       BST_CUDA(launch_ana_simt_f32(a, ana_weights<float>(h, 1), s));
-    } else if (h->precision == BST_BF16) {
+    } else if (tc_engine(h)) {
       Tc2Weights w = tc2_weights(h, 1, m);
       w.scratch = static_cast<__nv_bfloat16 *>(scratch);
       // exchange images after the activations if they fit, else the shared->shared exchange

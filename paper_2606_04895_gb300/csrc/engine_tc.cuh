@@ -78,9 +78,9 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= static_cast<uint64_t>(2) << 61;            // 128-byte swizzle
   return d;
 }
-// Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+// Instruction descriptor: kind::f16, A = B = BF16 (or, f16, both FP16), D = FP32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool f16 = false) {
+  return (1u << 4) | (f16 ? 0u : ((1u << 7) | (1u << 10))) | (static_cast<uint32_t>(N >> 3) << 17) |
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -102,6 +102,25 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int j) {
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t *>(&v);
+}
+// Operand type of the tensor-core engine: BF16 (8 significant bits) or, f16, FP16 (11
+// significant bits, the same MMA rate).  Round to nearest even in both.
+__device__ __forceinline__ uint32_t pack_op2(float lo, float hi, bool f16) {
+  if (f16) {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+  }
+  return pack_bf16x2(lo, hi);
+}
+__device__ __forceinline__ float op_round(float x, bool f16) {
+  return f16 ? __half2float(__float2half_rn(x)) : __bfloat162float(__float2bfloat16_rn(x));
+}
+// the value in the low / high 16 bits of a packed pair
+__device__ __forceinline__ float op_lo(uint32_t v, bool f16) {
+  return f16 ? __half2float(__ushort_as_half(static_cast<unsigned short>(v & 0xFFFFu))) : __uint_as_float(v << 16);
+}
+__device__ __forceinline__ float op_hi(uint32_t v, bool f16) {
+  return f16 ? __half2float(__ushort_as_half(static_cast<unsigned short>(v >> 16))) : __uint_as_float(v & 0xFFFF0000u);
 }
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)

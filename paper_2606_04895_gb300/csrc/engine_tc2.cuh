@@ -57,6 +57,8 @@ struct Tc2Weights {
   float bo, out_m, out_s;
   int out_log;        // chi2 = out_floor + exp(out_s out + out_m) instead of out_s out + out_m
   float out_floor;
+  int f16;            // operands FP16 instead of BF16; the adjoint is then seeded with
+                      // -w_o (1 - h_D^2) / 2 and the input gradient scaled by out_s
   __nv_bfloat16 *scratch;  // [rows][D-1][w] stored activations (unless in tensor memory)
   uint8_t *xchg;           // [CTAs][128 x NS BF16] slice images of the cluster exchange
   size_t xchg_bytes;
@@ -393,7 +395,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
       int s = 0;
       uint32_t go_par = 0, act_par = 0, own_par = 0;
       bool ok = true;
-      const uint32_t idn = idesc_bf16(128, TR), idg = idesc_bf16(128, 2 * dp);
+      const uint32_t idn = idesc_bf16(128, TR, E.f16 != 0), idg = idesc_bf16(128, 2 * dp, E.f16 != 0);
       // descriptors of K block 0 of the activation and of stage 0; K block kb / stage s / the
       // k-th 16-wide step are offsets of kb * 16384, s * STAGE and k * 32 bytes (address >> 4)
       const uint64_t adesc0 = sw128_desc(smem_u32(act)), bdesc0 = sw128_desc(smem_u32(stages));
@@ -503,7 +505,10 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
       return __shfl_sync(0xffffffffu, got, 0) != 0;
     };
     const size_t sstride = static_cast<size_t>(D > 1 ? D - 1 : 1) * W;
-    const float c0 = -0.5f * E.out_s;
+    const bool f16 = E.f16 != 0;
+    // adjoint seed scale (FP16: without out_s, applied to the input gradient instead, so the
+    // adjoint vectors stay far from the FP16 range limit whatever the output scale)
+    const float c0 = f16 ? -0.5f : -0.5f * E.out_s;
     for (int ev = 0;; ++ev) {
       const int h = ev & 1;
       bool need = false;
@@ -551,10 +556,10 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
         uint32_t hi2[4], lo2[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float h0 = __bfloat162float(__float2bfloat16_rn(zv[2 * u]));
-          const float h1 = __bfloat162float(__float2bfloat16_rn(zv[2 * u + 1]));
-          hi2[u] = pack_bf16x2(h0, h1);
-          lo2[u] = pack_bf16x2(zv[2 * u] - h0, zv[2 * u + 1] - h1);
+          const float h0 = op_round(zv[2 * u], f16);
+          const float h1 = op_round(zv[2 * u + 1], f16);
+          hi2[u] = pack_op2(h0, h1, f16);
+          lo2[u] = pack_op2(zv[2 * u] - h0, zv[2 * u + 1] - h1, f16);
         }
         const int j0 = 4 * ch;
         st_shared_v4(act_addr + sw128_off(r, j0), hi2[0], hi2[1], hi2[2], hi2[3]);
@@ -574,11 +579,11 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
           for (int u = 0; u < 8; ++u) {
             const int i = i0 + u;
             const float zval = (valid && seg < 3 && i < a.d) ? zr[i * zes] : 0.f;
-            const float hi = __bfloat162float(__float2bfloat16_rn(zval));
+            const float hi = op_round(zval, f16);
             v[u] = (seg == 1) ? (zval - hi) : hi;
           }
-          st_shared_v4(act_addr + (j >> 3) * 16384 + sw128_off(r, j & 7), pack_bf16x2(v[0], v[1]),
-                       pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+          st_shared_v4(act_addr + (j >> 3) * 16384 + sw128_off(r, j & 7), pack_op2(v[0], v[1], f16),
+                       pack_op2(v[2], v[3], f16), pack_op2(v[4], v[5], f16), pack_op2(v[6], v[7], f16));
         }
       }
       fence_proxy_async();
@@ -678,8 +683,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
             } else if (ht) {
 #pragma unroll
               for (int i = 0; i < 16; ++i) {
-                aux[2 * i] = __uint_as_float(hv16[i] << 16);           // low half: even column
-                aux[2 * i + 1] = __uint_as_float(hv16[i] & 0xFFFF0000u);  // high half: odd column
+                aux[2 * i] = op_lo(hv16[i], f16);      // low half: even column
+                aux[2 * i + 1] = op_hi(hv16[i], f16);  // high half: odd column
               }
             } else {
               // stored activations of this chunk were loaded one chunk ahead; start the next one
@@ -687,9 +692,12 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
               const uint4 *hp = more ? reinterpret_cast<const uint4 *>(hprev + gcol + 32) : nullptr;
 #pragma unroll
               for (int u = 0; u < 4; ++u) hnext[u] = more ? __ldcs(hp + u) : make_uint4(0, 0, 0, 0);
-              const __nv_bfloat16 *hh = reinterpret_cast<const __nv_bfloat16 *>(hcur);
+              const uint32_t *hh = reinterpret_cast<const uint32_t *>(hcur);
 #pragma unroll
-              for (int i = 0; i < 32; ++i) aux[i] = __bfloat162float(hh[i]);
+              for (int i = 0; i < 16; ++i) {
+                aux[2 * i] = op_lo(hh[i], f16);
+                aux[2 * i + 1] = op_hi(hh[i], f16);
+              }
             }
             if (!fwd) {
 #pragma unroll
@@ -712,6 +720,11 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
                     v[i] = c0 * wv[k] * (1.f - hv * hv);
                   }
                 }
+              } else if (f16) {
+                // FP16 keeps 11 significant bits: tanh.approx (about 2^-11 relative error) would
+                // dominate its rounding, so the accurate form is used
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = tanh_out(__uint_as_float(raw[i]) + aux[i]);
               } else {
 #pragma unroll
                 for (int i = 0; i < 32; ++i) v[i] = tanh_fast(__uint_as_float(raw[i]) + aux[i]);
@@ -723,7 +736,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
             if (distribute) {
               uint32_t pk[16];
 #pragma unroll
-              for (int i = 0; i < 16; ++i) pk[i] = pack_bf16x2(v[2 * i], v[2 * i + 1]);
+              for (int i = 0; i < 16; ++i) pk[i] = pack_op2(v[2 * i], v[2 * i + 1], f16);
               // before the first write into the activation buffer: the peers' MMAs of this
               // phase are done with it (the first chunk's math overlaps the wait)
               if (CS > 1 && cc == 0 && !wait_free(free_bar, free_par)) ok = false;
@@ -825,23 +838,23 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
           float s_out = 0.f;
           for (int pr = 0; pr < CS; ++pr) s_out += partial[pr * 128 + r];
           const float arg = E.out_s * (s_out + E.bo) + E.out_m;
-          if (E.out_log) {
-            // log output: chi2 = floor + t, t = exp(arg); the adjoint ran with the linear
-            // output's seed, so the gradient takes the factor t (d chi2 / d arg)
-            const float tx = expf(arg);
-            lle_v = -0.5f * (E.out_floor + tx);
-            if (grad) {
+          // log output: chi2 = floor + t, t = exp(arg); the adjoint ran with the linear output's
+          // seed, so the gradient takes the factor t (d chi2 / d arg); with FP16 operands also
+          // out_s (see c0)
+          const float tx = E.out_log ? expf(arg) : 1.f;
+          lle_v = -0.5f * (E.out_log ? E.out_floor + tx : arg);
+          const float gfac = tx * (f16 ? E.out_s : 1.f);
+          {
+            if (grad && (E.out_log || f16)) {
               if (fast) {
 #pragma unroll
-                for (int i = 0; i < RegChain8<float>::DB; ++i) rc.gp[i] *= tx;
+                for (int i = 0; i < RegChain8<float>::DB; ++i) rc.gp[i] *= gfac;
               } else {
                 float *gout = a.st.gle + row_off(a.st.gle_ld, row, a.dp);
                 const int ges = row_es(a.st.gle_ld);
-                for (int i = 0; i < a.d; ++i) gout[i * ges] *= tx;
+                for (int i = 0; i < a.d; ++i) gout[i * ges] *= gfac;
               }
             }
-          } else {
-            lle_v = -0.5f * arg;
           }
           a.st.lle[row] = lle_v;
         }

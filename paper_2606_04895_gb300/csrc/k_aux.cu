@@ -105,19 +105,21 @@ cudaError_t launch_pack_simt_f64(const double *P, const double *W1f, const doubl
 // BF16 tile packing.  A tile is rows x 64 BF16 (128 bytes per row) in the 128-byte-swizzled
 // K-major layout the tcgen05 shared-memory descriptors expect: the 16-byte chunk j of row r sits
 // at r * 128 + ((j ^ (r % 8)) * 16).  Each thread writes one 16-byte chunk.
-__device__ __forceinline__ void put_chunk(uint8_t *tile, int r, int j, const float v[8]) {
-  __nv_bfloat16 h[8];
+__device__ __forceinline__ void put_chunk(uint8_t *tile, int r, int j, const float v[8], int f16) {
+  uint16_t h[8];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(v[e]);
+  for (int e = 0; e < 8; ++e)
+    h[e] = f16 ? __half_as_ushort(__float2half_rn(v[e])) : __bfloat16_as_ushort(__float2bfloat16_rn(v[e]));
   *reinterpret_cast<uint4 *>(tile + r * 128 + ((j ^ (r & 7)) << 4)) = *reinterpret_cast<uint4 *>(h);
 }
-__device__ __forceinline__ float bf16_hi(double v) {
-  return __bfloat162float(__double2bfloat16(v));
+// FP64 -> operand type (BF16, or FP16 when f16), round to nearest even, back as float
+__device__ __forceinline__ float bf16_hi(double v, int f16) {
+  return f16 ? __half2float(__double2half(v)) : __bfloat162float(__double2bfloat16(v));
 }
 
 // Input-gradient split tiles: rows [W1f^T hi (dp rows); W1f^T lo (dp rows)], cols = hidden
 // units, one tile of 2 dp rows per 64-column k-block.
-__global__ void pack_tc_g1_kernel(const double *W1f, int dp, int w, uint8_t *out) {
+__global__ void pack_tc_g1_kernel(const double *W1f, int dp, int w, int f16, uint8_t *out) {
   const int rows = 2 * dp, kbw = w / 64;
   const size_t chunks = static_cast<size_t>(kbw) * rows * 8;
   const size_t id = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
@@ -129,20 +131,21 @@ __global__ void pack_tc_g1_kernel(const double *W1f, int dp, int w, uint8_t *out
   for (int e = 0; e < 8; ++e) {
     const int k = kb * 64 + j * 8 + e;
     const double wv = W1f[static_cast<size_t>(k) * dp + i];
-    const float hi = bf16_hi(wv);
+    const float hi = bf16_hi(wv, f16);
     v[e] = (r < dp) ? hi : static_cast<float>(wv - static_cast<double>(hi));
   }
-  put_chunk(out + static_cast<size_t>(kb) * rows * 128, r, j, v);
+  put_chunk(out + static_cast<size_t>(kb) * rows * 128, r, j, v, f16);
 }
-cudaError_t launch_pack_tc_g1(const double *W1f, int dp, int w, uint8_t *out, cudaStream_t s) {
+cudaError_t launch_pack_tc_g1(const double *W1f, int dp, int w, int f16, uint8_t *out, cudaStream_t s) {
   const size_t chunks = static_cast<size_t>(w / 64) * 2 * dp * 8;
-  pack_tc_g1_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(W1f, dp, w, out);
+  pack_tc_g1_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(W1f, dp, w, f16, out);
   return cudaGetLastError();
 }
 
 // Per-rank streams for the cluster kernel: rank r owns output rows [r NS, (r + 1) NS) of
 // every layer, packed as tiles of TR rows x 64 columns (same swizzle as above).
-__global__ void pack_tc2_l1_kernel(const double *W1f, int dp, int kb1, int rank, int NS, int TR, uint8_t *out) {
+__global__ void pack_tc2_l1_kernel(const double *W1f, int dp, int kb1, int rank, int NS, int TR, int f16,
+                                   uint8_t *out) {
   const int nsub = NS / TR;
   const size_t chunks = static_cast<size_t>(nsub) * kb1 * TR * 8;
   const size_t id = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
@@ -158,21 +161,22 @@ __global__ void pack_tc2_l1_kernel(const double *W1f, int dp, int kb1, int rank,
     float x = 0.f;
     if (seg < 3) {
       const double wv = W1f[static_cast<size_t>(k) * dp + i];
-      const float hi = bf16_hi(wv);
+      const float hi = bf16_hi(wv, f16);
       x = (seg == 2) ? static_cast<float>(wv - static_cast<double>(hi)) : hi;
     }
     v[e] = x;
   }
-  put_chunk(out + static_cast<size_t>(tile) * TR * 128, r, j, v);
+  put_chunk(out + static_cast<size_t>(tile) * TR * 128, r, j, v, f16);
 }
-cudaError_t launch_pack_tc2_l1(const double *W1f, int dp, int kb1, int rank, int NS, int TR, uint8_t *out,
+cudaError_t launch_pack_tc2_l1(const double *W1f, int dp, int kb1, int rank, int NS, int TR, int f16, uint8_t *out,
                                cudaStream_t s) {
   const size_t chunks = static_cast<size_t>(NS / TR) * kb1 * TR * 8;
-  pack_tc2_l1_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(W1f, dp, kb1, rank, NS, TR, out);
+  pack_tc2_l1_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(W1f, dp, kb1, rank, NS, TR, f16, out);
   return cudaGetLastError();
 }
 
-__global__ void pack_tc2_hidden_kernel(const double *P, int d, int D, int w, int rank, int NS, int TR, uint8_t *out) {
+__global__ void pack_tc2_hidden_kernel(const double *P, int d, int D, int w, int rank, int NS, int TR, int f16,
+                                       uint8_t *out) {
   const int nsub = NS / TR, kbw = w / 64;
   const size_t per_layer = static_cast<size_t>(nsub) * kbw;
   const size_t chunks = 2 * static_cast<size_t>(D - 1) * per_layer * TR * 8;
@@ -187,19 +191,19 @@ __global__ void pack_tc2_hidden_kernel(const double *P, int d, int D, int w, int
   const int l = adj ? D - static_cast<int>(seg - (D - 1)) : static_cast<int>(seg) + 2;
   const double *Wl = P + off_W(l, d, w);
   const int row = rank * NS + sub * TR + r;
-  __nv_bfloat16 hb[8];
+  uint16_t hb[8];
   for (int e = 0; e < 8; ++e) {
     const int col = kb * 64 + j * 8 + e;
     const double x = adj ? Wl[static_cast<size_t>(col) * w + row] : Wl[static_cast<size_t>(row) * w + col];
-    hb[e] = __double2bfloat16(x);
+    hb[e] = f16 ? __half_as_ushort(__double2half(x)) : __bfloat16_as_ushort(__double2bfloat16(x));
   }
   *reinterpret_cast<uint4 *>(out + tile * TR * 128 + r * 128 + ((j ^ (r & 7)) << 4)) = *reinterpret_cast<uint4 *>(hb);
 }
-cudaError_t launch_pack_tc2_hidden(const double *P, int d, int D, int w, int rank, int NS, int TR, uint8_t *out,
-                                   cudaStream_t s) {
+cudaError_t launch_pack_tc2_hidden(const double *P, int d, int D, int w, int rank, int NS, int TR, int f16,
+                                   uint8_t *out, cudaStream_t s) {
   if (D < 2) return cudaSuccess;
   const size_t chunks = 2 * static_cast<size_t>(D - 1) * (NS / TR) * (w / 64) * TR * 8;
-  pack_tc2_hidden_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(P, d, D, w, rank, NS, TR, out);
+  pack_tc2_hidden_kernel<<<blocks_for(chunks, 256), 256, 0, s>>>(P, d, D, w, rank, NS, TR, f16, out);
   return cudaGetLastError();
 }
 

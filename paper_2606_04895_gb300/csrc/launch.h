@@ -36,11 +36,11 @@ cudaError_t launch_pack_simt_f64(const double *P, const double *W1f, const doubl
                                  double *wo, cudaStream_t s);
 // BF16 tensor-core tiles (pre-swizzled): layer-1 split tiles, hidden fwd + adjoint tiles,
 // input-gradient split tiles; FP32 biases.
-cudaError_t launch_pack_tc2_l1(const double *W1f, int dp, int kb1, int rank, int NS, int TR, uint8_t *out,
+cudaError_t launch_pack_tc2_l1(const double *W1f, int dp, int kb1, int rank, int NS, int TR, int f16, uint8_t *out,
                                cudaStream_t s);
-cudaError_t launch_pack_tc2_hidden(const double *P, int d, int D, int w, int rank, int NS, int TR, uint8_t *out,
-                                   cudaStream_t s);
-cudaError_t launch_pack_tc_g1(const double *W1f, int dp, int w, uint8_t *out, cudaStream_t s);
+cudaError_t launch_pack_tc2_hidden(const double *P, int d, int D, int w, int rank, int NS, int TR, int f16,
+                                   uint8_t *out, cudaStream_t s);
+cudaError_t launch_pack_tc_g1(const double *W1f, int dp, int w, int f16, uint8_t *out, cudaStream_t s);
 cudaError_t launch_cast_f32(const double *src, float *dst, size_t n, cudaStream_t s);
 cudaError_t launch_cast_f64(const double *src, double *dst, size_t n, cudaStream_t s);
 cudaError_t launch_cast_f32_to_f64(const float *src, double *dst, size_t n, cudaStream_t s);

@@ -29,8 +29,8 @@ def make_emulator_sampler(prec, e, n, *, mu, L, lower, upper, theta0, gauss=None
     return s
 
 
-def oracle_emulator_model(e, *, mu, L, lower, upper, gauss=None, bf16=False):
-    return O.Model(e["d"], emulator=e, lower=lower, upper=upper, gauss=gauss, mu=mu, L=L, bf16=bf16)
+def oracle_emulator_model(e, *, mu, L, lower, upper, gauss=None, bf16=False, fp16=False):
+    return O.Model(e["d"], emulator=e, lower=lower, upper=upper, gauss=gauss, mu=mu, L=L, bf16=bf16, fp16=fp16)
 
 
 def rel_err(a, b, floor=1e-12):

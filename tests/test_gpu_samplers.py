@@ -2,9 +2,9 @@
 states and identical Philox streams.
 
 Decisions must agree wherever |log alpha - log u| > 1e-3 (the oracle's trace
-gives both); where they agree the new positions must match (FP64: 1e-9; FP32
-and BF16: 1e-3 absolute in x).  BF16 runs are compared with the oracle's BF16
-operand-rounding mode."""
+gives both); where they agree the new positions must match (FP64: 1e-9; FP32,
+BF16 and FP16: 1e-3 absolute in x).  BF16 and FP16 runs are compared with the
+oracle's operand-rounding mode of the same type."""
 import numpy as np
 import pytest
 import torch
@@ -16,7 +16,7 @@ from gpu_common import emulator_case, make_emulator_sampler, oracle_emulator_mod
 pytestmark = pytest.mark.gpu
 
 MARGIN = 1e-3
-POS_TOL = {"fp64": 1e-9, "fp32": 1e-3, "bf16": 1e-3}
+POS_TOL = {"fp64": 1e-9, "fp32": 1e-3, "bf16": 1e-3, "fp16": 1e-3}
 
 
 def _setup(prec, n, d=8, width=256, depth=3, seed=11, **kw):
@@ -25,7 +25,8 @@ def _setup(prec, n, d=8, width=256, depth=3, seed=11, **kw):
     lower, upper = np.full(d, -3.0), np.full(d, 3.0)
     theta0 = np.clip(mu + np.random.default_rng(9).normal(size=(n, d)) @ L.T, -2.9, 2.9)
     s = make_emulator_sampler(prec, e, n, mu=mu, L=L, lower=lower, upper=upper, theta0=theta0, seed=seed, **kw)
-    m = oracle_emulator_model(e, mu=mu, L=L, lower=lower, upper=upper, bf16=(prec == "bf16"))
+    m = oracle_emulator_model(e, mu=mu, L=L, lower=lower, upper=upper, bf16=(prec == "bf16"),
+                              fp16=(prec == "fp16"))
     z0 = np.linalg.solve(L, (theta0 - mu).T).T
     return s, m, z0, mu, L
 
@@ -48,7 +49,7 @@ def _check(prec, s, ref, samples, kernel, n, margin=MARGIN):
     assert np.all(np.abs(x_gpu[clear] - x_ref[clear]) < POS_TOL[prec])
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("kernel,eps,extra", [("mh", 0.5, {}), ("mala", 0.4, {}), ("hmc", 0.2, {"n_leapfrog": 5}),
                                               ("nuts", 0.3, {})])
 def test_one_step_parity(prec, kernel, eps, extra):
@@ -61,7 +62,7 @@ def test_one_step_parity(prec, kernel, eps, extra):
     s.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "fp16"])
 def test_aies_one_step_parity(prec):
     n = 256  # 4 ensembles of 64 walkers
     s, m, z0, mu, L = _setup(prec, n)
@@ -146,32 +147,35 @@ def _setup_gauss(prec, n, width, d=8, seed=11, depth=3):
     theta0[:, :6] = np.clip(theta0[:, :6], -2.9, 2.9)
     s = make_emulator_sampler(prec, e, n, mu=mu, L=L, lower=lower, upper=upper, theta0=theta0, gauss=gauss,
                               seed=seed)
-    m = oracle_emulator_model(e, mu=mu, L=L, lower=lower, upper=upper, gauss=gauss, bf16=(prec == "bf16"))
+    m = oracle_emulator_model(e, mu=mu, L=L, lower=lower, upper=upper, gauss=gauss, bf16=(prec == "bf16"),
+                              fp16=(prec == "fp16"))
     z0 = np.linalg.solve(L, (theta0 - mu).T).T
     return s, m, z0
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("width", [256, 512])
 @pytest.mark.parametrize("kernel,eps,extra", [("mh", 0.5, {}), ("mala", 0.4, {}), ("hmc", 0.2, {"n_leapfrog": 5})])
-def test_bf16_register_chains_gaussian_prior_parity(width, kernel, eps, extra):
+def test_bf16_register_chains_gaussian_prior_parity(width, kernel, eps, extra, prec):
     n = 300
-    s, m, z0 = _setup_gauss("bf16", n, width)
+    s, m, z0 = _setup_gauss(prec, n, width)
     out = torch.empty((1, n, 8), dtype=s.dtype, device="cuda")
     s.step(kernel, 1, eps=eps, samples=out, **extra)
     ref = O.run(m, kernel, z0, eps=eps, n_steps=1, seed=11, trace=True, **extra)
     # BF16 log alpha after five leapfrogs differs from the oracle's BF16-emulation mode (exact
     # tanh, FP64 sums) by up to a few 1e-3, so HMC decisions are compared outside 1e-2
-    _check("bf16", s, ref, out, kernel, n, margin=1e-2 if kernel == "hmc" else MARGIN)
+    _check(prec, s, ref, out, kernel, n, margin=1e-2 if kernel == "hmc" else MARGIN)
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("kernel,extra", [("mala", {}), ("hmc", {"n_leapfrog": 3}), ("mh", {})])
-def test_bf16_register_chains_record_every_step(kernel, extra):
+def test_bf16_register_chains_record_every_step(kernel, extra, prec):
     """The register-resident chains write their state, counters and samples while the next
     evaluation runs: after a launch every step's sample, the counters and the state agree
     with the oracle run step by step, and the last sample is x of the final state."""
     n, steps = 256, 6
-    s, m, z0 = _setup_gauss("bf16", n, 512)
+    s, m, z0 = _setup_gauss(prec, n, 512)
     out = torch.full((steps, n, 8), float("nan"), dtype=s.dtype, device="cuda")
     s.step(kernel, steps, eps=0.3 if kernel != "hmc" else 0.15, samples=out, **extra)
     ref = O.run(m, kernel, z0, eps=0.3 if kernel != "hmc" else 0.15, n_steps=steps, seed=11, trace=True, **extra)
@@ -191,15 +195,16 @@ def test_bf16_register_chains_record_every_step(kernel, extra):
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("width", [256, 512])
-def test_bf16_mala_two_cta_clusters(width):
+def test_bf16_mala_two_cta_clusters(width, prec):
     """MALA with 6000 chains (clusters of two CTAs per 128-chain tile) against the oracle."""
     n = 6000
-    s, m, z0 = _setup_gauss("bf16", n, width, depth=2)
+    s, m, z0 = _setup_gauss(prec, n, width, depth=2)
     out = torch.empty((1, n, 8), dtype=s.dtype, device="cuda")
     s.step("mala", 1, eps=0.4, samples=out)
     ref = O.run(m, "mala", z0, eps=0.4, n_steps=1, seed=11, trace=True)
-    _check("bf16", s, ref, out, "mala", n)
+    _check(prec, s, ref, out, "mala", n)
     s.close()
 
 
@@ -217,12 +222,13 @@ def _setup27(prec, n, width=256, depth=2, seed=11):
     theta0[:, :6] = np.clip(theta0[:, :6], -2.9, 2.9)
     s = make_emulator_sampler(prec, e, n, mu=mu, L=L, lower=lower, upper=upper, theta0=theta0, gauss=gauss,
                               seed=seed)
-    m = oracle_emulator_model(e, mu=mu, L=L, lower=lower, upper=upper, gauss=gauss, bf16=(prec == "bf16"))
+    m = oracle_emulator_model(e, mu=mu, L=L, lower=lower, upper=upper, gauss=gauss, bf16=(prec == "bf16"),
+                              fp16=(prec == "fp16"))
     z0 = np.linalg.solve(L, (theta0 - mu).T).T
     return s, m, z0
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("kernel,eps,extra", [("mh", 0.6, {}), ("mala", 0.6, {}), ("hmc", 0.5, {"n_leapfrog": 4}),
                                               ("nuts", 0.5, {}), ("aies", 0.0, {"aies_walkers": 64})])
 def test_27d_one_step_parity(prec, kernel, eps, extra):
@@ -232,7 +238,7 @@ def test_27d_one_step_parity(prec, kernel, eps, extra):
     kw = {k: v for k, v in extra.items() if k != "aies_walkers"}
     s.step(kernel, 1, eps=eps, samples=out, **kw)
     ref = O.run(m, kernel, z0, eps=eps, n_steps=1, seed=11, trace=True, **extra)
-    _check(prec, s, ref, out, kernel, n, margin=1e-2 if (prec == "bf16" and kernel == "hmc") else MARGIN)
+    _check(prec, s, ref, out, kernel, n, margin=1e-2 if (prec in ("bf16", "fp16") and kernel == "hmc") else MARGIN)
     s.close()
 
 

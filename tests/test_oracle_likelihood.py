@@ -67,9 +67,10 @@ def test_analytic_gradient_finite_differences(kind):
         assert np.allclose(g[0], fd, rtol=1e-6, atol=1e-6 * np.abs(fd).max())
 
 
-def _torch_emulator(e, x, bf16=False):
+def _torch_emulator(e, x, bf16=False, fp16=False):
     W, b, wo, bo = S.unpack_emulator(e)
-    r = (lambda t: t.to(torch.bfloat16).to(torch.float64)) if bf16 else (lambda t: t)
+    r = ((lambda t: t.to(torch.bfloat16).to(torch.float64)) if bf16 else
+         (lambda t: t.to(torch.float16).to(torch.float64)) if fp16 else (lambda t: t))
     X = torch.tensor(x, dtype=torch.float64, requires_grad=True)
     u = (X - torch.tensor(e["in_m"])) / torch.tensor(e["in_s"])
     h = torch.tanh(u @ torch.tensor(W[0]).T + torch.tensor(b[0]))
@@ -131,6 +132,39 @@ def test_emulator_bf16_mode_matches_torch_rounding():
     # and BF16 differs from FP64 by a BF16-sized amount, not zero, not O(1)
     diff = np.abs(lpb - m.loglike(x, grad=False))
     assert np.all(diff > 0) and np.all(diff < 0.05 * e["out_s"])
+
+
+def test_emulator_fp16_mode_matches_torch_rounding():
+    """FP16 mode: hidden-product operands rounded to binary16 (torch's float16 conversion of the
+    FP64 values); logL equals the torch expression, and the gradient equals the BF16-free FP64
+    gradient to FP16 accuracy (the adjoint vectors are rounded too)."""
+    e = S.emulator(8, width=64, depth=4, seed=2, out_s=4.0)
+    mf = O.Model(8, emulator=e, fp16=True)
+    m = O.Model(8, emulator=e)
+    x = np.random.default_rng(3).uniform(-2, 2, (5, 8))
+    lpf, gf = mf.loglike(x)
+    logl, _ = _torch_emulator(e, x, fp16=True)
+    assert np.allclose(lpf, logl.detach().numpy(), rtol=1e-12, atol=1e-12)
+    lp, g = m.loglike(x)
+    diff = np.abs(lpf - lp)
+    mb = O.Model(8, emulator=e, bf16=True)
+    diff_b = np.abs(mb.loglike(x, grad=False) - lp)
+    # FP16 keeps three more bits than BF16: its error is several times smaller
+    assert np.all(diff > 0) and diff.max() < 0.25 * diff_b.max()
+    assert np.max(np.abs(gf - g)) < 5e-3 * np.max(np.abs(g))
+
+
+def test_emulator_fp16_mode_gradient_scale_is_out_s():
+    """The FP16 mode seeds the adjoint without out_s and scales the input gradient by out_s, so the
+    gradient is out_s times that of out_s = 1 (same roundings) and stays finite at an out_s whose
+    seed would overflow binary16 (65504) if out_s were inside it."""
+    e1 = S.emulator(6, width=32, depth=2, seed=7, out_s=1.0)
+    eb = dict(e1, out_s=3.0e7)
+    x = np.random.default_rng(0).uniform(-1, 1, (4, 6))
+    _, g1 = O.Model(6, emulator=e1, fp16=True).loglike(x)
+    _, gb = O.Model(6, emulator=eb, fp16=True).loglike(x)
+    assert np.all(np.isfinite(gb))
+    assert np.allclose(gb, 3.0e7 * g1, rtol=1e-15, atol=0)
 
 
 def test_whitened_density_log_det_identity():

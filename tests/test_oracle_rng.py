@@ -146,3 +146,24 @@ def test_bf16_round_random_against_torch():
     ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
     got = np.array([O.bf16_round(float(v)) for v in x])
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("v", [0.0, 1.0, -1.0, 1.0 + 2.0**-11, 1.0 + 3 * 2.0**-11, 65504.0, 65519.9, 65520.0,
+                               -70000.0, 2.0**-14, 2.0**-14 * 0.75, 2.0**-24, 2.0**-25, 3 * 2.0**-26, 1e-9,
+                               0.1, -0.3, 1234.5678])
+def test_fp16_round_matches_numpy(v):
+    """binary16 rounding (ties to even, subnormals, overflow to inf) against numpy's conversion."""
+    ref = float(np.float64(v).astype(np.float16))
+    got = O.fp16_round(v)
+    assert got == ref or (np.isinf(got) and np.isinf(ref) and np.sign(got) == np.sign(ref)), (v, got, ref)
+
+
+def test_fp16_round_random_against_numpy_and_torch():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(6000) * np.exp(rng.uniform(-20, 12, 6000))
+    ref = x.astype(np.float16).astype(np.float64)
+    got = np.array([O.fp16_round(float(v)) for v in x])
+    assert np.array_equal(got, ref)
+    f32 = x.astype(np.float32)
+    t = torch.from_numpy(f32).to(torch.float16).to(torch.float64).numpy()
+    assert np.array_equal(np.array([O.fp16_round(float(v)) for v in f32]), t)
