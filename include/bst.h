@@ -211,6 +211,16 @@ bst_status bst_adapt_cov(bst_handle h, double jitter0, double *mu_out, double *L
 bst_status bst_welford_stats(bst_handle h, double *n, double *mean, double *M2);
 bst_status bst_welford_merge(bst_handle h, double n, const double *mean, const double *M2);
 
+/* Smooth bounds (Sec. 3.1: outside the box the density is extended by a smooth exponential
+ * penalty that keeps it differentiable).  width[d] (host, copied): width_i > 0 replaces
+ * dimension i's hard box by the factor exp(-r_i^2 / 2), r_i = (x_i - clamp(x_i, lower_i,
+ * upper_i)) / width_i, so log pi gains -r_i^2 / 2 and its gradient -r_i / width_i (both
+ * continuous at the bounds; 0 inside); width_i = 0 keeps dimension i's hard box; width = NULL
+ * restores hard bounds everywhere.  Applies to every later bst_step; the chains' log pi and
+ * gradient are re-evaluated now.  Synchronises.
+ * Errors: BST_ERR_STATE (before bst_init_chains), BST_ERR_ARG (negative or non-finite width). */
+bst_status bst_set_bounds_penalty(bst_handle h, const double *width);
+
 /* Checkpoint / resume.  Host FP64 copies of the chain state: z[n][d], logp[n],
  * grad[n][d] (whitened), iteration counters iter[n].  Philox draws are keyed by
  * (seed, chain, iter), so a restored state continues bit-identically. */

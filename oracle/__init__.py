@@ -65,6 +65,7 @@ class _Model(C.Structure):
         ("lower", C.c_void_p), ("upper", C.c_void_p), ("gauss", C.c_void_p),
         ("mu", C.c_void_p), ("L", C.c_void_p),
         ("out_log", C.c_int), ("out_floor", C.c_double),
+        ("pen_w", C.c_void_p),
     ]
 
 
@@ -80,6 +81,7 @@ class _Trace(C.Structure):
     _fields_ = [
         ("samples", C.c_void_p), ("trace_logalpha", C.c_void_p), ("trace_logu", C.c_void_p),
         ("trace_accept", C.c_void_p), ("trace_depth", C.c_void_p), ("trace_nleaf", C.c_void_p),
+        ("trace_margin", C.c_void_p),
     ]
 
 
@@ -161,7 +163,7 @@ class Model:
     """Owns the numpy arrays behind an ``orc_model`` (keeps them alive)."""
 
     def __init__(self, d, *, lik="emulator", lower=None, upper=None, gauss=None, mu=None, L=None,
-                 analytic=None, emulator=None, bf16=False, fp16=False):
+                 analytic=None, emulator=None, bf16=False, fp16=False, pen_w=None):
         self._keep = []
         s = _Model()
         s.d = d
@@ -195,6 +197,9 @@ class Model:
         g = None if gauss is None else np.ascontiguousarray(gauss, dtype=np.int32)
         self._keep += [lower, upper, mu, L, g]
         s.lower, s.upper, s.mu, s.L, s.gauss = _ptr(lower), _ptr(upper), _ptr(mu), _ptr(L), _ptr(g)
+        pw = None if pen_w is None else _f64(pen_w)
+        self._keep.append(pw)
+        s.pen_w = _ptr(pw)
         self.s = s
         self.d = d
 
@@ -257,9 +262,10 @@ def run(model: Model, kernel, z, *, eps, n_steps, seed, n_leapfrog=10, max_depth
         la = np.zeros((n_steps, n)); lu = np.zeros((n_steps, n))
         ac = np.zeros((n_steps, n), dtype=np.int32); dp = np.zeros((n_steps, n), dtype=np.int32)
         nl = np.zeros((n_steps, n), dtype=np.int32)
+        mg = np.full((n_steps, n), np.inf)
         t.trace_logalpha, t.trace_logu, t.trace_accept = _ptr(la), _ptr(lu), _ptr(ac)
-        t.trace_depth, t.trace_nleaf = _ptr(dp), _ptr(nl)
-        out.update(log_alpha=la, log_u=lu, accept=ac, depth=dp, nleaf=nl)
+        t.trace_depth, t.trace_nleaf, t.trace_margin = _ptr(dp), _ptr(nl), _ptr(mg)
+        out.update(log_alpha=la, log_u=lu, accept=ac, depth=dp, nleaf=nl, margin=mg)
     rc = lib().orc_run(model.ref, C.byref(p), n, _ptr(z), _ptr(lp), _ptr(g), _ptr(it), _ptr(acc_stat),
                        _ptr(accepts), _ptr(evals), _ptr(div), C.byref(t))
     if rc != 0:

@@ -273,7 +273,12 @@ void orc_loglike_batch(const orc_model *m, int n, const double *x, double *logl,
  * The prior is a hard box (0 inside, -inf outside) times N(0,1) on the dims
  * flagged gauss (constant terms dropped).  The gradient returned is that of
  * logL + the Gaussian prior, mapped to z by L^T, and is defined outside the
- * box as well (leapfrog points outside the box keep moving).                */
+ * box as well (leapfrog points outside the box keep moving).
+ * Smooth bounds (Sec. 3.1, the likelihood extended outside the box by a smooth
+ * exponential penalty): on a dim with pen_w[i] > 0 the box does not reject;
+ * instead the density is multiplied by exp(-r_i^2 / 2), r_i = the distance of
+ * x_i outside [lower_i, upper_i] divided by pen_w[i] (0 inside), whose log is
+ * continuous with a continuous gradient -r_i / pen_w[i] at the bounds.        */
 double orc_logpost_z(const orc_model *m, const double *z, double *grad_z, double *x_out) {
   const int d = m->d;
   double *x = (double *)malloc(sizeof(double) * (size_t)d);
@@ -286,7 +291,14 @@ double orc_logpost_z(const orc_model *m, const double *z, double *grad_z, double
   double lp = orc_loglike(m, x, grad_z ? gx : NULL);
   int inside = 1;
   for (int i = 0; i < d; ++i) {
-    if (!(x[i] >= m->lower[i] && x[i] <= m->upper[i])) inside = 0;
+    if (m->pen_w && m->pen_w[i] > 0.0) {
+      const double out = x[i] < m->lower[i] ? x[i] - m->lower[i] : (x[i] > m->upper[i] ? x[i] - m->upper[i] : 0.0);
+      const double r = out / m->pen_w[i];
+      lp += -0.5 * r * r;
+      if (grad_z) gx[i] += -r / m->pen_w[i];
+    } else if (!(x[i] >= m->lower[i] && x[i] <= m->upper[i])) {
+      inside = 0;
+    }
     if (m->gauss && m->gauss[i]) {
       lp += -0.5 * x[i] * x[i];
       if (grad_z) gx[i] += -x[i];
@@ -345,6 +357,7 @@ typedef struct {
   double log_alpha, log_u;
   int accepted;
   int depth, nleaf, diverged;
+  double margin; /* NUTS: smallest decision margin of the iteration (test bookkeeping) */
 } step_out;
 
 /* Random-walk MH in whitened units: z' = z + eps xi, xi ~ N(0, I). */
@@ -454,6 +467,11 @@ typedef struct {
   double H0;
   double acc_sum;   /* sum over leaves of min(1, exp(H0 - H))       */
   int multinomial;  /* weights exp(H0 - H) instead of the slice      */
+  double margin;    /* smallest distance of a decision from its threshold so far: log-scale
+                     * tests (slice, Delta_max, multinomial weights) in absolute units,
+                     * uniform-against-ratio tests in probability units, U-turn dot products
+                     * relative to the sum of the magnitudes of their terms.  Bookkeeping for
+                     * the parity tests only; no decision depends on it.                  */
 } nuts_ctx;
 
 typedef struct {
@@ -481,15 +499,31 @@ static void tree_free(nuts_tree *t) {
   free(t->zc); free(t->gc);
 }
 
-/* U-turn criterion: (theta+ - theta-) . r- >= 0 and (theta+ - theta-) . r+ >= 0. */
-static int no_uturn(int d, const double *zm, const double *qm, const double *zp, const double *qp) {
-  double a = 0.0, b = 0.0;
+static void note_margin(double *margin, double m) {
+  m = fabs(m);
+  if (m < *margin) *margin = m;
+}
+
+/* U-turn criterion: (theta+ - theta-) . r- >= 0 and (theta+ - theta-) . r+ >= 0.
+ * margin (may be NULL) receives the relative distance of the two products from 0. */
+static int no_uturn_m(int d, const double *zm, const double *qm, const double *zp, const double *qp,
+                      double *margin) {
+  double a = 0.0, b = 0.0, aa = 0.0, bb = 0.0;
   for (int i = 0; i < d; ++i) {
     double dz = zp[i] - zm[i];
     a += dz * qm[i];
     b += dz * qp[i];
+    aa += fabs(dz * qm[i]);
+    bb += fabs(dz * qp[i]);
+  }
+  if (margin) {
+    note_margin(margin, aa > 0.0 ? a / aa : 1.0);
+    note_margin(margin, bb > 0.0 ? b / bb : 1.0);
   }
   return a >= 0.0 && b >= 0.0;
+}
+static int no_uturn(int d, const double *zm, const double *qm, const double *zp, const double *qp) {
+  return no_uturn_m(d, zm, qm, zp, qp, NULL);
 }
 
 /* BuildTree(theta, r, u, v, j, eps).  Input: the state (z, q, g) to extend from.
@@ -513,9 +547,12 @@ static void build_tree(nuts_ctx *c, const double *z, const double *q, const doub
       out->lw = c->H0 - H;
       out->n = 0.0;
       out->s = (H - c->H0 < NUTS_DELTA_MAX) ? 1 : 0;
+      note_margin(&c->margin, H - c->H0 - NUTS_DELTA_MAX);
     } else {
       out->n = (c->log_u <= -H) ? 1.0 : 0.0;
       out->s = (c->log_u < NUTS_DELTA_MAX - H) ? 1 : 0;
+      note_margin(&c->margin, c->log_u + H);
+      note_margin(&c->margin, c->log_u - NUTS_DELTA_MAX + H);
     }
     if (!out->s) c->diverged = 1;
     c->acc_sum += accept_prob(c->H0 - H);
@@ -556,16 +593,18 @@ static void build_tree(nuts_ctx *c, const double *z, const double *q, const doub
     if (c->multinomial) {
       const double lw_tot = log_add_exp(out->lw, t2.lw);
       take = u < exp(t2.lw - lw_tot);
+      note_margin(&c->margin, u - exp(t2.lw - lw_tot));
       out->lw = lw_tot;
     } else {
       take = ntot > 0.0 && u * ntot < t2.n;
+      if (ntot > 0.0) note_margin(&c->margin, u - t2.n / ntot);
     }
     if (take) {
       memcpy(out->zc, t2.zc, sizeof(double) * (size_t)d);
       memcpy(out->gc, t2.gc, sizeof(double) * (size_t)d);
       out->lpc = t2.lpc;
     }
-    out->s = no_uturn(d, out->zm, out->qm, out->zp, out->qp);
+    out->s = no_uturn_m(d, out->zm, out->qm, out->zp, out->qp, &c->margin);
     out->n = ntot;
   } else {
     out->s = 0;
@@ -578,6 +617,7 @@ static void nuts_step(const orc_model *m, const orc_step_params *p, uint32_t cha
   const int d = m->d;
   nuts_ctx c;
   c.m = m; c.p = p; c.chain = chain; c.it = it; c.leaf = 0; c.diverged = 0; c.acc_sum = 0.0;
+  c.margin = INFINITY;
   c.multinomial = (p->kernel == ORC_NUTS_MULTINOMIAL);
   double *q0 = nalloc(d);
   orc_normals(p->seed, chain, it, ORC_P_XI, d, q0);
@@ -616,6 +656,7 @@ static void nuts_step(const orc_model *m, const orc_step_params *p, uint32_t cha
       /* with probability min(1, n'/n) (multinomial: min(1, w'/w)), move to the new
        * subtree's candidate */
       double ut = orc_uniform(p->seed, chain, it, ORC_P_NUTS_TOP, (uint32_t)j);
+      note_margin(&c.margin, c.multinomial ? ut - exp(t.lw - lw) : ut - t.n / n);
       if (c.multinomial ? (ut < exp(t.lw - lw)) : (ut * n < t.n)) {
         memcpy(zs, t.zc, sizeof(double) * (size_t)d);
         memcpy(gs, t.gc, sizeof(double) * (size_t)d);
@@ -624,7 +665,7 @@ static void nuts_step(const orc_model *m, const orc_step_params *p, uint32_t cha
     }
     n += t.n;
     if (c.multinomial && t.s) lw = log_add_exp(lw, t.lw);
-    s = t.s && no_uturn(d, zm, qm, zp, qp);
+    s = t.s && no_uturn_m(d, zm, qm, zp, qp, &c.margin);
     j++;
   }
   o->accepted = (memcmp(zs, z, sizeof(double) * (size_t)d) != 0);
@@ -636,6 +677,7 @@ static void nuts_step(const orc_model *m, const orc_step_params *p, uint32_t cha
   o->diverged = c.diverged;
   o->log_alpha = 0.0;
   o->log_u = c.log_u;
+  o->margin = c.margin;
   *acc_stat = c.leaf > 0 ? c.acc_sum / c.leaf : 0.0;
   tree_free(&t);
   free(q0); free(zm); free(qm); free(gm); free(zp); free(qp); free(gp); free(zs); free(gs);
@@ -651,6 +693,8 @@ static void record(const orc_model *m, const orc_trace *tr, int n_chains, int t,
   if (tr->trace_accept) tr->trace_accept[k] = o->accepted;
   if (tr->trace_depth) tr->trace_depth[k] = o->depth;
   if (tr->trace_nleaf) tr->trace_nleaf[k] = o->nleaf;
+  /* NUTS takes many decisions per iteration (o->nleaf > 0); the others one Metropolis test */
+  if (tr->trace_margin) tr->trace_margin[k] = o->nleaf > 0 ? o->margin : fabs(o->log_alpha - o->log_u);
 }
 
 /* AIES stretch move (Sec. 2.3).  Walkers of one ensemble are split into halves S0, S1;

@@ -66,6 +66,9 @@ typedef struct {
    * 1 chi2_hat = out_floor + exp(out_s out + out_m)                       */
   int out_log;
   double out_floor;
+  /* smooth bounds penalty (Sec. 3.1): pen_w[i] > 0 replaces the hard box of dim i by
+   * log prior -= ((x_i - clamp(x_i, lower_i, upper_i)) / pen_w[i])^2 / 2; NULL = hard box */
+  const double *pen_w;
 } orc_model;
 
 /* ---- Philox4x32-10 and the draws built on it ---- */
@@ -102,6 +105,8 @@ typedef struct {
   int *trace_accept;    /* [n_steps][n] or NULL                    */
   int *trace_depth;     /* [n_steps][n] NUTS doublings, or NULL    */
   int *trace_nleaf;     /* [n_steps][n] NUTS leapfrogs, or NULL    */
+  double *trace_margin; /* [n_steps][n] NUTS: the smallest distance of any decision of the
+                         * iteration from its threshold (see nuts_step), or NULL           */
 } orc_trace;
 
 int orc_run(const orc_model *m, const orc_step_params *p, int n_chains, double *z, double *lp,

@@ -262,6 +262,13 @@ class Sampler:
         L = np.ascontiguousarray(L, dtype=np.float64).reshape(self.d, self.d)
         _lib.check(self.lib.bst_set_whitening(self.h, _p(mu), _p(L)))
 
+    def set_bounds_penalty(self, width=None):
+        """Smooth bounds (Sec. 3.1): width[d] > 0 replaces a dimension's hard box by the penalty
+        factor exp(-r^2 / 2), r = distance outside the box / width; 0 keeps the hard box; None
+        restores hard bounds everywhere (bst_set_bounds_penalty)."""
+        w = None if width is None else _f64(np.broadcast_to(np.asarray(width, dtype=np.float64), (self.d,)))
+        _lib.check(self.lib.bst_set_bounds_penalty(self.h, None if w is None else _p(w)))
+
     def set_step_multipliers(self, m):
         """Step sizes eps m_i along the whitened directions: the whitening L diag(m)."""
         mu, L = self.whitening()

@@ -22,7 +22,7 @@ SYMBOLS = [
     "bst_version", "bst_last_error", "bst_create", "bst_destroy", "bst_set_emulator", "bst_get_emulator", "bst_set_emulator_output",
     "bst_set_analytic", "bst_init_chains", "bst_step", "bst_loglike", "bst_grad_loglike", "bst_welford_reset",
     "bst_welford_add", "bst_adapt_cov", "bst_get_state", "bst_set_state", "bst_get_whitening", "bst_get_counters",
-    "bst_train_step", "bst_train_grad", "bst_ess", "bst_draw_positions", "bst_set_whitening", "bst_r_minus_1", "bst_r_minus_1_parts", "bst_r_minus_1_combine", "bst_quantiles", "bst_credible_metric", "bst_sliced_wasserstein", "bst_sync", "bst_grad_loglike_noalloc",
+    "bst_train_step", "bst_train_grad", "bst_ess", "bst_draw_positions", "bst_set_whitening", "bst_set_bounds_penalty", "bst_r_minus_1", "bst_r_minus_1_parts", "bst_r_minus_1_combine", "bst_quantiles", "bst_credible_metric", "bst_sliced_wasserstein", "bst_sync", "bst_grad_loglike_noalloc",
     "bst_welford_stats", "bst_welford_merge", "bst_train_apply",
 ]
 
@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
         L.bst_ess.argtypes = [h, vp, i, vp]
         L.bst_r_minus_1.argtypes = [h, vp, i, vp]
         L.bst_set_whitening.argtypes = [h, vp, vp]
+        L.bst_set_bounds_penalty.argtypes = [h, vp]
         L.bst_draw_positions.argtypes = [h, i, vp, vp, vp, vp, vp]
         L.bst_quantiles.argtypes = [h, vp, i, vp, i, vp]
         L.bst_credible_metric.argtypes = [h, vp, i, C.c_double, vp, vp, vp]

@@ -70,6 +70,7 @@ struct bst_ctx {
   std::vector<int> gauss;
   double logdet = 0.0;
   int any_gauss = 0;
+  std::vector<double> pen_w;  // smooth-bound widths (empty or zeros: hard box)
   double *mu64 = nullptr, *L64 = nullptr, *mu64_new = nullptr, *L64_new = nullptr, *info64 = nullptr;
   double *stats64 = nullptr;  // [1 + kMaxD + kMaxD^2] Welford triple staging
 
@@ -226,6 +227,10 @@ StepArgs<R> make_args(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_st
       if (h->lower.size() >= static_cast<size_t>(d)) a.tgt.lower[i] = static_cast<R>(h->lower[i]);
       if (h->upper.size() >= static_cast<size_t>(d)) a.tgt.upper[i] = static_cast<R>(h->upper[i]);
       if (h->gauss.size() >= static_cast<size_t>(d)) a.tgt.gauss[i] = h->gauss[i];
+      if (h->pen_w.size() >= static_cast<size_t>(d) && h->pen_w[i] > 0.0) {
+        a.tgt.pen_iw[i] = static_cast<R>(1.0 / h->pen_w[i]);
+        a.tgt.any_pen = 1;
+      }
     }
   }
   a.st.z = static_cast<R *>(h->z);
@@ -1039,6 +1044,25 @@ bst_status bst_set_whitening(bst_handle h, const double *mu, const double *L) {
   else BST_CUDA(launch_remap_f32((float *)h->z, h->n, d, h->dp, h->mu64, h->L64, h->mu64_new, h->L64_new, 0));
   BST_CUDA(cudaDeviceSynchronize());
   BST_TRY(set_target(h, mu, Ll.data()));
+  BST_TRY(refresh(h, 0));
+  BST_CUDA(cudaDeviceSynchronize());
+  return check_status(h);
+}
+
+bst_status bst_set_bounds_penalty(bst_handle h, const double *width) {
+  NvtxRange nvtx_("bst_set_bounds_penalty");
+  if (!h) return fail(BST_ERR_ARG, "bst_set_bounds_penalty: NULL handle");
+  if (h->stage < 2) return fail(BST_ERR_STATE, "bst_set_bounds_penalty: call bst_init_chains first");
+  const int d = h->d;
+  if (width)
+    for (int i = 0; i < d; ++i)
+      if (!std::isfinite(width[i]) || width[i] < 0.0)
+        return fail(BST_ERR_ARG, "bst_set_bounds_penalty: widths must be finite and >= 0");
+  BST_CUDA(cudaSetDevice(h->device));
+  BST_CUDA(cudaDeviceSynchronize());
+  BST_TRY(check_status(h));
+  if (width) h->pen_w.assign(width, width + d);
+  else h->pen_w.clear();
   BST_TRY(refresh(h, 0));
   BST_CUDA(cudaDeviceSynchronize());
   return check_status(h);

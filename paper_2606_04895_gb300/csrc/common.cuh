@@ -128,11 +128,16 @@ struct TargetView {
   R lower[kMaxD];       // [d]
   R upper[kMaxD];       // [d]
   int gauss[kMaxD];     // [d]
+  // smooth bounds (Sec. 3.1): pen_iw[i] = 1 / w_i > 0 replaces dim i's hard box by the factor
+  // exp(-r_i^2 / 2), r_i = (x_i - clamp(x_i, lower_i, upper_i)) / w_i
+  int any_pen;
+  R pen_iw[kMaxD];
 
   // x = mu + L z over DM >= d entries; returns the log prior (0 / -inf outside the box /
-  // -x_g.x_g / 2 over the flagged dims, as four partial sums of R added in FP64).  XOUT stores
-  // x (DM entries); with grad, g[j] -= sum_{i >= j} L_ij x_g,i (the gradient of the Gaussian
-  // prior term through x = mu + L z, Algorithm 1).  Fully unrolled, so every element of mu and
+  // -x_g.x_g / 2 over the flagged dims, minus r.r / 2 over the dims with a smooth bound, as four
+  // partial sums of R added in FP64).  XOUT stores x (DM entries); with grad,
+  // g[j] -= sum_{i >= j} L_ij p_i with p_i = x_i (Gaussian dims) + r_i / w_i (smooth bounds): the
+  // gradient of the prior terms through x = mu + L z, Algorithm 1.  Fully unrolled, so every element of mu and
   // L is a constant-bank operand of its FMA.  x is accumulated column by column (z_j streamed,
   // each x_i still summed over j in ascending order) and the gradient row by row, so about DM
   // values are live at a time.
@@ -152,11 +157,20 @@ struct TargetView {
 #pragma unroll
     for (int i = 0; i < DM; ++i) {
       if (XOUT) x[i] = xs[i];
-      if (i < d && !(xs[i] >= lower[i] && xs[i] <= upper[i])) inside = false;
-      xs[i] = gauss[i] ? xs[i] : R(0);
-      part[i & 3] += xs[i] * xs[i];
+      const bool pen = any_pen && pen_iw[i] > R(0);
+      if (i < d && !pen && !(xs[i] >= lower[i] && xs[i] <= upper[i])) inside = false;
+      R p = gauss[i] ? xs[i] : R(0);
+      R q = p * p;
+      if (pen) {
+        const R out = xs[i] < lower[i] ? xs[i] - lower[i] : (xs[i] > upper[i] ? xs[i] - upper[i] : R(0));
+        const R r = out * pen_iw[i];
+        q += r * r;
+        p += r * pen_iw[i];
+      }
+      xs[i] = p;
+      part[i & 3] += q;
     }
-    if (grad && any_gauss) {
+    if (grad && (any_gauss || any_pen)) {
 #pragma unroll
       for (int j = 0; j < DM; ++j) {
         R sg = R(0);
@@ -180,11 +194,18 @@ struct TargetView {
       R s = mu[i];
       for (int j = 0; j <= i; ++j) s += L[i * kMaxD + j] * z[j];
       if (XOUT) x[i] = s;
-      if (!(s >= lower[i] && s <= upper[i])) inside = false;
+      const bool pen = any_pen && pen_iw[i] > R(0);
+      if (!pen && !(s >= lower[i] && s <= upper[i])) inside = false;
       xg[i] = gauss[i] ? s : R(0);
       lp -= 0.5 * static_cast<double>(xg[i]) * static_cast<double>(xg[i]);
+      if (pen) {
+        const R out = s < lower[i] ? s - lower[i] : (s > upper[i] ? s - upper[i] : R(0));
+        const R r = out * pen_iw[i];
+        lp -= 0.5 * static_cast<double>(r) * static_cast<double>(r);
+        xg[i] += r * pen_iw[i];
+      }
     }
-    if (grad && any_gauss)
+    if (grad && (any_gauss || any_pen))
       for (int j = 0; j < d; ++j) {
         R sg = R(0);
         for (int i = j; i < d; ++i) sg += L[i * kMaxD + j] * xg[i];

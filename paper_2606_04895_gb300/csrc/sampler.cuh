@@ -903,6 +903,35 @@ struct RegChain8 {
     return true;
   }
 
+  // Distance of x_i outside [lower_i, upper_i] (0 inside).
+  static __device__ __forceinline__ R bound_excess(const TargetView<R> &t, R x, int i) {
+    return x < t.lower[i] ? x - t.lower[i] : (x > t.upper[i] ? x - t.upper[i] : R(0));
+  }
+  // gz += the gradient (through x = mu + L z) of the Gaussian prior terms and the smooth-bound
+  // penalties at the point zv: gz_j -= sum_{i >= j} L_ij p_i, p_i = x_i (Gaussian dims) +
+  // r_i / w_i (smooth bounds).
+  __device__ void prior_grad(const StepArgs<R> &a, const R *zv, R *gz) const {
+    const int d = a.d;
+    R xp[DB];
+    to_x(a, zv, xp);
+#pragma unroll
+    for (int i = 0; i < DB; ++i) {
+      R p = (i < d && a.tgt.gauss[i]) ? xp[i] : R(0);
+      if (i < d && a.tgt.any_pen && a.tgt.pen_iw[i] > R(0))
+        p += bound_excess(a.tgt, xp[i], i) * a.tgt.pen_iw[i] * a.tgt.pen_iw[i];
+      xp[i] = p;
+    }
+#pragma unroll
+    for (int j = 0; j < DB; ++j)
+      if (j < d) {
+        R sg = 0;
+#pragma unroll
+        for (int i = j; i < DB; ++i)
+          if (i < d) sg -= a.tgt.L[i * kMaxD + j] * xp[i];
+        gz[j] += sg;
+      }
+  }
+
   // The part of post that does not depend on the evaluation in flight: x of the proposal and
   // its prior term, the accept uniform, and the noise of the next iteration's proposal.
   __device__ void prep(const StepArgs<R> &a, int c) {
@@ -913,8 +942,13 @@ struct RegChain8 {
 #pragma unroll
     for (int i = 0; i < DB; ++i)
       if (i < a.d) {
-        if (!(xp[i] >= a.tgt.lower[i] && xp[i] <= a.tgt.upper[i])) inside = false;
+        const bool pen = a.tgt.any_pen && a.tgt.pen_iw[i] > R(0);
+        if (!pen && !(xp[i] >= a.tgt.lower[i] && xp[i] <= a.tgt.upper[i])) inside = false;
         if (a.tgt.any_gauss && a.tgt.gauss[i]) lpr -= 0.5 * static_cast<double>(xp[i]) * static_cast<double>(xp[i]);
+        if (pen) {
+          const R r = bound_excess(a.tgt, xp[i], i) * a.tgt.pen_iw[i];
+          lpr -= 0.5 * static_cast<double>(r) * static_cast<double>(r);
+        }
       }
     u = draw_uniform<double>(a.seed, static_cast<uint32_t>(c), iter, kAccept, 0);
     lu32 = logf(static_cast<float>(u));
@@ -964,19 +998,7 @@ struct RegChain8 {
     R *q1 = xi, *g1 = gp, *z1 = zp;
     if (rec_pending) record(a, c, row);
     const double lp1 = static_cast<double>(lle) + (inside ? lpr : -INFINITY) + t.logdet;
-    if (t.any_gauss) {
-      R xp[DB];
-      to_x(a, z1, xp);
-#pragma unroll
-      for (int j = 0; j < DB; ++j)
-        if (j < d) {
-          R sg = 0;
-#pragma unroll
-          for (int i = j; i < DB; ++i)
-            if (i < d && a.tgt.gauss[i]) sg -= a.tgt.L[i * kMaxD + j] * xp[i];
-          g1[j] += sg;
-        }
-    }
+    if (t.any_gauss || t.any_pen) prior_grad(a, z1, g1);
     double qq = 0.0;
 #pragma unroll
     for (int i = 0; i < DB; ++i)
@@ -1059,19 +1081,7 @@ struct RegChain8 {
     prepped = false;
     // log pi_z(zp) and its gradient (logpi_eval)
     const double lpp = static_cast<double>(lle) + (inside ? lpr : -INFINITY) + t.logdet;
-    if (mala && t.any_gauss) {
-      R xp[DB];
-      to_x(a, zp, xp);
-#pragma unroll
-      for (int j = 0; j < DB; ++j)
-        if (j < d) {
-          R sg = 0;
-#pragma unroll
-          for (int i = j; i < DB; ++i)
-            if (i < d && a.tgt.gauss[i]) sg -= a.tgt.L[i * kMaxD + j] * xp[i];
-          gp[j] += sg;
-        }
-    }
+    if (mala && (t.any_gauss || t.any_pen)) prior_grad(a, zp, gp);
     bool acc;
     float p;
     if (!inside) {

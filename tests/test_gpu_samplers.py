@@ -36,11 +36,16 @@ def _check(prec, s, ref, samples, kernel, n, margin=MARGIN):
     x_gpu = samples[-1].double().cpu().numpy()
     x_ref = ref["samples"][-1]
     if kernel == "nuts":
+        # every decision of a NUTS iteration (slice, Delta_max, merges, top-level moves, U-turn
+        # tests) is at least `margin` away from its threshold on the clear chains (the oracle's
+        # trace gives the smallest distance): there the tree, the leapfrog count and the
+        # selected point must be the oracle's
+        clear = ref["margin"][-1] > margin
+        assert clear.mean() > 0.7, clear.mean()
         same = np.all(np.abs(x_gpu - x_ref) < POS_TOL[prec], axis=1)
-        frac = same.mean()
-        assert frac >= (1.0 if prec == "fp64" else 0.9), frac
+        assert np.all(same[clear]), np.flatnonzero(clear & ~same)
         ev = s.counters()["evals"]
-        assert np.mean(ev == ref["evals"]) >= (1.0 if prec == "fp64" else 0.9)
+        assert np.array_equal(ev[clear], ref["evals"][clear])
         return
     la, lu = ref["log_alpha"][-1], ref["log_u"][-1]
     clear = np.abs(la - lu) > margin
@@ -283,4 +288,40 @@ def test_27d_ragged_chain_count(prec, kernel, eps, extra):
     same = np.all(np.abs(x - ref["samples"]) < 2e-3, axis=(0, 2))
     assert same.mean() >= 0.9, same.mean()
     assert np.all(s.get_state()["iter"] == 2)
+    s.close()
+
+
+# ---------------------------------------------------------------- smooth bounds penalty (Sec. 3.1)
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("kernel,eps,extra", [("mh", 0.5, {}), ("mala", 0.4, {}), ("hmc", 0.2, {"n_leapfrog": 5}),
+                                              ("nuts", 0.3, {})])
+def test_bounds_penalty_one_step_parity(prec, kernel, eps, extra):
+    """Bounds inside the chains' spread with smooth penalties (some chains start outside): the
+    chains' log pi and gradient after bst_set_bounds_penalty, and one step of every sampler,
+    against the oracle with the same penalty widths."""
+    n, d = 300, 8
+    e = emulator_case(d, 256, 3, out_s=8.0, out_m=50.0)
+    mu, L = whitening(d, 1, scale=0.4)
+    lower, upper = np.full(d, -3.0), np.full(d, 3.0)
+    upper[0], lower[1], upper[5] = mu[0], mu[1] - 0.1, mu[5] + 0.2
+    pen = np.array([0.2, 0.05, 0.0, 0.0, 0.0, 0.5, 0.0, 0.0])
+    theta0 = mu + np.random.default_rng(9).normal(size=(n, d)) @ L.T
+    theta0[:, 2:5] = np.clip(theta0[:, 2:5], -2.9, 2.9)
+    theta0[:, 6:] = np.clip(theta0[:, 6:], -2.9, 2.9)
+    s = make_emulator_sampler(prec, e, n, mu=mu, L=L, lower=lower, upper=upper, theta0=theta0, seed=11)
+    s.set_bounds_penalty(pen)
+    m = O.Model(d, emulator=e, lower=lower, upper=upper, mu=mu, L=L, bf16=(prec == "bf16"), pen_w=pen)
+    z0 = np.linalg.solve(L, (theta0 - mu).T).T
+    st = s.get_state()
+    rl, rg = m.logpost(z0)
+    assert np.all(np.isfinite(rl)) and np.isfinite(st["logp"]).all()
+    assert (theta0[:, 0] > upper[0]).sum() > 50  # many chains start outside a smooth bound
+    tl, tg = {"fp64": (1e-10, 1e-9), "fp32": (1e-5, 1e-4), "bf16": (2e-3, 2e-2)}[prec]
+    assert np.max(np.abs(st["logp"] - rl) / np.maximum(np.abs(rl), 1.0)) < tl
+    from gpu_common import rel_err
+    assert rel_err(st["grad"], rg) < tg
+    out = torch.empty((1, n, d), dtype=s.dtype, device="cuda")
+    s.step(kernel, 1, eps=eps, samples=out, **extra)
+    ref = O.run(m, kernel, z0, eps=eps, n_steps=1, seed=11, trace=True, **extra)
+    _check(prec, s, ref, out, kernel, n, margin=1e-2 if (prec == "bf16" and kernel == "hmc") else MARGIN)
     s.close()

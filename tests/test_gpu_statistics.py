@@ -143,3 +143,38 @@ def test_mala_with_step_multipliers_keeps_the_posterior():
     x = out.double().cpu().numpy()[steps // 5:]
     _check(x, mean, cov)
     s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("kernel,eps,steps,kw", [("mala", 0.5, 3000, {}), ("hmc", 0.35, 800, {"n_leapfrog": 6}),
+                                                 ("nuts", 0.5, 500, {})])
+def test_bounds_penalty_closed_form_marginal_mean(prec, kernel, eps, steps, kw):
+    """Smooth bounds (Sec. 3.1): the linear 6-D target with the upper bound of dim 0 at its
+    posterior mean and penalty width w = sd_0.  The x_0 marginal is a half-normal of scale sd_0
+    joined to one of scale s' = sd_0 w / sqrt(sd_0^2 + w^2), masses in the ratio sd_0 : s', so its
+    mean is mu_0 + sqrt(2 / pi) (s' - sd_0); the GPU chains reproduce it within 5 MCSE."""
+    from paper_2606_04895_gb300 import Sampler
+    t, mean, cov = _closed_form()
+    Lp = np.linalg.cholesky(cov)
+    sd0 = np.sqrt(cov[0, 0])
+    upper = t["upper"].copy()
+    upper[0] = mean[0]
+    n = 512
+    s = Sampler(6, n, precision=prec, likelihood="analytic", seed=23)
+    s.set_analytic(t["A"], t["B"], t["c"], t["data"], t["sigma"], linear=True)
+    theta0 = mean + S.chains_init(n, 6, seed=2) @ Lp.T
+    theta0[:, 0] = np.minimum(theta0[:, 0], mean[0])
+    s.init_chains(theta0, t["lower"], upper, mu=mean, L=Lp)
+    w = np.zeros(6)
+    w[0] = sd0
+    s.set_bounds_penalty(w)
+    out = torch.empty((steps, n, 6), dtype=s.dtype, device="cuda")
+    s.step(kernel, steps, eps=eps, samples=out, **kw)
+    x0 = out.double().cpu().numpy()[steps // 5:, :, 0]
+    cm = x0.mean(axis=0)
+    se = cm.std(ddof=1) / np.sqrt(n)
+    sp = sd0 * w[0] / np.sqrt(sd0 ** 2 + w[0] ** 2)
+    want = mean[0] + np.sqrt(2.0 / np.pi) * (sp - sd0)
+    assert abs(cm.mean() - want) < 5 * se, (cm.mean() - want) / se
+    assert abs(cm.mean() - mean[0]) > 10 * se
+    s.close()

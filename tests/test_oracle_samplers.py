@@ -293,3 +293,84 @@ def test_aies_de_affine_invariance_and_argument_checks():
         O.run(m1, "aies_de", x0[:2], eps=0.0, n_steps=1, seed=1, aies_walkers=2)  # needs 2 partners
     with pytest.raises(ValueError):
         O.run(m1, "aies_de", x0, eps=0.0, n_steps=1, seed=1, de_sigma=-1.0)
+
+
+# ---------------------------------------------------------------- smooth bounds penalty (Sec. 3.1)
+def _penalised_marginal_mean(mu_k, sd_k, w):
+    """Marginal mean of x_k under N(mu, Sigma) times exp(-((x_k - mu_k)_+ / w)^2 / 2) (the upper
+    bound of dim k at its posterior mean, penalty width w): the x_k marginal is a left half-normal
+    of scale sd_k and a right half-normal of scale s' = sd_k w / sqrt(sd_k^2 + w^2), with masses
+    in the ratio sd_k : s', so its mean is mu_k + sqrt(2 / pi) (s' - sd_k)."""
+    sp = sd_k * w / np.sqrt(sd_k ** 2 + w ** 2)
+    return mu_k + np.sqrt(2.0 / np.pi) * (sp - sd_k)
+
+
+def test_bounds_penalty_is_zero_inside_and_continuous_at_the_bound():
+    t, mean, cov = _linear_problem()
+    L = np.linalg.cholesky(cov)
+    upper = t["upper"].copy()
+    upper[0] = mean[0]
+    w = np.full(6, 0.05)
+    hard = O.Model(6, lik="analytic", analytic=t, lower=t["lower"], upper=upper, mu=mean, L=L)
+    soft = O.Model(6, lik="analytic", analytic=t, lower=t["lower"], upper=upper, mu=mean, L=L, pen_w=w)
+    z_in = -np.abs(np.random.default_rng(0).normal(size=(5, 6)))  # x_0 below its bound
+    z_in[:, 0] = -np.abs(z_in[:, 0]) - 0.01
+    a, ga = hard.logpost(z_in)
+    b, gb = soft.logpost(z_in)
+    assert np.array_equal(a, b) and np.array_equal(ga, gb)
+    # on the two sides of the bound the values meet (continuity) and so do the gradients (C1)
+    zb = np.zeros((1, 6))
+    eps = 1e-9
+    zl, zr = zb.copy(), zb.copy()
+    zl[0, 0] -= eps / L[0, 0]
+    zr[0, 0] += eps / L[0, 0]
+    (vl, gl), (vr, gr) = soft.logpost(zl), soft.logpost(zr)
+    assert abs(vl[0] - vr[0]) < 1e-6 and np.allclose(gl, gr, atol=1e-5)
+    assert hard.logpost(zr, grad=False)[0] == -np.inf
+
+
+def test_bounds_penalty_gradient_finite_differences():
+    t, mean, cov = _linear_problem()
+    L = np.linalg.cholesky(cov)
+    upper = t["upper"].copy()
+    upper[[0, 3]] = mean[[0, 3]]
+    lower = t["lower"].copy()
+    lower[2] = mean[2] + 0.5 * np.sqrt(cov[2, 2])  # dim 2's lower bound above the mean
+    w = np.array([0.3, 1.0, 0.02, 0.5, 1.0, 1.0]) * np.sqrt(np.diag(cov))
+    m = O.Model(6, lik="analytic", analytic=t, lower=lower, upper=upper, mu=mean, L=L, pen_w=w)
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        z = rng.normal(size=6) * 1.5
+        _, g = m.logpost(z)
+        h = 1e-6
+        fd = np.array([(m.logpost(z + h * np.eye(6)[j], grad=False)[0] -
+                        m.logpost(z - h * np.eye(6)[j], grad=False)[0]) / (2 * h) for j in range(6)])
+        assert np.allclose(g[0], fd, rtol=1e-6, atol=1e-6 * np.abs(fd).max())
+
+
+@pytest.mark.parametrize("kernel,eps,steps,extra,wfac", [("mala", 0.5, 4000, {}, 1.0),
+                                                        ("hmc", 0.35, 1500, {"n_leapfrog": 6}, 1.0),
+                                                        ("mala", 0.3, 6000, {}, 0.2)])
+def test_bounds_penalty_closed_form_marginal_mean(kernel, eps, steps, extra, wfac):
+    """Linear 6-D target (exactly Gaussian posterior), upper bound of dim 0 at its posterior mean
+    with penalty width w = wfac sd_0: the sampled mean of x_0 equals the closed form of
+    _penalised_marginal_mean (w = sd_0: a half-normal joined to a narrower one; w = 0.2 sd_0:
+    nearer the truncated half-normal mean mu - sd sqrt(2 / pi))."""
+    t, mean, cov = _linear_problem()
+    Lp = np.linalg.cholesky(cov)
+    sd0 = np.sqrt(cov[0, 0])
+    upper = t["upper"].copy()
+    upper[0] = mean[0]
+    w = np.full(6, 1.0)
+    w[0] = wfac * sd0
+    m = O.Model(6, lik="analytic", analytic=t, lower=t["lower"], upper=upper, mu=mean, L=Lp, pen_w=w)
+    z0 = S.chains_init(128, 6, seed=7)
+    z0[:, 0] = -np.abs(z0[:, 0])
+    r = O.run(m, kernel, z0, eps=eps, n_steps=steps, seed=5, **extra)
+    x0 = r["samples"][steps // 5:, :, 0]
+    cm = x0.mean(axis=0)
+    se = cm.std(ddof=1) / np.sqrt(len(cm))
+    want = _penalised_marginal_mean(mean[0], sd0, w[0])
+    assert abs(cm.mean() - want) < 5 * se, (cm.mean() - want) / se
+    # and it differs from the unpenalised mean by many standard errors (the penalty acts)
+    assert abs(cm.mean() - mean[0]) > 10 * se
