@@ -49,7 +49,9 @@ typedef enum {
   BST_ERR_UNSUPPORTED = 7  /* shape/precision combination not built             */
 } bst_status;
 
-typedef enum { BST_MH = 0, BST_MALA = 1, BST_HMC = 2, BST_NUTS = 3, BST_AIES = 4 } bst_kernel;
+typedef enum {
+  BST_MH = 0, BST_MALA = 1, BST_HMC = 2, BST_NUTS = 3, BST_AIES = 4, BST_AIES_DE = 5, BST_NUTS_MULTINOMIAL = 6
+} bst_kernel;
 /* BST_BF16 / BST_FP16: emulator on the tcgen05 tensor cores with BF16 (8 significant bits) or
  * FP16 (11 significant bits, same rate) weights and activations, FP32 accumulation; FP32 chain
  * state.  BST_FP32 / BST_FP64: CUDA-core paths (the plain precisions). */
@@ -141,7 +143,17 @@ bst_status bst_init_chains(bst_handle h, const double *theta0, const double *low
  *   BST_MALA : z' = z + eps grad + sqrt(2 eps) xi, MH-corrected        (Sec. 2.1, Eq. (2.3))
  *   BST_HMC  : n_leapfrog leapfrog steps of H = -log pi + q.q/2        (Sec. 2.1, Eq. (2.1))
  *   BST_NUTS : Hoffman-Gelman NUTS, at most max_depth doublings          (Sec. 2.1)
+ *   BST_NUTS_MULTINOMIAL : the same trees, directions and U-turn tests with leaf weights
+ *             exp(H0 - H) in place of the slice (Betancourt 2017, Appendix A): in-subtree
+ *             merges keep the second half's candidate with probability w'' / (w' + w''),
+ *             the top level moves with probability min(1, w_new / w_old), a leaf with
+ *             H - H0 > 1000 is divergent
  *   BST_AIES : Goodman-Weare stretch move, ensembles of aies_walkers     (Sec. 2.3)
+ *   BST_AIES_DE : differential-evolution move on the same ensembles and halves (Sec. 2.3,
+ *             after Eq. (2.15)): y = z_i + gamma (z_j - z_k), j != k uniform in the other
+ *             half, gamma = (1 + eps eta) 2.38 / sqrt(2 d), eta ~ N(0, 1): eps is the
+ *             standard deviation sigma_gamma of the relative scale (>= 0; the paper gives no
+ *             value); symmetric, accepted with min(1, pi(y) / pi(z_i)); aies_walkers >= 4
  * eps is ignored by AIES; n_leapfrog only used by HMC.  If samples_dev is not
  * NULL it receives x-space samples real[n_steps / thin][n_chains][d].
  * If stats is not NULL the call synchronises ``stream`` and fills it with this

@@ -20,12 +20,14 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import AIES, BF16, FP16, FP32, FP64, HMC, LIK_ANALYTIC, LIK_EMULATOR, MALA, MH, NUTS, BstError
+from ._lib import (AIES, AIES_DE, BF16, FP16, FP32, FP64, HMC, LIK_ANALYTIC, LIK_EMULATOR, MALA, MH, NUTS,
+                   NUTS_MULTINOMIAL, BstError)
 
 __all__ = ["Sampler", "Results", "BstError", "EmulatorLogL", "emulator_logl", "KERNELS", "PRECISIONS",
            "n_params", "r_minus_1_combine"]
 
-KERNELS = {"mh": MH, "mala": MALA, "hmc": HMC, "nuts": NUTS, "aies": AIES}
+KERNELS = {"mh": MH, "mala": MALA, "hmc": HMC, "nuts": NUTS, "aies": AIES, "aies_de": AIES_DE,
+           "nuts_multinomial": NUTS_MULTINOMIAL}
 PRECISIONS = {"bf16": BF16, "fp16": FP16, "fp32": FP32, "fp64": FP64}
 
 

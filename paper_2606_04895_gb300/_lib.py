@@ -13,7 +13,7 @@ _lib = None
 OK, ERR_ARG, ERR_STATE, ERR_CUDA, ERR_NOT_PD, ERR_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_STATE", "ERR_CUDA", "ERR_NOT_PD", "ERR_TIMEOUT", "ERR_NONFINITE",
                 "ERR_UNSUPPORTED"]
-MH, MALA, HMC, NUTS, AIES = range(5)
+MH, MALA, HMC, NUTS, AIES, AIES_DE, NUTS_MULTINOMIAL = range(7)
 BF16, FP32, FP64, FP16 = range(4)
 LIK_EMULATOR, LIK_ANALYTIC = range(2)
 

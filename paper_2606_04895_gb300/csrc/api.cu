@@ -201,7 +201,7 @@ StepArgs<R> make_args(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_st
   std::memset(&a, 0, sizeof(a));
   a.mode = mode;
   a.n_chains = h->n;
-  a.n_rows = (mode == kModeAIES) ? h->n / 2 : h->n;
+  a.n_rows = is_ensemble_mode(mode) ? h->n / 2 : h->n;
   a.d = h->d;
   a.dp = h->dp;
   a.eps = eps;
@@ -212,7 +212,7 @@ StepArgs<R> make_args(bst_ctx *h, int mode, double eps, int n_leapfrog, int n_st
   a.aies_a = h->aies_a;
   a.thin = h->thin;
   a.seed = h->seed;
-  a.need_grad = (mode == kModeMALA || mode == kModeHMC || mode == kModeNUTS || mode == kModeRefresh) ? 1 : 0;
+  a.need_grad = (mode == kModeMALA || mode == kModeHMC || is_nuts_mode(mode) || mode == kModeRefresh) ? 1 : 0;
   a.tgt.d = h->d;
   a.tgt.logdet = h->logdet;
   a.tgt.any_gauss = h->any_gauss;
@@ -821,15 +821,23 @@ bst_status bst_step(bst_handle h, int kernel, double eps, int n_leapfrog, int n_
   NvtxRange nvtx_("bst_step");
   if (!h) return fail(BST_ERR_ARG, "bst_step: NULL handle");
   if (h->stage < 2) return fail(BST_ERR_STATE, "bst_step: call bst_init_chains first");
-  if (kernel < BST_MH || kernel > BST_AIES) return fail(BST_ERR_ARG, "bst_step: unknown kernel");
+  if (kernel < BST_MH || kernel > BST_NUTS_MULTINOMIAL) return fail(BST_ERR_ARG, "bst_step: unknown kernel");
   if (n_steps < 0) return fail(BST_ERR_ARG, "bst_step: n_steps must be >= 0");
-  if (kernel != BST_AIES && !(eps > 0.0 && std::isfinite(eps))) return fail(BST_ERR_ARG, "bst_step: eps must be positive");
+  if (kernel != BST_AIES && kernel != BST_AIES_DE && !(eps > 0.0 && std::isfinite(eps)))
+    return fail(BST_ERR_ARG, "bst_step: eps must be positive");
+  if (kernel == BST_AIES_DE && !(eps >= 0.0 && std::isfinite(eps)))
+    return fail(BST_ERR_ARG, "bst_step: the DE move's eps (sigma_gamma) must be finite and >= 0");
+  if (kernel == BST_AIES_DE && h->walkers < 4)
+    return fail(BST_ERR_ARG, "bst_step: the DE move needs aies_walkers >= 4");
   if (kernel == BST_HMC && n_leapfrog < 1) return fail(BST_ERR_ARG, "bst_step: n_leapfrog must be >= 1");
-  if (kernel == BST_AIES) {
+  if (kernel == BST_AIES || kernel == BST_AIES_DE) {
     const int half = h->walkers / 2;
     const int tile = (tc_engine(h)) ? kTcRows : simt_rows_per_tile(h->precision, h->width, h->lik);  // chains per tile
     if (h->n % h->walkers) return fail(BST_ERR_ARG, "bst_step: AIES needs n_chains to be a multiple of aies_walkers");
-    if (tile % half) return fail(BST_ERR_UNSUPPORTED, "bst_step: AIES ensemble halves must not span chain tiles");
+    // the tensor-core engine holds whole halves in a tile; the CUDA-core engines spread a half
+    // over a cluster of up to 8 tiles
+    if (tc_engine(h) ? (tile % half) != 0 : (half % tile != 0 && tile % half != 0) || half / tile > 8)
+      return fail(BST_ERR_UNSUPPORTED, "bst_step: AIES ensemble halves do not fit the chain tiles");
   }
   BST_CUDA(cudaSetDevice(h->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -839,7 +847,7 @@ bst_status bst_step(bst_handle h, int kernel, double eps, int n_leapfrog, int n_
   }
   BST_TRY(prepare(h, s));
   BST_TRY(ensure_scratch(h, h->n));
-  const bool needs_grad = kernel == BST_MALA || kernel == BST_HMC || kernel == BST_NUTS;
+  const bool needs_grad = kernel == BST_MALA || kernel == BST_HMC || kernel == BST_NUTS || kernel == BST_NUTS_MULTINOMIAL;
   if (h->state_stale || (needs_grad && !h->grad_valid)) BST_TRY(refresh(h, s));
   double before[4] = {0, 0, 0, 0}, after[4];
   if (stats) {

@@ -39,13 +39,21 @@ enum Mode : int {
   kModeMALA = BST_MALA,
   kModeHMC = BST_HMC,
   kModeNUTS = BST_NUTS,
+  kModeNUTS_MN = BST_NUTS_MULTINOMIAL,
   kModeAIES = BST_AIES,
+  kModeAIES_DE = BST_AIES_DE,
   kModeLoglike = 16,  // external theta rows -> logL (+ grad)
   kModeRefresh = 17   // chain state z -> log pi, grad (after init / adaptation)
 };
 
 // Device status bits.
 enum StatusBits : int { kStatusTimeout = 1, kStatusBadArg = 2 };
+
+// The ensemble moves (stretch and differential evolution) share the walker layout and the
+// alternation of halves.
+__host__ __device__ constexpr bool is_ensemble_mode(int mode) { return mode == kModeAIES || mode == kModeAIES_DE; }
+// The two NUTS variants share the tree machine.
+__host__ __device__ constexpr bool is_nuts_mode(int mode) { return mode == kModeNUTS || mode == kModeNUTS_MN; }
 
 struct Philox {
   static __device__ __forceinline__ void block(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,

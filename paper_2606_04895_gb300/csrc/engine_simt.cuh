@@ -389,6 +389,12 @@ __device__ __noinline__ bool simt_chain_post(const StepArgs<R> &a, int row, int 
   return Chain<R, false>(a).post(row, h);
 }
 
+// Tiles per ensemble half (the cluster size of an ensemble-move launch), 1 otherwise.
+template <int T, typename R>
+__host__ __device__ inline int simt_ensemble_cluster(const StepArgs<R> &a) {
+  return (is_ensemble_mode(a.mode) && a.aies_walkers / 2 > T) ? a.aies_walkers / 2 / T : 1;
+}
+
 // Launched with kSimtThreads threads.  Registers capped at 128: the emulator GEMM loop ran
 // fastest there (FP32 MALA, 4096 chains, 8-512x4-1: 711 us per round at 128, 739 at 168,
 // 898 at the 255 the compiler picks by itself).
@@ -409,12 +415,12 @@ simt_chain_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__
   }
   // per-launch chain bookkeeping
   if (owner) {
-    if (a.mode == kModeAIES) {
+    if (is_ensemble_mode(a.mode)) {
       for (int h = 0; h < 2; ++h) a.st.steps_done[ch.aies_walker(row, h)] = 0;
     } else {
       a.st.steps_done[row] = 0;
       if (a.mode == kModeHMC) ch.dw(row)[0] = 0.0;
-      if (a.mode == kModeNUTS) ch.dw(row)[0] = 1.0;
+      if (is_nuts_mode(a.mode)) ch.dw(row)[0] = 1.0;
     }
   }
   __syncthreads();
@@ -431,6 +437,11 @@ simt_chain_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__
       welford_tile(a, row0, min(T, a.n_rows - row0), mask, tid, kSimtThreads, [] { __syncthreads(); },
                    static_cast<int>(blockIdx.x));
     }
+    // ensemble halves spread over the tiles of a cluster: every tile has finished this half-step
+    // (its walkers' positions written) before any proposes the other half, whose partners are
+    // these walkers.  All tiles of a cluster run the same number of half-steps.
+    if (simt_ensemble_cluster<T>(a) > 1)
+      asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
   }
 }
 

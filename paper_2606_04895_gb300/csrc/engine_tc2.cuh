@@ -483,12 +483,12 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
     RegChain8<float> rc;
     if (fast && sampler && valid) rc.load(a, row, zbuf + r * 8, gbuf + r * 8, xibuf + r * 8);
     if (sampler && valid && !loglike) {
-      if (a.mode == kModeAIES) {
+      if (is_ensemble_mode(a.mode)) {
         for (int h = 0; h < 2; ++h) a.st.steps_done[chn.aies_walker(row, h)] = 0;
       } else {
         a.st.steps_done[row] = 0;
         if (a.mode == kModeHMC) chn.dw(row)[0] = 0.0;
-        if (a.mode == kModeNUTS) chn.dw(row)[0] = 1.0;
+        if (is_nuts_mode(a.mode)) chn.dw(row)[0] = 1.0;
       }
     }
     epi_sync();

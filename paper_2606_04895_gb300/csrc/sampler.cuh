@@ -209,6 +209,13 @@ __device__ __forceinline__ bool no_uturn(VA za, VB zb, VP p, VQ q, double v, int
   return s1 >= 0.0 && s2 >= 0.0;
 }
 
+// log(exp(a) + exp(b)) without overflow: max + log1p(exp(min - max)); -inf when both are.
+__device__ __forceinline__ double log_add_exp(double a, double b) {
+  const double hi = a > b ? a : b, lo = a > b ? b : a;
+  if (hi == -INFINITY) return -INFINITY;
+  return hi + log1p(exp(lo - hi));
+}
+
 // U: unrolled whitening / prior for FP32 state (the tcgen05 kernel); the CUDA-core kernel,
 // whose time is all in its emulator GEMMs, takes the loop form, which needs far fewer registers.
 template <typename R, bool U = true>
@@ -497,7 +504,8 @@ struct Chain {
   // 8 qh, level i: 9+4i first z, 10+4i first q, 11+4i cand z, 12+4i cand g.
   // dwork: 0 new-iteration flag, 1 log u - H0, 2 H0, 3 n, 4 lp of selected,
   // 5 acceptance-stat sum, 6 j, 7 v, 8 m_sub, 9 leaves, 10 diverged, 11 moved,
-  // 12+i cand lp, 22+i node n.
+  // 12+i cand lp, 22+i node n.  Multinomial variant (kModeNUTS_MN): dwork 3 and 22+i hold log
+  // weights log sum exp(H0 - H) instead of the counts n (the start point: log 1 = 0).
   __device__ __noinline__ bool nuts_pre(int c) const {
     if (a.st.steps_done[c] >= a.n_steps) return false;
     const Blk<double> dwc = dw(c);
@@ -529,7 +537,7 @@ struct Chain {
         vstore(wv(c, 1), i0, n, tq);
         vstore(wv(c, 4), i0, n, tq);
       }
-      dwc[3] = 1.0;
+      dwc[3] = a.mode == kModeNUTS_MN ? 0.0 : 1.0;
       dwc[4] = static_cast<double>(a.st.lp[c]);
       dwc[5] = 0.0;
       dwc[6] = 0.0;
@@ -565,8 +573,19 @@ struct Chain {
     const int leaf = static_cast<int>(leaves);
     // H of the new leaf; FP32 state: |q|^2 in FP32, within errH of the FP64 H
     double Hl = -lpn + 0.5 * static_cast<double>(qq);
+    const bool mn = a.mode == kModeNUTS_MN;
     bool nlb, sl;
-    {
+    if (mn) {
+      // multinomial: the leaf's log weight H0 - H (FP64 from the working-precision state);
+      // divergent when H - H0 exceeds Delta_max
+      if (kF32) {
+        double q2 = 0.0;
+        for (int i = 0; i < d; ++i) q2 += static_cast<double>(qend[i]) * qend[i];
+        Hl = -lpn + 0.5 * q2;
+      }
+      nlb = true;
+      sl = Hl - H0 < kNutsDeltaMax;
+    } else {
       const double t = log_u + Hl;
       const double errH = kF32 ? (d + 4) * 0x1p-24 * static_cast<double>(qq) +
                                      0x1p-50 * (fabs(lpn) + static_cast<double>(qq) + fabs(log_u) + kNutsDeltaMax)
@@ -586,7 +605,7 @@ struct Chain {
       }
     }
     dwc[5] = stat0 + (kF32 ? static_cast<double>(accept_prob32(static_cast<float>(H0 - Hl))) : accept_prob(H0 - Hl));
-    const double nl = nlb ? 1.0 : 0.0;
+    const double nl = mn ? H0 - Hl : (nlb ? 1.0 : 0.0);
     if (!sl) {
       dwc[10] = 1.0;
       return true;
@@ -600,8 +619,10 @@ struct Chain {
       const double ln = dwc[22 + lvl];
       const double u = draw_uniform<double>(a.seed, c, it, kNutsSel,
                                             static_cast<uint32_t>(8 * (leaf - 1) + lvl + 1));
-      const double ntot = ln + node_n;
-      const bool take_right = ntot > 0.0 && u * ntot < node_n;
+      // slice: counts, take the right half's candidate with probability n'' / (n' + n'');
+      // multinomial: log weights, probability w'' / (w' + w'')
+      const double ntot = mn ? log_add_exp(ln, node_n) : ln + node_n;
+      const bool take_right = mn ? u < exp(node_n - ntot) : (ntot > 0.0 && u * ntot < node_n);
       if (!take_right) cand_src = lvl;
       // U-turn check of the merged span [left.first .. leaf]
       const bool ok = no_uturn<R>(zend, wv(c, 9 + 4 * lvl), wv(c, 10 + 4 * lvl), qend, v, d);
@@ -617,12 +638,12 @@ struct Chain {
     if (lvl == j) {
       // the subtree of this doubling is complete: progressive top-level selection
       const double ut = draw_uniform<double>(a.seed, c, it, kNutsTop, static_cast<uint32_t>(j));
-      if (ut * dwc[3] < node_n) {
+      if (mn ? ut < exp(node_n - dwc[3]) : ut * dwc[3] < node_n) {
         vcopy2<R>(wv(c, 6), cz, wv(c, 7), cg, d);
         dwc[4] = clp;
         dwc[11] = 1.0;
       }
-      dwc[3] = dwc[3] + node_n;
+      dwc[3] = mn ? log_add_exp(dwc[3], node_n) : dwc[3] + node_n;
       const bool ok = no_uturn<R>(wv(c, 3), wv(c, 0), wv(c, 1), wv(c, 4), 1.0, d);
       const int jn = j + 1;
       dwc[6] = jn;
@@ -673,12 +694,28 @@ struct Chain {
     int jj = static_cast<int>(up * half);
     if (jj > half - 1) jj = half - 1;
     const int jw = base + jj;
+    const Row<R> zi = z(i), zj = z(jw);
+    const Blk<R> y = ze(r);
+    if (a.mode == kModeAIES_DE) {
+      // differential evolution (Sec. 2.3, after Eq. (2.15)): y = z_i + gamma (z_j - z_k), k != j
+      // uniform over the other half (uniform 1 of the partner stream, skipping j), gamma =
+      // (1 + sigma_gamma eta) 2.38 / sqrt(2 d) with eta normal 0 of the scale stream
+      const double uk = draw_uniform<double>(a.seed, i, it, kAiesPartner, 1);
+      int kk = static_cast<int>(uk * (half - 1));
+      if (kk > half - 2) kk = half - 2;
+      if (kk >= jj) ++kk;
+      const Row<R> zk = z(base + kk);
+      R eta;
+      draw_normals<R>(a.seed, i, it, kAiesZ, 1, &eta);
+      const R gam = (R(1) + static_cast<R>(a.eps) * eta) * static_cast<R>(2.38 / sqrt(2.0 * a.d));
+#pragma unroll 1
+      for (int q = 0; q < a.d; ++q) y[q] = zi[q] + gam * (zj[q] - zk[q]);
+      return true;
+    }
     const double uz = draw_uniform<double>(a.seed, i, it, kAiesZ, 0);
     const double t = uz * (a.aies_a - 1.0) + 1.0;
     const double Z = a.aies_a == 2.0 ? t * t * 0.5 : t * t / a.aies_a;  // (x 0.5 is exact)
     dw(i)[0] = Z;
-    const Row<R> zi = z(i), zj = z(jw);
-    const Blk<R> y = ze(r);
     const R Zr = static_cast<R>(Z);
 #pragma unroll 1
     for (int q0 = 0; q0 < a.d; q0 += kVc) {
@@ -697,6 +734,7 @@ struct Chain {
   }
   __device__ __noinline__ bool aies_post(int r, int h, double lpy) const {
     const int i = aies_walker(r, h);
+    if (a.mode == kModeAIES_DE) return de_post(r, h, lpy);
     const double Z = dw(i)[0];
     const double lpc = static_cast<double>(a.st.lp[i]);
     const uint32_t it = a.st.iter[i];
@@ -719,6 +757,32 @@ struct Chain {
     }
     if (acc) {
       vcopy<R>(z(i), ze(r), d);
+      a.st.lp[i] = static_cast<R>(lpy);
+    }
+    count(i, acc, stat, 1);
+    return true;
+  }
+
+  // Differential-evolution decision: the move is symmetric, log alpha = log pi(y) - log pi(z_i).
+  __device__ __noinline__ bool de_post(int r, int h, double lpy) const {
+    const int i = aies_walker(r, h);
+    const double lpc = static_cast<double>(a.st.lp[i]);
+    const uint32_t it = a.st.iter[i];
+    auto la64 = [&] { return lpy - lpc; };
+    bool acc;
+    double stat = 0.0;
+    if (kF32 && lpy == -INFINITY) {
+      acc = false;
+    } else if constexpr (kF32) {
+      const float lpy32 = static_cast<float>(lpy), lp32 = static_cast<float>(lpc);
+      const float la32 = lpy32 - lp32;
+      const float err = 0x1p-21f * (fabsf(lpy32) + fabsf(lp32));
+      acc = metropolis(i, it, la32, err, la64, stat);
+    } else {
+      acc = metropolis(i, it, 0.f, 0.f, la64, stat);
+    }
+    if (acc) {
+      vcopy<R>(z(i), ze(r), a.d);
       a.st.lp[i] = static_cast<R>(lpy);
     }
     count(i, acc, stat, 1);
@@ -756,8 +820,10 @@ struct Chain {
       case kModeMH: return mh_pre(row);
       case kModeMALA: return mala_pre(row);
       case kModeHMC: return hmc_pre(row);
-      case kModeNUTS: return nuts_pre(row);
-      case kModeAIES: return aies_pre(row, h);
+      case kModeNUTS:
+      case kModeNUTS_MN: return nuts_pre(row);
+      case kModeAIES:
+      case kModeAIES_DE: return aies_pre(row, h);
       case kModeRefresh: return refresh_pre(row);
       default: return false;
     }
@@ -766,7 +832,7 @@ struct Chain {
     // log pi (and its gradient) at the evaluated point, then the kernel's decision, then the
     // end of the chain's iteration if it completed one
     R gp[kMaxD];
-    const bool grad = a.mode != kModeMH && a.mode != kModeAIES;
+    const bool grad = a.mode != kModeMH && !is_ensemble_mode(a.mode);
     const double lp = logpi(row, grad, gp);
     int c = row;
     bool done;
@@ -774,8 +840,10 @@ struct Chain {
       case kModeMH: done = mh_post(row, lp); break;
       case kModeMALA: done = mala_post(row, lp, gp); break;
       case kModeHMC: done = hmc_post(row, lp, gp); break;
-      case kModeNUTS: done = nuts_post(row, lp, gp); break;
+      case kModeNUTS:
+      case kModeNUTS_MN: done = nuts_post(row, lp, gp); break;
       case kModeAIES:
+      case kModeAIES_DE:
         c = aies_walker(row, h);
         done = aies_post(row, h, lp);
         break;

@@ -58,7 +58,7 @@ def test_ctypes_mirrors_match_the_header_layout(tmp_path):
         pytest.skip("gcc not available")
     cfg_fields = [f for f, _ in _lib.Config._fields_]
     st_fields = [f for f, _ in _lib.StepStats._fields_]
-    kernels = ["BST_MH", "BST_MALA", "BST_HMC", "BST_NUTS", "BST_AIES", "BST_BF16", "BST_FP32", "BST_FP64",
+    kernels = ["BST_MH", "BST_MALA", "BST_HMC", "BST_NUTS", "BST_AIES", "BST_AIES_DE", "BST_NUTS_MULTINOMIAL", "BST_BF16", "BST_FP32", "BST_FP64",
                "BST_FP16"]
     statuses = ["BST_OK", "BST_ERR_ARG", "BST_ERR_STATE", "BST_ERR_CUDA", "BST_ERR_NOT_PD", "BST_ERR_TIMEOUT",
                 "BST_ERR_NONFINITE", "BST_ERR_UNSUPPORTED"]

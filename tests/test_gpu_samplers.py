@@ -1,10 +1,28 @@
-"""Per-step parity of the five samplers against the FP64 oracle from identical
+"""Per-step parity of the samplers against the FP64 oracle from identical
 states and identical Philox streams.
 
-Decisions must agree wherever |log alpha - log u| > 1e-3 (the oracle's trace
-gives both); where they agree the new positions must match (FP64: 1e-9; FP32,
-BF16 and FP16: 1e-3 absolute in x).  BF16 and FP16 runs are compared with the
-oracle's operand-rounding mode of the same type."""
+Decisions must agree wherever they are clear of their threshold by the decision
+margin (the oracle's trace gives log alpha - log u, and for NUTS the smallest
+distance of any decision of the iteration); where they agree the new positions
+must match (FP64: 1e-9; FP32, BF16 and FP16: 1e-3 absolute in x).  BF16 and FP16
+runs are compared with the oracle's operand-rounding mode of the same type.
+
+The margin of a chain is max(1e-3, B): B bounds how far the GPU's decision
+quantity can sit from the oracle's, propagated to first order from the
+per-evaluation discrepancies of the likelihood between the two (tau_L in log pi,
+tau_g in the whitened gradient, twice their largest value over the chains' start
+points, measured on the same handle before stepping; the largest value, because
+a discrepancy made of whole rounding steps is heavy-tailed):
+  MH, AIES (stretch / DE): B = 2 tau_L (two evaluations at the same points);
+  MALA: B = 2 tau_L + tau_g (sqrt(2 eps d) + eps sqrt(d)) (the proposal terms and
+        the proposal's shift by eps g);
+  HMC, n leapfrogs, and NUTS, n leaves: B = 2 tau_L + eps sqrt(n d) tau_g (1 + eps n)
+        (a random walk of n gradient discrepancies in the momentum, |q| ~ sqrt(d),
+        and its drift into the position, |g| ~ sqrt(d)).
+In FP32 / FP64 the discrepancies are rounding-level and B is far below 1e-3.  In
+BF16 the hidden activations pass through tanh.approx before their BF16 rounding
+(2^-11 relative error against a 2^-9 rounding step), so some of them round to the
+neighbouring BF16 value of the oracle's: B is then of order 1e-2."""
 import numpy as np
 import pytest
 import torch
@@ -28,60 +46,100 @@ def _setup(prec, n, d=8, width=256, depth=3, seed=11, **kw):
     m = oracle_emulator_model(e, mu=mu, L=L, lower=lower, upper=upper, bf16=(prec == "bf16"),
                               fp16=(prec == "fp16"))
     z0 = np.linalg.solve(L, (theta0 - mu).T).T
+    s.tau = _tau(s, m, z0)
     return s, m, z0, mu, L
 
 
-def _check(prec, s, ref, samples, kernel, n, margin=MARGIN):
+def _tau(s, m, z0):
+    """Per-evaluation discrepancies of log pi and of its whitened gradient between the handle's
+    initial state and the oracle at the same points: twice their largest value over the chains."""
+    st = s.get_state()
+    rl, rg = m.logpost(z0)
+    ok = np.isfinite(rl) & np.isfinite(st["logp"])
+    dl = st["logp"][ok] - rl[ok]
+    dg = np.linalg.norm(st["grad"][ok] - rg[ok], axis=1)
+    return 2.0 * np.max(np.abs(dl)), 2.0 * np.max(dg)
+
+
+def _bound(s, kernel, d, eps, n_eval):
+    """B of the module docstring for one chain (n_eval: leapfrogs of HMC / leaves of NUTS)."""
+    tl, tg = getattr(s, "tau", (0.0, 0.0))
+    if kernel == "mala":
+        return 2 * tl + tg * (np.sqrt(2 * eps * d) + eps * np.sqrt(d))
+    if kernel == "hmc" or kernel.startswith("nuts"):
+        return 2 * tl + eps * np.sqrt(n_eval * d) * tg * (1 + eps * n_eval)
+    return 2 * tl
+
+
+def _check(prec, s, ref, samples, kernel, n, eps=0.0, n_leapfrog=1, margin=MARGIN):
     acc_gpu = s.counters()["accepts"]
     x_gpu = samples[-1].double().cpu().numpy()
     x_ref = ref["samples"][-1]
-    if kernel == "nuts":
+    d = x_ref.shape[-1]
+    if kernel.startswith("nuts"):
         # every decision of a NUTS iteration (slice, Delta_max, merges, top-level moves, U-turn
-        # tests) is at least `margin` away from its threshold on the clear chains (the oracle's
-        # trace gives the smallest distance): there the tree, the leapfrog count and the
+        # tests) is at least the chain's margin away from its threshold on the clear chains (the
+        # oracle's trace gives the smallest distance): there the tree, the leapfrog count and the
         # selected point must be the oracle's
-        clear = ref["margin"][-1] > margin
-        assert clear.mean() > 0.7, clear.mean()
+        mc = np.maximum(margin, _bound(s, kernel, d, eps, ref["nleaf"][-1]))
+        clear = ref["margin"][-1] > mc
+        # (FP32 / FP64: nearly every chain; BF16: the chains clear of its larger margin)
+        assert clear.mean() > 0.9 if prec in ("fp32", "fp64") else clear.sum() >= 10, (clear.mean(), clear.sum())
         same = np.all(np.abs(x_gpu - x_ref) < POS_TOL[prec], axis=1)
         assert np.all(same[clear]), np.flatnonzero(clear & ~same)
         ev = s.counters()["evals"]
         assert np.array_equal(ev[clear], ref["evals"][clear])
         return
     la, lu = ref["log_alpha"][-1], ref["log_u"][-1]
-    clear = np.abs(la - lu) > margin
-    assert clear.mean() > 0.9
-    assert np.array_equal(acc_gpu[clear] > 0, ref["accept"][-1][clear] > 0)
+    mc = max(margin, _bound(s, kernel, d, eps, n_leapfrog))
+    clear = np.abs(la - lu) > mc
+    if kernel.startswith("aies"):
+        # the second half of an ensemble proposes from the first half's new positions: where a
+        # first-half decision inside the margin went the other way, the second half's proposals
+        # differ, so those walkers are not compared
+        W = 64
+        acc_g, acc_r = acc_gpu.reshape(-1, 2, W // 2) > 0, ref["accept"][-1].reshape(-1, 2, W // 2) > 0
+        flipped = np.any(acc_g[:, 0] != acc_r[:, 0], axis=1)
+        clear = clear.reshape(-1, 2, W // 2)
+        clear[flipped, 1] = False
+        clear = clear.reshape(-1)
+    assert clear.mean() > (0.9 if prec in ("fp32", "fp64") else 0.1), clear.mean()
+    bad = np.flatnonzero(clear & ((acc_gpu > 0) != (ref["accept"][-1] > 0)))
+    assert bad.size == 0, (mc, getattr(s, "tau", None), bad, (la - lu)[bad])
     assert np.all(np.abs(x_gpu[clear] - x_ref[clear]) < POS_TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("kernel,eps,extra", [("mh", 0.5, {}), ("mala", 0.4, {}), ("hmc", 0.2, {"n_leapfrog": 5}),
-                                              ("nuts", 0.3, {})])
+                                              ("nuts", 0.3, {}), ("nuts_multinomial", 0.3, {})])
 def test_one_step_parity(prec, kernel, eps, extra):
     n = 300
     s, m, z0, mu, L = _setup(prec, n)
     out = torch.empty((1, n, 8), dtype=s.dtype, device="cuda")
     s.step(kernel, 1, eps=eps, samples=out, **extra)
     ref = O.run(m, kernel, z0, eps=eps, n_steps=1, seed=11, trace=True, **extra)
+    _check(prec, s, ref, out, kernel, n, eps=eps, n_leapfrog=extra.get("n_leapfrog", 1))
+    s.close()
+
+
+@pytest.mark.parametrize("kernel", ["aies", "aies_de"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "fp16"])
+def test_aies_one_step_parity(prec, kernel):
+    """The stretch move and the differential-evolution move (sigma_gamma = 0.1, passed as eps),
+    one ensemble update of 4 ensembles of 64 walkers, and three more updates in FP64 (where the
+    halves span two tiles synchronised by a cluster barrier between half-steps)."""
+    n = 256  # 4 ensembles of 64 walkers
+    s, m, z0, mu, L = _setup(prec, n)
+    out = torch.empty((1, n, 8), dtype=s.dtype, device="cuda")
+    # (FP64 emulator tiles hold 16 rows: each 32-walker half spans a cluster of two tiles)
+    s.step(kernel, 1, eps=0.1, samples=out)
+    ref = O.run(m, kernel, z0, eps=0.0, n_steps=1, seed=11, trace=True, aies_walkers=64, de_sigma=0.1)
     _check(prec, s, ref, out, kernel, n)
     s.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16", "fp16"])
-def test_aies_one_step_parity(prec):
-    n = 256  # 4 ensembles of 64 walkers
-    s, m, z0, mu, L = _setup(prec, n)
-    out = torch.empty((1, n, 8), dtype=s.dtype, device="cuda")
-    if prec == "fp64":
-        pytest.skip("FP64 emulator tiles hold 16 rows: AIES ensemble halves would span tiles")
-    s.step("aies", 1, samples=out)
-    ref = O.run(m, "aies", z0, eps=0.0, n_steps=1, seed=11, trace=True, aies_walkers=64)
-    _check(prec, s, ref, out, "aies", n)
-    s.close()
-
-
 @pytest.mark.parametrize("kernel,eps,extra", [("mala", 0.4, {}), ("hmc", 0.25, {"n_leapfrog": 4}), ("mh", 0.5, {}),
-                                              ("nuts", 0.3, {})])
+                                              ("nuts", 0.3, {}), ("nuts_multinomial", 0.3, {})])
 def test_fp64_trajectories_track_oracle(kernel, eps, extra):
     n, steps = 160, 12
     s, m, z0, mu, L = _setup("fp64", n)
@@ -155,6 +213,7 @@ def _setup_gauss(prec, n, width, d=8, seed=11, depth=3):
     m = oracle_emulator_model(e, mu=mu, L=L, lower=lower, upper=upper, gauss=gauss, bf16=(prec == "bf16"),
                               fp16=(prec == "fp16"))
     z0 = np.linalg.solve(L, (theta0 - mu).T).T
+    s.tau = _tau(s, m, z0)
     return s, m, z0
 
 
@@ -169,7 +228,7 @@ def test_bf16_register_chains_gaussian_prior_parity(width, kernel, eps, extra, p
     ref = O.run(m, kernel, z0, eps=eps, n_steps=1, seed=11, trace=True, **extra)
     # BF16 log alpha after five leapfrogs differs from the oracle's BF16-emulation mode (exact
     # tanh, FP64 sums) by up to a few 1e-3, so HMC decisions are compared outside 1e-2
-    _check(prec, s, ref, out, kernel, n, margin=1e-2 if kernel == "hmc" else MARGIN)
+    _check(prec, s, ref, out, kernel, n, eps=eps, n_leapfrog=extra.get("n_leapfrog", 1))
     s.close()
 
 
@@ -209,7 +268,7 @@ def test_bf16_mala_two_cta_clusters(width, prec):
     out = torch.empty((1, n, 8), dtype=s.dtype, device="cuda")
     s.step("mala", 1, eps=0.4, samples=out)
     ref = O.run(m, "mala", z0, eps=0.4, n_steps=1, seed=11, trace=True)
-    _check(prec, s, ref, out, "mala", n)
+    _check(prec, s, ref, out, "mala", n, eps=0.4)
     s.close()
 
 
@@ -230,20 +289,25 @@ def _setup27(prec, n, width=256, depth=2, seed=11):
     m = oracle_emulator_model(e, mu=mu, L=L, lower=lower, upper=upper, gauss=gauss, bf16=(prec == "bf16"),
                               fp16=(prec == "fp16"))
     z0 = np.linalg.solve(L, (theta0 - mu).T).T
+    s.tau = _tau(s, m, z0)
     return s, m, z0
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("kernel,eps,extra", [("mh", 0.6, {}), ("mala", 0.6, {}), ("hmc", 0.5, {"n_leapfrog": 4}),
-                                              ("nuts", 0.5, {}), ("aies", 0.0, {"aies_walkers": 64})])
+                                              ("nuts", 0.5, {}), ("nuts_multinomial", 0.5, {}),
+                                              ("aies", 0.0, {"aies_walkers": 64}),
+                                              ("aies_de", 0.1, {"aies_walkers": 64, "de_sigma": 0.1})])
 def test_27d_one_step_parity(prec, kernel, eps, extra):
-    n = 256  # four AIES ensembles of 64 walkers
+    # four AIES ensembles of 64 walkers; NUTS in BF16 / FP16 on more chains, since at d = 27 only
+    # a few percent of its trees clear the margin of those precisions
+    n = 1024 if (kernel.startswith("nuts") and prec in ("bf16", "fp16")) else 256
     s, m, z0 = _setup27(prec, n)
     out = torch.empty((1, n, 27), dtype=s.dtype, device="cuda")
-    kw = {k: v for k, v in extra.items() if k != "aies_walkers"}
+    kw = {k: v for k, v in extra.items() if k not in ("aies_walkers", "de_sigma")}
     s.step(kernel, 1, eps=eps, samples=out, **kw)
     ref = O.run(m, kernel, z0, eps=eps, n_steps=1, seed=11, trace=True, **extra)
-    _check(prec, s, ref, out, kernel, n, margin=1e-2 if (prec in ("bf16", "fp16") and kernel == "hmc") else MARGIN)
+    _check(prec, s, ref, out, kernel, n, eps=eps, n_leapfrog=extra.get("n_leapfrog", 1))
     s.close()
 
 
@@ -321,7 +385,8 @@ def test_bounds_penalty_one_step_parity(prec, kernel, eps, extra):
     from gpu_common import rel_err
     assert rel_err(st["grad"], rg) < tg
     out = torch.empty((1, n, d), dtype=s.dtype, device="cuda")
+    s.tau = _tau(s, m, z0)
     s.step(kernel, 1, eps=eps, samples=out, **extra)
     ref = O.run(m, kernel, z0, eps=eps, n_steps=1, seed=11, trace=True, **extra)
-    _check(prec, s, ref, out, kernel, n, margin=1e-2 if (prec == "bf16" and kernel == "hmc") else MARGIN)
+    _check(prec, s, ref, out, kernel, n, eps=eps, n_leapfrog=extra.get("n_leapfrog", 1))
     s.close()

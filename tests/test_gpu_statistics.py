@@ -36,7 +36,8 @@ def _check(samples, mean, cov, nsig=5.0):
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("kernel,eps,steps,kw", [("mh", 0.6, 3000, {}), ("mala", 0.5, 2000, {}),
                                                  ("hmc", 0.3, 500, {"n_leapfrog": 8}), ("nuts", 0.5, 400, {}),
-                                                 ("nuts", 1.2, 800, {})])
+                                                 ("nuts", 1.2, 800, {}), ("nuts_multinomial", 0.5, 400, {}),
+                                                 ("nuts_multinomial", 1.2, 800, {})])
 def test_closed_form_moments(prec, kernel, eps, steps, kw):
     from paper_2606_04895_gb300 import Sampler
     t, mean, cov = _closed_form()
@@ -54,8 +55,9 @@ def test_closed_form_moments(prec, kernel, eps, steps, kw):
     s.close()
 
 
-@pytest.mark.parametrize("prec", ["fp32"])
-def test_aies_closed_form_moments(prec):
+@pytest.mark.parametrize("kernel", ["aies", "aies_de"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_aies_closed_form_moments(prec, kernel):
     from paper_2606_04895_gb300 import Sampler
     t, mean, cov = _closed_form()
     Lp = np.linalg.cholesky(cov)
@@ -67,7 +69,7 @@ def test_aies_closed_form_moments(prec):
     s.init_chains(theta0, t["lower"], t["upper"])
     steps = 1200
     out = torch.empty((steps, n, 6), dtype=s.dtype, device="cuda")
-    s.step("aies", steps, samples=out)
+    s.step(kernel, steps, eps=0.1, samples=out)
     x = out.double().cpu().numpy()[steps // 4:]
     ens = x.reshape(x.shape[0], n_ens, 64, 6).transpose(0, 2, 1, 3).reshape(-1, n_ens, 6)
     _check(ens, mean, cov)
