@@ -265,11 +265,17 @@ bst_status bst_get_counters(bst_handle h, int64_t *accepts, int64_t *evals, int6
                             double *accept_stat);
 
 /* Emulator training (the learned part): one Adam step (Kingma & Ba) of the
- * loss mean_i (out_i - (chi2_i - out_m)/out_s)^2 over the batch X_dev[m][d],
- * chi2_dev[m] (float, device).  FP32 master weights, forward with stored
- * activations, hand-written backward; the sampling weights are re-packed from
- * the master before the next evaluation.  loss_dev (float[1], may be NULL)
- * receives the batch loss before the update.  1 <= m <= 65536. */
+ * loss mean_i (out_i - (t(chi2_i) - out_m)/out_s)^2 over the batch X_dev[m][d],
+ * chi2_dev[m] (float, device), t the output transform (bst_set_emulator_output).
+ * FP32 master weights, forward with stored activations, hand-written backward;
+ * the sampling weights are re-packed from the master before the next
+ * evaluation.  Handles of precision BF16 / FP16 run the hidden-layer products
+ * (layers 2..depth: forward, adjoint, weight gradient) on the tcgen05 tensor
+ * cores with BF16 operands and FP32 accumulation when m is a multiple of 512
+ * and width a multiple of 128 (the input layer, the output head and the bias
+ * sums stay FP32); otherwise, and for FP32 / FP64 handles, every product runs
+ * in FP32 on the CUDA cores.  loss_dev (float[1], may be NULL) receives the
+ * batch loss before the update.  1 <= m <= 65536. */
 bst_status bst_train_step(bst_handle h, const float *X_dev, const float *chi2_dev, int m,
                           double lr, double beta1, double beta2, double adam_eps, float *loss_dev,
                           void *stream);

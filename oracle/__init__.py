@@ -115,7 +115,7 @@ def lib():
             L.orc_cholesky_jitter.argtypes = [i, vp, d, vp, vp]
             L.orc_cholesky_jitter.restype = i
             L.orc_remap_z.argtypes = [i, i, vp, vp, vp, vp, vp]
-            L.orc_train_loss_grad.argtypes = [i, i, i, vp, vp, vp, d, d, i, d, i, vp, vp, vp]
+            L.orc_train_loss_grad.argtypes = [i, i, i, vp, vp, vp, d, d, i, d, i, i, vp, vp, vp]
             L.orc_train_loss_grad.restype = d
             L.orc_adam.argtypes = [i, vp, vp, vp, vp, i, d, d, d, d]
             L.orc_ess.argtypes = [i, i, i, vp, vp]
@@ -307,11 +307,13 @@ def remap_z(mu_old, L_old, mu_new, L_new, z):
 
 
 # --------------------------------------------------------------------------- training
-def train_loss_grad(d, depth, width, params, in_m, in_s, out_m, out_s, X, chi2, out_log=0, out_floor=0.0):
+def train_loss_grad(d, depth, width, params, in_m, in_s, out_m, out_s, X, chi2, out_log=0, out_floor=0.0,
+                    bf16=False):
     P = _f64(params); X = _f64(X); y = _f64(chi2)
     g = np.zeros_like(P)
     loss = lib().orc_train_loss_grad(d, depth, width, _ptr(P), _ptr(_f64(in_m)), _ptr(_f64(in_s)),
-                                     float(out_m), float(out_s), int(out_log), float(out_floor), X.shape[0],
+                                     float(out_m), float(out_s), int(out_log), float(out_floor), int(bool(bf16)),
+                                     X.shape[0],
                                      _ptr(X), _ptr(y), _ptr(g))
     return loss, g
 

@@ -929,11 +929,16 @@ void orc_remap_z(int d, int n, const double *mu_old, const double *L_old, const 
 /* Loss = mean_i (out_i - y_i)^2 with y_i = (t(chi2_i) - out_m) / out_s (the standardised
  * regression target), t(c) = c for the linear output and log(max(c - out_floor, 1e-30)) for
  * the log output.  grad (same layout as params) = d loss / d params, by reverse-mode
- * differentiation. */
+ * differentiation.  bf16 = 1: the operands of the hidden-layer products (layers 2..D) are
+ * rounded to bfloat16 -- W_l and h_{l-1} in the forward product, the adjoint delta_l and
+ * h_{l-1} in the weight gradient, delta_l and W_l in the adjoint product -- with every sum
+ * exact (the mixed-precision training of the tensor-core path); the input layer, the output
+ * layer, the biases and the (1 - h^2) factors are exact.                                    */
 double orc_train_loss_grad(int d, int D, int w, const double *P, const double *in_m,
                            const double *in_s, double out_m, double out_s, int out_log,
-                           double out_floor, int mb, const double *X, const double *chi2,
+                           double out_floor, int bf16, int mb, const double *X, const double *chi2,
                            double *grad) {
+  const int rm = bf16 ? 1 : 0; /* oround mode */
   size_t np = (size_t)d * w + w + (size_t)(D - 1) * ((size_t)w * w + w) + w + 1;
   memset(grad, 0, sizeof(double) * np);
   double loss = 0.0;
@@ -956,7 +961,10 @@ double orc_train_loss_grad(int d, int D, int w, const double *P, const double *i
       double *hl = h + (size_t)l * w;
       for (int k = 0; k < w; ++k) {
         double a = bl[k];
-        for (int j = 0; j < fan_in; ++j) a += Wl[(size_t)k * fan_in + j] * hp[j];
+        if (l == 1)
+          for (int j = 0; j < fan_in; ++j) a += Wl[(size_t)k * fan_in + j] * hp[j];
+        else
+          for (int j = 0; j < fan_in; ++j) a += oround(Wl[(size_t)k * fan_in + j], rm) * oround(hp[j], rm);
         hl[k] = tanh(a);
       }
     }
@@ -976,14 +984,15 @@ double orc_train_loss_grad(int d, int D, int w, const double *P, const double *i
     for (int l = D; l >= 1; --l) {
       int fan_in = (l == 1) ? d : w;
       const double *Wl = P + off_W[l], *hp = h + (size_t)(l - 1) * w;
+      const int r = (l > 1) ? rm : 0;
       for (int k = 0; k < w; ++k) {
         grad[off_b[l] + k] += dl[k];
-        for (int j = 0; j < fan_in; ++j) grad[off_W[l] + (size_t)k * fan_in + j] += dl[k] * hp[j];
+        for (int j = 0; j < fan_in; ++j) grad[off_W[l] + (size_t)k * fan_in + j] += oround(dl[k], r) * oround(hp[j], r);
       }
       if (l > 1) {
         for (int j = 0; j < w; ++j) {
           double s = 0.0;
-          for (int k = 0; k < w; ++k) s += Wl[(size_t)k * w + j] * dl[k];
+          for (int k = 0; k < w; ++k) s += oround(Wl[(size_t)k * w + j], r) * oround(dl[k], r);
           dn[j] = s * (1.0 - hp[j] * hp[j]);
         }
         memcpy(dl, dn, sizeof(double) * (size_t)w);

@@ -124,7 +124,7 @@ void orc_remap_z(int d, int n, const double *mu_old, const double *L_old, const 
 /* ---- training ---- */
 double orc_train_loss_grad(int d, int depth, int width, const double *params, const double *in_m,
                            const double *in_s, double out_m, double out_s, int out_log,
-                           double out_floor, int m, const double *X, const double *chi2,
+                           double out_floor, int bf16, int m, const double *X, const double *chi2,
                            double *grad);
 void orc_adam(int n, double *p, const double *g, double *m1, double *m2, int t, double lr,
               double b1, double b2, double eps);

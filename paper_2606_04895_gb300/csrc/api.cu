@@ -1168,7 +1168,35 @@ static bst_status train_setup(bst_handle h, int m) {
     BST_TRY(dalloc_t(h, &h->tw.loss, 4));
     const size_t fmax = w > static_cast<size_t>(h->d) ? w : static_cast<size_t>(h->d);
     BST_TRY(dalloc_t(h, &h->tw.ws, static_cast<size_t>(kTrainSplits) * w * fmax));
+    h->tw.Hb = h->tw.HbT = h->tw.Db = h->tw.DbT = h->tw.Wb = h->tw.WbT = nullptr;
+    h->tw.wsg = nullptr;
+    if (tc_engine(h) && D >= 2) {
+      // BF16 operands of the tensor-core training GEMMs
+      const size_t nh = D - 1;
+      BST_TRY(dalloc(h, reinterpret_cast<void **>(&h->tw.Hb), nh * mm * w * 2));
+      BST_TRY(dalloc(h, reinterpret_cast<void **>(&h->tw.HbT), nh * mm * w * 2));
+      BST_TRY(dalloc(h, reinterpret_cast<void **>(&h->tw.Db), 2 * mm * w * 2));
+      BST_TRY(dalloc(h, reinterpret_cast<void **>(&h->tw.DbT), 2 * mm * w * 2));
+      BST_TRY(dalloc(h, reinterpret_cast<void **>(&h->tw.Wb), nh * w * w * 2));
+      BST_TRY(dalloc(h, reinterpret_cast<void **>(&h->tw.WbT), nh * w * w * 2));
+      BST_TRY(dalloc_t(h, &h->tw.wsg, static_cast<size_t>(kTcTrainSplits) * w * w));
+    }
     h->train_cap = m;
+  }
+  return BST_OK;
+}
+
+// The training gradient: on the tensor cores (BF16 operands, FP32 accumulation) for handles of a
+// tensor-core precision whose shapes fit its tiles, else on the CUDA cores in FP32.
+static bst_status train_grad_impl(bst_handle h, const float *X_dev, const float *chi2_dev, int m, float *grad_dev,
+                                  cudaStream_t s) {
+  const float om = static_cast<float>(h->out_m), os = static_cast<float>(h->out_s), of = static_cast<float>(h->out_floor);
+  if (h->tw.Hb && tc_train_shape_ok(h->d, h->depth, h->width, m)) {
+    BST_CUDA(launch_train_grad_tc(h->P32, h->in_m32, h->in_s32, om, os, h->out_log, of, h->d, h->depth, h->width, m,
+                                  X_dev, chi2_dev, grad_dev, h->tw, h->status, s));
+  } else {
+    BST_CUDA(launch_train_grad(h->P32, h->in_m32, h->in_s32, om, os, h->out_log, of, h->d, h->depth, h->width, m, X_dev,
+                               chi2_dev, grad_dev, h->tw, s));
   }
   return BST_OK;
 }
@@ -1180,8 +1208,7 @@ bst_status bst_train_grad(bst_handle h, const float *X_dev, const float *chi2_de
   BST_CUDA(cudaSetDevice(h->device));
   BST_TRY(train_setup(h, m));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  BST_CUDA(launch_train_grad(h->P32, h->in_m32, h->in_s32, static_cast<float>(h->out_m), static_cast<float>(h->out_s),
-                             h->out_log, static_cast<float>(h->out_floor), h->d, h->depth, h->width, m, X_dev, chi2_dev, grad_dev, h->tw, s));
+  BST_TRY(train_grad_impl(h, X_dev, chi2_dev, m, grad_dev, s));
   if (loss_dev) BST_CUDA(cudaMemcpyAsync(loss_dev, h->tw.loss, 4, cudaMemcpyDeviceToDevice, s));
   return BST_OK;
 }
@@ -1195,8 +1222,7 @@ bst_status bst_train_step(bst_handle h, const float *X_dev, const float *chi2_de
   BST_CUDA(cudaSetDevice(h->device));
   BST_TRY(train_setup(h, m));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  BST_CUDA(launch_train_grad(h->P32, h->in_m32, h->in_s32, static_cast<float>(h->out_m), static_cast<float>(h->out_s),
-                             h->out_log, static_cast<float>(h->out_floor), h->d, h->depth, h->width, m, X_dev, chi2_dev, h->G32, h->tw, s));
+  BST_TRY(train_grad_impl(h, X_dev, chi2_dev, m, h->G32, s));
   if (loss_dev) BST_CUDA(cudaMemcpyAsync(loss_dev, h->tw.loss, 4, cudaMemcpyDeviceToDevice, s));
   h->adam_t += 1;
   BST_CUDA(launch_adam(h->P32, h->G32, h->m1, h->m2, h->nparams, h->adam_t, static_cast<float>(lr),

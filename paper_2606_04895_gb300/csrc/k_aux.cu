@@ -850,6 +850,96 @@ cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in
   return cudaGetLastError();
 }
 
+// The same gradient with the hidden-layer products on the tensor cores (BF16 operands, FP32
+// accumulation; k_train_tc.cu).  The input layer (K = d), the output head, the bias sums and
+// the (1 - h^2) factors stay FP32 on the CUDA cores.  Needs m % 512 == 0, w % 128 == 0, D >= 2
+// (tc_train_shape_ok) and the BF16 buffers of tw.
+bool tc_train_shape_ok(int d, int D, int w, int m) {
+  (void)d;
+  return D >= 2 && tc_gemm_shape_ok(m, w, w, 1) && tc_gemm_shape_ok(w, w, m, kTcTrainSplits);
+}
+cudaError_t launch_train_grad_tc(const float *P, const float *in_m, const float *in_s, float out_m, float out_s,
+                                 int out_log, float out_floor, int d, int D, int w, int m, const float *X,
+                                 const float *chi2, float *G, TrainWork &tw, int *status, cudaStream_t s) {
+  if (!tc_train_shape_ok(d, D, w, m)) return cudaErrorInvalidValue;
+  const size_t mw = static_cast<size_t>(m) * w, ww = static_cast<size_t>(w) * w;
+  cudaMemsetAsync(tw.loss, 0, sizeof(float), s);
+  standardise_kernel<<<blocks_for(static_cast<size_t>(m) * d, 256), 256, 0, s>>>(X, in_m, in_s, m, d, tw.U);
+  cudaError_t e;
+  // BF16 copies of W_l and W_l^T (l = 2..D) from the FP32 masters
+  for (int l = 2; l <= D; ++l) {
+    e = launch_cast_transpose_bf16(P + off_W(l, d, w), w, w, tw.Wb + (l - 2) * ww, tw.WbT + (l - 2) * ww, s);
+    if (e != cudaSuccess) return e;
+  }
+  // forward: layer 1 on the CUDA cores (K = d), then H_l = tanh(H_{l-1} W_l^T + b_l) on the tensor cores
+  gemm_f32(m, w, d, tw.U, d, 1, P + off_W(1, d, w), 1, d, tw.H, w, EPI_TANH, P + off_b(1, d, w), nullptr, 0, s);
+  e = launch_cast_transpose_bf16(tw.H, m, w, tw.Hb, tw.HbT, s);
+  if (e != cudaSuccess) return e;
+  for (int l = 2; l <= D; ++l) {
+    TcGemmArgs a = {};
+    a.M = m;
+    a.N = w;
+    a.K = w;
+    a.epi = kTcEpiTanh;
+    a.C = tw.H + static_cast<size_t>(l - 1) * mw;
+    a.bias = P + off_b(l, d, w);
+    a.Cb = l < D ? tw.Hb + (l - 1) * mw : nullptr;
+    a.CbT = l < D ? tw.HbT + (l - 1) * mw : nullptr;
+    a.status = status;
+    e = launch_tc_gemm(tw.Hb + (l - 2) * mw, tw.Wb + (l - 2) * ww, 1, a, s);
+    if (e != cudaSuccess) return e;
+  }
+  const float *HD = tw.H + static_cast<size_t>(D - 1) * mw;
+  const size_t owo = off_wo(d, D, w);
+  train_head_kernel<<<blocks_for(static_cast<size_t>(m) * 32, 256), 256, 0, s>>>(HD, P + owo, P + owo + w, chi2, out_m,
+                                                                               out_s, out_log, out_floor, m, w,
+                                                                               tw.dout, tw.Dl, tw.loss);
+  gemm_f32(1, w, m, tw.dout, 0, 1, HD, w, 1, G + owo, w, EPI_STORE, nullptr, nullptr, 0, s);
+  colsum_kernel<<<1, 256, 0, s>>>(tw.dout, m, 1, G + owo + w);
+  int cur = 0;
+  e = launch_cast_transpose_bf16(tw.Dl, m, w, tw.Db, tw.DbT, s);
+  if (e != cudaSuccess) return e;
+  float *dl = tw.Dl, *dn = tw.Dn;
+  for (int l = D; l >= 2; --l) {
+    // G_l = delta_l^T H_{l-1} over the batch (split in kTcTrainSplits slices summed in order)
+    TcGemmArgs gw = {};
+    gw.M = w;
+    gw.N = w;
+    gw.K = m;
+    gw.epi = kTcEpiStore;
+    gw.C = tw.wsg;
+    gw.status = status;
+    e = launch_tc_gemm(tw.DbT + cur * mw, tw.HbT + (l - 2) * mw, kTcTrainSplits, gw, s);
+    if (e != cudaSuccess) return e;
+    sum_slices_kernel<<<blocks_for(ww, 256), 256, 0, s>>>(tw.wsg, kTcTrainSplits, ww, G + off_W(l, d, w));
+    colsum_kernel<<<blocks_for(w, 32), 256, 0, s>>>(dl, m, w, G + off_b(l, d, w));
+    // delta_{l-1} = (delta_l W_l) (1 - H_{l-1}^2), FP32 and its BF16 copies
+    TcGemmArgs gd = {};
+    gd.M = m;
+    gd.N = w;
+    gd.K = w;
+    gd.epi = kTcEpiDtanh;
+    gd.C = dn;
+    gd.H = tw.H + static_cast<size_t>(l - 2) * mw;
+    gd.Cb = l > 2 ? tw.Db + (1 - cur) * mw : nullptr;
+    gd.CbT = l > 2 ? tw.DbT + (1 - cur) * mw : nullptr;
+    gd.status = status;
+    e = launch_tc_gemm(tw.Db + cur * mw, tw.WbT + (l - 2) * ww, 1, gd, s);
+    if (e != cudaSuccess) return e;
+    float *t = dl;
+    dl = dn;
+    dn = t;
+    cur = 1 - cur;
+  }
+  // layer 1 (fan-in d) on the CUDA cores
+  gemm_f32(w, d, m, dl, 1, w, tw.U, d, 1, tw.ws, d, EPI_STORE, nullptr, nullptr, 0, s, kTrainSplits);
+  sum_slices_kernel<<<blocks_for(static_cast<size_t>(w) * d, 256), 256, 0, s>>>(tw.ws, kTrainSplits,
+                                                                              static_cast<size_t>(w) * d,
+                                                                              G + off_W(1, d, w));
+  colsum_kernel<<<blocks_for(w, 32), 256, 0, s>>>(dl, m, w, G + off_b(1, d, w));
+  return cudaGetLastError();
+}
+
 __global__ void adam_kernel(float *P, const float *G, float *m1, float *m2, size_t n, float lr, float b1, float b2,
                             float eps, float c1, float c2) {
   const size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;

@@ -105,7 +105,37 @@ struct TrainWork {
   float *dout;  // [m]
   float *loss;  // [1]
   float *ws;    // [kTrainSplits][w][w] partial weight gradients (split over the batch)
+  // tensor-core training (BF16 operands): null when the handle trains on the CUDA cores
+  __nv_bfloat16 *Hb, *HbT;   // [D-1][m][w] / [D-1][w][m] hidden activations h_1..h_{D-1}
+  __nv_bfloat16 *Db, *DbT;   // [2][m][w] / [2][w][m] adjoints (double-buffered)
+  __nv_bfloat16 *Wb, *WbT;   // [D-1][w][w] W_l and W_l^T, l = 2..D
+  float *wsg;                // [kTcTrainSplits][w][w] partial weight gradients of the tensor-core GEMM
 };
+constexpr int kTcTrainSplits = 8;
+
+// BF16 tcgen05 GEMM C[M][N] = A[M][K] . B[N][K]^T (k_train_tc.cu), K-major BF16 operands, FP32
+// accumulation; fused epilogues (C FP32, optional BF16 copies Cb [M][N] and CbT [N][M]):
+enum { kTcEpiStore = 0, kTcEpiTanh = 1, kTcEpiDtanh = 2 };
+struct TcGemmArgs {
+  int M, N, K;
+  int k_chunk;          // set by the launcher: K / splits (grid.z slices, C + z M N each)
+  int epi;              // kTcEpiStore: C = acc; kTcEpiTanh: tanh(acc + bias); kTcEpiDtanh: acc (1 - H^2)
+  float *C;
+  const float *bias;    // [N]
+  const float *H;       // [M][N]
+  __nv_bfloat16 *Cb;
+  __nv_bfloat16 *CbT;
+  int *status;
+};
+bool tc_gemm_shape_ok(int M, int N, int K, int splits);
+cudaError_t launch_tc_gemm(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int splits, const TcGemmArgs &args,
+                           cudaStream_t s);
+cudaError_t launch_cast_transpose_bf16(const float *X, int rows, int cols, __nv_bfloat16 *Xb, __nv_bfloat16 *XbT,
+                                       cudaStream_t s);
+bool tc_train_shape_ok(int d, int D, int w, int m);
+cudaError_t launch_train_grad_tc(const float *P, const float *in_m, const float *in_s, float out_m, float out_s,
+                                 int out_log, float out_floor, int d, int D, int w, int m, const float *X,
+                                 const float *chi2, float *G, TrainWork &tw, int *status, cudaStream_t s);
 constexpr int kTrainSplits = 4;
 cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in_s, float out_m, float out_s,
                               int out_log, float out_floor, int d, int D, int w, int m, const float *X,

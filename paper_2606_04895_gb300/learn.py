@@ -127,13 +127,14 @@ def fold_input_map(e, c, T):
 
 
 def train_emulator_log(tgt, *, n_train=1 << 20, width=512, depth=4, epochs=40, batch=4096, lr=1e-3, lr_min=1e-5,
-                       seed=4, log=None, device=None):
+                       seed=4, log=None, device=None, precision="bf16"):
     """Config-4 recipe with the log output and whitened inputs: 50 % box-uniform / 50 %
     Gaussian-at-3-sigma inputs (2^20), FP64 analytic chi^2 labels, MSE on the standardised
     log(chi2 - floor), Adam (lr 1e-3, cosine to lr_min) on FP32 masters in batches of 4096, all in
-    the library's training kernels.  The input is u = T (theta - theta*) (input_whitening),
-    folded into layer 1 afterwards.  Returns (emulator dict with the trained weights, history,
-    the training inputs and labels)."""
+    the library's training kernels: precision "bf16" trains the hidden layers on the tensor cores
+    (BF16 operands, FP32 accumulation), "fp32" on the CUDA cores.  The input is
+    u = T (theta - theta*) (input_whitening), folded into layer 1 afterwards.  Returns (emulator
+    dict with the trained weights, history, the training inputs and labels)."""
     import synthetic as S
     d = tgt["d"]
     theta = S.training_inputs(tgt, n_train, seed=seed)
@@ -145,7 +146,7 @@ def train_emulator_log(tgt, *, n_train=1 << 20, width=512, depth=4, epochs=40, b
     floor, out_m, out_s = log_output_standardisation(chi2)
     e0 = S.emulator(d, width=width, depth=depth, seed=seed + 1, in_m=np.zeros(d), in_s=np.ones(d), out_m=out_m,
                     out_s=out_s, out_log=1, out_floor=floor)
-    emu = Sampler(d, 8, precision="fp32", likelihood="emulator", seed=seed,
+    emu = Sampler(d, 8, precision=precision, likelihood="emulator", seed=seed,
                   **({} if device is None else {"device": device}))
     emu.set_emulator(e0["params"], depth, width, e0["in_m"], e0["in_s"], out_m, out_s, out_log=1, out_floor=floor)
     hist = fit(emu, u, chi2, epochs=epochs, batch=batch, lr=lr, lr_min=lr_min, seed=seed, log=log)

@@ -120,6 +120,57 @@ def test_training_gradient_log_output_matches_oracle():
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("out_log", [0, 1])
+def test_tensor_core_training_gradient_matches_oracle(prec, out_log):
+    """Handles of a tensor-core precision train the hidden layers on tcgen05 (BF16 operands,
+    FP32 accumulation; 8-512x4-1, batch 1024 = two 512-row multiples): loss and gradient against
+    the oracle's BF16 mixed-precision training mode (operands of the hidden-layer products rounded
+    at the same points) on the FP32-rounded inputs."""
+    from paper_2606_04895_gb300 import Sampler
+    d, D, w, m = 8, 4, 512, 1024
+    kw = dict(out_log=1, out_floor=240.0) if out_log else {}
+    om, osd = (3.0, 1.5) if out_log else (200.0, 50.0)
+    e = S.emulator(d, width=w, depth=D, seed=3, out_m=om, out_s=osd, **kw)
+    s = Sampler(d, 8, precision=prec, likelihood="emulator")
+    s.set_emulator(e["params"], D, w, e["in_m"], e["in_s"], e["out_m"], e["out_s"], **kw)
+    X = np.random.default_rng(0).uniform(-3, 3, (m, d))
+    rng = np.random.default_rng(1)
+    y = 241.0 + np.exp(3.0 + 1.5 * rng.normal(size=m)) if out_log else 200 + 50 * rng.normal(size=m)
+    loss, g = s.train_grad(torch.as_tensor(X, dtype=torch.float32, device="cuda"),
+                           torch.as_tensor(y, dtype=torch.float32, device="cuda"))
+    Xf = X.astype(np.float32).astype(np.float64)
+    yf = y.astype(np.float32).astype(np.float64)
+    Pf = e["params"].astype(np.float32).astype(np.float64)
+    lref, gref = O.train_loss_grad(d, D, w, Pf, e["in_m"], e["in_s"], e["out_m"], e["out_s"], Xf, yf,
+                                   bf16=True, **kw)
+    assert abs(loss.item() - lref) / lref < 1e-4
+    assert rel_err(g.cpu().numpy(), gref) < 3e-3, rel_err(g.cpu().numpy(), gref)
+    # and it is not the FP32 gradient: the BF16 rounding of the operands is visible
+    _, g64 = O.train_loss_grad(d, D, w, Pf, e["in_m"], e["in_s"], e["out_m"], e["out_s"], Xf, yf, **kw)
+    assert rel_err(gref, g64) > 1e-4
+    s.close()
+
+
+def test_tensor_core_training_reduces_loss():
+    """Adam on a BF16 handle (tensor-core training): the loss falls on a smooth target and the
+    sampling weights follow the master weights."""
+    from paper_2606_04895_gb300 import Sampler
+    d, D, w = 4, 3, 256
+    e = S.emulator(d, width=w, depth=D, seed=3, out_m=10.0, out_s=5.0)
+    s = Sampler(d, 8, precision="bf16", likelihood="emulator")
+    s.set_emulator(e["params"], D, w, e["in_m"], e["in_s"], e["out_m"], e["out_s"])
+    X = torch.as_tensor(np.random.default_rng(0).uniform(-3, 3, (2048, d)), dtype=torch.float32, device="cuda")
+    y = (X ** 2).sum(dim=1) * 2.0
+    loss = torch.zeros(1, device="cuda")
+    losses = []
+    for it in range(200):
+        s.train_step(X, y, lr=3e-3, loss_out=loss)
+        losses.append(loss.item())
+    assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+    s.close()
+
+
 def test_training_reduces_loss_and_updates_sampling_weights():
     from paper_2606_04895_gb300 import Sampler
     d, D, w = 4, 2, 256

@@ -122,6 +122,26 @@ def test_training_gradient_finite_differences_log_output():
         assert g[i] == pytest.approx((lp - lm) / (2 * h), rel=1e-5, abs=1e-9)
 
 
+def test_training_bf16_mode_is_a_bf16_sized_perturbation():
+    """The BF16 mixed-precision training mode rounds only the operands of the hidden-layer
+    products: its loss equals the exact loss to BF16 accuracy and its gradient differs from the
+    exact gradient by a BF16-sized amount (neither zero nor of the gradient's own size); a
+    one-hidden-layer network (depth 1) has no hidden-layer product, so there it is exact."""
+    d, D, w = 4, 3, 32
+    e = S.emulator(d, width=w, depth=D, seed=2)
+    X = np.random.default_rng(0).uniform(-3, 3, (17, d))
+    y = np.random.default_rng(1).normal(size=17) * 5 + 20
+    l0, g0 = O.train_loss_grad(d, D, w, e["params"], e["in_m"], e["in_s"], 18.0, 4.0, X, y)
+    l1, g1 = O.train_loss_grad(d, D, w, e["params"], e["in_m"], e["in_s"], 18.0, 4.0, X, y, bf16=True)
+    assert abs(l1 - l0) < 1e-2 * abs(l0)
+    rel = np.max(np.abs(g1 - g0)) / np.max(np.abs(g0))
+    assert 1e-5 < rel < 3e-2, rel
+    e1 = S.emulator(d, width=w, depth=1, seed=2)
+    a0, h0 = O.train_loss_grad(d, 1, w, e1["params"], e1["in_m"], e1["in_s"], 18.0, 4.0, X, y)
+    a1, h1 = O.train_loss_grad(d, 1, w, e1["params"], e1["in_m"], e1["in_s"], 18.0, 4.0, X, y, bf16=True)
+    assert a0 == a1 and np.array_equal(h0, h1)
+
+
 def test_adam_first_step_closed_form():
     p = np.array([1.0, -2.0, 0.5])
     g = np.array([0.3, -4.0, 1e-3])
