@@ -146,7 +146,7 @@ def trained_target(device, log=None):
     """The 8-D sterile-shaped target and its config-4 emulator, trained here by the library's
     kernels: 2^20 (theta, chi^2) pairs (50 % box-uniform, 50 % Gaussian at 3 sigma around theta*),
     FP64 analytic labels, 8-512x4-1 tanh, log output, Adam 1e-3 with a cosine to 1e-5, batches of
-    4096, TRAIN_EPOCHS epochs.  Returns (target, emulator dict, training record)."""
+    4096, TRAIN_EPOCHS epochs, hidden-layer products on the tensor cores (BF16 operands).  Returns (target, emulator dict, training record)."""
     import torch
     import synthetic as S
     from paper_2606_04895_gb300 import learn
@@ -161,8 +161,9 @@ def trained_target(device, log=None):
     rec = {"pairs": 1 << 20, "epochs": TRAIN_EPOCHS, "batch": 4096, "seconds_incl_labels": dt,
            "val_mse_std_log_chi2": hist["val_mse"][-1], "train_loss_first_last": [hist["train_loss"][0],
                                                                                   hist["train_loss"][-1]],
-           "samples_per_s": n_tr * TRAIN_EPOCHS / dt, "tflops_fp32": 6.0 * P * n_tr * TRAIN_EPOCHS / dt / 1e12,
-           "kernels": "FP32 CUDA-core training GEMMs (forward with stored activations, backward, Adam)"}
+           "samples_per_s": n_tr * TRAIN_EPOCHS / dt, "tflops": 6.0 * P * n_tr * TRAIN_EPOCHS / dt / 1e12,
+           "kernels": "BF16 tcgen05 hidden-layer GEMMs with TMA operands (forward with stored activations, "
+                      "adjoint, weight gradients); first layer, head and Adam on the CUDA cores, FP32 masters"}
     return tgt, e, rec
 
 
