@@ -314,7 +314,7 @@ def ess_leg(torch, s, kernel, eps, draws=ESS_DRAWS, truth=None, ref=None, **kw):
     emulator (`truth` = the analytic likelihood), the draws are also importance-reweighted by
     exp(logL_analytic - logL_emulator): the weights' efficiency (Kish) and the largest z-score of
     the reweighted means against `ref` = (mean, standard error) of the analytic chains."""
-    x = torch.empty((draws, s.n, s.d), dtype=torch.float32, device="cuda")
+    x = torch.empty((draws, s.n, s.d), dtype=s.dtype, device="cuda")
     c0 = int(s.counters()["evals"].sum())
     t = time_steps(torch, s, kernel, draws, eps, samples=x, **kw)
     ev = int(s.counters()["evals"].sum()) - c0
@@ -371,10 +371,11 @@ def extras(torch, device, seed, K):
     c0 = s.counters()["evals"].sum()
     t = time_steps(torch, s, "nuts", it, eps_n, samples=x)
     ev = s.counters()["evals"].sum() - c0
-    ess = s.ess(x)
+    ess, rm1 = s.ess(x), float(s.r_minus_1(x))
     out["nuts_27d"] = {"chains": 16384, "iterations_per_launch": it, "eps": eps_n, "evals_per_s": ev / t,
-                       "leapfrogs_per_iter": ev / (16384 * it), "min_ess_per_s": float(ess.min()) / t,
-                       "r_minus_1": s.r_minus_1(x), "tflops": 4.0 * P27 * ev / t / 1e12,
+                       "leapfrogs_per_iter": ev / (16384 * it),
+                       "min_ess_per_s": float(ess.min()) / t if rm1 < RHAT_MAX else None,
+                       "r_minus_1": rm1, "tflops": 4.0 * P27 * ev / t / 1e12,
                        "weights": "seeded (the cost does not depend on their values)"}
     s.close()
     s = _emulator_target(27, 16384, "bf16", seed + 12, device, nuis=21)
@@ -382,9 +383,9 @@ def extras(torch, device, seed, K):
     ka = 400
     x = torch.empty((ka, 16384, 27), dtype=torch.float32, device="cuda")
     t = time_steps(torch, s, "aies", ka, 0.0, samples=x)
-    ess = s.ess(x)
+    ess, rm1 = s.ess(x), float(s.r_minus_1(x))
     out["aies_27d"] = {"walkers": 16384, "ensembles": 256, "steps": ka, "evals_per_s": ka * 16384 / t,
-                       "min_ess_per_s": float(ess.min()) / t, "r_minus_1": s.r_minus_1(x),
+                       "min_ess_per_s": float(ess.min()) / t if rm1 < RHAT_MAX else None, "r_minus_1": rm1,
                        "tflops": 2.0 * P27 * ka * 16384 / t / 1e12,
                        "weights": "seeded (the cost does not depend on their values)"}
     s.close()
@@ -416,8 +417,99 @@ def extras(torch, device, seed, K):
     return out
 
 
-def sweep(torch, device, points=None):
-    """Throughput over chains x width x depth x dims x kernel x precision (reduced grid)."""
+def convergence_curves(torch, device, chunk=100, max_chunks=40, seed=0):
+    """Convergence against wall time on the 8-D target (the analogue of the Sec. 4.2 / 4.3
+    comparisons): the BF16 emulator trained here and the plain method (analytic likelihood, FP32),
+    both MALA on N_CHAINS chains from the same start (start_chains) through the same burn-in
+    (burn_in), then chunks of `chunk` iterations.  After each chunk: the synchronised host time
+    spent sampling since the start (burn-in included, metric calls excluded), R - 1 of the second
+    half of the post-burn-in draws, the largest 68 % credible metric against the intervals of a
+    long reference run of the plain method, and the sliced Wasserstein distance of the last 25
+    draws of every chain against 100,000 reference draws (200 directions)."""
+    from paper_2606_04895_gb300 import learn
+    tgt, e, _ = trained_target(device)
+    n, d = N_CHAINS, D
+
+    def run(s, n_chunks, record):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        start_chains(s, tgt, n, seed)
+        eps = burn_in(s, "mala", eps0=0.3)
+        torch.cuda.synchronize()
+        spent = time.perf_counter() - t0
+        X = torch.empty((chunk * n_chunks, n, d), dtype=s.dtype, device="cuda")
+        curve = []
+        for c in range(n_chunks):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            s.step("mala", chunk, eps=eps, samples=X[c * chunk:(c + 1) * chunk], stats=False)
+            torch.cuda.synchronize()
+            spent += time.perf_counter() - t1
+            if record is not None:
+                curve.append(dict(seconds=spent, **record(s, X, (c + 1) * chunk)))
+        return eps, spent, X, curve
+
+    # reference: a long run of the plain method
+    a = learn.analytic_sampler(tgt, n_chains=n, precision="fp32", seed=seed + 1)
+    _, _, Xr, _ = run(a, 4 * max_chunks, None)
+    a.close()
+    flat = Xr[Xr.shape[0] // 4:].reshape(-1, d)
+    sub = flat[:: max(1, flat.shape[0] // 2_000_000)]
+    lo = torch.quantile(sub.double(), 0.16, dim=0).cpu().numpy()
+    hi = torch.quantile(sub.double(), 0.84, dim=0).cpu().numpy()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    ref = flat[torch.randint(0, flat.shape[0], (100_000,), generator=g, device="cuda")].contiguous()
+    del Xr, flat, sub
+
+    def record(s, X, m):
+        xs = X[m // 2:m]
+        return {"iterations": m, "r_minus_1": float(s.r_minus_1(xs)),
+                "credible_metric_68": float(s.credible_metric(xs, 0.68, lo, hi).max()),
+                "sliced_wasserstein": float(s.sliced_wasserstein(X[m - 25:m].contiguous(), ref.to(X.dtype),
+                                                                 n_proj=200, seed=seed))}
+
+    out = {"chains": n, "chunk": chunk, "reference": "plain method (analytic FP32 MALA), "
+           f"{4 * max_chunks * chunk} iterations after the same burn-in; 68 % intervals of its last 3/4"}
+    legs = {"bf16_emulator_mala": lambda: learn.emulator_sampler(e, n, precision="bf16", seed=seed + 2),
+            "analytic_fp32_mala": lambda: learn.analytic_sampler(tgt, n_chains=n, precision="fp32", seed=seed + 3)}
+    for name, make in legs.items():
+        s = make()
+        eps, spent, X, curve = run(s, max_chunks, record)
+        below = [c["seconds"] for c in curve if c["r_minus_1"] < RHAT_MAX]
+        out[name] = {"eps": eps, "curve": curve, "seconds_to_r_minus_1_below": below[0] if below else None,
+                     "seconds_total": spent}
+        del X
+        s.close()
+    return out
+
+
+SWEEP_DRAWS, SWEEP_ESS_MAX_S = 400, 40.0
+
+
+def sweep(torch, device, points=None, ess=True):
+    """Throughput over chains x width x depth x dims x kernel x precision (reduced grid), timed on
+    seeded weights (the cost does not depend on their values).  With `ess`, also min-ESS/s per
+    8-D point on an emulator of that width and depth trained here on the 8-D target (40 epochs
+    at 512 x 4, 15 otherwise; BF16 tensor-core training up to width 512, FP32 above): the
+    chains start as in the headline (start_chains), run a shortened burn-in of the paper's
+    protocol (two iterations of step-size and covariance adaptation), then SWEEP_DRAWS draws per
+    chain (MH: 5x, acceptance target 0.3; HMC: 1.25x) go through ess_leg (an ESS only where
+    R - 1 < RHAT_MAX).  Points whose burn-in would take longer than SWEEP_ESS_MAX_S at their
+    measured throughput are skipped."""
+    import synthetic as S
+    from paper_2606_04895_gb300 import driver, learn
+    trained = {}
+
+    def trained_emulator(width, depth):
+        if (width, depth) not in trained:
+            tgt = S.target(D, seed=0)
+            e, _, _ = learn.train_emulator_log(tgt, width=width, depth=depth,
+                                               epochs=TRAIN_EPOCHS if (width, depth) == (WIDTH, DEPTH) else 15,
+                                               device=device, precision="bf16" if width <= 512 else "fp32")
+            trained[(width, depth)] = (tgt, e)
+        return trained[(width, depth)]
+
     pts = []
     for prec in ("bf16", "fp32", "fp64"):
         for n in (1024, 4096, 16384, 65536, 262144):
@@ -464,8 +556,31 @@ def sweep(torch, device, points=None):
         fl = (2 if fwd_only else 4) * (n_params(p["d"], p["depth"], p["width"]) - 1) * evals / t
         row = dict(p, evals_per_s=evals / t, tflops=fl / 1e12,
                    frac_bf16_peak=fl / 1e12 / burst if p["prec"] == "bf16" else None, steps=steps)
-        print(json.dumps(row), flush=True)
         s.close()
+        if ess:
+            adapt, cov, n_it = 200, 500, 2
+            burn_steps = n_it * (adapt + cov) + adapt
+            # MH mixes slowest per draw (and costs a forward pass only): more draws, and the
+            # usual random-walk acceptance target instead of the gradient samplers' 0.65
+            draws = {"mh": 5 * SWEEP_DRAWS, "hmc": 5 * SWEEP_DRAWS // 4}.get(p["kernel"], SWEEP_DRAWS)
+            acc_target = 0.3 if p["kernel"] == "mh" else 0.65
+            step_s = t / steps
+            if p["d"] != D or "nuis" in p or p["kernel"] not in ("mala", "mh", "hmc"):
+                row["ess_note"] = "no trained emulator of this target (throughput point only)"
+            elif step_s * (burn_steps + draws) > SWEEP_ESS_MAX_S:
+                row["ess_note"] = f"skipped: burn-in and draws would take over {SWEEP_ESS_MAX_S:.0f} s"
+            else:
+                tgt, e = trained_emulator(p["width"], p["depth"])
+                q = learn.emulator_sampler(e, p["n"], precision=p["prec"], seed=7, device=device)
+                start_chains(q, tgt, p["n"], 5)
+                ek, _ = driver.burn_in(q, p["kernel"], eps0=eps, n_iter=n_it, adapt_steps=adapt, cov_steps=cov,
+                                       target=acc_target, **kw)
+                rec, x = ess_leg(torch, q, p["kernel"], ek, draws=draws, **kw)
+                del x
+                q.close()
+                row.update(ess_target="8-D target, emulator trained here", ess_eps=ek, ess_draws_per_chain=draws,
+                           r_minus_1=rec["r_minus_1"], min_ess=rec["min_ess"], min_ess_per_s=rec["min_ess_per_s"])
+        print(json.dumps(row), flush=True)
 
 
 def main():
@@ -478,6 +593,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="print one JSON line per point of the throughput grid")
     ap.add_argument("--points", default=None, help="with --sweep: key=value[,key=value] filter, e.g. d=27")
+    ap.add_argument("--sweep-no-ess", action="store_true", help="with --sweep: throughput only, no min-ESS/s")
+    ap.add_argument("--convergence", action="store_true",
+                    help="print the convergence-against-wall-time curves (BF16 emulator vs the plain method)")
     ap.add_argument("--quick", action="store_true",
                     help="seeded (untrained) emulator, no burn-in and no side legs: three launches in total, "
                          "for profiler captures")
@@ -493,7 +611,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     if args.sweep:
-        sweep(torch, local, args.points)
+        sweep(torch, local, args.points, ess=not args.sweep_no_ess)
+        return 0
+    if args.convergence:
+        print(json.dumps({"convergence_8d": convergence_curves(torch, local)}), flush=True)
         return 0
     dist = None
     global DIST
