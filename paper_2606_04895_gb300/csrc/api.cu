@@ -1167,7 +1167,10 @@ static bst_status train_setup(bst_handle h, int m) {
     BST_TRY(dalloc_t(h, &h->tw.dout, mm));
     BST_TRY(dalloc_t(h, &h->tw.loss, 4));
     const size_t fmax = w > static_cast<size_t>(h->d) ? w : static_cast<size_t>(h->d);
-    BST_TRY(dalloc_t(h, &h->tw.ws, static_cast<size_t>(kTrainSplits) * w * fmax));
+    // split weight-gradient partials, or the slices of the batch-sliced column sums
+    const size_t ws_gemm = static_cast<size_t>(kTrainSplits) * w * fmax;
+    const size_t ws_sum = static_cast<size_t>(kWsumSlices) * w * static_cast<size_t>(h->d > 1 ? h->d : 1);
+    BST_TRY(dalloc_t(h, &h->tw.ws, ws_gemm > ws_sum ? ws_gemm : ws_sum));
     h->tw.Hb = h->tw.HbT = h->tw.Db = h->tw.DbT = h->tw.Wb = h->tw.WbT = nullptr;
     h->tw.wsg = nullptr;
     if (tc_engine(h) && D >= 2) {

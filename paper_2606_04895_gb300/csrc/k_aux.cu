@@ -792,20 +792,55 @@ __global__ void train_head_kernel(const float *HD, const float *wo, const float 
 // column sums: out[j] = sum_i X[i][j] (bias gradients).  A block of 256 threads takes 32
 // columns; its 8 row groups sum interleaved rows (i = g, g + 8, ...) and the 8 partial sums
 // are added in group order, so the result does not depend on scheduling.
-__global__ void colsum_kernel(const float *X, int rows, int cols, float *out) {
-  __shared__ float part[8][32];
+// Column sums over the batch, optionally weighted: out[j du + k] = sum_i X[i][j] U[i][k] (U null: du = 1,
+// plain sums) -- the bias and output-head gradients and the layer-1 weight gradient (fan-in d).  The
+// batch is split in `slices` runs of consecutive rows; one block per 32 columns and slice sums its
+// rows in a fixed order (8 row groups, combined in order), and sum_slices_kernel adds the slices in
+// order: deterministic, with enough blocks to fill the GPU (a product with so few output columns
+// leaves a tiled GEMM with a handful of blocks).
+__global__ void __launch_bounds__(256) wsum_kernel(const float *X, int rows, int cols, const float *U, int du,
+                                                   int slices, float *ws) {
+  __shared__ float part[8][32][kWsumMaxU + 1];
   const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int j = blockIdx.x * 32 + c;
-  float s = 0.f;
-  if (j < cols)
-    for (int i = g; i < rows; i += 8) s += X[static_cast<size_t>(i) * cols + j];
-  part[g][c] = s;
-  __syncthreads();
-  if (g == 0 && j < cols) {
-    float t = part[0][c];
-    for (int q = 1; q < 8; ++q) t += part[q][c];
-    out[j] = t;
+  const int j = blockIdx.x * 32 + c, sl = blockIdx.y;
+  const int r0 = static_cast<int>(static_cast<long long>(rows) * sl / slices);
+  const int r1 = static_cast<int>(static_cast<long long>(rows) * (sl + 1) / slices);
+  float acc[kWsumMaxU];
+#pragma unroll
+  for (int k = 0; k < kWsumMaxU; ++k) acc[k] = 0.f;
+  if (j < cols) {
+    for (int i = r0 + g; i < r1; i += 8) {
+      const float x = X[static_cast<size_t>(i) * cols + j];
+      if (U == nullptr) {
+        acc[0] += x;
+      } else {
+        const float *u = U + static_cast<size_t>(i) * du;
+#pragma unroll
+        for (int k = 0; k < kWsumMaxU; ++k)
+          if (k < du) acc[k] = fmaf(x, u[k], acc[k]);
+      }
+    }
   }
+#pragma unroll
+  for (int k = 0; k < kWsumMaxU; ++k)
+    if (k < du) part[g][c][k] = acc[k];
+  __syncthreads();
+  if (j < cols)
+    for (int k = g; k < du; k += 8) {
+      float t = part[0][c][k];
+      for (int q = 1; q < 8; ++q) t += part[q][c][k];
+      ws[(static_cast<size_t>(sl) * cols + j) * du + k] = t;
+    }
+}
+
+cudaError_t launch_wsum(const float *X, int rows, int cols, const float *U, int du, float *ws, float *out,
+                        cudaStream_t s) {
+  if (du < 1 || du > kWsumMaxU || (U == nullptr && du != 1) || rows < 1 || cols < 1) return cudaErrorInvalidValue;
+  const int slices = rows / 64 < 1 ? 1 : (rows / 64 < kWsumSlices ? rows / 64 : kWsumSlices);
+  wsum_kernel<<<dim3((cols + 31) / 32, slices), 256, 0, s>>>(X, rows, cols, U, du, slices, ws);
+  const size_t n = static_cast<size_t>(cols) * du;
+  sum_slices_kernel<<<blocks_for(n, 256), 256, 0, s>>>(ws, slices, n, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in_s, float out_m, float out_s,
@@ -826,19 +861,27 @@ cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in
   train_head_kernel<<<blocks_for(static_cast<size_t>(m) * 32, 256), 256, 0, s>>>(HD, P + owo, P + owo + w, chi2, out_m,
                                                                                out_s, out_log, out_floor, m, w,
                                                                                tw.dout, tw.Dl, tw.loss);
-  // g_wo[j] = sum_i dout_i H_D[i][j]  (1 x w = dout^T H_D) ; g_bo = sum_i dout_i
-  gemm_f32(1, w, m, tw.dout, 0, 1, HD, w, 1, G + owo, w, EPI_STORE, nullptr, nullptr, 0, s);
-  colsum_kernel<<<1, 256, 0, s>>>(tw.dout, m, 1, G + owo + w);
+  // g_wo[j] = sum_i dout_i H_D[i][j] ; g_bo = sum_i dout_i
+  cudaError_t e = launch_wsum(HD, m, w, tw.dout, 1, tw.ws, G + owo, s);
+  if (e != cudaSuccess) return e;
+  e = launch_wsum(tw.dout, m, 1, nullptr, 1, tw.ws, G + owo + w, s);
+  if (e != cudaSuccess) return e;
   float *dl = tw.Dl, *dn = tw.Dn;
   for (int l = D; l >= 1; --l) {
     const int fan = (l == 1) ? d : w;
     const float *Hprev = (l == 1) ? tw.U : tw.H + static_cast<size_t>(l - 2) * m * w;
     // g_W_l[k][j] = sum_i delta_l[i][k] Hprev[i][j]  (the batch split in kTrainSplits slices: a
-    // w x fan product has too few output tiles to fill the GPU)
-    gemm_f32(w, fan, m, dl, 1, w, Hprev, fan, 1, tw.ws, fan, EPI_STORE, nullptr, nullptr, 0, s, kTrainSplits);
-    sum_slices_kernel<<<blocks_for(static_cast<size_t>(w) * fan, 256), 256, 0, s>>>(
-        tw.ws, kTrainSplits, static_cast<size_t>(w) * fan, G + off_W(l, d, w));
-    colsum_kernel<<<blocks_for(w, 32), 256, 0, s>>>(dl, m, w, G + off_b(l, d, w));
+    // w x fan product has too few output tiles to fill the GPU; fan-in d: weighted column sums)
+    if (l == 1) {
+      e = launch_wsum(dl, m, w, tw.U, d, tw.ws, G + off_W(1, d, w), s);
+      if (e != cudaSuccess) return e;
+    } else {
+      gemm_f32(w, fan, m, dl, 1, w, Hprev, fan, 1, tw.ws, fan, EPI_STORE, nullptr, nullptr, 0, s, kTrainSplits);
+      sum_slices_kernel<<<blocks_for(static_cast<size_t>(w) * fan, 256), 256, 0, s>>>(
+          tw.ws, kTrainSplits, static_cast<size_t>(w) * fan, G + off_W(l, d, w));
+    }
+    e = launch_wsum(dl, m, w, nullptr, 1, tw.ws, G + off_b(l, d, w), s);
+    if (e != cudaSuccess) return e;
     if (l > 1) {
       // delta_{l-1} = (delta_l W_l) (1 - H_{l-1}^2)
       gemm_f32(m, w, w, dl, w, 1, P + off_W(l, d, w), w, 1, dn, w, EPI_DTANH, nullptr, Hprev, w, s);
@@ -894,8 +937,10 @@ cudaError_t launch_train_grad_tc(const float *P, const float *in_m, const float 
   train_head_kernel<<<blocks_for(static_cast<size_t>(m) * 32, 256), 256, 0, s>>>(HD, P + owo, P + owo + w, chi2, out_m,
                                                                                out_s, out_log, out_floor, m, w,
                                                                                tw.dout, tw.Dl, tw.loss);
-  gemm_f32(1, w, m, tw.dout, 0, 1, HD, w, 1, G + owo, w, EPI_STORE, nullptr, nullptr, 0, s);
-  colsum_kernel<<<1, 256, 0, s>>>(tw.dout, m, 1, G + owo + w);
+  e = launch_wsum(HD, m, w, tw.dout, 1, tw.ws, G + owo, s);
+  if (e != cudaSuccess) return e;
+  e = launch_wsum(tw.dout, m, 1, nullptr, 1, tw.ws, G + owo + w, s);
+  if (e != cudaSuccess) return e;
   int cur = 0;
   e = launch_cast_transpose_bf16(tw.Dl, m, w, tw.Db, tw.DbT, s);
   if (e != cudaSuccess) return e;
@@ -912,7 +957,8 @@ cudaError_t launch_train_grad_tc(const float *P, const float *in_m, const float 
     e = launch_tc_gemm(tw.DbT + cur * mw, tw.HbT + (l - 2) * mw, kTcTrainSplits, gw, s);
     if (e != cudaSuccess) return e;
     sum_slices_kernel<<<blocks_for(ww, 256), 256, 0, s>>>(tw.wsg, kTcTrainSplits, ww, G + off_W(l, d, w));
-    colsum_kernel<<<blocks_for(w, 32), 256, 0, s>>>(dl, m, w, G + off_b(l, d, w));
+    e = launch_wsum(dl, m, w, nullptr, 1, tw.ws, G + off_b(l, d, w), s);
+    if (e != cudaSuccess) return e;
     // delta_{l-1} = (delta_l W_l) (1 - H_{l-1}^2), FP32 and its BF16 copies
     TcGemmArgs gd = {};
     gd.M = m;
@@ -932,11 +978,10 @@ cudaError_t launch_train_grad_tc(const float *P, const float *in_m, const float 
     cur = 1 - cur;
   }
   // layer 1 (fan-in d) on the CUDA cores
-  gemm_f32(w, d, m, dl, 1, w, tw.U, d, 1, tw.ws, d, EPI_STORE, nullptr, nullptr, 0, s, kTrainSplits);
-  sum_slices_kernel<<<blocks_for(static_cast<size_t>(w) * d, 256), 256, 0, s>>>(tw.ws, kTrainSplits,
-                                                                              static_cast<size_t>(w) * d,
-                                                                              G + off_W(1, d, w));
-  colsum_kernel<<<blocks_for(w, 32), 256, 0, s>>>(dl, m, w, G + off_b(1, d, w));
+  e = launch_wsum(dl, m, w, tw.U, d, tw.ws, G + off_W(1, d, w), s);
+  if (e != cudaSuccess) return e;
+  e = launch_wsum(dl, m, w, nullptr, 1, tw.ws, G + off_b(1, d, w), s);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

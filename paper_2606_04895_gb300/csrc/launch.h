@@ -104,7 +104,8 @@ struct TrainWork {
   float *Dn;    // [m][w] adjoint buffer
   float *dout;  // [m]
   float *loss;  // [1]
-  float *ws;    // [kTrainSplits][w][w] partial weight gradients (split over the batch)
+  float *ws;    // [kTrainSplits][w][w] partial weight gradients (split over the batch), or the
+                //   [kWsumSlices][w][d] slices of the batch-sliced column sums
   // tensor-core training (BF16 operands): null when the handle trains on the CUDA cores
   __nv_bfloat16 *Hb, *HbT;   // [D-1][m][w] / [D-1][w][m] hidden activations h_1..h_{D-1}
   __nv_bfloat16 *Db, *DbT;   // [2][m][w] / [2][w][m] adjoints (double-buffered)
@@ -137,6 +138,10 @@ cudaError_t launch_train_grad_tc(const float *P, const float *in_m, const float 
                                  int out_log, float out_floor, int d, int D, int w, int m, const float *X,
                                  const float *chi2, float *G, TrainWork &tw, int *status, cudaStream_t s);
 constexpr int kTrainSplits = 4;
+// Batch-sliced column sums of the training gradient (bias and head gradients, the fan-in-d layer):
+// at most kWsumSlices slices of the batch, at most kWsumMaxU weights per row.
+constexpr int kWsumSlices = 32;
+constexpr int kWsumMaxU = 32;
 cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in_s, float out_m, float out_s,
                               int out_log, float out_floor, int d, int D, int w, int m, const float *X,
                               const float *chi2, float *G, TrainWork &tw, cudaStream_t s);
