@@ -33,6 +33,10 @@ D, N_CHAINS, WIDTH, DEPTH = 8, 4096, 512, 4
 TRAIN_EPOCHS = 40
 ESS_DRAWS = 2000     # post-burn-in draws per chain of every min-ESS/s leg (independent of --steps)
 RHAT_MAX = 0.01      # an ESS is reported only for draws whose R - 1 (Sec. 4.1) is below this
+# CUDA-core peaks of the FP32 and FP64 paths, derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x
+# 2.07 GHz (the maximum SM clock); FP64 at the part's nominal 1.25 TFLOP/s
+FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
 METRIC = "emulator logL+grad evals/sec (BF16 tcgen05 MALA, 8-D, 4096 chains, 8-512x4-1)"
 UNIT = "evals/s"
 
@@ -556,6 +560,8 @@ def sweep(torch, device, points=None, ess=True):
         fl = (2 if fwd_only else 4) * (n_params(p["d"], p["depth"], p["width"]) - 1) * evals / t
         row = dict(p, evals_per_s=evals / t, tflops=fl / 1e12,
                    frac_bf16_peak=fl / 1e12 / burst if p["prec"] == "bf16" else None, steps=steps)
+        if p["prec"] in ("fp32", "fp64"):
+            row["frac_cuda_core_peak"] = fl / 1e12 / (FP32_FMA_PEAK_TFLOPS if p["prec"] == "fp32" else FP64_PEAK_TFLOPS)
         s.close()
         if ess:
             adapt, cov, n_it = 200, 500, 2
@@ -752,6 +758,10 @@ def ess_legs(torch, device, s, e, tgt, eps, seed):
         legs[f"{prec}_mala"], xp = ess_leg(torch, p, "mala", ep, truth=truth, ref=ref)
         if prec == "fp16":
             legs["fp16_mala"]["chi2_error_vs_fp64"] = chi2_error_along(torch, p, e, xp)
+        else:
+            fl = 4.0 * (n_params(D, DEPTH, WIDTH) - 1) * legs["fp32_mala"]["evals_per_s"] / 1e12
+            legs["fp32_mala"].update(tflops_fp32=fl, frac_fp32_fma_peak=fl / FP32_FMA_PEAK_TFLOPS,
+                                     fp32_peak_note="derived: 152 SMs x 128 FMA lanes x 2 flop x 2.07 GHz")
         p.close()
     truth.close()
     out["ess_legs"] = legs

@@ -6,7 +6,7 @@ operand-rounding mode of the same type (same rounding points; FP32 vs FP64
 accumulation and the tanh approximation can flip an operand rounding now and
 then): BF16 2e-3 / 2e-2, FP16 3e-4 / 3e-3.  The precision claim against the FP64
 evaluation of the same network (test_chi2_error_against_fp64): FP16 operands stay
-within 0.05 in chi^2, the benchmark spec's bound; BF16 operands (8 significant bits)
+within 0.05 in chi^2, the accuracy target of the path; BF16 operands (8 significant bits)
 do not at the tested output scale and are held to their own arithmetic bound."""
 import numpy as np
 import pytest
