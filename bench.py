@@ -51,13 +51,14 @@ def peaks():
 
 
 # DRAM traffic of the timed step-kernel launch (4096 chains, 8-512x4-1, MALA): one-pass ncu
-# captures (dram__bytes_read.sum + dram__bytes_write.sum) of launches of two lengths, fitted
-# as a fixed part plus a part per MALA iteration (the x-space sample write is 131 KB per
-# iteration).  Valid for the kernel code they were taken on (sources without comments); None
-# once that changes.
+# captures (dram__bytes_read.sum + dram__bytes_write.sum) of launches of 20, 200 and 5000
+# iterations, interpolated piecewise linearly in the iteration count.  Up to a few hundred
+# iterations the sample record (131 KB per iteration) is still in L2 when the launch ends and
+# is written back afterwards; at 5000 iterations it streams to DRAM.  Valid for the kernel code
+# the captures were taken on (sources without comments); None once that changes.
 TRAFFIC_SOURCES = ['paper_2606_04895_gb300/csrc/common.cuh', 'paper_2606_04895_gb300/csrc/engine_tc.cuh', 'paper_2606_04895_gb300/csrc/engine_tc2.cuh', 'paper_2606_04895_gb300/csrc/sampler.cuh', 'paper_2606_04895_gb300/csrc/tc2_launch.cuh', 'paper_2606_04895_gb300/csrc/k_tc2_w512_c4x.cu']
-TRAFFIC_SOURCES_SHA256 = "940d555273b79f5d"
-TRAFFIC_K, TRAFFIC_BYTES = (20, 5000), (4.05e6 + 0.66586e6, 28.99e6 + 615.07e6)
+TRAFFIC_SOURCES_SHA256 = "4056ae9619c51804"
+TRAFFIC_POINTS = ((20, 4.064512e6 + 0.681728e6), (200, 4.321024e6 + 1.217024e6), (5000, 30.971392e6 + 615.299584e6))
 
 
 def kernel_sources_digest():
@@ -76,7 +77,11 @@ def step_kernel_traffic(k):
     """DRAM bytes of a k-iteration launch of the step kernel, or None (sources changed)."""
     if kernel_sources_digest() != TRAFFIC_SOURCES_SHA256:
         return None
-    (k0, k1), (b0, b1) = TRAFFIC_K, TRAFFIC_BYTES
+    pts = TRAFFIC_POINTS
+    seg = 0
+    while seg + 2 < len(pts) and k > pts[seg + 1][0]:
+        seg += 1
+    (k0, b0), (k1, b1) = pts[seg], pts[seg + 1]
     return b0 + (b1 - b0) * (k - k0) / (k1 - k0)
 
 
