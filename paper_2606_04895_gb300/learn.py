@@ -127,21 +127,24 @@ def fold_input_map(e, c, T):
 
 
 def train_emulator_log(tgt, *, n_train=1 << 20, width=512, depth=4, epochs=40, batch=4096, lr=1e-3, lr_min=1e-5,
-                       seed=4, log=None, device=None, precision="bf16"):
+                       seed=4, log=None, device=None, precision="bf16", gauss_frac=0.5, gauss_scale=3.0):
     """Config-4 recipe with the log output and whitened inputs: 50 % box-uniform / 50 %
-    Gaussian-at-3-sigma inputs (2^20), FP64 analytic chi^2 labels, MSE on the standardised
-    log(chi2 - floor), Adam (lr 1e-3, cosine to lr_min) on FP32 masters in batches of 4096, all in
-    the library's training kernels: precision "bf16" trains the hidden layers on the tensor cores
-    (BF16 operands, FP32 accumulation), "fp32" on the CUDA cores.  The input is
+    Gaussian-at-3-sigma inputs (2^20; `gauss_frac` and `gauss_scale` set the Gaussian share and
+    its widths, and the input whitening maps the first width to N(0, I)), FP64 analytic
+    chi^2 labels, MSE on the standardised log(chi2 - floor), Adam (lr 1e-3, cosine to lr_min) on
+    FP32 masters in batches of 4096, all in the library's training kernels: precision "bf16"
+    trains the hidden layers on the tensor cores (BF16 operands, FP32 accumulation), "fp32" on
+    the CUDA cores.  The input is
     u = T (theta - theta*) (input_whitening), folded into layer 1 afterwards.  Returns (emulator
     dict with the trained weights, history, the training inputs and labels)."""
     import synthetic as S
     d = tgt["d"]
-    theta = S.training_inputs(tgt, n_train, seed=seed)
+    theta = S.training_inputs(tgt, n_train, seed=seed, gauss_frac=gauss_frac, gauss_scale=gauss_scale)
     plain = analytic_sampler(tgt)
     chi2 = label(plain, theta)
     plain.close()
-    c, T = input_whitening(tgt)
+    s0 = gauss_scale if np.isscalar(gauss_scale) else gauss_scale[0]
+    c, T = input_whitening(tgt, scale2=s0 ** 2)
     u = (theta - c) @ T.T
     floor, out_m, out_s = log_output_standardisation(chi2)
     e0 = S.emulator(d, width=width, depth=depth, seed=seed + 1, in_m=np.zeros(d), in_s=np.ones(d), out_m=out_m,

@@ -162,16 +162,22 @@ def chains_init(n, d, *, seed=3, scale=1.0):
     return scale * np.random.default_rng(seed).standard_normal((n, d))
 
 
-def training_inputs(tgt, n, *, seed=4):
-    """theta for emulator training: 50% U(box), 50% N(theta*, 9 Sigma_Laplace)."""
+def training_inputs(tgt, n, *, seed=4, gauss_frac=0.5, gauss_scale=3.0):
+    """theta for emulator training: a fraction 1 - gauss_frac U(box), gauss_frac Gaussian around
+    theta* with covariance s^2 Sigma_Laplace, the Gaussian share split evenly over the widths s in
+    `gauss_scale` (a number or a tuple); the config-4 recipe is half and half at 3 sigma."""
     rng = np.random.default_rng(seed)
     d = tgt["d"]
-    n_u = n // 2
+    scales = (gauss_scale,) if np.isscalar(gauss_scale) else tuple(gauss_scale)
+    n_u = n - int(round(n * gauss_frac))
     lo = np.maximum(tgt["lower"], -BOX)
     hi = np.minimum(tgt["upper"], BOX)
     xu = lo + (hi - lo) * rng.random((n_u, d))
-    Lc = np.linalg.cholesky(9.0 * tgt["laplace_cov"])
-    xg = tgt["theta_star"] + rng.standard_normal((n - n_u, d)) @ Lc.T
-    xg = np.clip(xg, lo, hi)
-    x = np.concatenate([xu, xg])
+    parts = [xu]
+    n_g = n - n_u
+    for k, sc in enumerate(scales):
+        m = n_g // len(scales) + (1 if k < n_g % len(scales) else 0)
+        Lc = np.linalg.cholesky(sc ** 2 * tgt["laplace_cov"])
+        parts.append(np.clip(tgt["theta_star"] + rng.standard_normal((m, d)) @ Lc.T, lo, hi))
+    x = np.concatenate(parts)
     return x[rng.permutation(n)]
