@@ -477,6 +477,17 @@ bst_status refresh(bst_ctx *h, cudaStream_t s) {
 
 bst_status set_target(bst_ctx *h, const double *mu, const double *L) {
   const int d = h->d;
+  // an unchanged whitening (bitwise) keeps the folded layer-1 weights: the chains are refreshed,
+  // the weights are repacked only if something else made them dirty
+  bool same = static_cast<int>(h->mu.size()) == d && static_cast<int>(h->L.size()) == d * d;
+  for (int i = 0; same && i < d; ++i) {
+    same = std::memcmp(&h->mu[i], &mu[i], sizeof(double)) == 0;
+    for (int j = 0; same && j <= i; ++j) same = std::memcmp(&h->L[i * d + j], &L[i * d + j], sizeof(double)) == 0;
+  }
+  if (same) {
+    h->state_stale = true;
+    return BST_OK;
+  }
   h->mu.assign(mu, mu + d);
   h->L.assign(d * d, 0.0);
   double ld = 0.0;
