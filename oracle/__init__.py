@@ -10,9 +10,9 @@ of Emulators", arXiv 2606.04895) and the algorithms it cites; every function
 there names its source.  This module compiles it with gcc and wraps it with
 ctypes, converting numpy arrays to plain pointers.
 
-Parity pins: see ``tests/test_oracle_*.py``.  The Philox generator is pinned
-only statistically and by structure (parity with an external known-answer
-table is unpinned: no such table is available here).
+Parity pins: see ``tests/test_oracle_*.py``.  The Philox generator is pinned by
+the published known-answer vectors of Philox4x32-10 (``tests/golden/``) besides
+its statistical and structural tests.
 """
 from __future__ import annotations
 
