@@ -255,13 +255,19 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
   // each epilogue warp sends its own rows x columns to the peers as soon as they are written
   // (whole 64-column K blocks: 32 rows of a K block are 4 KB contiguous in the swizzled layout)
   constexpr bool kWarpSend = CS > 1 && CW % 64 == 0;
+  // One CTA per tile with the layer in two MMA halves (N = TR = NS / 2): every epilogue warp
+  // finishes its chunks of the first half of the columns first and signals a barrier of its
+  // own, so the next layer's MMAs on K blocks 0 .. KBW / 2 - 1 run while the epilogue works on
+  // the second half (which the MMAs of the first N half do not overwrite in tensor memory).
+  constexpr bool kHalfFirst = (CS == 1) && (NSUB == 2);
+  static_assert(!kHalfFirst || (CPW % 2 == 0 && (CPW / 2) * 32 * kTc2EQ == TR), "half-first chunk order");
 
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *act = base;
   uint8_t *stages = act + KBW * 16384;
   const int S = E.n_stages;
   uint64_t *bars = reinterpret_cast<uint64_t *>(stages + S * STAGE);
-  // bars: full[S] empty[S] go act_full acc fin peer_free part peer_free_last (cmd tmem) own
+  // bars: full[S] empty[S] go act_full acc fin peer_free part peer_free_last (cmd tmem) own own_h0
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S);
   const uint32_t go_bar = smem_u32(bars + 2 * S), actf_bar = smem_u32(bars + 2 * S + 1);
   const uint32_t acc_bar = smem_u32(bars + 2 * S + 2), fin_bar = smem_u32(bars + 2 * S + 3);
@@ -271,8 +277,10 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 8);
   // own slice of the next layer input written (the peers' slices complete act_full)
   const uint32_t own_bar = smem_u32(bars + 2 * S + 9);
+  // first half of the columns written (kHalfFirst); slot 2 S + 11 pads `partial` to 16 bytes
+  const uint32_t own_h0_bar = smem_u32(bars + 2 * S + 10);
   // everything from `partial` on is 16-byte aligned for vector access
-  float *partial = reinterpret_cast<float *>(bars + 2 * S + 10);  // [CS][128] (rank 0 gathers)
+  float *partial = reinterpret_cast<float *>(bars + 2 * S + 12);  // [CS][128] (rank 0 gathers)
   float *red = partial + CS * 128;                                // [EQ-1][128] column-group combine
   int *mask = reinterpret_cast<int *>(red + (kTc2EQ - 1) * 128);  // [128]
   float *sbias = reinterpret_cast<float *>(mask + 128);           // [D + 1][NS]: b_1..b_D, w_o slices
@@ -320,6 +328,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
     mbar_init(part_bar, CS);
     mbar_init(free2_bar, CS > 1 ? CS - 1 : 1);
     mbar_init(own_bar, kTc2EpiThreads / 32);  // one arrive per epilogue warp
+    mbar_init(own_h0_bar, kTc2EpiThreads / 32);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 1) {
@@ -393,7 +402,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
     if (lane == 0) {
       uint32_t upar = 0;  // bit s: parity of the next wait on stage s
       int s = 0;
-      uint32_t go_par = 0, act_par = 0, own_par = 0;
+      uint32_t go_par = 0, act_par = 0, own_par = 0, own_h0_par = 0;
       bool ok = true;
       const uint32_t idn = idesc_bf16(128, TR, E.f16 != 0), idg = idesc_bf16(128, 2 * dp, E.f16 != 0);
       // descriptors of K block 0 of the activation and of stage 0; K block kb / stage s / the
@@ -408,11 +417,16 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
         if (c == 0) break;
         const int phases = tc_num_phases(D, c == 2);
         for (int p = 0; p < phases && ok; ++p) {
-          if (!mbar_wait(own_bar, own_par, a.status)) {
+          // the whole layer input (layer 1), or its first half of the columns (kHalfFirst)
+          const bool split = kHalfFirst && p > 0;
+          if (!mbar_wait(split ? own_h0_bar : own_bar, split ? own_h0_par : own_par, a.status)) {
             ok = false;
             break;
           }
-          own_par ^= 1;
+          if (split)
+            own_h0_par ^= 1;
+          else
+            own_par ^= 1;
           tc_fence_after();
           const bool last = (p == 2 * D - 1);
           const int nsub = last ? 1 : NSUB;
@@ -422,6 +436,15 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
             int kb = (p == 0) ? 0 : rot;
             const uint32_t dcol = tmem + sb * TR;
             for (int j = 0; j < nkb; ++j) {
+              if (split && sb == 0 && j == KBW / 2) {
+                // the second half of the layer input
+                if (!mbar_wait(own_bar, own_par, a.status)) {
+                  ok = false;
+                  break;
+                }
+                own_par ^= 1;
+                tc_fence_after();
+              }
               if (CS > 1 && p > 0 && j == NOWN) {
                 // the peers' slices of this layer input have landed
                 if (!mbar_wait_cluster(actf_bar, act_par, a.status)) {
@@ -473,6 +496,12 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
     const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
     const uint32_t act_addr = smem_u32(act);
     const int col0 = static_cast<int>(rank) * NS + ch * CW;  // first global column of this warp
+    // column of chunk cc of this warp within the rank's slice: CW consecutive columns, or
+    // (kHalfFirst) its share of the first N half, then its share of the second
+    auto chunk_col = [&](int cc) -> int {
+      if (kHalfFirst) return (cc / (CPW / 2)) * TR + ch * (TR / kTc2EQ) + (cc % (CPW / 2)) * 32;
+      return ch * CW + cc * 32;
+    };
     Chain<float> chn(a);
     const bool loglike = a.mode == kModeLoglike;
     // this CTA's global image of its slice (l2x)
@@ -608,7 +637,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
                 : nullptr;
         uint4 hcur[4];
         {
-          const uint4 *hp = hprev ? reinterpret_cast<const uint4 *>(hprev + col0) : nullptr;
+          const uint4 *hp =
+              hprev ? reinterpret_cast<const uint4 *>(hprev + static_cast<int>(rank) * NS + chunk_col(0)) : nullptr;
 #pragma unroll
           for (int u = 0; u < 4; ++u) hcur[u] = hp ? __ldcs(hp + u) : make_uint4(0, 0, 0, 0);
         }
@@ -650,16 +680,16 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
           }
         } else {
           const int l = fwd ? p + 1 : 2 * D - p;  // layer index (adjoint: layer whose W^T is applied)
-          const float *bias = fwd ? sbias + (l - 1) * NS + ch * CW : nullptr;  // this warp's columns
-          const float *wos = sbias + D * NS + ch * CW;
+          const float *bias = fwd ? sbias + (l - 1) * NS : nullptr;  // this rank's columns
+          const float *wos = sbias + D * NS;
           __nv_bfloat16 *hkeep = (fwd && grad && !last_fwd && valid)
                                      ? E.scratch + static_cast<size_t>(row) * sstride + static_cast<size_t>(l - 1) * W
                                      : nullptr;
           float part = 0.f;
 #pragma unroll 1
           for (int cc = 0; cc < CPW; ++cc) {
-            const int gcol = col0 + cc * 32;                        // global column of the chunk
-            const int tcol = ch * CW + cc * 32;                     // TMEM column
+            const int tcol = chunk_col(cc);                         // TMEM column
+            const int gcol = static_cast<int>(rank) * NS + tcol;    // global column of the chunk
             uint32_t raw[32];
             tmem_ld32_nowait(trow + tcol, raw);
             // stored activation h_{l-1} of these columns (tensor-memory copy)
@@ -671,7 +701,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
             float aux[32];
             uint4 hnext[4];
             if (fwd) {
-              const float4 *bp = reinterpret_cast<const float4 *>(bias + cc * 32);
+              const float4 *bp = reinterpret_cast<const float4 *>(bias + tcol);
 #pragma unroll
               for (int u = 0; u < 8; ++u) {
                 const float4 b4 = bp[u];
@@ -689,7 +719,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
             } else {
               // stored activations of this chunk were loaded one chunk ahead; start the next one
               const bool more = hprev && cc + 1 < CPW;
-              const uint4 *hp = more ? reinterpret_cast<const uint4 *>(hprev + gcol + 32) : nullptr;
+              const uint4 *hp =
+                  more ? reinterpret_cast<const uint4 *>(hprev + static_cast<int>(rank) * NS + chunk_col(cc + 1)) : nullptr;
 #pragma unroll
               for (int u = 0; u < 4; ++u) hnext[u] = more ? __ldcs(hp + u) : make_uint4(0, 0, 0, 0);
               const uint32_t *hh = reinterpret_cast<const uint32_t *>(hcur);
@@ -706,7 +737,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
             float v[32];
             if (fwd) {
               if (last_fwd) {
-                const float4 *wp = reinterpret_cast<const float4 *>(wos + cc * 32);
+                const float4 *wp = reinterpret_cast<const float4 *>(wos + tcol);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                   const float4 w4 = wp[u];
@@ -759,6 +790,14 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
 #pragma unroll
                 for (int u = 0; u < 4; ++u) __stcs(dst + u, make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]));
               }
+            }
+            if (kHalfFirst && distribute && cc == CPW / 2 - 1) {
+              // this warp's chunks of the first half are read from tensor memory and written
+              // to the next layer's operand: the MMAs on those K blocks may start
+              fence_proxy_async();
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(own_h0_bar);
             }
           }
           if (fwd && grad && !last_fwd && h_tmem) tmem_wait_st();
@@ -892,7 +931,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
 inline size_t tc2_smem_bytes(int width, int cs, int stages, int depth) {
   const int ns = width / cs, tr = ns < 256 ? ns : 256;
   return 1024 + static_cast<size_t>(width / 64) * 16384 + static_cast<size_t>(stages) * tr * 128 +
-         8 * (2 * stages + 10) + 4 * (cs * 128 + kTc2EQ * 128) + 4 * static_cast<size_t>(depth + 1) * ns +
+         8 * (2 * stages + 12) + 4 * (cs * 128 + kTc2EQ * 128) + 4 * static_cast<size_t>(depth + 1) * ns +
          3 * 4 * 128 * 8 + 64;
 }
 inline int tc2_stages_for(int width, int cs, int depth, int smem_cap) {
