@@ -255,12 +255,15 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
   // each epilogue warp sends its own rows x columns to the peers as soon as they are written
   // (whole 64-column K blocks: 32 rows of a K block are 4 KB contiguous in the swizzled layout)
   constexpr bool kWarpSend = CS > 1 && CW % 64 == 0;
-  // One CTA per tile with the layer in two MMA halves (N = TR = NS / 2): every epilogue warp
-  // finishes its chunks of the first half of the columns first and signals a barrier of its
-  // own, so the next layer's MMAs on K blocks 0 .. KBW / 2 - 1 run while the epilogue works on
-  // the second half (which the MMAs of the first N half do not overwrite in tensor memory).
+  // One CTA per tile with the layer in two MMA halves (N = TR = NS / 2): the epilogue warps
+  // take the columns in quarters (each warp its share of a quarter, two chunks) and signal a
+  // barrier after the first half and one after the third quarter, so the next layer's MMAs on
+  // K blocks 0 .. KBW / 2 - 1, then on the third quarter's K blocks, run while the epilogue
+  // works on the rest (the MMAs of the first N half overwrite only tensor-memory columns of the
+  // first half, read by then).
   constexpr bool kHalfFirst = (CS == 1) && (NSUB == 2);
-  static_assert(!kHalfFirst || (CPW % 2 == 0 && (CPW / 2) * 32 * kTc2EQ == TR), "half-first chunk order");
+  constexpr int kQC = CPW >= 4 ? CPW / 4 : 1;  // chunks of a warp per quarter (kHalfFirst)
+  static_assert(!kHalfFirst || (CPW % 4 == 0 && kQC * 32 * kTc2EQ == TR / 2), "quarter chunk order");
 
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *act = base;
@@ -268,6 +271,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
   const int S = E.n_stages;
   uint64_t *bars = reinterpret_cast<uint64_t *>(stages + S * STAGE);
   // bars: full[S] empty[S] go act_full acc fin peer_free part peer_free_last (cmd tmem) own own_h0
+  //       own_q2
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S);
   const uint32_t go_bar = smem_u32(bars + 2 * S), actf_bar = smem_u32(bars + 2 * S + 1);
   const uint32_t acc_bar = smem_u32(bars + 2 * S + 2), fin_bar = smem_u32(bars + 2 * S + 3);
@@ -277,8 +281,9 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 8);
   // own slice of the next layer input written (the peers' slices complete act_full)
   const uint32_t own_bar = smem_u32(bars + 2 * S + 9);
-  // first half of the columns written (kHalfFirst); slot 2 S + 11 pads `partial` to 16 bytes
+  // first half / first three quarters of the columns written (kHalfFirst)
   const uint32_t own_h0_bar = smem_u32(bars + 2 * S + 10);
+  const uint32_t own_q2_bar = smem_u32(bars + 2 * S + 11);
   // everything from `partial` on is 16-byte aligned for vector access
   float *partial = reinterpret_cast<float *>(bars + 2 * S + 12);  // [CS][128] (rank 0 gathers)
   float *red = partial + CS * 128;                                // [EQ-1][128] column-group combine
@@ -329,6 +334,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
     mbar_init(free2_bar, CS > 1 ? CS - 1 : 1);
     mbar_init(own_bar, kTc2EpiThreads / 32);  // one arrive per epilogue warp
     mbar_init(own_h0_bar, kTc2EpiThreads / 32);
+    mbar_init(own_q2_bar, kTc2EpiThreads / 32);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 1) {
@@ -402,7 +408,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
     if (lane == 0) {
       uint32_t upar = 0;  // bit s: parity of the next wait on stage s
       int s = 0;
-      uint32_t go_par = 0, act_par = 0, own_par = 0, own_h0_par = 0;
+      uint32_t go_par = 0, act_par = 0, own_par = 0, own_h0_par = 0, own_q2_par = 0;
       bool ok = true;
       const uint32_t idn = idesc_bf16(128, TR, E.f16 != 0), idg = idesc_bf16(128, 2 * dp, E.f16 != 0);
       // descriptors of K block 0 of the activation and of stage 0; K block kb / stage s / the
@@ -437,7 +443,16 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
             const uint32_t dcol = tmem + sb * TR;
             for (int j = 0; j < nkb; ++j) {
               if (split && sb == 0 && j == KBW / 2) {
-                // the second half of the layer input
+                // the third quarter of the layer input
+                if (!mbar_wait(own_q2_bar, own_q2_par, a.status)) {
+                  ok = false;
+                  break;
+                }
+                own_q2_par ^= 1;
+                tc_fence_after();
+              }
+              if (split && sb == 0 && j == 3 * KBW / 4) {
+                // the last quarter
                 if (!mbar_wait(own_bar, own_par, a.status)) {
                   ok = false;
                   break;
@@ -497,10 +512,10 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
     const uint32_t act_addr = smem_u32(act);
     const int col0 = static_cast<int>(rank) * NS + ch * CW;  // first global column of this warp
     // column of chunk cc of this warp within the rank's slice: CW consecutive columns, or
-    // (kHalfFirst) its share of the first N half, then its share of the second
+    // (kHalfFirst) its share of each quarter of the columns in turn
     auto chunk_col = [&](int cc) -> int {
-      if (kHalfFirst) return (cc / (CPW / 2)) * TR + ch * (TR / kTc2EQ) + (cc % (CPW / 2)) * 32;
-      return ch * CW + cc * 32;
+      if constexpr (kHalfFirst) return (cc / kQC) * (TR / 2) + ch * (TR / 2 / kTc2EQ) + (cc % kQC) * 32;
+      else return ch * CW + cc * 32;
     };
     Chain<float> chn(a);
     const bool loglike = a.mode == kModeLoglike;
@@ -791,13 +806,14 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
                 for (int u = 0; u < 4; ++u) __stcs(dst + u, make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]));
               }
             }
-            if (kHalfFirst && distribute && cc == CPW / 2 - 1) {
-              // this warp's chunks of the first half are read from tensor memory and written
-              // to the next layer's operand: the MMAs on those K blocks may start
+            if (kHalfFirst && distribute && (cc == 2 * kQC - 1 || cc == 3 * kQC - 1)) {
+              // this warp's chunks of the first half (then of the third quarter) are read from
+              // tensor memory and written to the next layer's operand: the MMAs on those K
+              // blocks may start
               fence_proxy_async();
               tc_fence_before();
               __syncwarp();
-              if (lane == 0) mbar_arrive(own_h0_bar);
+              if (lane == 0) mbar_arrive(cc == 2 * kQC - 1 ? own_h0_bar : own_q2_bar);
             }
           }
           if (fwd && grad && !last_fwd && h_tmem) tmem_wait_st();
