@@ -198,6 +198,28 @@ def test_init_chains_log_pi_and_gradient(prec):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_bf16_one_cta_per_tile_width512(prec):
+    """10,240 points are 80 tiles of 128: more than half the SMs' worth, so each tile runs on one
+    CTA with the layer in two 256-column MMA halves and the epilogue in quarters, the next
+    layer's MMAs starting on the finished quarters (8-512x4-1).  Every fifth row against the
+    oracle (sampled outputs at a size the path runs at)."""
+    e = emulator_case(8, 512, 4, out_s=20.0, out_m=100.0)
+    s = _sampler(prec, e)
+    x = np.random.default_rng(21).uniform(-3, 3, (10240, 8))
+    ll, g = s.grad_loglike(x)
+    sub = np.arange(0, 10240, 5)
+    rl, rg = _ref(prec, 8, e).loglike(x[sub])
+    ll, g = ll.double().cpu().numpy()[sub], g.double().cpu().numpy()[sub]
+    tl, tg = TOL[prec]
+    assert np.max(np.abs(ll - rl) / np.maximum(np.abs(rl), 1.0)) < tl
+    assert rel_err(g, rg) < tg
+    # forward only (loglike) takes the same path
+    lf = s.loglike(x).double().cpu().numpy()[sub]
+    assert np.max(np.abs(lf - rl) / np.maximum(np.abs(rl), 1.0)) < tl
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("width", [256, 512])
 def test_bf16_two_cta_clusters(width, prec):
     """6000 points are 47 tiles of 128: the BF16 engine splits each layer over clusters of two

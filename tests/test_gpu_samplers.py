@@ -272,6 +272,19 @@ def test_bf16_mala_two_cta_clusters(width, prec):
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_bf16_mala_one_cta_per_tile_width512(prec):
+    """MALA with 10,240 chains (80 tiles: one CTA per tile, the layer in two MMA halves, the
+    epilogue in quarters overlapping the next layer's MMAs) against the oracle."""
+    n = 10240
+    s, m, z0 = _setup_gauss(prec, n, 512, depth=2)
+    out = torch.empty((1, n, 8), dtype=s.dtype, device="cuda")
+    s.step("mala", 1, eps=0.4, samples=out)
+    ref = O.run(m, "mala", z0, eps=0.4, n_steps=1, seed=11, trace=True)
+    _check(prec, s, ref, out, "mala", n, eps=0.4)
+    s.close()
+
+
 def _setup27(prec, n, width=256, depth=2, seed=11):
     """d = 27: six box-bounded dimensions and 21 nuisance dimensions under N(0, 1) priors, with
     a dense whitening factor (the general sampler code: chain vectors in global memory,
