@@ -219,6 +219,23 @@ def test_bf16_one_cta_per_tile_width512(prec):
     s.close()
 
 
+def test_bf16_gradient_at_262144_rows():
+    """The largest chain count of the throughput sweep: 262,144 rows of 8-512x4-1 (2048 tiles,
+    one CTA each, in waves over the SMs), every 128th row against the oracle."""
+    e = emulator_case(8, 512, 4, out_s=20.0, out_m=100.0)
+    s = _sampler("bf16", e)
+    n = 262144
+    x = np.random.default_rng(23).uniform(-3, 3, (n, 8))
+    ll, g = s.grad_loglike(x)
+    sub = np.arange(0, n, 128)
+    rl, rg = _ref("bf16", 8, e).loglike(x[sub])
+    ll, g = ll.double().cpu().numpy()[sub], g.double().cpu().numpy()[sub]
+    tl, tg = TOL["bf16"]
+    assert np.max(np.abs(ll - rl) / np.maximum(np.abs(rl), 1.0)) < tl
+    assert rel_err(g, rg) < tg
+    s.close()
+
+
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("width", [256, 512])
 def test_bf16_two_cta_clusters(width, prec):

@@ -346,6 +346,22 @@ def test_27d_one_step_parity(prec, kernel, eps, extra):
     s.close()
 
 
+@pytest.mark.parametrize("prec", ["bf16"])
+@pytest.mark.parametrize("kernel,eps", [("mala", 0.6), ("nuts", 0.5)])
+def test_27d_one_cta_per_tile_parity(prec, kernel, eps):
+    """The general sampler code at 10,240 chains of the 27-D target on a width-512 emulator:
+    80 tiles, one CTA each, the layer in two MMA halves and the epilogue in quarters (the
+    configuration the 27-D NUTS and AIES legs run at).  One step against the oracle on every
+    chain."""
+    n = 10240
+    s, m, z0 = _setup27(prec, n, width=512, depth=2)
+    out = torch.empty((1, n, 27), dtype=s.dtype, device="cuda")
+    s.step(kernel, 1, eps=eps, samples=out)
+    ref = O.run(m, kernel, z0, eps=eps, n_steps=1, seed=11, trace=True)
+    _check(prec, s, ref, out, kernel, n, eps=eps)
+    s.close()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("kernel,eps,extra", [("mala", 0.6, {}), ("nuts", 0.5, {}), ("hmc", 0.4, {"n_leapfrog": 3}),
                                               ("aies", 0.0, {})])
