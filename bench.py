@@ -728,8 +728,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.init_chains(h_theta.numpy(), lower, upper, mu=mu, L=L)
-        s.step("mala", K, eps=eps, samples=samples, stats=False)
-        h_samples.copy_(samples, non_blocking=True)
+        # the kernel writes the sample record into the pinned host buffer directly
+        s.step("mala", K, eps=eps, samples=h_samples, stats=False)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         s.set_state(st0)

@@ -155,7 +155,11 @@ bst_status bst_init_chains(bst_handle h, const double *theta0, const double *low
  *             standard deviation sigma_gamma of the relative scale (>= 0; the paper gives no
  *             value); symmetric, accepted with min(1, pi(y) / pi(z_i)); aies_walkers >= 4
  * eps is ignored by AIES; n_leapfrog only used by HMC.  If samples_dev is not
- * NULL it receives x-space samples real[n_steps / thin][n_chains][d].
+ * NULL it receives x-space samples real[n_steps / thin][n_chains][d]: device
+ * memory of the handle's device, or page-locked host memory that the device can address
+ * (cudaHostAlloc / cudaHostRegister; the kernel then writes the record to host memory
+ * directly, with no copy after the call, and the caller reads it once the stream is
+ * synchronised).  Any other pointer returns BST_ERR_ARG before anything is launched.
  * If stats is not NULL the call synchronises ``stream`` and fills it with this
  * call's totals; otherwise it only enqueues. */
 bst_status bst_step(bst_handle h, int kernel, double eps, int n_leapfrog, int n_steps,

@@ -129,11 +129,18 @@ class Sampler:
         _lib.check(self.lib.bst_init_chains(self.h, _p(th), _p(lo), _p(up), _p(g), _p(mu), _p(L)))
 
     def step(self, kernel, n_steps, *, eps=0.1, n_leapfrog=10, samples=None, stats=True, stream=None):
-        """Advance all chains n_steps iterations.  samples: optional device tensor
-        [n_steps // thin][n_chains][d] receiving x-space samples."""
+        """Advance all chains n_steps iterations.  samples: optional tensor
+        [n_steps // thin][n_chains][d] receiving x-space samples, on the device or in pinned
+        host memory (written there by the kernel directly; read it after synchronising)."""
         k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         if samples is not None:
-            self._check_dev(samples, (n_steps // self.thin, self.n, self.d))
+            if isinstance(samples, torch.Tensor) and not samples.is_cuda:
+                if not (samples.is_pinned() and samples.dtype == self.dtype and samples.is_contiguous()):
+                    raise BstError(_lib.ERR_ARG, f"expected a contiguous pinned {self.dtype} host tensor")
+                if tuple(samples.shape) != (n_steps // self.thin, self.n, self.d):
+                    raise BstError(_lib.ERR_ARG, f"expected shape {(n_steps // self.thin, self.n, self.d)}")
+            else:
+                self._check_dev(samples, (n_steps // self.thin, self.n, self.d))
         st = _lib.StepStats() if stats else None
         _lib.check(self.lib.bst_step(self.h, k, float(eps), int(n_leapfrog), int(n_steps),
                                      None if samples is None else C.c_void_p(samples.data_ptr()),

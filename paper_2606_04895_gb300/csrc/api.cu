@@ -851,6 +851,25 @@ bst_status bst_step(bst_handle h, int kernel, double eps, int n_leapfrog, int n_
       return fail(BST_ERR_UNSUPPORTED, "bst_step: AIES ensemble halves do not fit the chain tiles");
   }
   BST_CUDA(cudaSetDevice(h->device));
+  // the sample record: device memory of this device, or page-locked host memory mapped into
+  // the device's address space (written by the kernel directly, over the host link)
+  void *samples_ptr = samples_dev;
+  if (samples_dev) {
+    cudaPointerAttributes at = {};
+    if (cudaPointerGetAttributes(&at, samples_dev) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(BST_ERR_ARG, "bst_step: samples is neither device memory nor page-locked host memory");
+    }
+    if (at.type == cudaMemoryTypeHost) {
+      if (!at.devicePointer) return fail(BST_ERR_ARG, "bst_step: page-locked samples buffer not mapped for the device");
+      samples_ptr = at.devicePointer;
+    } else if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+      if (at.type == cudaMemoryTypeDevice && at.device != h->device)
+        return fail(BST_ERR_ARG, "bst_step: samples buffer on another device");
+    } else {
+      return fail(BST_ERR_ARG, "bst_step: samples must be device memory or page-locked host memory");
+    }
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (n_steps == 0) {
     if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -865,7 +884,7 @@ bst_status bst_step(bst_handle h, int kernel, double eps, int n_leapfrog, int n_
     BST_CUDA(cudaStreamSynchronize(s));
     BST_TRY(sum_counters(h, before));
   }
-  BST_TRY(run(h, kernel, eps, n_leapfrog, n_steps, samples_dev, 0, s));
+  BST_TRY(run(h, kernel, eps, n_leapfrog, n_steps, samples_ptr, 0, s));
   if (!needs_grad) h->grad_valid = false;
   if (stats) {
     BST_CUDA(cudaStreamSynchronize(s));

@@ -186,6 +186,31 @@ def test_checkpoint_resume_is_bit_identical():
     a.close(); c.close()
 
 
+def test_samples_into_pinned_host_memory():
+    """The sample record can go straight to page-locked host memory (the kernel writes it over
+    the host link): bit-identical to the record in device memory from the same start, and a
+    pageable host buffer is refused by the library before anything runs."""
+    import ctypes as C
+    from paper_2606_04895_gb300 import KERNELS
+    n, k = 256, 5
+    a, _, _ = _setup_gauss("bf16", n, 512)
+    b, _, _ = _setup_gauss("bf16", n, 512)
+    dev = torch.empty((k, n, 8), dtype=a.dtype, device="cuda")
+    a.step("mala", k, eps=0.3, samples=dev, stats=False)
+    host = torch.full((k, n, 8), float("nan"), dtype=b.dtype).pin_memory()
+    b.step("mala", k, eps=0.3, samples=host, stats=False)
+    torch.cuda.synchronize()
+    assert torch.equal(host, dev.cpu())
+    assert np.array_equal(a.get_state()["z"], b.get_state()["z"])
+    pageable = np.zeros((k, n, 8), dtype=np.float32)
+    rc = b.lib.bst_step(b.h, KERNELS["mala"], 0.3, 10, k, pageable.ctypes.data_as(C.c_void_p), None, None)
+    assert rc != 0
+    assert not pageable.any()
+    with pytest.raises(Exception):
+        b.step("mala", k, eps=0.3, samples=torch.zeros((k, n, 8), dtype=b.dtype))
+    a.close(); b.close()
+
+
 def test_thinning_and_sample_shape():
     from paper_2606_04895_gb300 import Sampler
     n = 64
