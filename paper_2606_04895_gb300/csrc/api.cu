@@ -72,6 +72,8 @@ struct bst_ctx {
   int any_gauss = 0;
   std::vector<double> pen_w;  // smooth-bound widths (empty or zeros: hard box)
   double *mu64 = nullptr, *L64 = nullptr, *mu64_new = nullptr, *L64_new = nullptr, *info64 = nullptr;
+  double *theta64 = nullptr;  // [n][d] initial positions staged for init_chains
+  size_t theta_cap = 0;
   double *stats64 = nullptr;  // [1 + kMaxD + kMaxD^2] Welford triple staging
 
   // emulator
@@ -803,24 +805,25 @@ bst_status bst_init_chains(bst_handle h, const double *theta0, const double *low
       h->gauss[i] = gauss[i] ? 1 : 0;
       h->any_gauss |= h->gauss[i];
     }
-  // z0 = L^-1 (theta0 - mu), forward substitution in FP64, rows padded to dp
-  std::vector<double> z(static_cast<size_t>(n) * h->dp, 0.0);
-  for (int c = 0; c < n; ++c) {
-    for (int i = 0; i < d; ++i) {
-      double s = theta0[static_cast<size_t>(c) * d + i] - h->mu[i];
-      for (int j = 0; j < i; ++j) s -= h->L[i * d + j] * z[static_cast<size_t>(c) * h->dp + j];
-      z[static_cast<size_t>(c) * h->dp + i] = s / h->L[i * d + i];
-    }
-  }
-  BST_TRY(upload_real(h, h->z, z.data(), z.size()));
+  // z0 = L^-1 (theta0 - mu) on the device (FP64 forward substitution): theta0 is copied in once
+  // (a DMA when it is page-locked) and the counters are cleared on the same stream
   const size_t nn = n;
-  BST_CUDA(cudaMemset(h->iter, 0, nn * 4));
-  BST_CUDA(cudaMemset(h->acc_stat, 0, nn * 8));
-  BST_CUDA(cudaMemset(h->accepts, 0, nn * 8));
-  BST_CUDA(cudaMemset(h->evals, 0, nn * 8));
-  BST_CUDA(cudaMemset(h->divs, 0, nn * 8));
-  BST_CUDA(cudaMemset(h->work, 0, chains_padded(h->n) * h->work_stride * h->rs));
-  BST_CUDA(cudaMemset(h->status, 0, 64));
+  if (h->theta_cap < nn * d) {
+    dfree(h, h->theta64);
+    h->theta64 = nullptr;
+    h->theta_cap = 0;
+    BST_TRY(dalloc_t(h, &h->theta64, nn * d));
+    h->theta_cap = nn * d;
+  }
+  BST_CUDA(cudaMemcpyAsync(h->theta64, theta0, nn * d * 8, cudaMemcpyHostToDevice, 0));
+  BST_CUDA(launch_init_z(h->rs == 8, h->theta64, h->mu64, h->L64, n, d, h->dp, h->z, 0));
+  BST_CUDA(cudaMemsetAsync(h->iter, 0, nn * 4, 0));
+  BST_CUDA(cudaMemsetAsync(h->acc_stat, 0, nn * 8, 0));
+  BST_CUDA(cudaMemsetAsync(h->accepts, 0, nn * 8, 0));
+  BST_CUDA(cudaMemsetAsync(h->evals, 0, nn * 8, 0));
+  BST_CUDA(cudaMemsetAsync(h->divs, 0, nn * 8, 0));
+  BST_CUDA(cudaMemsetAsync(h->work, 0, chains_padded(h->n) * h->work_stride * h->rs, 0));
+  BST_CUDA(cudaMemsetAsync(h->status, 0, 64, 0));
   h->stage = 2;
   BST_TRY(refresh(h, 0));
   BST_CUDA(cudaDeviceSynchronize());

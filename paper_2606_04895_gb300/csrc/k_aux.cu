@@ -843,6 +843,31 @@ cudaError_t launch_wsum(const float *X, int rows, int cols, const float *U, int 
   return cudaGetLastError();
 }
 
+// Initial whitened positions z0 = L^-1 (theta0 - mu) (Algorithm 1's map inverted), one chain per
+// thread, forward substitution in FP64, rows padded to dp with zeros, stored in the working type.
+template <typename R>
+__global__ void init_z_kernel(const double *theta, const double *mu, const double *L, int n, int d, int dp, R *z) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double zz[kMaxD];
+  for (int i = 0; i < d; ++i) {
+    double s = theta[static_cast<size_t>(c) * d + i] - mu[i];
+    for (int j = 0; j < i; ++j) s -= L[i * d + j] * zz[j];
+    zz[i] = s / L[i * d + i];
+  }
+  for (int i = 0; i < dp; ++i) z[static_cast<size_t>(c) * dp + i] = static_cast<R>(i < d ? zz[i] : 0.0);
+}
+
+cudaError_t launch_init_z(bool f64, const double *theta, const double *mu, const double *L, int n, int d, int dp,
+                          void *z, cudaStream_t s) {
+  if (n < 1 || d < 1 || d > kMaxD || dp < d) return cudaErrorInvalidValue;
+  if (f64)
+    init_z_kernel<double><<<blocks_for(n, 128), 128, 0, s>>>(theta, mu, L, n, d, dp, static_cast<double *>(z));
+  else
+    init_z_kernel<float><<<blocks_for(n, 128), 128, 0, s>>>(theta, mu, L, n, d, dp, static_cast<float *>(z));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_train_grad(const float *P, const float *in_m, const float *in_s, float out_m, float out_s,
                               int out_log, float out_floor, int d, int D, int w, int m, const float *X,
                               const float *chi2, float *G, TrainWork &tw, cudaStream_t s) {

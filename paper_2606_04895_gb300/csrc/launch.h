@@ -42,6 +42,9 @@ cudaError_t launch_pack_tc2_hidden(const double *P, int d, int D, int w, int ran
                                    uint8_t *out, cudaStream_t s);
 cudaError_t launch_pack_tc_g1(const double *W1f, int dp, int w, int f16, uint8_t *out, cudaStream_t s);
 cudaError_t launch_cast_f32(const double *src, float *dst, size_t n, cudaStream_t s);
+// Initial whitened positions z0 = L^-1 (theta0 - mu) (FP64 forward substitution; z in FP64 or FP32).
+cudaError_t launch_init_z(bool f64, const double *theta, const double *mu, const double *L, int n, int d, int dp,
+                          void *z, cudaStream_t s);
 cudaError_t launch_cast_f64(const double *src, double *dst, size_t n, cudaStream_t s);
 cudaError_t launch_cast_f32_to_f64(const float *src, double *dst, size_t n, cudaStream_t s);
 // Analytic fold: Bf = B L_c, cf = B mu_c + c, Nf = N L_n, dataf = data - N mu_n (mode 0) or
