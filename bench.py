@@ -794,6 +794,11 @@ def ess_legs(torch, device, s, e, tgt, eps, seed):
             fl = 4.0 * (n_params(D, DEPTH, WIDTH) - 1) * legs["fp32_mala"]["evals_per_s"] / 1e12
             legs["fp32_mala"].update(tflops_fp32=fl, frac_fp32_fma_peak=fl / FP32_FMA_PEAK_TFLOPS,
                                      fp32_peak_note="derived: 152 SMs x 128 FMA lanes x 2 flop x 2.07 GHz")
+            # HMC on the plain FP32 path, as the BF16 HMC leg (L = 10, ESS_DRAWS // 4 draws)
+            p.init_chains(x_now, tgt["lower"], tgt["upper"], mu=mu, L=L)
+            eh32 = driver.dual_average_eps(p, "hmc", eps / 2, n_iter=10, chunk=10, n_leapfrog=10)
+            legs["fp32_hmc"], _ = ess_leg(torch, p, "hmc", eh32, draws=ESS_DRAWS // 4, truth=truth, ref=ref,
+                                          n_leapfrog=10)
         p.close()
     truth.close()
     out["ess_legs"] = legs
@@ -806,6 +811,7 @@ def ess_legs(torch, device, s, e, tgt, eps, seed):
     out["speedups_min_ess_per_s"] = {
         "bf16_over_fp32_emulator": ratio("bf16_mala", "fp32_mala"),
         "fp16_over_fp32_emulator": ratio("fp16_mala", "fp32_mala"),
+        "bf16_hmc_over_fp32_hmc": ratio("bf16_hmc", "fp32_hmc"),
         "bf16_reweighted_over_analytic_fp32": (legs["bf16_mala"].get("min_ess_per_s_reweighted") /
                                                legs["analytic_fp32_mala"]["min_ess_per_s"]
                                                if legs["bf16_mala"].get("min_ess_per_s_reweighted") and
