@@ -42,6 +42,10 @@ __host__ __device__ constexpr int tc2_tcols(int W, int CS) { return W / CS < 64 
 __host__ __device__ constexpr int tc2_tmem_max_depth(int W, int CS) {
   return tc2_h_in_tmem(W, CS) ? (512 - tc2_tcols(W, CS)) / (W / CS / 2) + 1 : 1 << 20;
 }
+// K blocks per weight stage: with 128-column slices (16 KB per K block) two consecutive K
+// blocks, which are contiguous in the weight streams, share one copy and one barrier, so the
+// MMA thread waits once per eight MMAs instead of once per four.
+__host__ __device__ constexpr int tc2_stage_kblocks(int W, int CS) { return (W == 512 && CS == 4) ? 2 : 1; }
 
 struct Tc2Weights {
   int depth, width, dp, kb1, k16_l1;
@@ -246,7 +250,9 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
   constexpr int NS = W / CS;            // output columns of this rank
   constexpr int TR = NS < 256 ? NS : 256;  // rows of a weight tile == MMA N
   constexpr int NSUB = NS / TR;
-  constexpr int STAGE = TR * 128;
+  constexpr int KT = TR * 128;                  // bytes of a weight tile (one K block)
+  constexpr int G = tc2_stage_kblocks(W, CS);   // K blocks per stage
+  constexpr int STAGE = G * KT;
   constexpr int SLICE_BYTES = 128 * NS * 2;  // one rank's slice of an activation
   constexpr int TCOLS = NS < 64 ? 64 : NS;   // TMEM columns (>= 2 dp for the input gradient)
   constexpr int CW = NS / kTc2EQ;            // slice columns per epilogue warp
@@ -264,6 +270,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
   constexpr bool kHalfFirst = (CS == 1) && (NSUB == 2);
   constexpr int kQC = CPW >= 4 ? CPW / 4 : 1;  // chunks of a warp per quarter (kHalfFirst)
   static_assert(!kHalfFirst || (CPW % 4 == 0 && kQC * 32 * kTc2EQ == TR / 2), "quarter chunk order");
+  // the barrier checks of the MMA thread (own K blocks, quarters) fall on stage boundaries
+  static_assert(G == 1 || (!kHalfFirst && NOWN % G == 0 && KBW % G == 0), "K blocks per stage");
 
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *act = base;
@@ -378,24 +386,27 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
           const bool last = (p == 2 * D - 1);
           const int nsub = last ? 1 : NSUB;
           const int nkb = (p == 0) ? E.kb1 : KBW;
-          const uint32_t bytes = last ? 2 * dp * 128 : STAGE;
+          const uint32_t bytes = last ? 2 * dp * 128 : KT;  // per K block
           for (int sb = 0; sb < nsub && ok; ++sb) {
             int kb = (p == 0) ? 0 : rot;
-            for (int j = 0; j < nkb; ++j) {
+            for (int j = 0; j < nkb;) {
+              // K blocks kb .. kb + g - 1 in one stage (the rotation never splits a stage)
+              const int g = min(G, min(nkb - j, nkb - kb));
               const uint8_t *src;
-              if (p == 0) src = l1 + static_cast<size_t>(sb * nkb + kb) * STAGE;
-              else if (!last) src = hid + (static_cast<size_t>(p - 1) * NSUB * KBW + sb * KBW + kb) * STAGE;
+              if (p == 0) src = l1 + static_cast<size_t>(sb * nkb + kb) * KT;
+              else if (!last) src = hid + (static_cast<size_t>(p - 1) * NSUB * KBW + sb * KBW + kb) * KT;
               else src = E.g1 + static_cast<size_t>(kb) * bytes;
               if (!mbar_wait(empty0 + 8 * s, ((fpar >> s) & 1u) ^ 1u, a.status)) {
                 ok = false;
                 break;
               }
-              mbar_expect_tx(full0 + 8 * s, bytes);
-              bulk_g2s(smem_u32(stages + s * STAGE), src, bytes, full0 + 8 * s);
+              mbar_expect_tx(full0 + 8 * s, g * bytes);
+              bulk_g2s(smem_u32(stages + s * STAGE), src, g * bytes, full0 + 8 * s);
               fpar ^= 1u << s;
               used |= 1u << s;
               s = (s + 1 == S) ? 0 : s + 1;
-              kb = (kb + 1 == nkb) ? 0 : kb + 1;
+              j += g;
+              kb = (kb + g == nkb) ? 0 : kb + g;
             }
           }
         }
@@ -411,8 +422,9 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
       uint32_t go_par = 0, act_par = 0, own_par = 0, own_h0_par = 0, own_q2_par = 0;
       bool ok = true;
       const uint32_t idn = idesc_bf16(128, TR, E.f16 != 0), idg = idesc_bf16(128, 2 * dp, E.f16 != 0);
-      // descriptors of K block 0 of the activation and of stage 0; K block kb / stage s / the
-      // k-th 16-wide step are offsets of kb * 16384, s * STAGE and k * 32 bytes (address >> 4)
+      // descriptors of K block 0 of the activation and of stage 0; K block kb / stage s / its
+      // i-th K block / the k-th 16-wide step are offsets of kb * 16384, s * STAGE, i * kbytes
+      // and k * 32 bytes (address >> 4)
       const uint64_t adesc0 = sw128_desc(smem_u32(act)), bdesc0 = sw128_desc(smem_u32(stages));
       const int rot = static_cast<int>(rank) * NOWN;  // own K blocks first (as the producer)
       const uint16_t peer_mask = static_cast<uint16_t>(((1u << CS) - 1u) & ~(1u << rank));
@@ -438,10 +450,13 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
           const int nsub = last ? 1 : NSUB;
           const int nkb = (p == 0) ? E.kb1 : KBW;
           const uint32_t id = last ? idg : idn;
+          const int kbytes = last ? 2 * dp * 128 : KT;  // bytes of one K block in a stage
           for (int sb = 0; sb < nsub && ok; ++sb) {
             int kb = (p == 0) ? 0 : rot;
             const uint32_t dcol = tmem + sb * TR;
-            for (int j = 0; j < nkb; ++j) {
+            for (int j = 0; j < nkb;) {
+              // the producer's stage split: K blocks kb .. kb + g - 1 in stage s
+              const int g = min(G, min(nkb - j, nkb - kb));
               if (split && sb == 0 && j == KBW / 2) {
                 // the third quarter of the layer input
                 if (!mbar_wait(own_q2_bar, own_q2_par, a.status)) {
@@ -475,14 +490,17 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
               }
               upar ^= 1u << s;
               tc_fence_after();
-              const uint64_t ad = adesc0 + static_cast<uint64_t>(kb * (16384 >> 4));
-              const uint64_t bd = bdesc0 + static_cast<uint64_t>(s * (STAGE >> 4));
-              const int k16 = (p == 0) ? min(4, E.k16_l1 - 4 * kb) : 4;
-              for (int k = 0; k < k16; ++k)
-                mma_bf16(dcol, ad + 2 * k, bd + 2 * k, id, (j > 0 || k > 0) ? 1u : 0u);
+              for (int i = 0; i < g; ++i) {
+                const uint64_t ad = adesc0 + static_cast<uint64_t>((kb + i) * (16384 >> 4));
+                const uint64_t bd = bdesc0 + static_cast<uint64_t>((s * STAGE + i * kbytes) >> 4);
+                const int k16 = (p == 0) ? min(4, E.k16_l1 - 4 * (kb + i)) : 4;
+                for (int k = 0; k < k16; ++k)
+                  mma_bf16(dcol, ad + 2 * k, bd + 2 * k, id, (j + i > 0 || k > 0) ? 1u : 0u);
+              }
               mma_commit(empty0 + 8 * s);
               s = (s + 1 == S) ? 0 : s + 1;
-              kb = (kb + 1 == nkb) ? 0 : kb + 1;
+              j += g;
+              kb = (kb + g == nkb) ? 0 : kb + g;
             }
           }
           if (ok) {
@@ -946,7 +964,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1) tc2_chain_kernel(const __grid_
 
 inline size_t tc2_smem_bytes(int width, int cs, int stages, int depth) {
   const int ns = width / cs, tr = ns < 256 ? ns : 256;
-  return 1024 + static_cast<size_t>(width / 64) * 16384 + static_cast<size_t>(stages) * tr * 128 +
+  return 1024 + static_cast<size_t>(width / 64) * 16384 +
+         static_cast<size_t>(stages) * tc2_stage_kblocks(width, cs) * tr * 128 +
          8 * (2 * stages + 12) + 4 * (cs * 128 + kTc2EQ * 128) + 4 * static_cast<size_t>(depth + 1) * ns +
          3 * 4 * 128 * 8 + 64;
 }
